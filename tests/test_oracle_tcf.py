@@ -1,0 +1,196 @@
+"""Pins for the oracle TCF (paper Sec. 4): query answers equal fingerprint
+membership (brute force), conservation of the stored multiset, the placement
+rules (shortcut below 3B/4, two-choice by fill, other block, backing table),
+sorted blocks (Sec. 4.3), the false-positive closed form 2B/2^f (Sec. 4.1)
+generalised to partial load, and deletes without false negatives."""
+import collections
+
+import numpy as np
+import pytest
+
+from paper_2212_09005_gb300.workloads import uniform_keys
+
+
+def live_multiset(T, keys):
+    return collections.Counter(T.fingerprints(keys).tolist())
+
+
+def stored_multiset(T, tag_to_g):
+    """Fingerprints read back from the table (blocks and backing)."""
+    out = collections.Counter()
+    blocks = T.blocks()
+    nz = np.nonzero(blocks)
+    for b, s in zip(*nz):
+        t = int(blocks[b, s])
+        b2 = int(b) ^ tag_to_g[t]
+        out[(min(int(b), b2) << T.f) | t] += 1
+    for e in T.buckets().ravel().tolist():
+        if e:
+            out[e] += 1
+    return out
+
+
+def tag_g_map(T, keys):
+    b1, b2, t = T.keyinfo(keys)
+    return {int(a): int(x ^ y) for a, x, y in zip(t, b1, b2)}
+
+
+@pytest.mark.parametrize("log2_slots,f", [(12, 16), (14, 16), (13, 8)])
+def test_membership_equals_fingerprint_multiset(oracle, log2_slots, f):
+    T = oracle.TCF(log2_slots, f, seed=log2_slots + f)
+    n = int(0.9 * (1 << log2_slots))
+    keys = uniform_keys(60 + log2_slots, n)
+    keys = np.concatenate([keys, keys[:50]])  # duplicates: multiset inserts
+    gmap = tag_g_map(T, keys)
+    inserted = []
+    for s in range(0, len(keys), 1000):
+        batch = keys[s:s + 1000]
+        st = T.insert(batch)
+        inserted.extend(batch[st == 0].tolist())
+        blocks = T.blocks()
+        # Sec. 4.3: blocks hold sorted tags, EMPTY (0) padding at the end
+        for row in blocks[np.unique(T.keyinfo(batch)[0])]:
+            k = int((row != 0).sum())
+            assert (row[:k] != 0).all() and not row[k:].any()
+            assert (np.diff(row[:k].astype(np.int64)) >= 0).all()
+    live = live_multiset(T, np.array(inserted, np.uint64))
+    assert stored_multiset(T, gmap) == live
+    probe = np.concatenate([keys[:3000], uniform_keys(70 + log2_slots, 20000)])
+    exp = np.array([live.get(int(x), 0) > 0 for x in T.fingerprints(probe)], np.uint8)
+    assert np.array_equal(T.query(probe), exp)
+
+
+def test_placement_rules_via_trace(oracle):
+    T = oracle.TCF(12, 16, seed=5)  # 256 blocks of 16
+    B, tsc = T.B, T.tsc
+    keys = uniform_keys(61, int(0.92 * (1 << 12)))
+    for s in range(0, len(keys), 700):
+        batch = keys[s:s + 700]
+        fill0 = (T.blocks() != 0).sum(1)
+        bfill0 = (T.buckets() != 0).sum(1)
+        st, ph, wh = T.insert(batch, trace=True)
+        b1, b2, t = T.keyinfo(batch)
+        # phase A: shortcut into b1, as many as the 3B/4 threshold allows
+        cand = collections.Counter(b1.tolist())
+        acc = collections.Counter(b1[ph == 0].tolist())
+        for b, c in cand.items():
+            assert acc.get(b, 0) == min(c, max(0, tsc - int(fill0[b])))
+        assert np.array_equal(wh[ph == 0], b1[ph == 0])
+        # phase B: target = less full block after phase A, tie -> b1
+        fillA = fill0.copy()
+        for b, c in acc.items():
+            fillA[b] += c
+        tgt = np.where(fillA[b1] <= fillA[b2], b1, b2)
+        assert np.array_equal(wh[ph == 1], tgt[ph == 1])
+        # phase C: the other block
+        other = np.where(tgt == b1, b2, b1)
+        assert np.array_equal(wh[ph == 2], other[ph == 2])
+        # blocks never overflow; phase C / D only after the earlier block filled
+        after = (T.blocks() != 0).sum(1)
+        assert after.max() <= B
+        for i in np.nonzero(ph >= 2)[0]:
+            assert after[tgt[i]] == B
+        for i in np.nonzero(ph >= 3)[0]:
+            assert after[other[i]] == B
+        # within a block and phase, accepted candidates precede rejected ones in
+        # (tag, batch index) order
+        for phase, grp in ((0, b1), (1, tgt), (2, other)):
+            into = collections.defaultdict(list)
+            for i in np.nonzero(ph >= phase)[0]:
+                into[int(grp[i])].append((int(t[i]), int(i), ph[i] == phase))
+            for lst in into.values():
+                lst.sort()
+                seen_reject = False
+                for _, _, accepted in lst:
+                    if not accepted:
+                        seen_reject = True
+                    assert not (accepted and seen_reject)
+        assert (st[ph == 4] == 1).all() and (st[ph < 4] == 0).all()
+        # phase D: bucket fills grow by the keys sent there, up to W entries
+        assert ((T.buckets() != 0).sum(1) - bfill0).sum() == (ph == 3).sum()
+
+
+def test_backing_table_and_full_status(oracle):
+    """Overfill a tiny TCF: keys beyond the blocks go to the backing table, and
+    beyond that are rejected with status 1; queries stay exact."""
+    T = oracle.TCF(6, 16, seed=9)  # 4 blocks of 16, 8 buckets of 8
+    keys = uniform_keys(62, 200)
+    st, ph, wh = T.insert(keys, trace=True)
+    assert (ph == 3).sum() == T.backing_count()
+    assert (st == 1).sum() > 0
+    ok = keys[st == 0]
+    assert T.query(ok).all()
+    assert T.stored_count() == len(ok)
+    for row in T.buckets().tolist():
+        k = sum(1 for e in row if e)
+        assert all(e == 0 for e in row[k:])
+        assert row[:k] == sorted(row[:k])
+
+
+def test_delete_half_no_false_negatives(oracle):
+    T = oracle.TCF(14, 16, seed=13)
+    keys = uniform_keys(63, int(0.9 * (1 << 14)))
+    for s in range(0, len(keys), 2048):
+        assert (T.insert(keys[s:s + 2048]) == 0).all()
+    gone = keys[::2]
+    kept = keys[1::2]
+    st = T.remove(gone)
+    assert (st == 0).all()
+    assert T.query(kept).all()
+    live = live_multiset(T, kept)
+    q = T.query(gone)
+    exp = np.array([live.get(int(x), 0) > 0 for x in T.fingerprints(gone)], np.uint8)
+    assert np.array_equal(q, exp)
+    assert T.stored_count() == len(kept)
+    # deleting again: only fingerprints still present (other keys' copies) succeed
+    st2 = T.remove(gone[:500])
+    want = collections.Counter(T.fingerprints(gone[:500]).tolist())
+    assert (st2 == 0).sum() == sum(min(c, live.get(fp, 0)) for fp, c in want.items())
+
+
+def test_delete_duplicates_and_absent(oracle):
+    T = oracle.TCF(10, 16, seed=21)
+    keys = uniform_keys(64, 100)
+    T.insert(np.concatenate([keys, keys[:10]]))
+    dele = np.concatenate([keys[:10], keys[:10], keys[:10]])
+    st = T.remove(dele)
+    # two copies each of keys[0..9]: 20 deletes succeed, 10 report not found
+    assert (st == 0).sum() == 20 and (st == 2).sum() == 10
+    assert T.stored_count() == 90
+    live = live_multiset(T, keys[10:])
+    exp = np.array([live.get(int(x), 0) > 0 for x in T.fingerprints(keys[:10])], np.uint8)
+    assert np.array_equal(T.query(keys[:10]), exp)
+
+
+@pytest.mark.parametrize("f", [16, 8])
+def test_fpr_closed_form(oracle, f):
+    """A fresh key is a false positive iff its fingerprint ({b1, b2}, tag) is stored.
+    With d distinct stored fingerprints among nb/2 block pairs per tag, and tag
+    probabilities p_t (2^-f, doubled for the two remapped values), the rate is
+    2 d / nb * sum(p_t^2) = 2 d (2^f + 4) / (nb 4^f); at full load this is the
+    paper's 2B/2^f (Sec. 4.1)."""
+    log2_slots = 18 if f == 16 else 16
+    T = oracle.TCF(log2_slots, f, seed=17)
+    keys = uniform_keys(65, int(0.9 * (1 << log2_slots)))
+    for s in range(0, len(keys), 1 << 14):
+        T.insert(keys[s:s + (1 << 14)])
+    d = len(set(T.fingerprints(keys).tolist()))
+    eps = 2 * d * (2 ** f + 4) / (T.nb * 4 ** f)
+    neg = uniform_keys(1065, 1 << 20)
+    fpr = T.query(neg).mean()
+    sigma = np.sqrt(eps * (1 - eps) / neg.size)
+    assert abs(fpr - eps) <= 4 * sigma, (fpr, eps, sigma)
+    # and the paper's full-load form bounds it from above
+    assert eps <= 2 * T.B / 2 ** f * (1 + 8 / 2 ** f)
+
+
+def test_ninety_percent_load_small_backing_share(oracle):
+    """Sec. 4.2: with the backing table the TCF reaches 90% load; the share of
+    items in the backing table stays small (the paper reports < 0.07% for its
+    point TCF; the phased bulk mode here is checked against 1%)."""
+    T = oracle.TCF(18, 16, seed=2)
+    keys = uniform_keys(2, int(0.9 * (1 << 18)))
+    for s in range(0, len(keys), 1 << 12):
+        assert (T.insert(keys[s:s + (1 << 12)]) == 0).all()
+    assert T.backing_count() < 0.01 * len(keys)
+    assert T.query(keys).all()
