@@ -1,0 +1,218 @@
+"""GPU filters for GB300: the two-choice filter (TCF) and the counting quotient
+filter (GQF) of "High-Performance Filters for GPUs" (arXiv 2212.09005).
+
+This module is a thin ctypes binding over the C ABI in include/gpufilter.h:
+it marshals torch CUDA tensors (device pointers) and the current CUDA stream
+into the library's calls. Every step of every operation runs in the
+library's CUDA kernels; there is no CPU fallback. If libgpufilter.so has not
+been built, importing works but creating a filter raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = [
+    "Filter", "TCF", "GQF", "lib", "build", "FilterError",
+    "FILTER_TCF", "FILTER_GQF", "MODE_BULK", "MODE_POINT",
+    "KEY_OK", "KEY_FULL", "KEY_NOT_FOUND", "STATUS_FULL", "STATUS_TIMEOUT",
+]
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgpufilter.so")
+
+FILTER_TCF, FILTER_GQF = 1, 2
+MODE_BULK, MODE_POINT = 0, 1
+KEY_OK, KEY_FULL, KEY_NOT_FOUND = 0, 1, 2
+ERR_FULL, ERR_TIMEOUT, ERR_INTERNAL = 4, 5, 7
+STATUS_FULL, STATUS_TIMEOUT, STATUS_INTERNAL = 1 << ERR_FULL, 1 << ERR_TIMEOUT, 1 << ERR_INTERNAL
+
+# entry points declared in include/gpufilter.h
+EXPORTS = [
+    "filter_create", "filter_destroy", "filter_clear", "filter_insert", "filter_query",
+    "filter_remove", "filter_count", "filter_get_stats", "filter_export_size",
+    "filter_export", "filter_import", "filter_error_string",
+    "filter_trace_enable", "filter_trace_reset", "filter_trace_summary",
+]
+
+
+class FilterConfig(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("log2_slots", C.c_uint32), ("tag_bits", C.c_uint32),
+                ("mode", C.c_uint32), ("hash_seed", C.c_uint64), ("max_batch", C.c_uint64)]
+
+
+class FilterStats(C.Structure):
+    _fields_ = [("status_word", C.c_uint64), ("failed_keys", C.c_uint64),
+                ("backing_used", C.c_uint64), ("table_bytes", C.c_uint64),
+                ("device_bytes", C.c_uint64), ("nslots", C.c_uint64)]
+
+
+class TraceEntry(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_uint64), ("units", C.c_uint64),
+                ("ms", C.c_double)]
+
+
+class FilterError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    from . import _build
+
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FilterError(f"{LIB_PATH} is missing: build the CUDA library first "
+                              "(paper_2212_09005_gb300.build())")
+        L = C.CDLL(LIB_PATH)
+        vp, u64, i32 = C.c_void_p, C.c_uint64, C.c_int
+        L.filter_create.argtypes = [C.POINTER(FilterConfig), vp, C.POINTER(vp)]
+        L.filter_destroy.argtypes = [vp]
+        L.filter_clear.argtypes = [vp, vp]
+        for name in ("filter_insert", "filter_query", "filter_remove", "filter_count"):
+            getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
+        L.filter_get_stats.argtypes = [vp, vp, C.POINTER(FilterStats)]
+        L.filter_export_size.argtypes = [vp, C.POINTER(u64)]
+        L.filter_export.argtypes = [vp, vp, u64, vp]
+        L.filter_import.argtypes = [vp, vp, u64, vp]
+        L.filter_trace_enable.argtypes = [i32]
+        L.filter_trace_reset.argtypes = []
+        L.filter_trace_summary.argtypes = [C.c_uint32, C.POINTER(TraceEntry), C.POINTER(C.c_uint32)]
+        L.filter_error_string.argtypes = [i32]
+        L.filter_error_string.restype = C.c_char_p
+        for name in EXPORTS:
+            if name != "filter_error_string":
+                getattr(L, name).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = lib().filter_error_string(rc).decode()
+        raise FilterError(f"{what}: {msg} (code {rc})")
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dptr(t, dtype_bytes=None):
+    """Device pointer of a contiguous CUDA tensor."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise FilterError("expected a CUDA tensor (device memory)")
+    if not t.is_contiguous():
+        raise FilterError("expected a contiguous tensor")
+    if dtype_bytes is not None and t.element_size() != dtype_bytes:
+        raise FilterError(f"expected {dtype_bytes}-byte elements")
+    return C.c_void_p(t.data_ptr())
+
+
+class Filter:
+    """One filter on the current CUDA device."""
+
+    def __init__(self, kind: int, log2_slots: int, tag_bits: int, mode: int = MODE_BULK,
+                 seed: int = 0, max_batch: int = 1 << 22, stream=None):
+        self.cfg = FilterConfig(kind, log2_slots, tag_bits, mode, seed & 0xFFFFFFFFFFFFFFFF,
+                                max(1, int(max_batch)))
+        h = C.c_void_p()
+        _check(lib().filter_create(C.byref(self.cfg), _stream(stream), C.byref(h)), "filter_create")
+        self._h = h
+        self.kind, self.log2_slots, self.tag_bits, self.mode = kind, log2_slots, tag_bits, mode
+        self.seed, self.max_batch = seed, max(1, int(max_batch))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().filter_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- batched operations (asynchronous on the stream) ----
+    def insert(self, keys, status=None, stream=None):
+        _check(lib().filter_insert(self._h, _dptr(keys, 8), keys.numel(), _dptr(status, 1),
+                                   _stream(stream)), "filter_insert")
+
+    def query(self, keys, found, stream=None):
+        _check(lib().filter_query(self._h, _dptr(keys, 8), keys.numel(), _dptr(found, 1),
+                                  _stream(stream)), "filter_query")
+
+    def remove(self, keys, status=None, stream=None):
+        _check(lib().filter_remove(self._h, _dptr(keys, 8), keys.numel(), _dptr(status, 1),
+                                   _stream(stream)), "filter_remove")
+
+    def count(self, keys, counts, stream=None):
+        _check(lib().filter_count(self._h, _dptr(keys, 8), keys.numel(), _dptr(counts, 8),
+                                  _stream(stream)), "filter_count")
+
+    def clear(self, stream=None):
+        _check(lib().filter_clear(self._h, _stream(stream)), "filter_clear")
+
+    # ---- synchronous helpers ----
+    def stats(self, stream=None) -> dict:
+        s = FilterStats()
+        _check(lib().filter_get_stats(self._h, _stream(stream), C.byref(s)), "filter_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in FilterStats._fields_}
+
+    def export(self, stream=None) -> np.ndarray:
+        n = C.c_uint64()
+        _check(lib().filter_export_size(self._h, C.byref(n)), "filter_export_size")
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib().filter_export(self._h, buf.ctypes.data_as(C.c_void_p), n.value, _stream(stream)),
+               "filter_export")
+        return buf
+
+    def import_(self, image: np.ndarray, stream=None):
+        image = np.ascontiguousarray(image, dtype=np.uint8)
+        _check(lib().filter_import(self._h, image.ctypes.data_as(C.c_void_p), image.size,
+                                   _stream(stream)), "filter_import")
+
+
+def TCF(log2_slots: int, tag_bits: int = 16, mode: int = MODE_BULK, seed: int = 0,
+        max_batch: int = 1 << 22, stream=None) -> Filter:
+    return Filter(FILTER_TCF, log2_slots, tag_bits, mode, seed, max_batch, stream)
+
+
+def GQF(q: int, r: int = 8, seed: int = 0, max_batch: int = 1 << 22, stream=None) -> Filter:
+    return Filter(FILTER_GQF, q, r, 0, seed, max_batch, stream)
+
+
+def trace_enable(on: bool = True):
+    """Record CUDA events around every library kernel launch (process-wide)."""
+    _check(lib().filter_trace_enable(1 if on else 0), "filter_trace_enable")
+
+
+def trace_reset():
+    _check(lib().filter_trace_reset(), "filter_trace_reset")
+
+
+def trace_summary() -> dict:
+    """{kernel name: {"launches", "units", "ms"}} for the launches recorded so far."""
+    n = C.c_uint32()
+    _check(lib().filter_trace_summary(0, None, C.byref(n)), "filter_trace_summary")
+    arr = (TraceEntry * max(1, n.value))()
+    _check(lib().filter_trace_summary(n.value, arr, C.byref(n)), "filter_trace_summary")
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "units": int(arr[i].units),
+                                   "ms": float(arr[i].ms)} for i in range(n.value)}

@@ -1,0 +1,164 @@
+// The C ABI of include/gpufilter.h: argument checks, allocation, dispatch.
+#include <cstring>
+#include <new>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+const char *last_cuda_error();
+}
+
+static cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+static bool valid(const filter_t *f) { return f != nullptr && f->arena.base != nullptr; }
+
+extern "C" {
+
+int filter_create(const filter_config *cfg, void *stream, filter_t **out)
+{
+    if (!cfg || !out) return FILTER_ERR_ARG;
+    *out = nullptr;
+    filter *F = new (std::nothrow) filter();
+    if (!F) return FILTER_ERR_OOM;
+    F->cfg = *cfg;
+    if (F->cfg.max_batch == 0) F->cfg.max_batch = 1;
+    uint64_t tb = 0, sb = 0;
+    int rc;
+    if (cfg->kind == FILTER_TCF) rc = gf::tcf_setup(F, tb, sb, true);
+    else if (cfg->kind == FILTER_GQF) rc = gf::gqf_setup(F, tb, sb, true);
+    else rc = FILTER_ERR_ARG;
+    if (rc != FILTER_OK) {
+        delete F;
+        return rc;
+    }
+    const size_t total = tb + sb + (64u << 10);
+    cudaGetDevice(&F->device);
+    if (cudaMalloc(&F->arena.base, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete F;
+        return FILTER_ERR_OOM;
+    }
+    F->arena.size = total;
+    if (cudaMalloc(&F->ctr, sizeof(gf::DevCounters)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(F->arena.base);
+        delete F;
+        return FILTER_ERR_OOM;
+    }
+    if (cfg->kind == FILTER_TCF) rc = gf::tcf_setup(F, tb, sb, false);
+    else rc = gf::gqf_setup(F, tb, sb, false);
+    if (rc == FILTER_OK && F->arena.used > F->arena.size) rc = FILTER_ERR_INTERNAL;
+    if (rc == FILTER_OK) rc = (cfg->kind == FILTER_TCF) ? gf::tcf_clear(F, as_stream(stream)) : gf::gqf_clear(F, as_stream(stream));
+    if (rc != FILTER_OK) {
+        cudaFree(F->ctr);
+        cudaFree(F->arena.base);
+        delete F;
+        return rc;
+    }
+    *out = F;
+    return FILTER_OK;
+}
+
+int filter_destroy(filter_t *f)
+{
+    if (!f) return FILTER_OK;
+    int rc = FILTER_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) rc = FILTER_ERR_CUDA;
+    if (f->ctr) cudaFree(f->ctr);
+    if (f->arena.base) cudaFree(f->arena.base);
+    f->arena.base = nullptr;
+    delete f;
+    return rc;
+}
+
+int filter_clear(filter_t *f, void *stream)
+{
+    if (!valid(f)) return FILTER_ERR_ARG;
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_clear(f, as_stream(stream)) : gf::gqf_clear(f, as_stream(stream));
+}
+
+int filter_insert(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_status, void *stream)
+{
+    if (!valid(f) || n > f->cfg.max_batch || (n && !d_keys)) return FILTER_ERR_ARG;
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_insert(f, d_keys, n, d_status, as_stream(stream))
+                                     : gf::gqf_insert(f, d_keys, n, d_status, as_stream(stream));
+}
+
+int filter_query(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_found, void *stream)
+{
+    if (!valid(f) || (n && (!d_keys || !d_found))) return FILTER_ERR_ARG;
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_query(f, d_keys, n, d_found, as_stream(stream))
+                                     : gf::gqf_count(f, d_keys, n, nullptr, d_found, as_stream(stream));
+}
+
+int filter_remove(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_status, void *stream)
+{
+    if (!valid(f) || n > f->cfg.max_batch || (n && !d_keys)) return FILTER_ERR_ARG;
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_remove(f, d_keys, n, d_status, as_stream(stream))
+                                     : gf::gqf_remove(f, d_keys, n, d_status, as_stream(stream));
+}
+
+int filter_count(filter_t *f, const uint64_t *d_keys, uint64_t n, uint64_t *d_counts, void *stream)
+{
+    if (!valid(f) || (n && (!d_keys || !d_counts))) return FILTER_ERR_ARG;
+    if (f->cfg.kind != FILTER_GQF) return FILTER_ERR_UNSUPPORTED;
+    return gf::gqf_count(f, d_keys, n, d_counts, nullptr, as_stream(stream));
+}
+
+int filter_get_stats(filter_t *f, void *stream, filter_stats *out)
+{
+    if (!valid(f) || !out) return FILTER_ERR_ARG;
+    gf::DevCounters c;
+    if (cudaMemcpyAsync(&c, f->ctr, sizeof(c), cudaMemcpyDeviceToHost, as_stream(stream)) != cudaSuccess ||
+        cudaStreamSynchronize(as_stream(stream)) != cudaSuccess)
+        return FILTER_ERR_CUDA;
+    std::memset(out, 0, sizeof(*out));
+    out->status_word = c.status;
+    out->failed_keys = c.failed;
+    out->backing_used = f->cfg.kind == FILTER_TCF ? c.backing : 0;
+    out->table_bytes = f->cfg.kind == FILTER_TCF ? gf::tcf_image_bytes(f) : gf::gqf_image_bytes(f);
+    out->device_bytes = f->arena.size + sizeof(gf::DevCounters);
+    out->nslots = f->cfg.kind == FILTER_TCF ? f->tcf.G.nb * f->tcf.G.B : f->gqf.nslots;
+    return FILTER_OK;
+}
+
+int filter_export_size(filter_t *f, uint64_t *nbytes)
+{
+    if (!valid(f) || !nbytes) return FILTER_ERR_ARG;
+    *nbytes = f->cfg.kind == FILTER_TCF ? gf::tcf_image_bytes(f) : gf::gqf_image_bytes(f);
+    return FILTER_OK;
+}
+
+int filter_export(filter_t *f, void *host_buf, uint64_t nbytes, void *stream)
+{
+    uint64_t want = 0;
+    if (!valid(f) || !host_buf || filter_export_size(f, &want) != FILTER_OK || nbytes != want) return FILTER_ERR_ARG;
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_copy_image(f, host_buf, true, as_stream(stream))
+                                     : gf::gqf_copy_image(f, host_buf, true, as_stream(stream));
+}
+
+int filter_import(filter_t *f, const void *host_buf, uint64_t nbytes, void *stream)
+{
+    uint64_t want = 0;
+    if (!valid(f) || !host_buf || filter_export_size(f, &want) != FILTER_OK || nbytes != want) return FILTER_ERR_ARG;
+    void *h = const_cast<void *>(host_buf);
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_copy_image(f, h, false, as_stream(stream))
+                                     : gf::gqf_copy_image(f, h, false, as_stream(stream));
+}
+
+const char *filter_error_string(int code)
+{
+    switch (code) {
+    case FILTER_OK: return "ok";
+    case FILTER_ERR_ARG: return "invalid argument";
+    case FILTER_ERR_OOM: return "device allocation failed";
+    case FILTER_ERR_UNSUPPORTED: return "operation not supported by this filter kind";
+    case FILTER_ERR_FULL: return "filter full";
+    case FILTER_ERR_TIMEOUT: return "bounded device wait gave up";
+    case FILTER_ERR_CUDA: return gf::last_cuda_error();
+    case FILTER_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown error";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,948 @@
+// Counting quotient filter (GQF), paper Sec. 5, for sm_103a.
+//
+// Table (double-buffered): per 64-slot block a 32-byte metadata record
+// {occupieds, runends, offset}, and an array of r-bit remainders.
+//
+// Bulk insert / delete (Sec. 5.4-5.5, Sec. 7): fingerprints are computed,
+// radix-sorted and reduced to <fingerprint, count> groups (the paper's
+// map-reduce for skewed inputs). The groups are then merged into the table in
+// ONE pass over quotient tiles of TQ quotients instead of the paper's
+// even-odd region phases: a run of quotient x with encoded length L ends at
+// e_x = max(x + L - 1, e_prev + L), so run placement is a prefix scan under
+// the operator (A1, B1) . (A2, B2) = (max(A2, A1 + B2), B1 + B2). Each CTA
+// decodes the old runs of its tile (located through the offset of its first
+// block and select over runends), merges them with the tile's new groups,
+// computes the run lengths, takes its incoming end from the preceding tiles
+// by decoupled look-back, and writes its runs, runends, occupieds and
+// offsets into the other buffer. Every slot of the new buffer is written by
+// exactly one tile.
+//
+// Count / query (Sec. 5.1 via the cited CQF): offset of the home block,
+// rank over occupieds, select over runends, then a scan of the run.
+#include "gf_internal.cuh"
+
+namespace gf {
+
+static constexpr int MT = 256;          // merge threads per CTA
+static constexpr int QPT = 8;           // quotients per thread
+static constexpr int TQ = MT * QPT;     // quotients per tile
+static constexpr int TBLK = TQ / 64;    // blocks per tile
+static constexpr int OLDBUF = 3072;     // staged old slots
+static constexpr int OUTBUF = 3072;     // staged new slots
+static constexpr int RWORDS = OUTBUF / 64 + 2;
+static constexpr long long NEG_INF = -(1ll << 60);
+
+struct Meta {
+    unsigned long long occ, rend;
+    unsigned int off, pad0;
+    unsigned long long pad1;
+};
+static_assert(sizeof(Meta) == 32, "metadata record is 32 bytes");
+
+__host__ __device__ __forceinline__ uint32_t ndig(uint64_t v, uint32_t r)
+{
+    uint32_t n = 0;
+    while (v) {
+        n++;
+        v = (r >= 64) ? 0 : (v >> r);
+    }
+    return n;
+}
+__host__ __device__ __forceinline__ uint32_t enc_len(uint64_t c, uint32_t r) { return c == 1 ? 1u : 3u + ndig(c - 2, r); }
+
+// ---------------------------------------------------------------------------
+// fingerprints, group flags, compaction
+// ---------------------------------------------------------------------------
+__global__ void gqf_fp_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H, uint64_t *fp, uint32_t *idx)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        fp[i] = fingerprint(keys[i], H);
+        if (idx) idx[i] = (uint32_t)i;
+    }
+}
+
+// flags[i] = 1 where a new fingerprint starts; flags[n] = 0
+__global__ void gqf_flags(const uint64_t *__restrict__ fp, uint64_t n, uint32_t *flags)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x)
+        flags[i] = (i < n && (i == 0 || fp[i] != fp[i - 1])) ? 1u : 0u;
+}
+
+// after the scan, pos[i] = number of group starts before i, pos[n] = m
+__global__ void gqf_compact(const uint64_t *__restrict__ fp, uint64_t n, const uint32_t *__restrict__ pos,
+                            uint64_t *ufp, uint32_t *ustart)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (i == 0 || fp[i] != fp[i - 1]) {
+            uint32_t u = pos[i];
+            ufp[u] = fp[i];
+            ustart[u] = (uint32_t)i;
+        }
+        if (i == 0) ustart[pos[n]] = (uint32_t)n;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The merge kernel
+// ---------------------------------------------------------------------------
+struct MergeArgs {
+    const Meta *meta_old;
+    const uint8_t *rem_old;
+    Meta *meta_new;
+    uint8_t *rem_new;
+    const uint64_t *ufp;
+    const uint32_t *ustart;
+    const uint32_t *pm;      // number of groups (device)
+    uint64_t m_limit;        // use groups [0, min(m, m_limit))
+    uint32_t *removed;       // delete: copies removed per group
+    unsigned long long *ts;  // look-back state: [0] tile counter, then 4 words per tile
+    DevCounters *ctr;
+    uint64_t N, nslots, nblk, ntiles;
+    uint32_t r;
+    int del, dry;
+};
+
+__device__ __forceinline__ void agg_combine(long long &A, long long &Bs, long long A2, long long B2)
+{
+    // (A, Bs) then (A2, B2)
+    long long a = A + B2;
+    A = a > A2 ? a : A2;
+    Bs += B2;
+}
+
+template <int R>
+struct SlotIO {
+    using T = typename std::conditional<R == 8, uint8_t, uint16_t>::type;
+};
+
+template <int R>
+__device__ __forceinline__ uint32_t rd_slot(const uint8_t *rem, uint64_t i)
+{
+    if (R == 8) return rem[i];
+    return reinterpret_cast<const uint16_t *>(rem)[i];
+}
+template <int R>
+__device__ __forceinline__ void wr_slot(uint8_t *rem, uint64_t i, uint32_t v)
+{
+    if (R == 8) rem[i] = (uint8_t)v;
+    else reinterpret_cast<uint16_t *>(rem)[i] = (uint16_t)v;
+}
+
+template <int R>
+struct MergeSmem {
+    unsigned long long occ[TBLK];
+    unsigned int kpre[MT + 1];
+    int oend[TQ];                   // old run ends relative to Q0
+    unsigned int nfirst[MT + 1];
+    typename SlotIO<R>::T old[OLDBUF];
+    typename SlotIO<R>::T out[OUTBUF];
+    unsigned long long rend[RWORDS];
+    unsigned char newocc[MT];
+    long long wA[MT / 32], wB[MT / 32];
+    long long prev_end_old, os0, ein, w0, w1, tileP;
+    unsigned long long glo, ghi;
+    unsigned int tile, kold, oldlen, err;
+};
+
+// old slot reader: staged when inside the staged window
+template <int R>
+__device__ __forceinline__ uint32_t old_at(const MergeSmem<R> &S, const MergeArgs &a, long long p)
+{
+    long long d = p - S.os0;
+    if (d >= 0 && d < (long long)S.oldlen) return S.old[d];
+    if (p < 0 || p >= (long long)a.nslots) return 0u;
+    return rd_slot<R>(a.rem_old, (uint64_t)p);
+}
+
+// sequential reader of the groups of one old run [p, e]
+struct OldRun {
+    long long p, e;
+};
+
+template <int R>
+__device__ __forceinline__ bool old_next(const MergeSmem<R> &S, const MergeArgs &a, OldRun &o, uint32_t &v,
+                                         uint64_t &c)
+{
+    if (o.p > o.e) return false;
+    v = old_at<R>(S, a, o.p);
+    if (o.p + 2 <= o.e && old_at<R>(S, a, o.p + 1) == v) {
+        uint32_t nd = old_at<R>(S, a, o.p + 2);
+        if (o.p + 2 + (long long)nd > o.e) nd = (uint32_t)(o.e - o.p - 2);  // malformed: stay in the run
+        uint64_t acc = 0;
+        for (uint32_t d = 0; d < nd; d++) acc = (acc << R) | old_at<R>(S, a, o.p + 3 + d);
+        c = acc + 2;
+        o.p += 3 + nd;
+    } else {
+        c = 1;
+        o.p += 1;
+    }
+    return true;
+}
+
+// emit one group's encoding at position pos (staged or global)
+template <int R>
+__device__ __forceinline__ void put_slot(MergeSmem<R> &S, const MergeArgs &a, long long pos, uint32_t v)
+{
+    long long d = pos - S.w0;
+    if (d >= 0 && d < OUTBUF) S.out[d] = (typename SlotIO<R>::T)v;
+    else if (pos < (long long)a.nslots) wr_slot<R>(a.rem_new, (uint64_t)pos, v);
+}
+
+template <int R>
+__device__ __forceinline__ long long put_group(MergeSmem<R> &S, const MergeArgs &a, long long pos, uint32_t v,
+                                               uint64_t c)
+{
+    put_slot<R>(S, a, pos++, v);
+    if (c == 1) return pos;
+    uint64_t x = c - 2;
+    uint32_t nd = ndig(x, R);
+    put_slot<R>(S, a, pos++, v);
+    put_slot<R>(S, a, pos++, nd);
+    for (uint32_t d = 0; d < nd; d++) put_slot<R>(S, a, pos++, (uint32_t)((x >> (R * (nd - 1 - d))) & ((1u << R) - 1u)));
+    return pos;
+}
+
+// Merge the old groups of one run with the new groups [g, gend) of quotient y.
+// WRITE = false: return the encoded length (and record removals);
+// WRITE = true: write the run starting at `pos`.
+template <int R, bool WRITE>
+__device__ __forceinline__ uint32_t merge_run(MergeSmem<R> &S, const MergeArgs &a, OldRun o, bool has_old,
+                                              uint32_t g, uint32_t gend, long long pos)
+{
+    const uint64_t rmask = (1ull << R) - 1ull;
+    uint32_t len = 0;
+    uint32_t ov = 0, nv = 0;
+    uint64_t oc = 0, nc = 0;
+    bool ho = has_old && old_next<R>(S, a, o, ov, oc);
+    bool hn = g < gend;
+    if (hn) {
+        nv = (uint32_t)(a.ufp[g] & rmask);
+        nc = a.ustart[g + 1] - a.ustart[g];
+    }
+    while (ho || hn) {
+        uint32_t v;
+        uint64_t c;
+        if (ho && (!hn || ov < nv)) {
+            v = ov;
+            c = oc;
+            ho = old_next<R>(S, a, o, ov, oc);
+        } else {
+            v = nv;
+            if (ho && ov == nv) {
+                if (a.del) {
+                    uint64_t rm = oc < nc ? oc : nc;
+                    c = oc - rm;
+                    if (!WRITE && a.removed) a.removed[g] = (uint32_t)rm;
+                } else {
+                    c = oc + nc;
+                }
+                ho = old_next<R>(S, a, o, ov, oc);
+            } else {
+                if (a.del) {
+                    c = 0;
+                    if (!WRITE && a.removed) a.removed[g] = 0;
+                } else {
+                    c = nc;
+                }
+            }
+            g++;
+            hn = g < gend;
+            if (hn) {
+                nv = (uint32_t)(a.ufp[g] & rmask);
+                nc = a.ustart[g + 1] - a.ustart[g];
+            }
+        }
+        if (c == 0) continue;
+        if (WRITE) pos = put_group<R>(S, a, pos, v, c);
+        else len += enc_len(c, R);
+    }
+    return len;
+}
+
+__device__ __forceinline__ unsigned long long ld_vol(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+template <int R>
+__global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
+{
+    __shared__ MergeSmem<R> S;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        S.tile = (unsigned)atomicAdd(&a.ts[0], 1ull);
+        S.err = 0;
+    }
+    __syncthreads();
+    const uint64_t tile = S.tile;
+    const long long Q0 = (long long)tile * TQ;
+    const uint64_t j0 = tile * TBLK;
+    const uint64_t m_eff = min((uint64_t)*a.pm, a.m_limit);
+    const long long slot_end = min((long long)a.nslots, Q0 + TQ);
+
+    // 1. old occupieds of the tile
+    if (tid < TBLK) S.occ[tid] = (j0 + tid < a.nblk) ? a.meta_old[j0 + tid].occ : 0ull;
+    __syncthreads();
+    const uint32_t mybyte = (uint32_t)(S.occ[tid >> 3] >> ((tid & 7) * 8)) & 0xffu;
+
+    // 2. old run index prefix per thread
+    {
+        uint32_t c = __popc(mybyte), incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __shared__ unsigned int wsum[MT / 32];
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; w++) pre += wsum[w];
+        S.kpre[tid] = pre + incl - c;
+        if (tid == MT - 1) {
+            S.kpre[MT] = pre + incl;
+            S.kold = pre + incl;
+        }
+    }
+    // 4a. new group range of the tile (successor search, Sec. 5.4)
+    if (tid < 2) {
+        long long qb = Q0 + (tid == 0 ? 0 : TQ);
+        uint64_t key = (qb >= (long long)a.N) ? (a.N << a.r) : ((uint64_t)qb << a.r);
+        uint64_t lo = 0, hi = m_eff;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (a.ufp[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        if (tid == 0) S.glo = lo;
+        else S.ghi = lo;
+    }
+    __syncthreads();
+    const uint32_t kold = S.kold;
+
+    // 3. old run ends (warp 0): select over runends after the offset of block j0
+    if (warp == 0 && kold > 0) {
+        const Meta &m0 = a.meta_old[j0];
+        const long long base = Q0 + (long long)m0.off;
+        const bool q0occ = (S.occ[0] & 1ull) != 0;
+        long long sp = q0occ ? base : base + 1;
+        uint32_t found = 0;
+        long long w = sp >> 6;
+        bool first = true;
+        while (found < kold) {
+            long long ww = w + lane;
+            unsigned long long bits = (ww < (long long)a.nblk) ? a.meta_old[ww].rend : 0ull;
+            if (first && lane == 0) bits &= (~0ull) << (sp & 63);
+            uint32_t c = __popcll(bits), incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            uint32_t idx = found + incl - c;
+            while (bits && idx < kold) {
+                int b = __ffsll((long long)bits) - 1;
+                S.oend[idx] = (int)(ww * 64 + b - Q0);
+                bits &= bits - 1;
+                idx++;
+            }
+            found += __shfl_sync(0xffffffffu, incl, 31);
+            w += 32;
+            first = false;
+            if (w >= (long long)a.nblk + 32) {
+                if (lane == 0) S.err = 1;
+                break;
+            }
+        }
+        // end of the run before the tile's first run
+        if (lane == 0) {
+            long long pe;
+            if (q0occ) {
+                pe = Q0 - 1;
+                for (long long p = base - 1; p >= Q0; p--) {
+                    if ((a.meta_old[p >> 6].rend >> (p & 63)) & 1ull) {
+                        pe = p;
+                        break;
+                    }
+                }
+            } else {
+                pe = base;
+            }
+            S.prev_end_old = pe;
+        }
+    }
+    // 4b. per-thread new group ranges
+    for (int t = tid; t <= MT; t += MT) S.nfirst[t] = (unsigned)S.ghi;
+    __syncthreads();
+    for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
+        long long y = (long long)(a.ufp[g] >> a.r);
+        unsigned t = (unsigned)((y - Q0) >> 3);
+        bool start = (g == S.glo) || ((((long long)(a.ufp[g - 1] >> a.r)) - Q0) >> 3) != (long long)t;
+        if (start) S.nfirst[t] = (unsigned)g;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        unsigned nxt = (unsigned)S.ghi;
+        for (int t = MT; t >= 0; t--) {
+            if (S.nfirst[t] > nxt) S.nfirst[t] = nxt;
+            nxt = S.nfirst[t];
+        }
+        // 5. staged window of the old runs
+        if (kold > 0 && S.err == 0) {
+            long long yfirst = -1;
+            for (int w = 0; w < TBLK && yfirst < 0; w++)
+                if (S.occ[w]) yfirst = Q0 + 64 * w + __ffsll((long long)S.occ[w]) - 1;
+            long long os0 = yfirst > S.prev_end_old + 1 ? yfirst : S.prev_end_old + 1;
+            long long oe = Q0 + S.oend[kold - 1];
+            S.os0 = os0;
+            long long len = oe - os0 + 1;
+            S.oldlen = (unsigned)(len < OLDBUF ? len : OLDBUF);
+        } else {
+            S.os0 = 0;
+            S.oldlen = 0;
+        }
+    }
+    __syncthreads();
+    for (unsigned p = tid; p < S.oldlen; p += MT) S.old[p] = (typename SlotIO<R>::T)rd_slot<R>(a.rem_old, (uint64_t)(S.os0 + p));
+    __syncthreads();
+
+    // 6. pass 1: run lengths of this thread's quotients
+    const bool old_ok = S.err == 0;
+    const long long ybase = Q0 + (long long)tid * QPT;
+    const uint32_t n0 = S.nfirst[tid], n1 = S.nfirst[tid + 1];
+    uint32_t L[QPT];
+    long long tA = NEG_INF, tB = 0;
+    {
+        uint32_t k = S.kpre[tid];
+        uint32_t g = n0;
+        for (int c = 0; c < QPT; c++) {
+            long long y = ybase + c;
+            bool ho = old_ok && ((mybyte >> c) & 1u);
+            OldRun o{0, -1};
+            if (ho) {
+                long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
+                o.e = Q0 + S.oend[k];
+                o.p = y > pe + 1 ? y : pe + 1;
+                k++;
+            }
+            uint32_t ge = g;
+            while (ge < n1 && (long long)(a.ufp[ge] >> a.r) == y) ge++;
+            L[c] = (ho || ge > g) ? merge_run<R, false>(S, a, o, ho, g, ge, 0) : 0u;
+            g = ge;
+            if (L[c]) agg_combine(tA, tB, y + L[c] - 1, L[c]);
+        }
+    }
+    // 7. exclusive scan of the thread aggregates across the CTA
+    long long iA = tA, iB = tB;  // inclusive
+    for (int o = 1; o < 32; o <<= 1) {
+        long long pA = __shfl_up_sync(0xffffffffu, iA, o);
+        long long pB = __shfl_up_sync(0xffffffffu, iB, o);
+        if (lane >= o) {
+            long long A = pA, Bs = pB;
+            agg_combine(A, Bs, iA, iB);
+            iA = A;
+            iB = Bs;
+        }
+    }
+    if (lane == 31) {
+        S.wA[warp] = iA;
+        S.wB[warp] = iB;
+    }
+    long long xA = __shfl_up_sync(0xffffffffu, iA, 1), xB = __shfl_up_sync(0xffffffffu, iB, 1);
+    if (lane == 0) {
+        xA = NEG_INF;
+        xB = 0;
+    }
+    __syncthreads();
+    {
+        long long pA = NEG_INF, pB = 0;
+        for (int w = 0; w < warp; w++) agg_combine(pA, pB, S.wA[w], S.wB[w]);
+        agg_combine(pA, pB, xA, xB);
+        xA = pA;
+        xB = pB;
+    }
+    // 8. decoupled look-back over tiles (thread 0)
+    if (tid == 0) {
+        long long TA = NEG_INF, TB = 0;
+        for (int w = 0; w < MT / 32; w++) agg_combine(TA, TB, S.wA[w], S.wB[w]);
+        unsigned long long *st = a.ts + 1 + 4 * tile;
+        long long ein = -1;
+        if (tile > 0) {
+            st[1] = (unsigned long long)TA;
+            st[2] = (unsigned long long)TB;
+            __threadfence();
+            atomicExch(&st[0], 1ull);
+            long long gA = NEG_INF, gB = 0;  // composition of the tiles passed so far
+            long long j = (long long)tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                unsigned long long *sj = a.ts + 1 + 4 * j;
+                unsigned long long fl = ld_vol(&sj[0]);
+                if (fl == 0) {
+                    if (++spins > SPIN_LIMIT) {
+                        atomicOr(&a.ctr->status, ST_TIMEOUT);
+                        break;
+                    }
+                    continue;
+                }
+                __threadfence();
+                if (fl == 2) {
+                    long long P = (long long)ld_vol(&sj[3]);
+                    long long v = P + gB;
+                    ein = v > gA ? v : gA;
+                    break;
+                }
+                long long A = (long long)ld_vol(&sj[1]), Bj = (long long)ld_vol(&sj[2]);
+                agg_combine(A, Bj, gA, gB);
+                gA = A;
+                gB = Bj;
+                j--;
+            }
+        }
+        long long v = ein + TB;
+        long long P = v > TA ? v : TA;
+        st[3] = (unsigned long long)P;
+        __threadfence();
+        atomicExch(&st[0], 2ull);
+        S.ein = ein;
+        S.tileP = P;
+        atomicMax(&a.ctr->gqf_end, P);
+        if (P >= (long long)a.nslots) atomicExch(&a.ctr->overflow, 1ull);
+        long long w0 = Q0 > ein + 1 ? Q0 : ein + 1;
+        long long w1 = slot_end > P + 1 ? slot_end : P + 1;
+        if (w1 > (long long)a.nslots) w1 = (long long)a.nslots;
+        if (w0 > w1) w0 = w1;
+        S.w0 = w0;
+        S.w1 = w1;
+    }
+    __syncthreads();
+    if (S.err) atomicOr(&a.ctr->status, ST_INTERNAL);
+    if (a.dry) return;
+
+    // 9. pass 2: write
+    const long long w0 = S.w0, w1 = S.w1;
+    const long long staged = (w1 - w0) < OUTBUF ? (w1 - w0) : OUTBUF;
+    for (int p = tid; p < OUTBUF; p += MT) S.out[p] = 0;
+    for (int p = tid; p < RWORDS; p += MT) S.rend[p] = 0ull;
+    for (long long p = w0 + OUTBUF + tid; p < w1; p += MT) wr_slot<R>(a.rem_new, (uint64_t)p, 0u);
+    __syncthreads();
+    const long long wbase = w0 >> 6;
+    long long e;
+    {
+        long long v = S.ein + xB;
+        e = v > xA ? v : xA;
+    }
+    const long long e_thread_in = e;
+    uint32_t newbyte = 0;
+    long long first_end = -1;
+    {
+        uint32_t k = S.kpre[tid];
+        uint32_t g = n0;
+        for (int c = 0; c < QPT; c++) {
+            long long y = ybase + c;
+            bool ho = old_ok && ((mybyte >> c) & 1u);
+            OldRun o{0, -1};
+            if (ho) {
+                long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
+                o.e = Q0 + S.oend[k];
+                o.p = y > pe + 1 ? y : pe + 1;
+                k++;
+            }
+            uint32_t ge = g;
+            while (ge < n1 && (long long)(a.ufp[ge] >> a.r) == y) ge++;
+            if (L[c]) {
+                long long start = y > e + 1 ? y : e + 1;
+                long long end = start + L[c] - 1;
+                merge_run<R, true>(S, a, o, ho, g, ge, start);
+                if (end < (long long)a.nslots) {
+                    long long wi = (end >> 6) - wbase;
+                    if (end - w0 < OUTBUF && wi >= 0 && wi < RWORDS)
+                        atomicOr(&S.rend[wi], 1ull << (end & 63));
+                    else
+                        atomicOr(&a.meta_new[end >> 6].rend, 1ull << (end & 63));
+                }
+                e = end;
+                newbyte |= 1u << c;
+                if (c == 0) first_end = end;
+            }
+            g = ge;
+        }
+    }
+    S.newocc[tid] = (unsigned char)newbyte;
+    // offsets: the thread whose first quotient starts a block
+    if ((tid & 7) == 0) {
+        uint64_t j = j0 + (tid >> 3);
+        if (j < a.nblk) {
+            long long ref = (newbyte & 1u) ? first_end : e_thread_in;
+            long long o = ref - 64 * (long long)j;
+            a.meta_new[j].off = (unsigned)(o > 0 ? o : 0);
+        }
+    }
+    __syncthreads();
+    // flush staged remainders and runend words
+    for (long long p = tid; p < staged; p += MT) wr_slot<R>(a.rem_new, (uint64_t)(w0 + p), S.out[p]);
+    for (int p = tid; p < RWORDS; p += MT)
+        if (S.rend[p]) atomicOr(&a.meta_new[wbase + p].rend, S.rend[p]);
+    if (tid < TBLK && j0 + tid < a.nblk) {
+        unsigned long long w = 0;
+        for (int b = 0; b < 8; b++) w |= (unsigned long long)S.newocc[tid * 8 + b] << (8 * b);
+        a.meta_new[j0 + tid].occ = w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-key status after a batch
+// ---------------------------------------------------------------------------
+// pos: scanned group-start flags (pos[i + 1] - 1 = group of sorted element i)
+__global__ void gqf_status_kernel(uint64_t n, const uint32_t *__restrict__ pos, const uint32_t *__restrict__ ustart,
+                                  const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ removed,
+                                  uint64_t m_keep, int del, uint8_t *status)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t g = pos[i + 1] - 1;
+        uint8_t s;
+        if (del) s = (i - ustart[g]) < removed[g] ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;
+        else s = (g < m_keep) ? FILTER_KEY_OK : FILTER_KEY_FULL;
+        status[sidx[i]] = s;
+    }
+}
+
+// keys of the groups past the kept prefix were rejected
+__global__ void gqf_account_full(DevCounters *ctr, const uint32_t *ustart, uint64_t m_keep, uint64_t n)
+{
+    uint64_t kept = m_keep ? ustart[m_keep] : 0;
+    if (kept < n) {
+        atomicAdd(&ctr->failed, (unsigned long long)(n - kept));
+        atomicOr(&ctr->status, ST_FULL);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// count / query
+// ---------------------------------------------------------------------------
+template <int R>
+__global__ void __launch_bounds__(256) gqf_count_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H,
+                                                        const Meta *__restrict__ meta,
+                                                        const uint8_t *__restrict__ rem, uint64_t nblk,
+                                                        uint64_t *counts, uint8_t *found)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t fp = fingerprint(__ldg(keys + i), H);
+        const uint64_t x = fp >> R;
+        const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
+        const uint64_t j = x >> 6;
+        const ulonglong2 or_ = __ldg(reinterpret_cast<const ulonglong2 *>(meta + j));
+        const unsigned long long occ = or_.x;
+        uint64_t c = 0;
+        if ((occ >> (x & 63)) & 1ull) {
+            const long long base = (long long)(64 * j) + (long long)__ldg(&meta[j].off);
+            const unsigned sh = (unsigned)(x & 63);
+            const unsigned long long upto = (sh == 63) ? ~0ull : ((1ull << (sh + 1)) - 1ull);
+            int d = __popcll(occ & upto & ~1ull);
+            long long end = base;
+            if (d > 0) {
+                long long w = base >> 6;
+                unsigned bsh = (unsigned)(base & 63);
+                unsigned long long bits = (bsh == 63) ? 0ull : (__ldg(&meta[w].rend) & (~0ull << (bsh + 1)));
+                while (true) {
+                    int pc = __popcll(bits);
+                    if (pc >= d) {
+                        for (int k = 1; k < d; k++) bits &= bits - 1;
+                        end = 64 * w + __ffsll((long long)bits) - 1;
+                        break;
+                    }
+                    d -= pc;
+                    if (++w >= (long long)nblk) {
+                        end = -1;
+                        break;
+                    }
+                    bits = __ldg(&meta[w].rend);
+                }
+            }
+            if (end >= 0) {
+                // start: one past the last runend in [x, end - 1], else x
+                long long start = (long long)x;
+                long long p = end - 1;
+                while (p >= (long long)x) {
+                    long long w = p >> 6;
+                    unsigned long long bits = __ldg(&meta[w].rend);
+                    unsigned pb = (unsigned)(p & 63);
+                    bits &= (pb == 63) ? ~0ull : ((1ull << (pb + 1)) - 1ull);
+                    if (64 * w < (long long)x) bits &= ~0ull << (x & 63);
+                    if (bits) {
+                        start = 64 * w + 63 - __clzll((long long)bits) + 1;
+                        break;
+                    }
+                    p = 64 * w - 1;
+                }
+                long long q = start;
+                while (q <= end) {
+                    uint32_t s = rd_slot<R>(rem, (uint64_t)q);
+                    uint64_t cc = 1;
+                    long long step = 1;
+                    if (q + 2 <= end && rd_slot<R>(rem, (uint64_t)(q + 1)) == s) {
+                        uint32_t nd = rd_slot<R>(rem, (uint64_t)(q + 2));
+                        if (q + 2 + (long long)nd > end) nd = (uint32_t)(end - q - 2);
+                        uint64_t acc = 0;
+                        for (uint32_t dd = 0; dd < nd; dd++) acc = (acc << R) | rd_slot<R>(rem, (uint64_t)(q + 3 + dd));
+                        cc = acc + 2;
+                        step = 3 + nd;
+                    }
+                    if (s == v) {
+                        c = cc;
+                        break;
+                    }
+                    if (s > v) break;
+                    q += step;
+                }
+            }
+        }
+        if (counts) counts[i] = c;
+        if (found) found[i] = c ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static uint64_t tail_slots(uint32_t q)
+{
+    uint64_t N = 1ull << q;
+    uint64_t s = ((1072ull * q + 63) / 64) * 64;
+    if (s > N) s = N;
+    if (s < 64) s = 64;
+    return s;
+}
+
+int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only)
+{
+    const filter_config &c = F->cfg;
+    if (c.tag_bits != 8 && c.tag_bits != 16) return FILTER_ERR_ARG;
+    if (c.log2_slots < 6 || c.log2_slots > 36 || c.log2_slots + c.tag_bits > 64) return FILTER_ERR_ARG;
+    GqfState &Q = F->gqf;
+    Q.q = c.log2_slots;
+    Q.r = c.tag_bits;
+    Q.p = Q.q + Q.r;
+    Q.N = 1ull << Q.q;
+    Q.S = tail_slots(Q.q);
+    Q.nslots = Q.N + Q.S;
+    Q.nblk = Q.nslots / 64;
+    Q.ntiles = (Q.nblk + TBLK - 1) / TBLK;
+    Q.H.p = Q.p;
+    Q.H.s = (Q.p + 1) / 2;
+    Q.H.mask = Q.p >= 64 ? ~0ull : ((1ull << Q.p) - 1ull);
+    Q.H.seed = c.hash_seed & Q.H.mask;
+    const uint64_t M = c.max_batch ? c.max_batch : 1;
+    if (M >= 0xffffffffull) return FILTER_ERR_ARG;
+    const uint64_t metaB = Q.nblk * 32, remB = Q.nslots * (Q.r / 8);
+    table_bytes = 2 * (metaB + remB);
+    scratch_bytes = 0;
+    auto add = [&](uint64_t bytes) { scratch_bytes += (bytes + 255) & ~255ull; };
+    for (int k = 0; k < 4; k++) add(M * 8);  // fp_a, fp_b, fp_c, ufp
+    for (int k = 0; k < 3; k++) add(M * 4);  // idx_a, idx_b, idx_c
+    add((M + 1) * 4);                        // ustart
+    add((M + 1) * 4);                        // flags
+    add(M * 4);                              // removed
+    add((Q.ntiles * 4 + 2) * 8);             // look-back state
+    add(radix_tmp_words(M) * 4);
+    uint64_t scan_n = radix_tmp_words(M);
+    if (M + 1 > scan_n) scan_n = M + 1;
+    add(scan_tmp_words(scan_n) * 8);
+    if (plan_only) return FILTER_OK;
+    Arena &A = F->arena;
+    for (int b = 0; b < 2; b++) {
+        Q.meta[b] = A.take<uint8_t>(metaB);
+        Q.rem[b] = A.take<uint8_t>(remB);
+    }
+    Q.cur = 0;
+    Q.fp_a = A.take<uint64_t>(M);
+    Q.fp_b = A.take<uint64_t>(M);
+    Q.fp_c = A.take<uint64_t>(M);
+    Q.ufp = A.take<uint64_t>(M);
+    Q.idx_a = A.take<uint32_t>(M);
+    Q.idx_b = A.take<uint32_t>(M);
+    Q.idx_c = A.take<uint32_t>(M);
+    Q.ustart = A.take<uint32_t>(M + 1);
+    Q.flags = A.take<uint32_t>(M + 1);
+    Q.removed = A.take<uint32_t>(M);
+    Q.tile_state = A.take<unsigned long long>(Q.ntiles * 4 + 2);
+    Q.radix_tmp = A.take<uint32_t>(radix_tmp_words(M));
+    F->scan_tmp = A.take<uint64_t>(scan_tmp_words(scan_n));
+    return FILTER_OK;
+}
+
+int gqf_clear(filter *F, cudaStream_t st)
+{
+    GqfState &Q = F->gqf;
+    for (int b = 0; b < 2; b++) {
+        GF_CUDA(cudaMemsetAsync(Q.meta[b], 0, Q.nblk * 32, st));
+        GF_CUDA(cudaMemsetAsync(Q.rem[b], 0, Q.nslots * (Q.r / 8), st));
+    }
+    Q.cur = 0;
+    GF_CUDA(cudaMemsetAsync(F->ctr, 0, sizeof(DevCounters), st));
+    return FILTER_OK;
+}
+
+// sort + reduce: leaves groups in ufp / ustart, group count in flags[n]
+static void gqf_prepare(filter *F, const uint64_t *keys, uint64_t n, bool need_idx, cudaStream_t st,
+                        uint32_t **sorted_idx)
+{
+    GqfState &Q = F->gqf;
+    const int g = grid_for(n, 256, 8);
+    {
+        gf::TraceScope ts_("gqf_fp_kernel", n, st);
+        gqf_fp_kernel<<<g, 256, 0, st>>>(keys, n, Q.H, Q.fp_a, need_idx ? Q.idx_a : nullptr);
+    }
+    radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp,
+                   F->scan_tmp, F->ctr, st);
+    {
+        gf::TraceScope ts_("gqf_flags", n + 1, st);
+        gqf_flags<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(Q.fp_b, n, Q.flags);
+    }
+    exclusive_scan_u32(Q.flags, Q.flags, n + 1, F->scan_tmp, F->ctr, st);
+    {
+        gf::TraceScope ts_("gqf_compact", n, st);
+        gqf_compact<<<g, 256, 0, st>>>(Q.fp_b, n, Q.flags, Q.ufp, Q.ustart);
+    }
+    *sorted_idx = Q.idx_b;
+}
+
+static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, cudaStream_t st)
+{
+    GqfState &Q = F->gqf;
+    const int nb = Q.cur ^ 1;
+    MergeArgs a;
+    a.meta_old = reinterpret_cast<const Meta *>(Q.meta[Q.cur]);
+    a.rem_old = Q.rem[Q.cur];
+    a.meta_new = reinterpret_cast<Meta *>(Q.meta[nb]);
+    a.rem_new = Q.rem[nb];
+    a.ufp = Q.ufp;
+    a.ustart = Q.ustart;
+    a.pm = Q.flags + n;
+    a.m_limit = m_limit;
+    a.removed = del ? Q.removed : nullptr;
+    a.ts = Q.tile_state;
+    a.ctr = F->ctr;
+    a.N = Q.N;
+    a.nslots = Q.nslots;
+    a.nblk = Q.nblk;
+    a.ntiles = Q.ntiles;
+    a.r = Q.r;
+    a.del = del;
+    a.dry = dry;
+    GF_CUDA(cudaMemsetAsync(Q.tile_state, 0, (Q.ntiles * 4 + 2) * 8, st));
+    GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
+    GF_CUDA(cudaMemsetAsync(&F->ctr->gqf_end, 0xff, 8, st));  // -1
+    if (!dry) GF_CUDA(cudaMemsetAsync(Q.meta[nb], 0, Q.nblk * 32, st));
+    {
+        gf::TraceScope ts_("gqf_merge_kernel", Q.nslots, st);
+        if (Q.r == 8) gqf_merge_kernel<8><<<(unsigned)Q.ntiles, MT, 0, st>>>(a);
+        else gqf_merge_kernel<16><<<(unsigned)Q.ntiles, MT, 0, st>>>(a);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+template <class T>
+static int read_dev(const T *d, T *h, cudaStream_t st)
+{
+    GF_CUDA(cudaMemcpyAsync(h, d, sizeof(T), cudaMemcpyDeviceToHost, st));
+    GF_CUDA(cudaStreamSynchronize(st));
+    return FILTER_OK;
+}
+
+int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = F->gqf;
+    uint32_t *sidx = nullptr;
+    gqf_prepare(F, keys, n, status != nullptr, st, &sidx);
+    int rc = gqf_merge(F, n, ~0ull, 0, 0, st);
+    if (rc) return rc;
+    unsigned long long ovf = 0;
+    if ((rc = read_dev(&F->ctr->overflow, &ovf, st))) return rc;
+    uint64_t m_keep = ~0ull;
+    if (ovf) {
+        // keep the longest prefix of the sorted groups that fits (dry runs)
+        uint32_t m = 0;
+        if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
+        uint64_t lo = 0, hi = m;  // lo fits, hi does not
+        while (hi - lo > 1) {
+            uint64_t mid = (lo + hi) / 2;
+            if ((rc = gqf_merge(F, n, mid, 0, 1, st))) return rc;
+            unsigned long long o2 = 0;
+            if ((rc = read_dev(&F->ctr->overflow, &o2, st))) return rc;
+            if (o2) hi = mid;
+            else lo = mid;
+        }
+        m_keep = lo;
+        if ((rc = gqf_merge(F, n, m_keep, 0, 0, st))) return rc;
+        {
+            gf::TraceScope ts_("gqf_account_full", 1, st);
+            gqf_account_full<<<1, 1, 0, st>>>(F->ctr, Q.ustart, m_keep, n);
+        }
+        GF_CUDA(cudaGetLastError());
+    }
+    Q.cur ^= 1;
+    if (status) {
+        {
+            gf::TraceScope ts_("gqf_status_kernel", n, st);
+            gqf_status_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(n, Q.flags, Q.ustart, sidx, Q.removed, m_keep, 0,
+                                                                  status);
+        }
+        GF_CUDA(cudaGetLastError());
+    }
+    return FILTER_OK;
+}
+
+int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = F->gqf;
+    uint32_t *sidx = nullptr;
+    gqf_prepare(F, keys, n, status != nullptr, st, &sidx);
+    int rc = gqf_merge(F, n, ~0ull, 1, 0, st);
+    if (rc) return rc;
+    Q.cur ^= 1;
+    if (status) {
+        {
+            gf::TraceScope ts_("gqf_status_kernel", n, st);
+            gqf_status_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(n, Q.flags, Q.ustart, sidx, Q.removed, 0, 1, status);
+        }
+        GF_CUDA(cudaGetLastError());
+    }
+    return FILTER_OK;
+}
+
+int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uint8_t *found, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = F->gqf;
+    const int g = grid_for(n, 256, 16);
+    const Meta *meta = reinterpret_cast<const Meta *>(Q.meta[Q.cur]);
+    {
+        gf::TraceScope ts_("gqf_count_kernel", n, st);
+        if (Q.r == 8) gqf_count_kernel<8><<<g, 256, 0, st>>>(keys, n, Q.H, meta, Q.rem[Q.cur], Q.nblk, counts, found);
+        else gqf_count_kernel<16><<<g, 256, 0, st>>>(keys, n, Q.H, meta, Q.rem[Q.cur], Q.nblk, counts, found);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+uint64_t gqf_image_bytes(const filter *F) { return F->gqf.nblk * 32 + F->gqf.nslots * (F->gqf.r / 8); }
+
+int gqf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st)
+{
+    GqfState &Q = F->gqf;
+    char *h = static_cast<char *>(host);
+    const uint64_t metaB = Q.nblk * 32, remB = Q.nslots * (Q.r / 8);
+    if (to_host) {
+        GF_CUDA(cudaMemcpyAsync(h, Q.meta[Q.cur], metaB, cudaMemcpyDeviceToHost, st));
+        GF_CUDA(cudaMemcpyAsync(h + metaB, Q.rem[Q.cur], remB, cudaMemcpyDeviceToHost, st));
+    } else {
+        GF_CUDA(cudaMemcpyAsync(Q.meta[Q.cur], h, metaB, cudaMemcpyHostToDevice, st));
+        GF_CUDA(cudaMemcpyAsync(Q.rem[Q.cur], h + metaB, remB, cudaMemcpyHostToDevice, st));
+    }
+    GF_CUDA(cudaStreamSynchronize(st));
+    return FILTER_OK;
+}
+
+}  // namespace gf

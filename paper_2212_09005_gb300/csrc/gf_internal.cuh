@@ -1,0 +1,256 @@
+// Internal declarations shared by the gpufilter CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gpufilter.h"
+
+namespace gf {
+
+// ---------------------------------------------------------------------------
+// Error plumbing
+// ---------------------------------------------------------------------------
+#define GF_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) {                        \
+            gf::set_last_cuda_error(e_, #call, __LINE__); \
+            return FILTER_ERR_CUDA;                     \
+        }                                               \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char *what, int line);
+
+// Device status word bits (sticky, atomically OR-ed by kernels).
+static constexpr unsigned long long ST_FULL = 1ull << FILTER_ERR_FULL;
+static constexpr unsigned long long ST_TIMEOUT = 1ull << FILTER_ERR_TIMEOUT;
+static constexpr unsigned long long ST_INTERNAL = 1ull << FILTER_ERR_INTERNAL;
+
+// Iteration cap for every spin-wait in the library's kernels. A wait that
+// reaches it records ST_TIMEOUT and returns; it never traps.
+static constexpr uint32_t SPIN_LIMIT = 1u << 24;
+
+// Shared device counters of one filter: [0] status word, [1] failed keys,
+// [2..] per-call scratch counters.
+struct DevCounters {
+    unsigned long long status;
+    unsigned long long failed;
+    unsigned long long backing;
+    unsigned long long overflow;  // GQF merge: 1 if a run would pass the tail
+    unsigned int pend[8];         // TCF: pending-list lengths per phase
+    unsigned int tile_ctr[4];     // dynamic tile counters
+    long long gqf_end;            // GQF merge: end of the last run (dry runs)
+    unsigned long long pad[5];
+};
+
+// ---------------------------------------------------------------------------
+// Hashing (paper Sec. 5.1 fingerprint h; Sec. 4 block/tag hash). Bijective:
+// xor-shifts by s >= p/2 and products with odd constants mod 2^p.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x)
+{
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+struct PHash {
+    uint64_t mask;  // 2^p - 1
+    uint64_t seed;  // seed mod 2^p
+    uint32_t p, s;  // width and shift ceil(p/2)
+};
+
+__host__ __device__ __forceinline__ uint64_t fold_p(uint64_t x, const PHash &H)
+{
+    if (H.p >= 64) return x;
+    uint64_t r = 0;
+    while (x) {
+        r ^= x & H.mask;
+        x >>= H.p;
+    }
+    return r;
+}
+
+__host__ __device__ __forceinline__ uint64_t fingerprint(uint64_t key, const PHash &H)
+{
+    uint64_t x = fold_p(key, H) ^ H.seed;
+    x ^= x >> H.s;
+    x = (x * 0xff51afd7ed558ccdull) & H.mask;
+    x ^= x >> H.s;
+    x = (x * 0xc4ceb9fe1a85ec53ull) & H.mask;
+    x ^= x >> H.s;
+    return x;
+}
+
+struct TcfGeom {
+    uint64_t nb;      // blocks (power of two)
+    uint64_t nbk;     // backing buckets
+    uint64_t seed;
+    uint32_t f, B;    // tag bits, tags per 32-byte block
+    uint32_t tsc;     // shortcut threshold 3B/4
+    uint32_t tmask;
+};
+
+struct KeyInfo {
+    uint64_t b1, b2;
+    uint32_t t;
+};
+
+__host__ __device__ __forceinline__ uint64_t tcf_g(uint32_t t, uint64_t nb)
+{
+    uint64_t g = mix64((uint64_t)t) & (nb - 1);
+    return g ? g : 1;
+}
+
+__host__ __device__ __forceinline__ KeyInfo tcf_keyinfo(uint64_t key, const TcfGeom &G)
+{
+    KeyInfo k;
+    uint64_t h = mix64(key ^ G.seed);
+    uint32_t t = (uint32_t)((h >> 44) & G.tmask);
+    if (t < 2) t += 2;
+    k.t = t;
+    k.b1 = h & (G.nb - 1);
+    k.b2 = k.b1 ^ tcf_g(t, G.nb);
+    return k;
+}
+
+__host__ __device__ __forceinline__ uint64_t tcf_entry(const KeyInfo &k, uint32_t f)
+{
+    uint64_t lo = k.b1 < k.b2 ? k.b1 : k.b2;
+    return (lo << f) | k.t;
+}
+
+__host__ __device__ __forceinline__ uint64_t tcf_bucket(uint64_t e, uint64_t nbk)
+{
+    return ((mix64(e) >> 32) * nbk) >> 32;
+}
+
+// ---------------------------------------------------------------------------
+// Scratch arena: one cudaMalloc per filter, carved into aligned pieces.
+// ---------------------------------------------------------------------------
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0, used = 0;
+    template <class T>
+    T *take(size_t count)
+    {
+        size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Generic device primitives (gf_prims.cu)
+// ---------------------------------------------------------------------------
+// In-place-safe exclusive scan of n uint32 (out may equal in). Needs
+// scan_tmp_words(n) words of temporary state. Values must sum below 2^32.
+size_t scan_tmp_words(uint64_t n);
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint64_t *tmp,
+                        DevCounters *ctr, cudaStream_t st);
+
+// LSD radix sort of 64-bit keys on bits [0, bits), optional 32-bit values.
+// Result lands in keys_out / vals_out. `tmp` holds radix_tmp_words(n) words.
+size_t radix_tmp_words(uint64_t n);
+void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
+                    const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt,
+                    uint64_t n, uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp,
+                    DevCounters *ctr, cudaStream_t st);
+
+// Kernel tracing: a TraceScope around a launch records CUDA events before and
+// after it when tracing is on.
+extern bool g_trace_on;
+int trace_open(const char *name, uint64_t units, cudaStream_t st);
+void trace_close(int slot, cudaStream_t st);
+struct TraceScope {
+    int slot;
+    cudaStream_t st;
+    TraceScope(const char *name, uint64_t units, cudaStream_t s) : slot(-1), st(s)
+    {
+        if (g_trace_on) slot = trace_open(name, units, s);
+    }
+    ~TraceScope()
+    {
+        if (slot >= 0) trace_close(slot, st);
+    }
+};
+
+// grid size helper: a multiple of the SM count
+int grid_for(uint64_t work, int threads, int per_sm = 8);
+int sm_count();
+
+}  // namespace gf
+
+// ---------------------------------------------------------------------------
+// The filter object
+// ---------------------------------------------------------------------------
+struct TcfState {
+    gf::TcfGeom G;
+    uint32_t mode;
+    uint8_t *blocks;   // nb * 32
+    uint64_t *bk;      // nbk * 8
+    uint8_t *fill;     // nb (bulk mode)
+    // scratch
+    uint32_t *cnt;     // max(nb, nbk) + 1, kept zero between phases
+    uint32_t *off;     // max(nb, nbk) + 1
+    uint64_t *rec;     // max_batch
+    uint64_t *rec2;    // max_batch
+    uint32_t *pend0;   // max_batch
+    uint64_t *pend1;   // max_batch
+    uint32_t *pend2;   // max_batch
+};
+
+struct GqfState {
+    uint32_t q, r, p;
+    uint64_t N, S, nslots, nblk, ntiles;
+    gf::PHash H;
+    uint8_t *meta[2];  // nblk * 32
+    uint8_t *rem[2];   // nslots * r/8
+    int cur;           // which buffer holds the table
+    // scratch
+    uint64_t *fp_a, *fp_b, *fp_c;  // max_batch
+    uint32_t *idx_a, *idx_b, *idx_c;
+    uint64_t *ufp;     // unique fingerprints
+    uint32_t *ucnt;    // group sizes
+    uint32_t *ustart;  // group start in the sorted batch (+1 sentinel)
+    uint32_t *flags;   // max_batch + 1
+    uint32_t *removed; // per group: copies removed (delete) / accepted flag
+    unsigned long long *tile_state;  // ntiles * 4 (look-back)
+    uint32_t *radix_tmp;
+};
+
+struct filter {
+    filter_config cfg;
+    gf::Arena arena;
+    void *table_mem = nullptr;
+    size_t table_bytes_alloc = 0;
+    gf::DevCounters *ctr = nullptr;
+    uint64_t *scan_tmp = nullptr;
+    TcfState tcf;
+    GqfState gqf;
+    int device = 0;
+};
+
+namespace gf {
+int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);
+int tcf_clear(filter *F, cudaStream_t st);
+int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
+int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, cudaStream_t st);
+int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
+uint64_t tcf_image_bytes(const filter *F);
+int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st);
+
+int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);
+int gqf_clear(filter *F, cudaStream_t st);
+int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
+int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
+int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uint8_t *found,
+              cudaStream_t st);
+uint64_t gqf_image_bytes(const filter *F);
+int gqf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st);
+}  // namespace gf

@@ -1,0 +1,439 @@
+// Generic device primitives: exclusive scan (single pass, decoupled
+// look-back) and LSD radix sort of 64-bit keys with optional 32-bit values.
+// The GQF sorts fingerprints before inserting them (paper Sec. 5.4, "Sorting
+// hashes"); the TCF groups batches by block with the scan.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "gf_internal.cuh"
+
+namespace gf {
+
+static int g_sm_count = 0;
+
+int sm_count()
+{
+    if (g_sm_count == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            g_sm_count <= 0)
+            g_sm_count = 152;
+    }
+    return g_sm_count;
+}
+
+int grid_for(uint64_t work, int threads, int per_sm)
+{
+    uint64_t want = (work + threads - 1) / threads;
+    uint64_t cap = (uint64_t)sm_count() * per_sm;
+    if (want > cap) want = cap;
+    if (want < 1) want = 1;
+    return (int)want;
+}
+
+// ---------------------------------------------------------------------------
+// Exclusive scan. Tiles of SCAN_T threads x SCAN_I items; tile order taken
+// from an atomic counter so that every tile's predecessors are running or
+// done. State word per tile: (flag << 32) | value, flag 1 = tile aggregate,
+// 2 = inclusive prefix.
+// ---------------------------------------------------------------------------
+static constexpr int SCAN_T = 256;
+static constexpr int SCAN_I = 16;
+static constexpr uint64_t SCAN_TILE = SCAN_T * SCAN_I;
+
+size_t scan_tmp_words(uint64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p)
+{
+    return *(const volatile unsigned long long *)p;
+}
+
+__global__ void __launch_bounds__(SCAN_T) scan_kernel(const uint32_t *in, uint32_t *out, uint64_t n,
+                                                      unsigned long long *tmp,
+                                                      unsigned long long *status)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_warp[SCAN_T / 32];
+    __shared__ uint32_t s_prefix;
+    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&tmp[0], 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    unsigned long long *st = tmp + 1;
+    const uint64_t base = tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_I;
+    uint32_t v[SCAN_I];
+    if (base + SCAN_I <= n) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(in + base);
+#pragma unroll
+        for (int k = 0; k < SCAN_I / 4; k++) {
+            uint4 q = p[k];
+            v[4 * k] = q.x;
+            v[4 * k + 1] = q.y;
+            v[4 * k + 2] = q.z;
+            v[4 * k + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_I; k++) v[k] = (base + k < n) ? in[base + k] : 0u;
+    }
+    uint32_t sum = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_I; k++) {
+        uint32_t x = v[k];
+        v[k] = sum;
+        sum += x;
+    }
+    // block-wide exclusive scan of the thread sums
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < SCAN_T / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < SCAN_T / 32) s_warp[lane] = wi - w;
+        if (lane == SCAN_T / 32 - 1) {
+            // lane 7 holds the tile total; look back
+            uint32_t total = wi;
+            uint32_t prefix = 0;
+            if (tile == 0) {
+                atomicExch(&st[0], (2ull << 32) | total);
+            } else {
+                atomicExch(&st[tile], (1ull << 32) | total);
+                int64_t j = (int64_t)tile - 1;
+                uint32_t spins = 0;
+                while (j >= 0) {
+                    unsigned long long w2 = ld_volatile(&st[j]);
+                    uint32_t flag = (uint32_t)(w2 >> 32);
+                    if (flag == 0) {
+                        if (++spins > SPIN_LIMIT) {
+                            atomicOr(status, ST_TIMEOUT);
+                            break;
+                        }
+                        continue;
+                    }
+                    prefix += (uint32_t)w2;
+                    if (flag == 2) break;
+                    j--;
+                }
+                atomicExch(&st[tile], (2ull << 32) | (uint32_t)(prefix + total));
+            }
+            s_prefix = prefix;
+        }
+    }
+    __syncthreads();
+    const uint32_t add = s_prefix + s_warp[warp] + (incl - sum);
+    if (base + SCAN_I <= n) {
+        uint4 *p = reinterpret_cast<uint4 *>(out + base);
+#pragma unroll
+        for (int k = 0; k < SCAN_I / 4; k++)
+            p[k] = make_uint4(v[4 * k] + add, v[4 * k + 1] + add, v[4 * k + 2] + add, v[4 * k + 3] + add);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_I; k++)
+            if (base + k < n) out[base + k] = v[k] + add;
+    }
+}
+
+void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint64_t *tmp,
+                        DevCounters *ctr, cudaStream_t st)
+{
+    if (n == 0) return;
+    uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    cudaMemsetAsync(tmp, 0, (tiles + 1) * sizeof(uint64_t), st);
+    TraceScope ts_("scan_kernel", n, st);
+    scan_kernel<<<(unsigned)tiles, SCAN_T, 0, st>>>(in, out, n, (unsigned long long *)tmp,
+                                                   &ctr->status);
+}
+
+// ---------------------------------------------------------------------------
+// LSD radix sort, 8-bit digits. Per pass: per-tile digit histograms, one
+// exclusive scan over the digit-major count matrix, then a stable scatter that
+// ranks each tile's keys with warp match and stages them in shared memory so
+// that the global writes are runs of consecutive addresses.
+// ---------------------------------------------------------------------------
+static constexpr int RS_T = 256;
+static constexpr int RS_I = 16;
+static constexpr int RS_TILE = RS_T * RS_I;
+static constexpr int RS_WARPS = RS_T / 32;
+
+size_t radix_tmp_words(uint64_t n)
+{
+    uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+    return tiles * 256 + 1;
+}
+
+__global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *keys, uint64_t n, uint32_t shift,
+                                                uint32_t *counts, uint64_t ntiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+#pragma unroll 4
+    for (int k = 0; k < RS_I; k++) {
+        uint64_t i = base + (uint64_t)k * RS_T + threadIdx.x;
+        uint32_t d = (i < n) ? ((uint32_t)(keys[i] >> shift) & 255u) : 256u;
+        // aggregate equal digits within the warp first (skewed inputs)
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int leader = __ffs(peers) - 1;
+        if (d < 256u && (int)(threadIdx.x & 31) == leader) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    counts[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+template <bool VALS>
+__global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ kin,
+                                                   uint64_t *__restrict__ kout,
+                                                   const uint32_t *__restrict__ vin,
+                                                   uint32_t *__restrict__ vout, uint64_t n,
+                                                   uint32_t shift, const uint32_t *__restrict__ offs,
+                                                   uint64_t ntiles)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem);              // [8][256]
+    uint32_t *dstart = wcnt + RS_WARPS * 256;                          // [256]
+    uint32_t *dglob = dstart + 256;                                    // [256]
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(dglob + 256);       // [4096]
+    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + RS_TILE);   // [4096]
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_T) wcnt[i] = 0;
+    __syncthreads();
+
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+    const unsigned lt = (1u << lane) - 1u;
+    uint64_t key[RS_I];
+    uint32_t val[RS_I];
+    uint16_t rank[RS_I];
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
+        bool ok = i < n;
+        key[r] = ok ? kin[i] : 0;
+        if (VALS) val[r] = ok ? vin[i] : 0;
+        uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t b = (d < 256) ? wcnt[warp * 256 + d] : 0;
+        __syncwarp();
+        if (d < 256 && lane == __ffs(peers) - 1) wcnt[warp * 256 + d] = b + __popc(peers);
+        __syncwarp();
+        rank[r] = (uint16_t)(b + __popc(peers & lt));
+    }
+    __syncthreads();
+    {
+        // per digit: warp-exclusive offsets and the tile total
+        const int d = threadIdx.x;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) {
+            uint32_t c = wcnt[w * 256 + d];
+            wcnt[w * 256 + d] = acc;
+            acc += c;
+        }
+        // exclusive scan of the totals across digits (256 threads)
+        uint32_t incl = acc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __shared__ uint32_t s_w[RS_WARPS];
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        uint32_t wpre = 0;
+        for (int w = 0; w < warp; w++) wpre += s_w[w];
+        dstart[d] = wpre + incl - acc;
+        dglob[d] = offs[(uint64_t)d * ntiles + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
+        if (i < n) {
+            uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
+            uint32_t pos = dstart[d] + wcnt[warp * 256 + d] + rank[r];
+            skeys[pos] = key[r];
+            if (VALS) svals[pos] = val[r];
+        }
+    }
+    __syncthreads();
+    const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)RS_TILE ? (n - base) : RS_TILE);
+    for (uint32_t k = threadIdx.x; k < cnt; k += RS_T) {
+        uint64_t kk = skeys[k];
+        uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        uint64_t g = (uint64_t)dglob[d] + (k - dstart[d]);
+        kout[g] = kk;
+        if (VALS) vout[g] = svals[k];
+    }
+}
+
+static constexpr size_t RS_SMEM = (RS_WARPS * 256 + 512) * 4 + RS_TILE * 8 + RS_TILE * 4;
+
+void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
+                    const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt, uint64_t n,
+                    uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp, DevCounters *ctr,
+                    cudaStream_t st)
+{
+    if (n == 0) return;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
+        cudaFuncSetAttribute(rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
+        attr_done = true;
+    }
+    const bool vals = vals_in != nullptr;
+    uint32_t npass = (bits + 7) / 8;
+    if (npass == 0) {
+        cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st);
+        if (vals) cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, st);
+        return;
+    }
+    const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    const uint64_t *ksrc = keys_in;
+    const uint32_t *vsrc = vals_in;
+    for (uint32_t p = 0; p < npass; p++) {
+        bool to_out = ((npass - 1 - p) % 2) == 0;
+        uint64_t *kdst = to_out ? keys_out : keys_alt;
+        uint32_t *vdst = to_out ? vals_out : vals_alt;
+        uint32_t shift = 8 * p;
+        {
+            TraceScope ts_("rs_hist", n, st);
+            rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, tmp, ntiles);
+        }
+        exclusive_scan_u32(tmp, tmp, ntiles * 256, scan_tmp, ctr, st);
+        TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
+        if (vals)
+            rs_scatter<true><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, vsrc, vdst, n, shift,
+                                                                     tmp, ntiles);
+        else
+            rs_scatter<false><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, nullptr, nullptr, n,
+                                                                      shift, tmp, ntiles);
+        ksrc = kdst;
+        vsrc = vdst;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Kernel tracing
+// ---------------------------------------------------------------------------
+bool g_trace_on = false;
+
+struct TraceRec {
+    const char *name;
+    uint64_t units;
+    cudaEvent_t a, b;
+};
+static std::vector<TraceRec> g_trace;
+static std::vector<cudaEvent_t> g_event_pool;
+static std::mutex g_trace_mu;
+
+static cudaEvent_t pool_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+int trace_open(const char *name, uint64_t units, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    if (g_trace.size() >= (1u << 20)) return -1;
+    TraceRec r{name, units, pool_event(), pool_event()};
+    cudaEventRecord(r.a, st);
+    g_trace.push_back(r);
+    return (int)g_trace.size() - 1;
+}
+
+void trace_close(int slot, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    if (slot >= 0 && slot < (int)g_trace.size()) cudaEventRecord(g_trace[slot].b, st);
+}
+
+static void trace_clear_locked()
+{
+    for (auto &r : g_trace) {
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_trace.clear();
+}
+
+static char g_last_err[256];
+
+void set_last_cuda_error(cudaError_t e, const char *what, int line)
+{
+    snprintf(g_last_err, sizeof(g_last_err), "%s (line %d): %s", what, line, cudaGetErrorString(e));
+}
+
+const char *last_cuda_error() { return g_last_err[0] ? g_last_err : "CUDA runtime error"; }
+
+}  // namespace gf
+
+extern "C" {
+
+int filter_trace_enable(int on)
+{
+    gf::g_trace_on = on != 0;
+    return FILTER_OK;
+}
+
+int filter_trace_reset(void)
+{
+    std::lock_guard<std::mutex> g(gf::g_trace_mu);
+    for (auto &r : gf::g_trace) cudaEventSynchronize(r.b);
+    gf::trace_clear_locked();
+    return FILTER_OK;
+}
+
+int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kernels)
+{
+    std::lock_guard<std::mutex> g(gf::g_trace_mu);
+    std::vector<filter_trace_entry> acc;
+    for (auto &r : gf::g_trace) {
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return FILTER_ERR_CUDA;
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return FILTER_ERR_CUDA;
+        filter_trace_entry *e = nullptr;
+        for (auto &x : acc)
+            if (std::strncmp(x.name, r.name, sizeof(x.name)) == 0) e = &x;
+        if (!e) {
+            filter_trace_entry z;
+            std::memset(&z, 0, sizeof(z));
+            std::strncpy(z.name, r.name, sizeof(z.name) - 1);
+            acc.push_back(z);
+            e = &acc.back();
+        }
+        e->launches++;
+        e->units += r.units;
+        e->ms += ms;
+    }
+    if (n_kernels) *n_kernels = (uint32_t)acc.size();
+    for (uint32_t i = 0; i < cap && i < acc.size(); i++) out[i] = acc[i];
+    return FILTER_OK;
+}
+
+}  // extern "C"
+
+namespace gf {
+
+}  // namespace gf

@@ -1,0 +1,911 @@
+// Two-choice filter (TCF), paper Sec. 4, for sm_103a.
+//
+// Table: nb blocks of 32 bytes (one DRAM sector), B = 256 / f tags each, plus a
+// backing table of nbk buckets of 8 uint64 entries (Sec. 4.2 "Backing table").
+//
+// Query (Sec. 4): probe both candidate blocks with two 16-byte loads each and a
+// SIMD compare (__vcmpeq2 / __vcmpeq4), then the backing bucket (L2-resident)
+// if the tag was in neither block.
+//
+// Bulk insert, deterministic mode (Sec. 4.2 shortcut + Sec. 4 two choices +
+// Sec. 4.2 backing table + Sec. 4.3 sorted blocks). Each phase groups its
+// candidates by destination block with a counting sort (histogram in a
+// per-block counter array, exclusive scan, scatter), then one thread per
+// block takes the k smallest (tag, batch index) candidates that fit, merges
+// them into its sorted block, and emits the rest to the next phase:
+//   A shortcut into b1 while fill + j < 3B/4, B the less-full block under the
+//   post-A fills, C the other block, D the backing bucket.
+// Blocks keep a fill byte array beside them so that the two-choice decision
+// reads 1 byte from L2 instead of a 32-byte sector from HBM.
+//
+// Point mode (Alg. 1): one thread per key; the tag goes into the first EMPTY
+// or TOMBSTONE slot by an atomic compare-and-swap, retried a bounded number of
+// times; deletes swap the tag for TOMBSTONE.
+#include "gf_internal.cuh"
+
+namespace gf {
+
+static constexpr int TPB = 256;
+static constexpr uint32_t BK_W = 8;  // backing bucket entries
+static constexpr int MAXSEL = 32;    // largest B
+
+// ---------------------------------------------------------------------------
+// 32-byte block in registers
+// ---------------------------------------------------------------------------
+template <int F>
+struct Blk {
+    static constexpr int B = 256 / F;
+    uint32_t w[8];
+
+    __device__ __forceinline__ void load(const uint8_t *blocks, uint64_t b)
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
+        uint4 lo = p[0], hi = p[1];
+        w[0] = lo.x; w[1] = lo.y; w[2] = lo.z; w[3] = lo.w;
+        w[4] = hi.x; w[5] = hi.y; w[6] = hi.z; w[7] = hi.w;
+    }
+    __device__ __forceinline__ void load_ro(const uint8_t *blocks, uint64_t b)
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
+        uint4 lo = __ldg(p), hi = __ldg(p + 1);
+        w[0] = lo.x; w[1] = lo.y; w[2] = lo.z; w[3] = lo.w;
+        w[4] = hi.x; w[5] = hi.y; w[6] = hi.z; w[7] = hi.w;
+    }
+    __device__ __forceinline__ void load_l2(const uint8_t *blocks, uint64_t b)
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
+        uint4 lo = __ldcg(p), hi = __ldcg(p + 1);
+        w[0] = lo.x; w[1] = lo.y; w[2] = lo.z; w[3] = lo.w;
+        w[4] = hi.x; w[5] = hi.y; w[6] = hi.z; w[7] = hi.w;
+    }
+    __device__ __forceinline__ void store(uint8_t *blocks, uint64_t b) const
+    {
+        uint4 *p = reinterpret_cast<uint4 *>(blocks + b * 32);
+        p[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        p[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+    __device__ __forceinline__ uint32_t tag(int s) const
+    {
+        if (F == 16) return (w[s >> 1] >> ((s & 1) * 16)) & 0xffffu;
+        return (w[s >> 2] >> ((s & 3) * 8)) & 0xffu;
+    }
+    __device__ __forceinline__ bool has(uint32_t t) const
+    {
+        uint32_t m = 0;
+        if (F == 16) {
+            uint32_t tt = t | (t << 16);
+#pragma unroll
+            for (int k = 0; k < 8; k++) m |= __vcmpeq2(w[k], tt);
+        } else {
+            uint32_t tt = t * 0x01010101u;
+#pragma unroll
+            for (int k = 0; k < 8; k++) m |= __vcmpeq4(w[k], tt);
+        }
+        return m != 0;
+    }
+    // tags >= 2 (neither EMPTY nor TOMBSTONE)
+    __device__ __forceinline__ int live() const
+    {
+        int c = 0;
+        if (F == 16) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) c += __popc(__vcmpgeu2(w[k], 0x00020002u));
+            return c >> 4;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) c += __popc(__vcmpgeu4(w[k], 0x02020202u));
+            return c >> 3;
+        }
+    }
+    __device__ __forceinline__ int nonzero() const
+    {
+        int c = 0;
+        if (F == 16) {
+#pragma unroll
+            for (int k = 0; k < 8; k++) c += __popc(__vcmpne2(w[k], 0u));
+            return c >> 4;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; k++) c += __popc(__vcmpne4(w[k], 0u));
+            return c >> 3;
+        }
+    }
+    // pack B tags (ascending, zero padded) from an array
+    __device__ __forceinline__ void pack(const uint32_t *t)
+    {
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (F == 16) w[k] = (t[2 * k] & 0xffffu) | (t[2 * k + 1] << 16);
+            else w[k] = (t[4 * k] & 0xffu) | ((t[4 * k + 1] & 0xffu) << 8) | ((t[4 * k + 2] & 0xffu) << 16) |
+                        (t[4 * k + 3] << 24);
+        }
+    }
+};
+
+// keep the `have` smallest values seen so far in a[0..have), ascending, at most k
+__device__ __forceinline__ int topk_push(uint64_t *a, int have, int k, uint64_t v)
+{
+    if (have == k) {
+        if (k == 0 || v >= a[k - 1]) return have;
+        have--;
+    }
+    int j = have;
+    while (j > 0 && a[j - 1] > v) {
+        a[j] = a[j - 1];
+        j--;
+    }
+    a[j] = v;
+    return have + 1;
+}
+
+// ---------------------------------------------------------------------------
+// Query (both modes)
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restrict__ keys, uint64_t n,
+                                                        TcfGeom G, const uint8_t *__restrict__ blocks,
+                                                        const uint64_t *__restrict__ bk,
+                                                        const DevCounters *ctr,
+                                                        uint8_t *__restrict__ out)
+{
+    const bool backing = ctr->backing != 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
+        KeyInfo k = tcf_keyinfo(__ldg(keys + i), G);
+        Blk<F> x, y;
+        x.load_ro(blocks, k.b1);
+        y.load_ro(blocks, k.b2);
+        bool hit = x.has(k.t) || y.has(k.t);
+        if (!hit && backing) {
+            uint64_t e = tcf_entry(k, G.f);
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bk + tcf_bucket(e, G.nbk) * BK_W);
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                ulonglong2 v = __ldg(p + s);
+                hit |= (v.x == e) | (v.y == e);
+            }
+        }
+        out[i] = hit ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Counting-sort grouping kernels
+// ---------------------------------------------------------------------------
+// source of a phase's candidate list
+enum Src : int { SRC_KEYS = 0, SRC_PEND_U32 = 1, SRC_PEND_U64 = 2 };
+// how a candidate picks its destination
+enum Dst : int { DST_B1 = 0, DST_TARGET = 1, DST_ALT = 2, DST_B2 = 3, DST_BUCKET = 4 };
+
+__device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t pend_word, const TcfGeom &G,
+                                            const uint8_t *fill)
+{
+    switch (dst) {
+    case DST_B1: return k.b1;
+    case DST_B2: return k.b2;
+    case DST_TARGET: return fill[k.b1] <= fill[k.b2] ? k.b1 : k.b2;
+    case DST_ALT: return pend_word >> 32;
+    default: return tcf_bucket(tcf_entry(k, G.f), G.nbk);
+    }
+}
+
+template <int SRC, int DST>
+__global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, uint64_t n_keys,
+                                                      const void *pend, const unsigned *npend, TcfGeom G,
+                                                      const uint8_t *fill, uint32_t *cnt)
+{
+    const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
+    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TPB) {
+        uint64_t pw = 0, i = j;
+        if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[j];
+        if (SRC == SRC_PEND_U64) {
+            pw = static_cast<const uint64_t *>(pend)[j];
+            i = pw & 0xffffffffu;
+        }
+        KeyInfo k = tcf_keyinfo(keys[i], G);
+        atomicAdd(&cnt[dest_of(DST, k, pw, G, fill)], 1u);
+    }
+}
+
+// rec = (tag << 32) | batch index, or the backing entry with the index in recI
+template <int SRC, int DST>
+__global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restrict__ keys, uint64_t n_keys,
+                                                         const void *pend, const unsigned *npend, TcfGeom G,
+                                                         const uint8_t *fill, uint32_t *cnt,
+                                                         const uint32_t *__restrict__ off, uint64_t *rec,
+                                                         uint32_t *recI)
+{
+    const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
+    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TPB) {
+        uint64_t pw = 0, i = j;
+        if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[j];
+        if (SRC == SRC_PEND_U64) {
+            pw = static_cast<const uint64_t *>(pend)[j];
+            i = pw & 0xffffffffu;
+        }
+        KeyInfo k = tcf_keyinfo(keys[i], G);
+        uint64_t d = dest_of(DST, k, pw, G, fill);
+        uint32_t pos = off[d] + atomicSub(&cnt[d], 1u) - 1u;
+        if (DST == DST_BUCKET) {
+            rec[pos] = tcf_entry(k, G.f);
+            recI[pos] = (uint32_t)i;
+        } else {
+            rec[pos] = ((uint64_t)k.t << 32) | i;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk insert: per-block acceptance
+// ---------------------------------------------------------------------------
+// phase 0 (A): cap = 3B/4, rejects -> pend_u32; phase 1 (B): cap = B, rejects
+// -> pend_u64 (alt block << 32 | index); phase 2 (C): cap = B, rejects -> pend_u32
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill,
+                                                        const uint32_t *__restrict__ off,
+                                                        const uint64_t *__restrict__ rec, int phase,
+                                                        uint32_t cap, uint32_t *pend32, uint64_t *pend64,
+                                                        unsigned *npend)
+{
+    constexpr int B = Blk<F>::B;
+    for (uint64_t b = blockIdx.x * (uint64_t)TPB + threadIdx.x; b < G.nb; b += (uint64_t)gridDim.x * TPB) {
+        const uint32_t s = off[b], e = off[b + 1];
+        if (s == e) continue;
+        const uint32_t cnt = e - s;
+        const uint32_t f0 = fill[b];
+        const uint32_t k = cap > f0 ? min(cnt, cap - f0) : 0u;
+        uint64_t a[MAXSEL];
+        int have = 0;
+        uint64_t thr = 0;  // records <= thr are accepted
+        if (k > 0) {
+            for (uint32_t j = s; j < e; j++) have = topk_push(a, have, (int)k, rec[j]);
+            thr = a[k - 1];
+            Blk<F> blk;
+            blk.load(blocks, b);
+            uint32_t t_out[B];
+            int ia = 0, ib = 0;
+#pragma unroll
+            for (int p = 0; p < B; p++) {
+                uint32_t ta = (ia < (int)f0) ? blk.tag(ia) : 0xffffffffu;
+                uint32_t tb = (ib < (int)k) ? (uint32_t)(a[ib] >> 32) : 0xffffffffu;
+                if (ta == 0xffffffffu && tb == 0xffffffffu) {
+                    t_out[p] = 0;
+                } else if (ta <= tb) {
+                    t_out[p] = ta;
+                    ia++;
+                } else {
+                    t_out[p] = tb;
+                    ib++;
+                }
+            }
+            blk.pack(t_out);
+            blk.store(blocks, b);
+            fill[b] = (uint8_t)(f0 + k);
+        }
+        if (k == cnt) continue;
+        for (uint32_t j = s; j < e; j++) {
+            uint64_t r = rec[j];
+            if (k > 0 && r <= thr) continue;
+            uint32_t i = (uint32_t)r;
+            unsigned slot = atomicAdd(npend, 1u);
+            if (phase == 1) {
+                uint64_t alt = b ^ tcf_g((uint32_t)(r >> 32), G.nb);
+                pend64[slot] = (alt << 32) | i;
+            } else {
+                pend32[slot] = i;
+            }
+        }
+    }
+}
+
+// backing buckets: candidates (entry in rec, index in recI) taken in (entry,
+// index) order while there is room; the rest are FULL
+__global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk,
+                                                         const uint32_t *__restrict__ off,
+                                                         const uint64_t *__restrict__ rec,
+                                                         const uint32_t *__restrict__ recI, uint8_t *status,
+                                                         DevCounters *ctr)
+{
+    for (uint64_t q = blockIdx.x * (uint64_t)TPB + threadIdx.x; q < G.nbk; q += (uint64_t)gridDim.x * TPB) {
+        const uint32_t s = off[q], e = off[q + 1];
+        if (s == e) continue;
+        uint64_t cur[BK_W];
+        int used = 0;
+        for (int j = 0; j < (int)BK_W; j++) {
+            cur[j] = bk[q * BK_W + j];
+            used += cur[j] != 0;
+        }
+        const uint32_t cnt = e - s;
+        const uint32_t k = min(cnt, BK_W - (uint32_t)used);
+        // select the k smallest (entry, index) pairs by repeated minimum
+        uint64_t pe = 0;
+        uint32_t pi = 0;
+        bool have_prev = false;
+        uint64_t acc_e[BK_W];
+        for (uint32_t m = 0; m < k; m++) {
+            uint64_t be = ~0ull;
+            uint32_t bi = 0xffffffffu;
+            for (uint32_t j = s; j < e; j++) {
+                uint64_t ee = rec[j];
+                uint32_t ii = recI[j];
+                bool after = !have_prev || ee > pe || (ee == pe && ii > pi);
+                bool better = ee < be || (ee == be && ii < bi);
+                if (after && better) {
+                    be = ee;
+                    bi = ii;
+                }
+            }
+            acc_e[m] = be;
+            pe = be;
+            pi = bi;
+            have_prev = true;
+        }
+        // merge accepted (ascending) into the bucket's sorted entries
+        uint64_t outv[BK_W];
+        int ia = 0, ib = 0;
+        for (int p = 0; p < (int)BK_W; p++) {
+            uint64_t va = ia < used ? cur[ia] : ~0ull;
+            uint64_t vb = ib < (int)k ? acc_e[ib] : ~0ull;
+            if (va == ~0ull && vb == ~0ull) outv[p] = 0;
+            else if (va <= vb) { outv[p] = va; ia++; }
+            else { outv[p] = vb; ib++; }
+        }
+        for (int j = 0; j < (int)BK_W; j++) bk[q * BK_W + j] = outv[j];
+        if (k > 0) atomicAdd(&ctr->backing, (unsigned long long)k);
+        if (k < cnt) {
+            // rejected: every pair after the k-th accepted one
+            for (uint32_t j = s; j < e; j++) {
+                uint64_t ee = rec[j];
+                uint32_t ii = recI[j];
+                bool acc = k > 0 && (ee < pe || (ee == pe && ii <= pi));
+                if (!acc) {
+                    if (status) status[ii] = FILTER_KEY_FULL;
+                    atomicAdd(&ctr->failed, 1ull);
+                }
+            }
+            atomicOr(&ctr->status, ST_FULL);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk delete: per-block matching. For each tag present c times in the block,
+// the c smallest (tag, index) candidates with that tag remove one copy each.
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill,
+                                                        const uint32_t *__restrict__ off,
+                                                        const uint64_t *__restrict__ rec, uint32_t *pend32,
+                                                        unsigned *npend)
+{
+    constexpr int B = Blk<F>::B;
+    for (uint64_t b = blockIdx.x * (uint64_t)TPB + threadIdx.x; b < G.nb; b += (uint64_t)gridDim.x * TPB) {
+        const uint32_t s = off[b], e = off[b + 1];
+        if (s == e) continue;
+        const uint32_t f0 = fill[b];
+        Blk<F> blk;
+        blk.load(blocks, b);
+        uint32_t tags[B];
+#pragma unroll
+        for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
+        // per distinct stored tag: threshold record (the c-th smallest with that tag)
+        uint32_t dt[B];
+        uint32_t dc[B];
+        uint64_t thr[B];
+        uint32_t used[B];
+        int nd = 0;
+        for (int p = 0; p < (int)f0; p++) {
+            if (nd > 0 && dt[nd - 1] == tags[p]) {
+                dc[nd - 1]++;
+            } else {
+                dt[nd] = tags[p];
+                dc[nd] = 1;
+                nd++;
+            }
+        }
+        for (int d = 0; d < nd; d++) {
+            uint64_t a[MAXSEL];
+            int have = 0;
+            uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
+            for (uint32_t j = s; j < e; j++) {
+                uint64_t r = rec[j];
+                if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
+            }
+            used[d] = (uint32_t)have;
+            thr[d] = have ? a[have - 1] : 0;
+        }
+        // rebuild the block without the removed copies
+        uint32_t t_out[B];
+        int o = 0, removed = 0;
+        for (int d = 0; d < nd; d++) {
+            for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = dt[d];
+            removed += (int)used[d];
+        }
+        for (int p = o; p < B; p++) t_out[p] = 0;
+        if (removed) {
+            blk.pack(t_out);
+            blk.store(blocks, b);
+            fill[b] = (uint8_t)(f0 - removed);
+        }
+        // unmatched candidates go on
+        for (uint32_t j = s; j < e; j++) {
+            uint64_t r = rec[j];
+            uint32_t t = (uint32_t)(r >> 32);
+            bool matched = false;
+            for (int d = 0; d < nd; d++)
+                if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
+            if (!matched) pend32[atomicAdd(npend, 1u)] = (uint32_t)r;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk,
+                                                         const uint32_t *__restrict__ off,
+                                                         const uint64_t *__restrict__ rec,
+                                                         const uint32_t *__restrict__ recI, uint8_t *status,
+                                                         DevCounters *ctr)
+{
+    for (uint64_t q = blockIdx.x * (uint64_t)TPB + threadIdx.x; q < G.nbk; q += (uint64_t)gridDim.x * TPB) {
+        const uint32_t s = off[q], e = off[q + 1];
+        if (s == e) continue;
+        // distinct stored entries (the bucket is sorted) with their copy counts
+        uint64_t dv[BK_W];
+        uint32_t dc[BK_W], used[BK_W], thr[BK_W];
+        int nd = 0;
+        for (int j = 0; j < (int)BK_W; j++) {
+            uint64_t v = bk[q * BK_W + j];
+            if (!v) continue;
+            if (nd > 0 && dv[nd - 1] == v) {
+                dc[nd - 1]++;
+            } else {
+                dv[nd] = v;
+                dc[nd] = 1;
+                nd++;
+            }
+        }
+        // for each stored entry, the dc smallest candidate indices with that entry match
+        for (int d = 0; d < nd; d++) {
+            uint64_t a[BK_W];
+            int have = 0;
+            for (uint32_t j = s; j < e; j++)
+                if (rec[j] == dv[d]) have = topk_push(a, have, (int)dc[d], (uint64_t)recI[j]);
+            used[d] = (uint32_t)have;
+            thr[d] = have ? (uint32_t)a[have - 1] : 0u;
+        }
+        int removed = 0;
+        uint64_t outv[BK_W];
+        int o = 0;
+        for (int d = 0; d < nd; d++) {
+            removed += (int)used[d];
+            for (uint32_t c = used[d]; c < dc[d]; c++) outv[o++] = dv[d];
+        }
+        for (int j = o; j < (int)BK_W; j++) outv[j] = 0;
+        if (removed) {
+            for (int j = 0; j < (int)BK_W; j++) bk[q * BK_W + j] = outv[j];
+            atomicAdd(&ctr->backing, (unsigned long long)(-(long long)removed));
+        }
+        for (uint32_t j = s; j < e; j++) {
+            uint64_t v = rec[j];
+            uint32_t ii = recI[j];
+            bool matched = false;
+            for (int d = 0; d < nd; d++)
+                if (dv[d] == v && used[d] > 0 && ii <= thr[d]) matched = true;
+            if (!matched && status) status[ii] = FILTER_KEY_NOT_FOUND;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Point mode (Alg. 1)
+// ---------------------------------------------------------------------------
+template <int F>
+__device__ bool point_put(uint8_t *blocks, uint64_t b, uint32_t t, DevCounters *ctr)
+{
+    constexpr int B = Blk<F>::B;
+    for (int attempt = 0; attempt < 4 * B; attempt++) {
+        Blk<F> blk;
+        blk.load_l2(blocks, b);
+        int s = -1;
+#pragma unroll
+        for (int p = 0; p < B; p++)
+            if (s < 0 && blk.tag(p) < 2) s = p;
+        if (s < 0) return false;
+        uint32_t seen = blk.tag(s);
+        if (F == 16) {
+            unsigned short *slot = reinterpret_cast<unsigned short *>(blocks + b * 32) + s;
+            if (atomicCAS(slot, (unsigned short)seen, (unsigned short)t) == (unsigned short)seen) return true;
+        } else {
+            unsigned int *word = reinterpret_cast<unsigned int *>(blocks + b * 32) + (s >> 2);
+            unsigned sh = (s & 3) * 8;
+            unsigned int cur = blk.w[s >> 2];
+            unsigned int want = (cur & ~(0xffu << sh)) | (t << sh);
+            if (atomicCAS(word, cur, want) == cur) return true;
+        }
+    }
+    atomicOr(&ctr->status, ST_TIMEOUT);
+    return false;
+}
+
+template <int F>
+__device__ bool point_take(uint8_t *blocks, uint64_t b, uint32_t t, DevCounters *ctr)
+{
+    constexpr int B = Blk<F>::B;
+    for (int attempt = 0; attempt < 4 * B; attempt++) {
+        Blk<F> blk;
+        blk.load_l2(blocks, b);
+        int s = -1;
+#pragma unroll
+        for (int p = 0; p < B; p++)
+            if (s < 0 && blk.tag(p) == t) s = p;
+        if (s < 0) return false;
+        if (F == 16) {
+            unsigned short *slot = reinterpret_cast<unsigned short *>(blocks + b * 32) + s;
+            if (atomicCAS(slot, (unsigned short)t, (unsigned short)1) == (unsigned short)t) return true;
+        } else {
+            unsigned int *word = reinterpret_cast<unsigned int *>(blocks + b * 32) + (s >> 2);
+            unsigned sh = (s & 3) * 8;
+            unsigned int cur = blk.w[s >> 2];
+            unsigned int want = (cur & ~(0xffu << sh)) | (1u << sh);
+            if (atomicCAS(word, cur, want) == cur) return true;
+        }
+    }
+    atomicOr(&ctr->status, ST_TIMEOUT);
+    return false;
+}
+
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_point_insert(const uint64_t *__restrict__ keys, uint64_t n, TcfGeom G,
+                                                        uint8_t *blocks, uint64_t *bk, uint8_t *status,
+                                                        DevCounters *ctr)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
+        KeyInfo k = tcf_keyinfo(keys[i], G);
+        Blk<F> x;
+        x.load_l2(blocks, k.b1);
+        int f1 = x.live();
+        bool done = false;
+        if (f1 < (int)G.tsc) done = point_put<F>(blocks, k.b1, k.t, ctr);  // shortcut (Sec. 4.2)
+        if (!done) {
+            Blk<F> y;
+            y.load_l2(blocks, k.b2);
+            x.load_l2(blocks, k.b1);
+            uint64_t first = x.live() <= y.live() ? k.b1 : k.b2;
+            done = point_put<F>(blocks, first, k.t, ctr) ||
+                   point_put<F>(blocks, first == k.b1 ? k.b2 : k.b1, k.t, ctr);
+        }
+        if (!done) {
+            uint64_t e = tcf_entry(k, G.f);
+            unsigned long long *p =
+                reinterpret_cast<unsigned long long *>(bk + tcf_bucket(e, G.nbk) * BK_W);
+            for (int s = 0; s < (int)BK_W && !done; s++)
+                if (atomicCAS(p + s, 0ull, (unsigned long long)e) == 0ull) done = true;
+            if (done) atomicAdd(&ctr->backing, 1ull);
+        }
+        if (!done) {
+            if (status) status[i] = FILTER_KEY_FULL;
+            atomicAdd(&ctr->failed, 1ull);
+            atomicOr(&ctr->status, ST_FULL);
+        } else if (status) {
+            status[i] = FILTER_KEY_OK;
+        }
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_point_remove(const uint64_t *__restrict__ keys, uint64_t n, TcfGeom G,
+                                                        uint8_t *blocks, uint64_t *bk, uint8_t *status,
+                                                        DevCounters *ctr)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
+        KeyInfo k = tcf_keyinfo(keys[i], G);
+        bool done = point_take<F>(blocks, k.b1, k.t, ctr) || point_take<F>(blocks, k.b2, k.t, ctr);
+        if (!done) {
+            uint64_t e = tcf_entry(k, G.f);
+            unsigned long long *p =
+                reinterpret_cast<unsigned long long *>(bk + tcf_bucket(e, G.nbk) * BK_W);
+            for (int s = 0; s < (int)BK_W && !done; s++)
+                if (atomicCAS(p + s, (unsigned long long)e, 0ull) == (unsigned long long)e) done = true;
+            if (done) atomicAdd(&ctr->backing, (unsigned long long)-1ll);
+        }
+        if (status) status[i] = done ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;
+    }
+}
+
+// fill bytes and backing count from the table image (after import)
+template <int F>
+__global__ void tcf_refill(TcfGeom G, const uint8_t *blocks, uint8_t *fill)
+{
+    for (uint64_t b = blockIdx.x * (uint64_t)TPB + threadIdx.x; b < G.nb; b += (uint64_t)gridDim.x * TPB) {
+        Blk<F> x;
+        x.load(blocks, b);
+        fill[b] = (uint8_t)x.nonzero();
+    }
+}
+
+__global__ void tcf_count_backing(TcfGeom G, const uint64_t *bk, DevCounters *ctr)
+{
+    unsigned long long c = 0;
+    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < G.nbk * BK_W; j += (uint64_t)gridDim.x * TPB)
+        c += bk[j] != 0;
+    if (c) atomicAdd(&ctr->backing, c);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only)
+{
+    const filter_config &c = F->cfg;
+    if (c.tag_bits != 8 && c.tag_bits != 16) return FILTER_ERR_ARG;
+    if (c.mode != FILTER_MODE_BULK && c.mode != FILTER_MODE_POINT) return FILTER_ERR_ARG;
+    const uint32_t B = 256 / c.tag_bits, lb = (B == 16) ? 4 : 5;
+    if (c.log2_slots < lb + 1 || c.log2_slots > lb + 32) return FILTER_ERR_ARG;
+    TcfState &T = F->tcf;
+    T.mode = c.mode;
+    T.G.f = c.tag_bits;
+    T.G.B = B;
+    T.G.tsc = 3 * B / 4;
+    T.G.tmask = (1u << c.tag_bits) - 1u;
+    T.G.nb = 1ull << (c.log2_slots - lb);
+    T.G.seed = c.hash_seed;
+    const uint64_t N = 1ull << c.log2_slots;
+    uint64_t cap = (N + 99) / 100;
+    T.G.nbk = (cap + BK_W - 1) / BK_W;
+    if (T.G.nbk < 8) T.G.nbk = 8;
+    const uint64_t M = c.max_batch ? c.max_batch : 1;
+    if (M > 0xffffffffull) return FILTER_ERR_ARG;
+    const uint64_t groups = (T.G.nb > T.G.nbk ? T.G.nb : T.G.nbk) + 1;
+    table_bytes = T.G.nb * 32 + T.G.nbk * BK_W * 8 + T.G.nb;
+    scratch_bytes = 0;
+    auto add = [&](uint64_t bytes) { scratch_bytes += (bytes + 255) & ~255ull; };
+    add(groups * 4);
+    add(groups * 4);
+    add(M * 8);
+    add(M * 8);
+    add(M * 4);
+    add(M * 8);
+    add(M * 4);
+    add(scan_tmp_words(groups) * 8);
+    if (plan_only) return FILTER_OK;
+    Arena &A = F->arena;
+    // table memory comes first in the arena
+    T.blocks = A.take<uint8_t>(T.G.nb * 32);
+    T.bk = A.take<uint64_t>(T.G.nbk * BK_W);
+    T.fill = A.take<uint8_t>(T.G.nb);
+    T.cnt = A.take<uint32_t>(groups);
+    T.off = A.take<uint32_t>(groups);
+    T.rec = A.take<uint64_t>(M);
+    T.rec2 = A.take<uint64_t>(M);
+    T.pend0 = A.take<uint32_t>(M);
+    T.pend1 = A.take<uint64_t>(M);
+    T.pend2 = A.take<uint32_t>(M);
+    F->scan_tmp = A.take<uint64_t>(scan_tmp_words(groups));
+    return FILTER_OK;
+}
+
+int tcf_clear(filter *F, cudaStream_t st)
+{
+    TcfState &T = F->tcf;
+    const uint64_t groups = (T.G.nb > T.G.nbk ? T.G.nb : T.G.nbk) + 1;
+    GF_CUDA(cudaMemsetAsync(T.blocks, 0, T.G.nb * 32, st));
+    GF_CUDA(cudaMemsetAsync(T.bk, 0, T.G.nbk * BK_W * 8, st));
+    GF_CUDA(cudaMemsetAsync(T.fill, 0, T.G.nb, st));
+    GF_CUDA(cudaMemsetAsync(T.cnt, 0, groups * 4, st));
+    GF_CUDA(cudaMemsetAsync(F->ctr, 0, sizeof(DevCounters), st));
+    return FILTER_OK;
+}
+
+template <int F>
+static void tcf_bulk_insert(filter *FL, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    TcfState &T = FL->tcf;
+    const TcfGeom G = T.G;
+    DevCounters *ctr = FL->ctr;
+    unsigned *np = ctr->pend;
+    const int gk = grid_for(n, TPB, 8);
+    const int gb = grid_for(G.nb, TPB, 8);
+    const int gq = grid_for(G.nbk, TPB, 8);
+    cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
+    // A: shortcut into b1
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
+                                                                T.rec, nullptr);
+    }
+    {
+        gf::TraceScope ts_("tcf_block_insert", G.nb, st);
+        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 0, G.tsc, T.pend0, nullptr, &np[0]);
+    }
+    // B: the less full of b1, b2 under the post-A fills
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt,
+                                                                        T.off, T.rec, nullptr);
+    }
+    {
+        gf::TraceScope ts_("tcf_block_insert", G.nb, st);
+        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 1, G.B, nullptr, T.pend1, &np[1]);
+    }
+    // C: the other block
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, n, T.pend1, &np[1], G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, n, T.pend1, &np[1], G, T.fill, T.cnt, T.off,
+                                                                     T.rec, nullptr);
+    }
+    {
+        gf::TraceScope ts_("tcf_block_insert", G.nb, st);
+        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 2, G.B, T.pend2, nullptr, &np[2]);
+    }
+    // D: backing buckets
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt,
+                                                                        T.off, T.rec, T.pend0);
+    }
+    {
+        gf::TraceScope ts_("tcf_bucket_insert", G.nbk, st);
+        tcf_bucket_insert<<<gq, TPB, 0, st>>>(G, T.bk, T.off, T.rec, T.pend0, status, ctr);
+    }
+}
+
+template <int F>
+static void tcf_bulk_remove(filter *FL, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    TcfState &T = FL->tcf;
+    const TcfGeom G = T.G;
+    DevCounters *ctr = FL->ctr;
+    unsigned *np = ctr->pend;
+    const int gk = grid_for(n, TPB, 8);
+    const int gb = grid_for(G.nb, TPB, 8);
+    const int gq = grid_for(G.nbk, TPB, 8);
+    cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
+    // 1: primary block
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
+                                                                T.rec, nullptr);
+    }
+    {
+        gf::TraceScope ts_("tcf_block_remove", G.nb, st);
+        tcf_block_remove<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, T.pend0, &np[0]);
+    }
+    // 2: secondary block
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt, T.off,
+                                                                    T.rec, nullptr);
+    }
+    {
+        gf::TraceScope ts_("tcf_block_remove", G.nb, st);
+        tcf_block_remove<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, T.pend2, &np[2]);
+    }
+    // 3: backing bucket; what is left is not found
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt);
+    }
+    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, FL->scan_tmp, ctr, st);
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt,
+                                                                        T.off, T.rec, T.pend0);
+    }
+    {
+        gf::TraceScope ts_("tcf_bucket_remove", G.nbk, st);
+        tcf_bucket_remove<<<gq, TPB, 0, st>>>(G, T.bk, T.off, T.rec, T.pend0, status, ctr);
+    }
+}
+
+int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    if (status) GF_CUDA(cudaMemsetAsync(status, 0, n, st));
+    TcfState &T = F->tcf;
+    if (T.mode == FILTER_MODE_POINT) {
+        const int g = grid_for(n, TPB, 16);
+        {
+            gf::TraceScope ts_("tcf_point_insert", n, st);
+            if (T.G.f == 16) tcf_point_insert<16><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
+            else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
+        }
+    } else {
+        if (T.G.f == 16) tcf_bulk_insert<16>(F, keys, n, status, st);
+        else tcf_bulk_insert<8>(F, keys, n, status, st);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    if (status) GF_CUDA(cudaMemsetAsync(status, 0, n, st));
+    TcfState &T = F->tcf;
+    if (T.mode == FILTER_MODE_POINT) {
+        const int g = grid_for(n, TPB, 16);
+        {
+            gf::TraceScope ts_("tcf_point_remove", n, st);
+            if (T.G.f == 16) tcf_point_remove<16><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
+            else tcf_point_remove<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
+        }
+    } else {
+        if (T.G.f == 16) tcf_bulk_remove<16>(F, keys, n, status, st);
+        else tcf_bulk_remove<8>(F, keys, n, status, st);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    TcfState &T = F->tcf;
+    const int g = grid_for(n, TPB, 16);
+    {
+        gf::TraceScope ts_("tcf_query_kernel", n, st);
+        if (T.G.f == 16) tcf_query_kernel<16><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+        else tcf_query_kernel<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+uint64_t tcf_image_bytes(const filter *F) { return F->tcf.G.nb * 32 + F->tcf.G.nbk * BK_W * 8; }
+
+int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st)
+{
+    TcfState &T = F->tcf;
+    char *h = static_cast<char *>(host);
+    const uint64_t nbB = T.G.nb * 32, bkB = T.G.nbk * BK_W * 8;
+    if (to_host) {
+        GF_CUDA(cudaMemcpyAsync(h, T.blocks, nbB, cudaMemcpyDeviceToHost, st));
+        GF_CUDA(cudaMemcpyAsync(h + nbB, T.bk, bkB, cudaMemcpyDeviceToHost, st));
+    } else {
+        GF_CUDA(cudaMemcpyAsync(T.blocks, h, nbB, cudaMemcpyHostToDevice, st));
+        GF_CUDA(cudaMemcpyAsync(T.bk, h + nbB, bkB, cudaMemcpyHostToDevice, st));
+        const int g = grid_for(T.G.nb, TPB, 8);
+        {
+            gf::TraceScope ts_("tcf_refill", T.G.nb, st);
+            if (T.G.f == 16) tcf_refill<16><<<g, TPB, 0, st>>>(T.G, T.blocks, T.fill);
+            else tcf_refill<8><<<g, TPB, 0, st>>>(T.G, T.blocks, T.fill);
+        }
+        GF_CUDA(cudaMemsetAsync(&F->ctr->backing, 0, 8, st));
+        {
+            gf::TraceScope ts_("tcf_count_backing", T.G.nbk * BK_W, st);
+            tcf_count_backing<<<grid_for(T.G.nbk * BK_W, TPB, 4), TPB, 0, st>>>(T.G, T.bk, F->ctr);
+        }
+    }
+    GF_CUDA(cudaStreamSynchronize(st));
+    return FILTER_OK;
+}
+
+}  // namespace gf

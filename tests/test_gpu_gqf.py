@@ -1,0 +1,193 @@
+"""GPU parity for the GQF (paper Sec. 5): the CUDA library's table image must
+equal the oracle's byte for byte, and counts / answers / statuses must equal
+the oracle's, on seeded inputs (several tiles, ragged tails, duplicates,
+deletes, table overflow) and at the paper-scale configurations."""
+import collections
+
+import numpy as np
+import pytest
+
+from paper_2212_09005_gb300 import workloads as W
+from gpu_util import dev_u64, zeros_u8, zeros_u64, host, first_diff
+from gqf_golden import load, expected_image, group_arrays
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_09005_gb300 as gf
+
+    gf.lib()
+    return gf
+
+
+def run_batches(gf, oracle, q, r, seed, batches, deletes=()):
+    O = oracle.GQF(q, r, seed=seed)
+    G = gf.GQF(q, r, seed=seed, max_batch=max(len(b) for b in list(batches) + list(deletes) + [[0]]))
+    for b in batches:
+        st_o = O.insert(b)
+        st = zeros_u8(len(b))
+        G.insert(dev_u64(b), st)
+        assert np.array_equal(host(st), st_o)
+        d = first_diff(G.export(), O.export())
+        assert d is None, d
+    for b in deletes:
+        st_o = O.remove(b)
+        st = zeros_u8(len(b))
+        G.remove(dev_u64(b), st)
+        assert np.array_equal(host(st), st_o)
+        d = first_diff(G.export(), O.export())
+        assert d is None, d
+    return O, G
+
+
+@pytest.mark.parametrize("q,r", [(8, 8), (11, 8), (13, 8), (10, 16), (14, 16)])
+def test_batches_with_duplicates_image_and_counts(gf, oracle, q, r):
+    base = W.uniform_keys(500 + q, 1 << q)
+    sizes = [1, 7, 300, (1 << q) // 3, (1 << q) // 4]
+    batches, at = [], 0
+    for s in sizes:
+        b = base[at:at + s]
+        at += s
+        batches.append(np.concatenate([b, b[: s // 3], b[:2]]))
+    O, G = run_batches(gf, oracle, q, r, seed=q, batches=batches)
+    probe = np.concatenate([base[:at], W.uniform_keys(900 + q, 5000)])
+    c = zeros_u64(len(probe))
+    G.count(dev_u64(probe), c)
+    assert np.array_equal(host(c), O.count(probe))
+    f = zeros_u8(len(probe))
+    G.query(dev_u64(probe), f)
+    assert np.array_equal(host(f), (O.count(probe) > 0).astype(np.uint8))
+
+
+def test_deletes_status_and_image(gf, oracle):
+    q, r = 12, 8
+    keys = W.uniform_keys(501, 3000)
+    ins = np.concatenate([keys, keys[:500], keys[:500], keys[:7]])
+    absent = W.uniform_keys(502, 100)
+    dels = [
+        np.concatenate([np.repeat(keys[:20], 4), keys[1000:1500], absent]),
+        keys[::3],
+        ins,  # everything, including copies already gone
+    ]
+    O, G = run_batches(gf, oracle, q, r, seed=5, batches=[ins], deletes=dels)
+    assert not G.export().any()
+
+
+def test_worked_example_from_keys(gf, oracle):
+    """The hand-derived golden table, reached through keys whose fingerprints
+    are the example's groups (keys = inverse hash of each fingerprint)."""
+    spec = load("gqf_q7_r8_worked.txt")
+    q, r = spec["q"], spec["r"]
+    p = q + r
+    fps, cnt = group_arrays(spec)
+    keys = []
+    for f, c in zip(fps.tolist(), cnt.tolist()):
+        k = oracle.unmix_p(f, p)  # seed 0: fingerprint = mix_p(key) for key < 2^p
+        keys += [k] * min(c, 5000)
+    # counts above 5000 are reached with a second, repeated batch
+    G = gf.GQF(q, r, seed=0, max_batch=200000)
+    G.insert(dev_u64(np.array(keys, np.uint64)))
+    rest = []
+    for f, c in zip(fps.tolist(), cnt.tolist()):
+        if c > 5000:
+            rest += [oracle.unmix_p(f, p)] * (c - 5000)
+    if rest:
+        G.insert(dev_u64(np.array(rest, np.uint64)))
+    exp = expected_image(spec, 256, 4)
+    d = first_diff(G.export(), exp)
+    assert d is None, d
+
+
+def test_overflow_longest_prefix(gf, oracle):
+    """More keys than slots: the longest sorted prefix of the groups is kept,
+    the other keys get FULL, exactly as in the oracle."""
+    q, r = 7, 8  # 128 + 128 slots
+    keys = W.uniform_keys(503, 300)
+    O = oracle.GQF(q, r, seed=1)
+    G = gf.GQF(q, r, seed=1, max_batch=300)
+    failed = 0
+    for b in (keys[:100], keys[100:]):
+        st_o = O.insert(b)
+        failed += int((st_o == gf.KEY_FULL).sum())
+        st = zeros_u8(len(b))
+        G.insert(dev_u64(b), st)
+        assert np.array_equal(host(st), st_o)
+        d = first_diff(G.export(), O.export())
+        assert d is None, d
+    assert failed > 0
+    s_ = G.stats()
+    assert s_["status_word"] & gf.STATUS_FULL
+    assert s_["failed_keys"] == failed
+
+
+def test_empty_and_single(gf, oracle):
+    G = gf.GQF(6, 8, seed=0, max_batch=16)
+    G.insert(dev_u64(np.zeros(0, np.uint64)))
+    assert not G.export().any()
+    O, G2 = run_batches(gf, oracle, 6, 8, seed=2, batches=[np.array([12345], np.uint64)])
+    c = zeros_u64(1)
+    G2.count(dev_u64(np.array([12345], np.uint64)), c)
+    assert host(c)[0] == 1
+
+
+def test_zipf_small_exact_counts(gf, oracle):
+    q = 16
+    keys = W.zipf_keys(3, 300000, 1.0, 1 << 20)  # universe 2^20 <= 2^p
+    O, G = run_batches(gf, oracle, q, 8, seed=3, batches=[keys[:200000], keys[200000:]])
+    u, c = np.unique(keys, return_counts=True)
+    got = zeros_u64(len(u))
+    G.count(dev_u64(u), got)
+    assert np.array_equal(host(got), c.astype(np.uint64))
+
+
+def test_uniform_config_2_20(gf, oracle):
+    """2^20 slots, 8-bit remainders: one batch of floor(0.9 * 2^20) keys, then
+    queries of those keys and 2^20 fresh keys; image, answers and FPR."""
+    w = W.gqf_uniform_workload(20, seed=1)
+    O, G = run_batches(gf, oracle, 20, 8, seed=1, batches=[w["insert"]])
+    probe = np.concatenate([w["insert"], w["negatives"]])
+    f = zeros_u8(len(probe))
+    G.query(dev_u64(probe), f)
+    got = host(f)
+    assert got[: len(w["insert"])].all()
+    exp = (O.count(probe) > 0).astype(np.uint8)
+    assert np.array_equal(got, exp)
+    d = len(O.groups()[0])
+    eps = d / 2 ** 28
+    fpr = got[len(w["insert"]):].mean()
+    assert abs(fpr - eps) <= 4 * np.sqrt(eps * (1 - eps) / len(w["negatives"]))
+
+
+@pytest.mark.slow
+def test_counting_config_2_28_zipf(gf, oracle):
+    """2^28 slots, 2.4e8 Zipf(1.0) keys over 2^32 in one batch: every sampled
+    count equals the key's true multiplicity (fingerprints are injective, p = 36),
+    and the whole table image equals the canonical builder's."""
+    import torch
+
+    w = W.gqf_zipf_workload()
+    keys = w["insert"]
+    G = gf.GQF(28, 8, seed=3, max_batch=len(keys))
+    st = zeros_u8(len(keys))
+    G.insert(dev_u64(keys), st)
+    assert not host(st).any()
+    u, c = np.unique(keys, return_counts=True)
+    qk = w["query"]
+    got = zeros_u64(len(qk))
+    G.count(dev_u64(qk), got)
+    exp = c[np.searchsorted(u, qk)].astype(np.uint64)
+    assert np.array_equal(host(got), exp)
+    O = oracle.GQF(28, 8, seed=3)
+    fu = O.fingerprints(u)
+    order = np.argsort(fu)
+    img = oracle.gqf_build(28, 8, fu[order], c[order].astype(np.uint64))
+    d = first_diff(G.export(), img)
+    assert d is None, d
+    del G
+    torch.cuda.empty_cache()
