@@ -1,0 +1,448 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the filter hot path on GB300.
+
+One step = every operation of the hot path over one pass of the paper-scale
+workloads, all through the C ABI:
+  TCF, 2^26 slots, 16-bit tags, bulk mode: empty the table; insert
+    floor(0.9 * 2^26) uniform keys in 2^22-key batches; query 2^24 inserted
+    keys and 2^24 fresh keys; delete a random half of the inserted keys in
+    2^22-key batches; query the 2^25 probes again.
+  Counting GQF, 2^28 slots, 8-bit remainders: empty the table; insert 2.4e8
+    Zipf(1.0) keys over a 2^32 universe in one batch; count 2^24 keys sampled
+    from the stream; delete those 2^24 keys (one copy each); count them again.
+value = operations per second over the whole step (inserts + queries +
+deletes + counts), inputs resident in HBM. Inputs (2.9 GB of keys) exceed the
+L2 (129 MB), so no explicit L2 flush is done between steps.
+
+--impl reference times the CPU oracle (tests only, single thread) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "insert & query Gops/s at 90% load, % of HBM/L2 roofline; batched/served p99"
+UNIT = "Gops/s"
+WORKLOAD = ("TCF 2^26 slots f=16 bulk: 15 x 2^22-key insert batches to 90% load, 2^24 pos + 2^24 neg "
+            "queries, delete random half, re-query; counting GQF 2^28 slots r=8: insert 2.4e8 "
+            "Zipf(1.0) keys over 2^32, count 2^24 sampled keys, delete them, re-count")
+
+# Algorithmic bytes per work unit of each kernel (units are what the library
+# records per launch: keys, slots, blocks or buckets).
+BYTES_PER_UNIT = {
+    "rs_scatter": 16.0,          # key read + key write
+    "rs_scatter_kv": 24.0,       # key + index read and write
+    "rs_hist": 8.0,              # key read
+    "scan_kernel": 8.0,          # u32 read + write
+    "gqf_fp_kernel": 16.0,       # key read + fingerprint write
+    "gqf_flags": 12.0,           # fingerprint read + flag write
+    "gqf_compact": 12.0,         # fingerprint + position read
+    "gqf_merge_kernel": 3.0,     # per slot: old table read + new table write (r = 8: 1.5 B/slot each)
+    "gqf_count_kernel": 80.0,    # key + metadata sector + remainder sector + count
+    "gqf_status_kernel": 13.0,
+    "tcf_query_kernel": 73.0,    # key + two 32-byte blocks + found byte
+    "tcf_group_hist": 8.0,       # key read
+    "tcf_group_scatter": 16.0,   # key read + record write
+    "tcf_block_insert": 69.0,    # per block: offsets + fill + 32-byte block read and write
+    "tcf_block_remove": 69.0,
+    "tcf_bucket_insert": 132.0,  # per bucket: offsets + 64-byte bucket read and write
+    "tcf_bucket_remove": 132.0,
+    "tcf_point_insert": 104.0,
+    "tcf_point_remove": 104.0,
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def make_inputs():
+    from paper_2212_09005_gb300 import workloads as W
+
+    t = W.tcf_workload()
+    g = W.gqf_zipf_workload()
+    ins = t["insert"]
+    probe = np.concatenate([ins[t["pos_idx"]], t["negatives"]])
+    dels = ins[t["del_idx"]]
+    return {
+        "tcf_ins": ins, "tcf_batch": t["batch"], "tcf_probe": probe, "tcf_del": dels,
+        "gqf_ins": g["insert"], "gqf_q": g["query"], "n_pos": len(t["pos_idx"]),
+    }
+
+
+def ops_per_step(inp):
+    return (len(inp["tcf_ins"]) + 2 * len(inp["tcf_probe"]) + len(inp["tcf_del"])
+            + len(inp["gqf_ins"]) + 3 * len(inp["gqf_q"]))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def ncu_traffic():
+    """Per-kernel DRAM bytes per work unit from the committed ncu summary."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    out = {}
+    if os.path.exists(p):
+        for line in open(p):
+            line = line.split("#", 1)[0].split()
+            if len(line) >= 3:
+                out[line[0]] = (float(line[1]), float(line[2]))  # units per launch, bytes per launch
+    return out
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+class Runner:
+    def __init__(self, inp, device):
+        import torch
+
+        import paper_2212_09005_gb300 as gf
+
+        self.gf, self.torch, self.inp = gf, torch, inp
+        self.dev = device
+        to = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
+        self.d = {k: to(inp[k]) for k in ("tcf_ins", "tcf_probe", "tcf_del", "gqf_ins", "gqf_q")}
+        self.found = torch.zeros(len(inp["tcf_probe"]), dtype=torch.uint8, device=device)
+        self.found2 = torch.zeros_like(self.found)
+        self.cnt = torch.zeros(len(inp["gqf_q"]), dtype=torch.int64, device=device)
+        self.cnt2 = torch.zeros_like(self.cnt)
+        self.B = inp["tcf_batch"]
+        self.tcf = gf.TCF(26, 16, gf.MODE_BULK, seed=2, max_batch=self.B)
+        self.gqf = gf.GQF(28, 8, seed=3, max_batch=len(inp["gqf_ins"]))
+
+    def step(self, src=None):
+        """One pass of the hot path. `src` maps input names to device tensors."""
+        d = src or self.d
+        tcf, gqf, B = self.tcf, self.gqf, self.B
+        tcf.clear()
+        ins = d["tcf_ins"]
+        for s in range(0, ins.numel(), B):
+            tcf.insert(ins[s:s + B])
+        tcf.query(d["tcf_probe"], self.found)
+        dl = d["tcf_del"]
+        for s in range(0, dl.numel(), B):
+            tcf.remove(dl[s:s + B])
+        tcf.query(d["tcf_probe"], self.found2)
+        gqf.clear()
+        gqf.insert(d["gqf_ins"])
+        gqf.count(d["gqf_q"], self.cnt)
+        gqf.remove(d["gqf_q"])
+        gqf.count(d["gqf_q"], self.cnt2)
+
+    def _recount_ok(self):
+        # each sampled key was deleted once per occurrence in the sample
+        q = self.inp["gqf_q"]
+        u, inv, occ = np.unique(q, return_inverse=True, return_counts=True)
+        before = self.cnt.cpu().numpy()
+        after = self.cnt2.cpu().numpy()
+        return bool((after == np.maximum(before - occ[inv], 0)).all())
+
+    def checks(self):
+        """Cheap correctness guards on the last step's results."""
+        t = self.torch
+        t.cuda.synchronize()
+        npos = self.inp["n_pos"]
+        st_t, st_g = self.tcf.stats(), self.gqf.stats()
+        ok = {
+            "tcf_pos_found": bool(self.found[:npos].all().item()),
+            "tcf_fpr": float(self.found[npos:].float().mean().item()),
+            "gqf_counts_pos": bool((self.cnt >= 1).all().item()),
+            "gqf_recount_ok": self._recount_ok(),
+            "tcf_status_word": st_t["status_word"], "gqf_status_word": st_g["status_word"],
+            "tcf_backing_used": st_t["backing_used"],
+        }
+        return ok
+
+
+def run_ours(args, rank, world, device_index):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2212_09005_gb300 as gf
+
+    torch.cuda.set_device(device_index)
+    device = torch.device("cuda", device_index)
+    inp = make_inputs()
+    R = Runner(inp, device)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        R.step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    gf.trace_reset()
+    gf.trace_enable(True)
+    clocks = ClockSampler(device_index)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        R.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    gf.trace_enable(False)
+    trace = gf.trace_summary()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    checks = R.checks()
+    ops = ops_per_step(inp)
+    value = ops * args.steps * world / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel, from the live trace of the timed region
+    peak, peak_src = peaks()
+    traffic = ncu_traffic()
+    kern = []
+    tot_ms = sum(v["ms"] for v in trace.values())
+    for name, v in trace.items():
+        bpu = BYTES_PER_UNIT.get(name)
+        gbs = (bpu * v["units"] / (v["ms"] / 1e3) / 1e9) if (bpu and v["ms"] > 0) else None
+        kern.append({"kernel": name, "launches": v["launches"], "ms": round(v["ms"], 3),
+                     "share": round(v["ms"] / tot_ms, 4) if tot_ms else None,
+                     "achieved_gbs": round(gbs, 1) if gbs else None})
+    kern.sort(key=lambda k: -k["ms"])
+    top = kern[0] if kern else None
+    roof = None
+    if top and top["achieved_gbs"]:
+        name = top["kernel"]
+        per_launch_units = trace[name]["units"] / trace[name]["launches"]
+        tr = None
+        if name in traffic:
+            u, b = traffic[name]
+            tr = b * per_launch_units / u if u else None
+        roof = {"bound": "hbm", "kernel": name, "achieved": top["achieved_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": round(top["achieved_gbs"] / peak, 4), "peak_source": peak_src,
+                "traffic": tr, "algorithmic_bytes_per_launch": BYTES_PER_UNIT[name] * per_launch_units}
+    launches = sum(v["launches"] for v in trace.values())
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(R, args, world, device)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_sample(inp)
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded SplitMix64 uniform keys, Zipf rejection-inversion keys)",
+        "config": {"workload": WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
+                   "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+        "cpu_baseline": cpu, "kernels": kern[:12], "checks": checks,
+    }
+    return line
+
+
+def run_e2e(R, args, world, device):
+    """Same step through the C ABI with inputs in pinned host memory: every step
+    copies its keys host->device and its results device->host."""
+    import torch
+    import torch.distributed as dist
+
+    inp = R.inp
+    names = ("tcf_ins", "tcf_probe", "tcf_del", "gqf_ins", "gqf_q")
+    hostb = {k: torch.from_numpy(np.ascontiguousarray(inp[k]).view(np.int64)).pin_memory() for k in names}
+    devb = {k: torch.empty(hostb[k].shape, dtype=torch.int64, device=device) for k in names}
+    out_found = torch.empty(R.found.shape, dtype=torch.uint8).pin_memory()
+    out_cnt = torch.empty(R.cnt.shape, dtype=torch.int64).pin_memory()
+    h2d = sum(hostb[k].numel() * 8 for k in names)
+    d2h = 2 * (out_found.numel() + out_cnt.numel() * 8)
+
+    def step():
+        for k in names:
+            devb[k].copy_(hostb[k], non_blocking=True)
+        R.step(devb)
+        out_found.copy_(R.found, non_blocking=True)
+        out_cnt.copy_(R.cnt, non_blocking=True)
+        out_found.copy_(R.found2, non_blocking=True)
+        out_cnt.copy_(R.cnt2, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([sec], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    v = ops_per_step(inp) * args.steps * world / sec / 1e9
+    return {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (bounded sample of the same workload)
+# ---------------------------------------------------------------------------
+def cpu_sample(inp, frac_gqf: int = 16):
+    """Time the oracle on: the first 2^22-key TCF batch into the 2^26-slot table,
+    2^21 + 2^21 TCF queries, 2^21 TCF deletes; 1/16 of the Zipf stream into the
+    2^28-slot GQF, and 2^19 counts, deletes and re-counts."""
+    import oracle as O
+
+    B = inp["tcf_batch"]
+    t_ins = inp["tcf_ins"][:B]
+    npos = inp["n_pos"]
+    probe = np.concatenate([inp["tcf_probe"][: B // 2], inp["tcf_probe"][npos:npos + B // 2]])
+    t_del = t_ins[: B // 2]
+    g_ins = inp["gqf_ins"][: len(inp["gqf_ins"]) // frac_gqf]
+    g_q = g_ins[: 1 << 19]
+    T = O.TCF(26, 16, seed=2)
+    G = O.GQF(28, 8, seed=3)
+    t0 = time.perf_counter()
+    T.insert(t_ins)
+    T.query(probe)
+    T.remove(t_del)
+    G.insert(g_ins)
+    G.count(g_q)
+    G.remove(g_q)
+    G.count(g_q)
+    sec = time.perf_counter() - t0
+    ops = len(t_ins) + len(probe) + len(t_del) + len(g_ins) + 3 * len(g_q)
+    return {"value": round(ops / sec / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"TCF 2^26: one 2^22-key insert batch, {len(probe)} queries, {len(t_del)} deletes; "
+                       f"GQF 2^28: {len(g_ins)} Zipf keys, {len(g_q)} counts + deletes + re-counts"),
+            "seconds": round(sec, 2), "ops": ops}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    inp = make_inputs()
+    for _ in range(max(3, args.warmup)):
+        cpu_sample(inp, frac_gqf=64)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_sample(inp, frac_gqf=64)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = float(np.mean(vals))
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(1e3 * float(np.mean(secs)), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded SplitMix64 uniform keys, Zipf rejection-inversion keys)",
+        "config": {"workload": WORKLOAD, "sample": r["sample"], "parallelism": "single host thread"},
+        "cpu_baseline": {"value": round(v, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r["sample"]},
+        "e2e": {"value": round(v, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

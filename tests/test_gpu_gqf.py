@@ -137,9 +137,10 @@ def test_empty_and_single(gf, oracle):
 
 
 def test_zipf_small_exact_counts(gf, oracle):
-    q = 16
-    keys = W.zipf_keys(3, 300000, 1.0, 1 << 20)  # universe 2^20 <= 2^p
+    q = 18
+    keys = W.zipf_keys(3, 300000, 1.0, 1 << 20)  # universe 2^20 <= 2^p; ~90K distinct
     O, G = run_batches(gf, oracle, q, 8, seed=3, batches=[keys[:200000], keys[200000:]])
+    assert G.stats()["failed_keys"] == 0
     u, c = np.unique(keys, return_counts=True)
     got = zeros_u64(len(u))
     G.count(dev_u64(u), got)
