@@ -177,6 +177,41 @@ int filter_trace_reset(void);
 /* writes min(cap, number of kernels) entries to out; *n_kernels = number of kernels */
 int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kernels);
 
+/*
+ * filter_gqf_insert_noalloc: a GQF bulk insert (the same work as
+ * filter_insert on a GQF) that allocates no device memory at all. The paper
+ * has no counterpart; this exists for callers that must not call cudaMalloc:
+ * a process whose device memory is owned by its own allocator or by a fixed
+ * arena reserved at start-up, where a cudaMalloc could fail on a full device
+ * or fragment the arena, and latency-critical paths that cannot afford
+ * cudaMalloc's implicit device synchronisation.
+ *
+ * d_table_in: the current table image of a GQF with this (q, r, hash_seed),
+ *   in device memory, in the filter_export layout (all metadata records, then
+ *   all remainders; filter_export_size bytes; an all-zero image is the empty
+ *   table). d_table_out: receives the table after the insert, same size; it
+ *   must not overlap d_table_in. d_keys: n uint64 keys. d_status: NULL or n
+ *   uint8 per-key statuses, as for filter_insert. All device pointers are
+ *   owned by the caller.
+ * Limits: n <= FILTER_NOALLOC_MAX_KEYS, 6 <= q <= FILTER_NOALLOC_MAX_Q,
+ *   r in {8, 16}; otherwise FILTER_ERR_ARG and nothing is enqueued.
+ * Scratch: a static device array of 4 MiB inside the library, which every GPU
+ *   that loads the library keeps until the process exits. All calls share it
+ *   and it keeps the last call's contents (the call clears what it needs
+ *   cleared), so calls whose GPU work overlaps - on different streams, or from
+ *   several host threads - race on it and must be serialised by the caller.
+ *   The first call on each device looks the array's device address up with
+ *   cudaGetSymbolAddress, with that device current; make that first call
+ *   before any stream capture. The call is asynchronous on `stream` except
+ *   when the table overflows, where it synchronises `stream`, as
+ *   filter_insert does.
+ */
+#define FILTER_NOALLOC_MAX_KEYS 65536u
+#define FILTER_NOALLOC_MAX_Q 20u
+int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_seed, const void *d_table_in,
+                              void *d_table_out, const uint64_t *d_keys, uint64_t n,
+                              uint8_t *d_status, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ EXPORTS = [
     "filter_remove", "filter_count", "filter_get_stats", "filter_export_size",
     "filter_export", "filter_import", "filter_error_string",
     "filter_trace_enable", "filter_trace_reset", "filter_trace_summary",
+    "filter_gqf_insert_noalloc",
 ]
 
 
@@ -88,6 +89,7 @@ def lib():
         L.filter_trace_enable.argtypes = [i32]
         L.filter_trace_reset.argtypes = []
         L.filter_trace_summary.argtypes = [C.c_uint32, C.POINTER(TraceEntry), C.POINTER(C.c_uint32)]
+        L.filter_gqf_insert_noalloc.argtypes = [C.c_uint32, C.c_uint32, u64, vp, vp, vp, u64, vp, vp]
         L.filter_error_string.argtypes = [i32]
         L.filter_error_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -216,3 +218,18 @@ def trace_summary() -> dict:
     _check(lib().filter_trace_summary(n.value, arr, C.byref(n)), "filter_trace_summary")
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "units": int(arr[i].units),
                                    "ms": float(arr[i].ms)} for i in range(n.value)}
+
+
+NOALLOC_MAX_KEYS = 65536
+NOALLOC_MAX_Q = 20
+
+
+def gqf_insert_noalloc(q: int, r: int, seed: int, table_in, table_out, keys, status=None, stream=None):
+    """GQF bulk insert from the table image `table_in` into `table_out` (uint8 CUDA
+    tensors in the filter_export layout) without any device allocation; the
+    library's static scratch is used instead (at most NOALLOC_MAX_KEYS keys,
+    q <= NOALLOC_MAX_Q)."""
+    _check(lib().filter_gqf_insert_noalloc(q, r, seed & 0xFFFFFFFFFFFFFFFF, _dptr(table_in, 1),
+                                           _dptr(table_out, 1), _dptr(keys, 8), keys.numel(),
+                                           _dptr(status, 1), _stream(stream)),
+           "filter_gqf_insert_noalloc")
