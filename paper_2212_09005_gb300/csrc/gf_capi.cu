@@ -12,6 +12,19 @@ static cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
 
 static bool valid(const filter_t *f) { return f != nullptr && f->arena.base != nullptr; }
 
+// every device buffer of the filter got an address
+static bool pointers_set(const filter *F)
+{
+    if (!F->ctr || !F->scan_tmp) return false;
+    if (F->cfg.kind == FILTER_TCF) {
+        const TcfState &T = F->tcf;
+        return T.blocks && T.bk && T.fill && T.cnt && T.off && T.rec && T.rec2 && T.pend0 && T.pend1 && T.pend2;
+    }
+    const GqfState &Q = F->gqf;
+    return Q.meta[0] && Q.meta[1] && Q.rem[0] && Q.rem[1] && Q.fp_a && Q.fp_b && Q.fp_c && Q.ufp && Q.idx_a &&
+           Q.idx_b && Q.idx_c && Q.ustart && Q.flags && Q.removed && Q.tile_state && Q.tile_lo && Q.radix_tmp;
+}
+
 extern "C" {
 
 int filter_create(const filter_config *cfg, void *stream, filter_t **out)
@@ -48,6 +61,7 @@ int filter_create(const filter_config *cfg, void *stream, filter_t **out)
     if (cfg->kind == FILTER_TCF) rc = gf::tcf_setup(F, tb, sb, false);
     else rc = gf::gqf_setup(F, tb, sb, false);
     if (rc == FILTER_OK && F->arena.used > F->arena.size) rc = FILTER_ERR_INTERNAL;
+    if (rc == FILTER_OK && !pointers_set(F)) rc = FILTER_ERR_INTERNAL;
     if (rc == FILTER_OK) rc = (cfg->kind == FILTER_TCF) ? gf::tcf_clear(F, as_stream(stream)) : gf::gqf_clear(F, as_stream(stream));
     if (rc != FILTER_OK) {
         cudaFree(F->ctr);

@@ -19,6 +19,8 @@
 //
 // Count / query (Sec. 5.1 via the cited CQF): offset of the home block,
 // rank over occupieds, select over runends, then a scan of the run.
+#include <type_traits>
+
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -93,9 +95,10 @@ struct MergeArgs {
     const uint64_t *ufp;
     const uint32_t *ustart;
     const uint32_t *pm;      // number of groups (device)
+    const uint32_t *tlo;     // first group of each tile (ntiles + 1 entries)
     uint64_t m_limit;        // use groups [0, min(m, m_limit))
     uint32_t *removed;       // delete: copies removed per group
-    unsigned long long *ts;  // look-back state: [0] tile counter, then 4 words per tile
+    unsigned long long *ts;  // look-back state: [0] tile counter, then one status word per tile
     DevCounters *ctr;
     uint64_t N, nslots, nblk, ntiles;
     uint32_t r;
@@ -131,9 +134,11 @@ __device__ __forceinline__ void wr_slot(uint8_t *rem, uint64_t i, uint32_t v)
 template <int R>
 struct MergeSmem {
     unsigned long long occ[TBLK];
-    unsigned int kpre[MT + 1];
+    unsigned int kpre[MT + 1];      // old runs before each thread's 8 quotients
     int oend[TQ];                   // old run ends relative to Q0
-    unsigned int nfirst[MT + 1];
+    unsigned int Lq[TQ];            // new run length per quotient
+    unsigned int qfirst[TQ];        // first new group of each quotient (or ~0)
+    int qstart[TQ];                 // new run start relative to Q0
     typename SlotIO<R>::T old[OLDBUF];
     typename SlotIO<R>::T out[OUTBUF];
     unsigned long long rend[RWORDS];
@@ -143,6 +148,17 @@ struct MergeSmem {
     unsigned long long glo, ghi;
     unsigned int tile, kold, oldlen, err;
 };
+
+// new group g: quotient offset from Q0, remainder and batch count
+template <int R>
+__device__ __forceinline__ void new_group(const MergeSmem<R> &, const MergeArgs &a, long long Q0, uint32_t g,
+                                          uint32_t &qoff, uint32_t &rem, uint64_t &cnt)
+{
+    const uint64_t f = a.ufp[g];
+    qoff = (uint32_t)((long long)(f >> R) - Q0);
+    rem = (uint32_t)(f & ((1ull << R) - 1ull));
+    cnt = a.ustart[g + 1] - a.ustart[g];
+}
 
 // old slot reader: staged when inside the staged window
 template <int R>
@@ -207,18 +223,15 @@ __device__ __forceinline__ long long put_group(MergeSmem<R> &S, const MergeArgs 
 // WRITE = true: write the run starting at `pos`.
 template <int R, bool WRITE>
 __device__ __forceinline__ uint32_t merge_run(MergeSmem<R> &S, const MergeArgs &a, OldRun o, bool has_old,
-                                              uint32_t g, uint32_t gend, long long pos)
+                                              uint32_t g, uint32_t gend, long long pos, long long Q0)
 {
-    const uint64_t rmask = (1ull << R) - 1ull;
     uint32_t len = 0;
+    uint32_t qoff_unused;
     uint32_t ov = 0, nv = 0;
     uint64_t oc = 0, nc = 0;
     bool ho = has_old && old_next<R>(S, a, o, ov, oc);
     bool hn = g < gend;
-    if (hn) {
-        nv = (uint32_t)(a.ufp[g] & rmask);
-        nc = a.ustart[g + 1] - a.ustart[g];
-    }
+    if (hn) new_group<R>(S, a, Q0, g, qoff_unused, nv, nc);
     while (ho || hn) {
         uint32_t v;
         uint64_t c;
@@ -247,10 +260,7 @@ __device__ __forceinline__ uint32_t merge_run(MergeSmem<R> &S, const MergeArgs &
             }
             g++;
             hn = g < gend;
-            if (hn) {
-                nv = (uint32_t)(a.ufp[g] & rmask);
-                nc = a.ustart[g + 1] - a.ustart[g];
-            }
+            if (hn) new_group<R>(S, a, Q0, g, qoff_unused, nv, nc);
         }
         if (c == 0) continue;
         if (WRITE) pos = put_group<R>(S, a, pos, v, c);
@@ -277,7 +287,6 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
     const uint64_t tile = S.tile;
     const long long Q0 = (long long)tile * TQ;
     const uint64_t j0 = tile * TBLK;
-    const uint64_t m_eff = min((uint64_t)*a.pm, a.m_limit);
     const long long slot_end = min((long long)a.nslots, Q0 + TQ);
 
     // 1. old occupieds of the tile
@@ -303,18 +312,10 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
             S.kold = pre + incl;
         }
     }
-    // 4a. new group range of the tile (successor search, Sec. 5.4)
-    if (tid < 2) {
-        long long qb = Q0 + (tid == 0 ? 0 : TQ);
-        uint64_t key = (qb >= (long long)a.N) ? (a.N << a.r) : ((uint64_t)qb << a.r);
-        uint64_t lo = 0, hi = m_eff;
-        while (lo < hi) {
-            uint64_t mid = (lo + hi) >> 1;
-            if (a.ufp[mid] < key) lo = mid + 1;
-            else hi = mid;
-        }
-        if (tid == 0) S.glo = lo;
-        else S.ghi = lo;
+    // 4a. new group range of the tile (precomputed by successor search)
+    if (tid == 0) {
+        S.glo = a.tlo[tile];
+        S.ghi = a.tlo[tile + 1];
     }
     __syncthreads();
     const uint32_t kold = S.kold;
@@ -356,12 +357,17 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
         if (lane == 0) {
             long long pe;
             if (q0occ) {
+                // last runend in [Q0, base - 1]; Q0 is a multiple of 64
                 pe = Q0 - 1;
-                for (long long p = base - 1; p >= Q0; p--) {
-                    if ((a.meta_old[p >> 6].rend >> (p & 63)) & 1ull) {
-                        pe = p;
+                for (long long p = base - 1; p >= Q0;) {
+                    long long w = p >> 6;
+                    unsigned pb = (unsigned)(p & 63);
+                    unsigned long long bits = a.meta_old[w].rend & (pb == 63 ? ~0ull : ((1ull << (pb + 1)) - 1ull));
+                    if (bits) {
+                        pe = 64 * w + 63 - __clzll((long long)bits);
                         break;
                     }
+                    p = 64 * w - 1;
                 }
             } else {
                 pe = base;
@@ -369,22 +375,27 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
             S.prev_end_old = pe;
         }
     }
-    // 4b. per-thread new group ranges
-    for (int t = tid; t <= MT; t += MT) S.nfirst[t] = (unsigned)S.ghi;
-    __syncthreads();
-    for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
-        long long y = (long long)(a.ufp[g] >> a.r);
-        unsigned t = (unsigned)((y - Q0) >> 3);
-        bool start = (g == S.glo) || ((((long long)(a.ufp[g - 1] >> a.r)) - Q0) >> 3) != (long long)t;
-        if (start) S.nfirst[t] = (unsigned)g;
+    // 4b. per-quotient new-group index and (insert) summed encoded lengths
+    const unsigned NONE = 0xffffffffu;
+    for (int y = tid; y < TQ; y += MT) {
+        S.Lq[y] = 0;
+        S.qfirst[y] = NONE;
     }
     __syncthreads();
-    if (tid == 0) {
-        unsigned nxt = (unsigned)S.ghi;
-        for (int t = MT; t >= 0; t--) {
-            if (S.nfirst[t] > nxt) S.nfirst[t] = nxt;
-            nxt = S.nfirst[t];
+    const bool old_ok = S.err == 0;
+    for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
+        uint32_t qo, rm;
+        uint64_t cn;
+        new_group<R>(S, a, Q0, (uint32_t)g, qo, rm, cn);
+        atomicMin(&S.qfirst[qo], (unsigned)g);
+        if (!a.del) {
+            atomicAdd(&S.Lq[qo], enc_len(cn, R));
+        } else if (a.removed) {
+            const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
+            if (!ho) a.removed[g] = 0;  // nothing stored to delete
         }
+    }
+    if (tid == 0) {
         // 5. staged window of the old runs
         if (kold > 0 && S.err == 0) {
             long long yfirst = -1;
@@ -404,33 +415,47 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
     for (unsigned p = tid; p < S.oldlen; p += MT) S.old[p] = (typename SlotIO<R>::T)rd_slot<R>(a.rem_old, (uint64_t)(S.os0 + p));
     __syncthreads();
 
-    // 6. pass 1: run lengths of this thread's quotients
-    const bool old_ok = S.err == 0;
-    const long long ybase = Q0 + (long long)tid * QPT;
-    const uint32_t n0 = S.nfirst[tid], n1 = S.nfirst[tid + 1];
-    uint32_t L[QPT];
-    long long tA = NEG_INF, tB = 0;
-    {
-        uint32_t k = S.kpre[tid];
-        uint32_t g = n0;
-        for (int c = 0; c < QPT; c++) {
-            long long y = ybase + c;
-            bool ho = old_ok && ((mybyte >> c) & 1u);
-            OldRun o{0, -1};
-            if (ho) {
-                long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
-                o.e = Q0 + S.oend[k];
-                o.p = y > pe + 1 ? y : pe + 1;
-                k++;
+    // 6. run length of every quotient: copy length for old-only runs, the summed
+    // encodings for new-only runs, a full merge where both exist
+    for (int y = tid; y < TQ; y += MT) {
+        const bool ho = old_ok && ((S.occ[y >> 6] >> (y & 63)) & 1ull);
+        const unsigned gf = S.qfirst[y];
+        const bool hn = gf != NONE;
+        if (!ho && !hn) continue;
+        if (!ho) {
+            if (a.del) S.Lq[y] = 0;
+            continue;
+        }
+        const unsigned byte = (unsigned)(S.occ[y >> 6] >> ((y & 56))) & 0xffu;
+        const unsigned k = S.kpre[y >> 3] + __popc(byte & ((1u << (y & 7)) - 1u));
+        const long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
+        OldRun o;
+        o.e = Q0 + S.oend[k];
+        o.p = (Q0 + y) > pe + 1 ? (Q0 + y) : pe + 1;
+        if (!hn) {
+            S.Lq[y] = (unsigned)(o.e - o.p + 1);
+        } else {
+            uint32_t ge = gf;
+            while (ge < S.ghi) {
+                uint32_t qo, rm;
+                uint64_t cn;
+                new_group<R>(S, a, Q0, ge, qo, rm, cn);
+                if ((int)qo != y) break;
+                ge++;
             }
-            uint32_t ge = g;
-            while (ge < n1 && (long long)(a.ufp[ge] >> a.r) == y) ge++;
-            L[c] = (ho || ge > g) ? merge_run<R, false>(S, a, o, ho, g, ge, 0) : 0u;
-            g = ge;
-            if (L[c]) agg_combine(tA, tB, y + L[c] - 1, L[c]);
+            S.Lq[y] = merge_run<R, false>(S, a, o, true, gf, ge, 0, Q0);
         }
     }
-    // 7. exclusive scan of the thread aggregates across the CTA
+    __syncthreads();
+
+    // 7. placement: thread tid owns quotients 8 tid .. 8 tid + 7
+    const long long ybase = Q0 + (long long)tid * QPT;
+    long long tA = NEG_INF, tB = 0;
+#pragma unroll
+    for (int c = 0; c < QPT; c++) {
+        const unsigned L = S.Lq[tid * QPT + c];
+        if (L) agg_combine(tA, tB, ybase + c + L - 1, L);
+    }
     long long iA = tA, iB = tB;  // inclusive
     for (int o = 1; o < 32; o <<= 1) {
         long long pA = __shfl_up_sync(0xffffffffu, iA, o);
@@ -459,65 +484,111 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
         xA = pA;
         xB = pB;
     }
-    // 8. decoupled look-back over tiles (thread 0)
-    if (tid == 0) {
+    // 8. decoupled look-back over tiles, CTA-wide: 256 predecessors per round.
+    // One status word per tile: bits 62-63 flag (1 aggregate, 2 inclusive end);
+    // aggregate payload (A - Q0 + 1) << 31 | B, with 0 in the A field for a tile
+    // without runs; inclusive payload P + 1. A tile whose aggregate does not fit
+    // publishes only its inclusive end.
+    {
+        const unsigned full = 0xffffffffu;
+        __shared__ long long lbA[MT / 32], lbB[MT / 32], lbP;
+        __shared__ int lb_incl;
+        __shared__ unsigned lb_timeout;
         long long TA = NEG_INF, TB = 0;
         for (int w = 0; w < MT / 32; w++) agg_combine(TA, TB, S.wA[w], S.wB[w]);
-        unsigned long long *st = a.ts + 1 + 4 * tile;
+        unsigned long long *st = a.ts + 1;
+        const long long arel = (TA == NEG_INF) ? 0 : TA - Q0 + 1;
+        const bool packable = TB < (1ll << 31) && arel >= 0 && arel < (1ll << 31);
+        if (tid == 0) {
+            lb_timeout = 0;
+            if (tile > 0 && packable)
+                atomicExch(&st[tile], (1ull << 62) | ((unsigned long long)arel << 31) | (unsigned long long)TB);
+        }
         long long ein = -1;
         if (tile > 0) {
-            st[1] = (unsigned long long)TA;
-            st[2] = (unsigned long long)TB;
-            __threadfence();
-            atomicExch(&st[0], 1ull);
-            long long gA = NEG_INF, gB = 0;  // composition of the tiles passed so far
-            long long j = (long long)tile - 1;
-            uint32_t spins = 0;
+            long long gA = NEG_INF, gB = 0;  // composition of the newer tiles of earlier rounds
+            long long jtop = (long long)tile - 1;
             while (true) {
-                unsigned long long *sj = a.ts + 1 + 4 * j;
-                unsigned long long fl = ld_vol(&sj[0]);
-                if (fl == 0) {
-                    if (++spins > SPIN_LIMIT) {
-                        atomicOr(&a.ctr->status, ST_TIMEOUT);
-                        break;
+                const long long j = jtop - tid;
+                unsigned long long wd = 2ull << 62;  // before tile 0: inclusive end -1
+                if (j >= 0) {
+                    wd = ld_vol(&st[j]);
+                    uint32_t spins = 0, ns = 32;
+                    while ((wd >> 62) == 0) {
+                        if (++spins > (SPIN_LIMIT >> 2)) {
+                            lb_timeout = 1;
+                            break;
+                        }
+                        __nanosleep(ns);
+                        if (ns < 512) ns <<= 1;
+                        wd = ld_vol(&st[j]);
                     }
-                    continue;
                 }
-                __threadfence();
-                if (fl == 2) {
-                    long long P = (long long)ld_vol(&sj[3]);
-                    long long v = P + gB;
-                    ein = v > gA ? v : gA;
+                const unsigned flag = (unsigned)(wd >> 62);
+                if (tid == 0) lb_incl = MT;
+                __syncthreads();
+                if (flag == 2) atomicMin(&lb_incl, tid);
+                __syncthreads();
+                const int Lc = lb_incl;
+                long long A = NEG_INF, Bv = 0;
+                if (tid < Lc && flag == 1) {
+                    const unsigned long long ar = (wd >> 31) & 0x7fffffffull;
+                    Bv = (long long)(wd & 0x7fffffffull);
+                    A = ar ? (long long)ar - 1 + j * TQ : NEG_INF;
+                }
+                // ordered composition, thread tid + 1 being the older tile
+                for (int o = 1; o < 32; o <<= 1) {
+                    long long oA = __shfl_down_sync(full, A, o), oB = __shfl_down_sync(full, Bv, o);
+                    if (lane + o < 32) {
+                        agg_combine(oA, oB, A, Bv);
+                        A = oA;
+                        Bv = oB;
+                    }
+                }
+                if (lane == 0) {
+                    lbA[warp] = A;
+                    lbB[warp] = Bv;
+                }
+                if (tid == Lc) lbP = (long long)(wd & ((1ull << 62) - 1ull)) - 1;
+                __syncthreads();
+                long long WA = NEG_INF, WB = 0;
+                for (int w = MT / 32 - 1; w >= 0; w--) agg_combine(WA, WB, lbA[w], lbB[w]);
+                agg_combine(WA, WB, gA, gB);
+                if (lb_timeout) {
+                    if (tid == 0) atomicOr(&a.ctr->status, ST_TIMEOUT);
                     break;
                 }
-                long long A = (long long)ld_vol(&sj[1]), Bj = (long long)ld_vol(&sj[2]);
-                agg_combine(A, Bj, gA, gB);
-                gA = A;
-                gB = Bj;
-                j--;
+                if (Lc < MT) {
+                    long long v = lbP + WB;
+                    ein = v > WA ? v : WA;
+                    break;
+                }
+                gA = WA;
+                gB = WB;
+                jtop -= MT;
             }
         }
-        long long v = ein + TB;
-        long long P = v > TA ? v : TA;
-        st[3] = (unsigned long long)P;
-        __threadfence();
-        atomicExch(&st[0], 2ull);
-        S.ein = ein;
-        S.tileP = P;
-        atomicMax(&a.ctr->gqf_end, P);
-        if (P >= (long long)a.nslots) atomicExch(&a.ctr->overflow, 1ull);
-        long long w0 = Q0 > ein + 1 ? Q0 : ein + 1;
-        long long w1 = slot_end > P + 1 ? slot_end : P + 1;
-        if (w1 > (long long)a.nslots) w1 = (long long)a.nslots;
-        if (w0 > w1) w0 = w1;
-        S.w0 = w0;
-        S.w1 = w1;
+        if (tid == 0) {
+            long long v = ein + TB;
+            long long P = v > TA ? v : TA;
+            atomicExch(&st[tile], (2ull << 62) | (unsigned long long)(P + 1));
+            S.ein = ein;
+            S.tileP = P;
+            atomicMax(&a.ctr->gqf_end, P);
+            if (P >= (long long)a.nslots) atomicExch(&a.ctr->overflow, 1ull);
+            long long w0 = Q0 > ein + 1 ? Q0 : ein + 1;
+            long long w1 = slot_end > P + 1 ? slot_end : P + 1;
+            if (w1 > (long long)a.nslots) w1 = (long long)a.nslots;
+            if (w0 > w1) w0 = w1;
+            S.w0 = w0;
+            S.w1 = w1;
+        }
     }
     __syncthreads();
     if (S.err) atomicOr(&a.ctr->status, ST_INTERNAL);
     if (a.dry) return;
 
-    // 9. pass 2: write
+    // 9. starts, runends, occupieds and offsets (thread tid: its 8 quotients)
     const long long w0 = S.w0, w1 = S.w1;
     const long long staged = (w1 - w0) < OUTBUF ? (w1 - w0) : OUTBUF;
     for (int p = tid; p < OUTBUF; p += MT) S.out[p] = 0;
@@ -533,47 +604,80 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
     const long long e_thread_in = e;
     uint32_t newbyte = 0;
     long long first_end = -1;
-    {
-        uint32_t k = S.kpre[tid];
-        uint32_t g = n0;
-        for (int c = 0; c < QPT; c++) {
-            long long y = ybase + c;
-            bool ho = old_ok && ((mybyte >> c) & 1u);
-            OldRun o{0, -1};
-            if (ho) {
-                long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
-                o.e = Q0 + S.oend[k];
-                o.p = y > pe + 1 ? y : pe + 1;
-                k++;
-            }
-            uint32_t ge = g;
-            while (ge < n1 && (long long)(a.ufp[ge] >> a.r) == y) ge++;
-            if (L[c]) {
-                long long start = y > e + 1 ? y : e + 1;
-                long long end = start + L[c] - 1;
-                merge_run<R, true>(S, a, o, ho, g, ge, start);
-                if (end < (long long)a.nslots) {
-                    long long wi = (end >> 6) - wbase;
-                    if (end - w0 < OUTBUF && wi >= 0 && wi < RWORDS)
-                        atomicOr(&S.rend[wi], 1ull << (end & 63));
-                    else
-                        atomicOr(&a.meta_new[end >> 6].rend, 1ull << (end & 63));
-                }
-                e = end;
-                newbyte |= 1u << c;
-                if (c == 0) first_end = end;
-            }
-            g = ge;
+#pragma unroll
+    for (int c = 0; c < QPT; c++) {
+        const unsigned L = S.Lq[tid * QPT + c];
+        if (!L) continue;
+        const long long y = ybase + c;
+        const long long start = y > e + 1 ? y : e + 1;
+        const long long end = start + L - 1;
+        S.qstart[tid * QPT + c] = (int)(start - Q0);
+        if (end < (long long)a.nslots) {
+            const long long wi = (end >> 6) - wbase;
+            if (end - w0 < OUTBUF && wi >= 0 && wi < RWORDS)
+                atomicOr(&S.rend[wi], 1ull << (end & 63));
+            else
+                atomicOr(&a.meta_new[end >> 6].rend, 1ull << (end & 63));
         }
+        e = end;
+        newbyte |= 1u << c;
+        if (c == 0) first_end = end;
     }
     S.newocc[tid] = (unsigned char)newbyte;
-    // offsets: the thread whose first quotient starts a block
     if ((tid & 7) == 0) {
-        uint64_t j = j0 + (tid >> 3);
+        const uint64_t j = j0 + (tid >> 3);
         if (j < a.nblk) {
-            long long ref = (newbyte & 1u) ? first_end : e_thread_in;
-            long long o = ref - 64 * (long long)j;
+            const long long ref = (newbyte & 1u) ? first_end : e_thread_in;
+            const long long o = ref - 64 * (long long)j;
             a.meta_new[j].off = (unsigned)(o > 0 ? o : 0);
+        }
+    }
+    __syncthreads();
+
+    // 10. write the runs: old-only runs are copied, mixed runs merged, and the
+    // groups of new-only runs encoded by one thread each
+    for (int y = tid; y < TQ; y += MT) {
+        const unsigned L = S.Lq[y];
+        if (!L) continue;
+        const bool ho = old_ok && ((S.occ[y >> 6] >> (y & 63)) & 1ull);
+        if (!ho) continue;
+        const unsigned gf = S.qfirst[y];
+        const unsigned byte = (unsigned)(S.occ[y >> 6] >> ((y & 56))) & 0xffu;
+        const unsigned k = S.kpre[y >> 3] + __popc(byte & ((1u << (y & 7)) - 1u));
+        const long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
+        OldRun o;
+        o.e = Q0 + S.oend[k];
+        o.p = (Q0 + y) > pe + 1 ? (Q0 + y) : pe + 1;
+        const long long start = Q0 + S.qstart[y];
+        if (gf == NONE) {
+            for (long long p = 0; p < (long long)L; p++) put_slot<R>(S, a, start + p, old_at<R>(S, a, o.p + p));
+        } else {
+            uint32_t ge = gf;
+            while (ge < S.ghi) {
+                uint32_t qo, rm;
+                uint64_t cn;
+                new_group<R>(S, a, Q0, ge, qo, rm, cn);
+                if ((int)qo != y) break;
+                ge++;
+            }
+            merge_run<R, true>(S, a, o, true, gf, ge, start, Q0);
+        }
+    }
+    if (!a.del) {
+        for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
+            uint32_t qo, rm;
+            uint64_t cn;
+            new_group<R>(S, a, Q0, (uint32_t)g, qo, rm, cn);
+            const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
+            if (ho) continue;  // written by the merge above
+            long long pos = Q0 + S.qstart[qo];
+            for (uint32_t h = S.qfirst[qo]; h < (uint32_t)g; h++) {
+                uint32_t q2, r2;
+                uint64_t c2;
+                new_group<R>(S, a, Q0, h, q2, r2, c2);
+                pos += enc_len(c2, R);
+            }
+            put_group<R>(S, a, pos, rm, cn);
         }
     }
     __syncthreads();
@@ -585,6 +689,27 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
         unsigned long long w = 0;
         for (int b = 0; b < 8; b++) w |= (unsigned long long)S.newocc[tid * 8 + b] << (8 * b);
         a.meta_new[j0 + tid].occ = w;
+    }
+}
+
+// first group of every tile: successor search of the tile's first fingerprint
+// in the sorted groups (paper Sec. 5.4, "the starts of buffers are set using
+// successor search")
+__global__ void gqf_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t *pm, uint64_t m_limit,
+                                uint64_t N, uint32_t r, uint64_t ntiles, uint32_t *tlo)
+{
+    const uint64_t m = min((uint64_t)*pm, m_limit);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= ntiles;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q0 = t * TQ;
+        const uint64_t key = q0 >= N ? (N << r) : (q0 << r);
+        uint64_t lo = 0, hi = m;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (ufp[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        tlo[t] = (uint32_t)lo;
     }
 }
 
@@ -733,39 +858,39 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     const uint64_t M = c.max_batch ? c.max_batch : 1;
     if (M >= 0xffffffffull) return FILTER_ERR_ARG;
     const uint64_t metaB = Q.nblk * 32, remB = Q.nslots * (Q.r / 8);
-    table_bytes = 2 * (metaB + remB);
-    scratch_bytes = 0;
-    auto add = [&](uint64_t bytes) { scratch_bytes += (bytes + 255) & ~255ull; };
-    for (int k = 0; k < 4; k++) add(M * 8);  // fp_a, fp_b, fp_c, ufp
-    for (int k = 0; k < 3; k++) add(M * 4);  // idx_a, idx_b, idx_c
-    add((M + 1) * 4);                        // ustart
-    add((M + 1) * 4);                        // flags
-    add(M * 4);                              // removed
-    add((Q.ntiles * 4 + 2) * 8);             // look-back state
-    add(radix_tmp_words(M) * 4);
+    // every buffer is listed once: the same list sizes the arena (plan) and
+    // carves it (allocation)
+    uint64_t bytes = 0;
+    Arena &A = F->arena;
+    auto piece = [&](auto *&ptr, uint64_t count) {
+        using T = typename std::remove_reference<decltype(*ptr)>::type;
+        const uint64_t b = (count * sizeof(T) + 255) & ~255ull;
+        bytes += b;
+        if (!plan_only) ptr = A.take<T>(count);
+    };
+    for (int b = 0; b < 2; b++) {
+        piece(Q.meta[b], metaB);
+        piece(Q.rem[b], remB);
+    }
+    table_bytes = bytes;
     uint64_t scan_n = radix_tmp_words(M);
     if (M + 1 > scan_n) scan_n = M + 1;
-    add(scan_tmp_words(scan_n) * 8);
-    if (plan_only) return FILTER_OK;
-    Arena &A = F->arena;
-    for (int b = 0; b < 2; b++) {
-        Q.meta[b] = A.take<uint8_t>(metaB);
-        Q.rem[b] = A.take<uint8_t>(remB);
-    }
+    piece(Q.fp_a, M);
+    piece(Q.fp_b, M);
+    piece(Q.fp_c, M);
+    piece(Q.ufp, M);
+    piece(Q.idx_a, M);
+    piece(Q.idx_b, M);
+    piece(Q.idx_c, M);
+    piece(Q.ustart, M + 1);
+    piece(Q.flags, M + 1);
+    piece(Q.removed, M);
+    piece(Q.tile_state, Q.ntiles * 4 + 2);
+    piece(Q.tile_lo, Q.ntiles + 1);
+    piece(Q.radix_tmp, radix_tmp_words(M));
+    piece(F->scan_tmp, scan_tmp_words(scan_n));
+    scratch_bytes = bytes - table_bytes;
     Q.cur = 0;
-    Q.fp_a = A.take<uint64_t>(M);
-    Q.fp_b = A.take<uint64_t>(M);
-    Q.fp_c = A.take<uint64_t>(M);
-    Q.ufp = A.take<uint64_t>(M);
-    Q.idx_a = A.take<uint32_t>(M);
-    Q.idx_b = A.take<uint32_t>(M);
-    Q.idx_c = A.take<uint32_t>(M);
-    Q.ustart = A.take<uint32_t>(M + 1);
-    Q.flags = A.take<uint32_t>(M + 1);
-    Q.removed = A.take<uint32_t>(M);
-    Q.tile_state = A.take<unsigned long long>(Q.ntiles * 4 + 2);
-    Q.radix_tmp = A.take<uint32_t>(radix_tmp_words(M));
-    F->scan_tmp = A.take<uint64_t>(scan_tmp_words(scan_n));
     return FILTER_OK;
 }
 
@@ -817,6 +942,7 @@ static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, 
     a.ufp = Q.ufp;
     a.ustart = Q.ustart;
     a.pm = Q.flags + n;
+    a.tlo = Q.tile_lo;
     a.m_limit = m_limit;
     a.removed = del ? Q.removed : nullptr;
     a.ts = Q.tile_state;
@@ -832,6 +958,11 @@ static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, 
     GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
     GF_CUDA(cudaMemsetAsync(&F->ctr->gqf_end, 0xff, 8, st));  // -1
     if (!dry) GF_CUDA(cudaMemsetAsync(Q.meta[nb], 0, Q.nblk * 32, st));
+    {
+        gf::TraceScope ts_("gqf_tile_ranges", Q.ntiles + 1, st);
+        gqf_tile_ranges<<<grid_for(Q.ntiles + 1, 256, 4), 256, 0, st>>>(Q.ufp, Q.flags + n, m_limit, Q.N, Q.r,
+                                                                       Q.ntiles, Q.tile_lo);
+    }
     {
         gf::TraceScope ts_("gqf_merge_kernel", Q.nslots, st);
         if (Q.r == 8) gqf_merge_kernel<8><<<(unsigned)Q.ntiles, MT, 0, st>>>(a);

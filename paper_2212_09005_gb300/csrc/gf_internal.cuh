@@ -216,11 +216,11 @@ struct GqfState {
     uint64_t *fp_a, *fp_b, *fp_c;  // max_batch
     uint32_t *idx_a, *idx_b, *idx_c;
     uint64_t *ufp;     // unique fingerprints
-    uint32_t *ucnt;    // group sizes
     uint32_t *ustart;  // group start in the sorted batch (+1 sentinel)
     uint32_t *flags;   // max_batch + 1
     uint32_t *removed; // per group: copies removed (delete) / accepted flag
     unsigned long long *tile_state;  // ntiles * 4 (look-back)
+    uint32_t *tile_lo;               // ntiles + 1: first group of each tile
     uint32_t *radix_tmp;
 };
 

@@ -104,34 +104,38 @@ __global__ void __launch_bounds__(SCAN_T) scan_kernel(const uint32_t *in, uint32
             if (lane >= o) wi += y;
         }
         if (lane < SCAN_T / 32) s_warp[lane] = wi - w;
-        if (lane == SCAN_T / 32 - 1) {
-            // lane 7 holds the tile total; look back
-            uint32_t total = wi;
-            uint32_t prefix = 0;
-            if (tile == 0) {
-                atomicExch(&st[0], (2ull << 32) | total);
-            } else {
-                atomicExch(&st[tile], (1ull << 32) | total);
-                int64_t j = (int64_t)tile - 1;
-                uint32_t spins = 0;
-                while (j >= 0) {
-                    unsigned long long w2 = ld_volatile(&st[j]);
-                    uint32_t flag = (uint32_t)(w2 >> 32);
-                    if (flag == 0) {
-                        if (++spins > SPIN_LIMIT) {
-                            atomicOr(status, ST_TIMEOUT);
-                            break;
-                        }
-                        continue;
-                    }
-                    prefix += (uint32_t)w2;
-                    if (flag == 2) break;
-                    j--;
+        // tile total sits in lane 7; look back over 32 predecessors at a time
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, SCAN_T / 32 - 1);
+        uint32_t prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) atomicExch(&st[0], (2ull << 32) | total);
+        } else {
+            if (lane == 0) atomicExch(&st[tile], (1ull << 32) | total);
+            int64_t jtop = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            while (true) {
+                const int64_t j = jtop - lane;
+                unsigned long long w2 = 2ull << 32;  // before tile 0: inclusive prefix 0
+                if (j >= 0) {
+                    w2 = ld_volatile(&st[j]);
+                    while ((w2 >> 32) == 0 && ++spins <= SPIN_LIMIT) w2 = ld_volatile(&st[j]);
                 }
-                atomicExch(&st[tile], (2ull << 32) | (uint32_t)(prefix + total));
+                const uint32_t flag = (uint32_t)(w2 >> 32);
+                if (__ballot_sync(0xffffffffu, flag == 0)) {
+                    if (lane == 0) atomicOr(status, ST_TIMEOUT);
+                    break;
+                }
+                const unsigned incl_mask = __ballot_sync(0xffffffffu, flag == 2);
+                const int L = incl_mask ? __ffs(incl_mask) - 1 : 31;
+                uint32_t part = (lane <= L) ? (uint32_t)w2 : 0u;
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                prefix += part;
+                if (incl_mask) break;
+                jtop -= 32;
             }
-            s_prefix = prefix;
+            if (lane == 0) atomicExch(&st[tile], (2ull << 32) | (uint32_t)(prefix + total));
         }
+        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
     const uint32_t add = s_prefix + s_warp[warp] + (incl - sum);
@@ -219,12 +223,18 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
     uint64_t key[RS_I];
     uint32_t val[RS_I];
     uint16_t rank[RS_I];
+    // all loads first, so that the tile's 16 keys per thread are in flight together
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         bool ok = i < n;
-        key[r] = ok ? kin[i] : 0;
-        if (VALS) val[r] = ok ? vin[i] : 0;
+        key[r] = ok ? __ldcs(kin + i) : 0;
+        if (VALS) val[r] = ok ? __ldcs(vin + i) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
+        bool ok = i < n;
         uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t b = (d < 256) ? wcnt[warp * 256 + d] : 0;

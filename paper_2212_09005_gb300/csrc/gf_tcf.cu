@@ -21,6 +21,8 @@
 // Point mode (Alg. 1): one thread per key; the tag goes into the first EMPTY
 // or TOMBSTONE slot by an atomic compare-and-swap, retried a bounded number of
 // times; deletes swap the tag for TOMBSTONE.
+#include <type_traits>
+
 #include "gf_internal.cuh"
 
 namespace gf {
@@ -384,6 +386,43 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
         const uint32_t f0 = fill[b];
         Blk<F> blk;
         blk.load(blocks, b);
+        if (e - s <= 8) {
+            // small segment: sort the candidates, then each takes the first
+            // remaining copy of its tag; the block stays sorted
+            uint64_t r8[8];
+            int c = 0;
+            for (uint32_t j = s; j < e; j++) {
+                uint64_t v = rec[j];
+                int q = c++;
+                while (q > 0 && r8[q - 1] > v) {
+                    r8[q] = r8[q - 1];
+                    q--;
+                }
+                r8[q] = v;
+            }
+            uint32_t gone = 0;
+            for (int q = 0; q < c; q++) {
+                const uint32_t t = (uint32_t)(r8[q] >> 32);
+                int hit = -1;
+#pragma unroll
+                for (int p = 0; p < B; p++)
+                    if (hit < 0 && p < (int)f0 && !((gone >> p) & 1u) && blk.tag(p) == t) hit = p;
+                if (hit >= 0) gone |= 1u << hit;
+                else pend32[atomicAdd(npend, 1u)] = (uint32_t)r8[q];
+            }
+            if (gone) {
+                uint32_t t_out[B];
+                int o = 0;
+#pragma unroll
+                for (int p = 0; p < B; p++)
+                    if (p < (int)f0 && !((gone >> p) & 1u)) t_out[o++] = blk.tag(p);
+                for (int p = o; p < B; p++) t_out[p] = 0;
+                blk.pack(t_out);
+                blk.store(blocks, b);
+                fill[b] = (uint8_t)o;
+            }
+            continue;
+        }
         uint32_t tags[B];
 #pragma unroll
         for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
@@ -654,31 +693,29 @@ int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     const uint64_t M = c.max_batch ? c.max_batch : 1;
     if (M > 0xffffffffull) return FILTER_ERR_ARG;
     const uint64_t groups = (T.G.nb > T.G.nbk ? T.G.nb : T.G.nbk) + 1;
-    table_bytes = T.G.nb * 32 + T.G.nbk * BK_W * 8 + T.G.nb;
-    scratch_bytes = 0;
-    auto add = [&](uint64_t bytes) { scratch_bytes += (bytes + 255) & ~255ull; };
-    add(groups * 4);
-    add(groups * 4);
-    add(M * 8);
-    add(M * 8);
-    add(M * 4);
-    add(M * 8);
-    add(M * 4);
-    add(scan_tmp_words(groups) * 8);
-    if (plan_only) return FILTER_OK;
+    // every buffer is listed once: the same list sizes the arena (plan) and
+    // carves it (allocation); the table comes first
+    uint64_t bytes = 0;
     Arena &A = F->arena;
-    // table memory comes first in the arena
-    T.blocks = A.take<uint8_t>(T.G.nb * 32);
-    T.bk = A.take<uint64_t>(T.G.nbk * BK_W);
-    T.fill = A.take<uint8_t>(T.G.nb);
-    T.cnt = A.take<uint32_t>(groups);
-    T.off = A.take<uint32_t>(groups);
-    T.rec = A.take<uint64_t>(M);
-    T.rec2 = A.take<uint64_t>(M);
-    T.pend0 = A.take<uint32_t>(M);
-    T.pend1 = A.take<uint64_t>(M);
-    T.pend2 = A.take<uint32_t>(M);
-    F->scan_tmp = A.take<uint64_t>(scan_tmp_words(groups));
+    auto piece = [&](auto *&ptr, uint64_t count) {
+        using T_ = typename std::remove_reference<decltype(*ptr)>::type;
+        const uint64_t b = (count * sizeof(T_) + 255) & ~255ull;
+        bytes += b;
+        if (!plan_only) ptr = A.take<T_>(count);
+    };
+    piece(T.blocks, T.G.nb * 32);
+    piece(T.bk, T.G.nbk * BK_W);
+    piece(T.fill, T.G.nb);
+    table_bytes = bytes;
+    piece(T.cnt, groups);
+    piece(T.off, groups);
+    piece(T.rec, M);
+    piece(T.rec2, M);
+    piece(T.pend0, M);
+    piece(T.pend1, M);
+    piece(T.pend2, M);
+    piece(F->scan_tmp, scan_tmp_words(groups));
+    scratch_bytes = bytes - table_bytes;
     return FILTER_OK;
 }
 
