@@ -69,7 +69,7 @@ typedef struct filter_config {
     uint32_t tag_bits;    /* TCF: f in {8, 16}; GQF: r in {8, 16} */
     uint32_t mode;        /* TCF: FILTER_MODE_BULK or FILTER_MODE_POINT; GQF: 0 */
     uint64_t hash_seed;   /* xor-ed into keys before hashing */
-    uint64_t max_batch;   /* largest n of one call; sizes the scratch memory */
+    uint64_t max_batch;   /* largest n of one call; sizes the scratch memory (GQF: < 2^30) */
 } filter_config;
 
 typedef struct filter_stats {

@@ -856,7 +856,7 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     Q.H.mask = Q.p >= 64 ? ~0ull : ((1ull << Q.p) - 1ull);
     Q.H.seed = c.hash_seed & Q.H.mask;
     const uint64_t M = c.max_batch ? c.max_batch : 1;
-    if (M >= 0xffffffffull) return FILTER_ERR_ARG;
+    if (M >= (1ull << 30)) return FILTER_ERR_ARG;  // 30-bit counts in the sort and group arrays
     const uint64_t metaB = Q.nblk * 32, remB = Q.nslots * (Q.r / 8);
     // every buffer is listed once: the same list sizes the arena (plan) and
     // carves it (allocation)

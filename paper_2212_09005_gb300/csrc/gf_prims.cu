@@ -163,40 +163,49 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint64_t 
 }
 
 // ---------------------------------------------------------------------------
-// LSD radix sort, 8-bit digits. Per pass: per-tile digit histograms, one
-// exclusive scan over the digit-major count matrix, then a stable scatter that
-// ranks each tile's keys with warp match and stages them in shared memory so
-// that the global writes are runs of consecutive addresses.
+// LSD radix sort with digits of up to 9 bits (the fewest passes that cover the
+// key bits, e.g. 4 x 9 bits for 36-bit fingerprints). Per pass: per-tile digit
+// histograms, one exclusive scan over the digit-major count matrix, then a
+// stable scatter that ranks each tile's keys with warp match and stages them
+// in shared memory so that the global writes are runs of consecutive
+// addresses.
 // ---------------------------------------------------------------------------
 static constexpr int RS_T = 256;
 static constexpr int RS_I = 16;
 static constexpr int RS_TILE = RS_T * RS_I;
 static constexpr int RS_WARPS = RS_T / 32;
+static constexpr int RS_MAXB = 512;  // buckets of the widest digit
 
 size_t radix_tmp_words(uint64_t n)
 {
     uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
-    return tiles * 256 + 1;
+    return tiles * RS_MAXB + 1;
 }
 
-__global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *keys, uint64_t n, uint32_t shift,
-                                                uint32_t *counts, uint64_t ntiles)
+__global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ keys, uint64_t n, uint32_t shift,
+                                                uint32_t nb, uint32_t *counts, uint64_t ntiles)
 {
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
+    __shared__ uint32_t h[RS_MAXB];
+    for (uint32_t d = threadIdx.x; d < nb; d += RS_T) h[d] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
-#pragma unroll 4
-    for (int k = 0; k < RS_I; k++) {
-        uint64_t i = base + (uint64_t)k * RS_T + threadIdx.x;
-        uint32_t d = (i < n) ? ((uint32_t)(keys[i] >> shift) & 255u) : 256u;
-        // aggregate equal digits within the warp first (skewed inputs)
+    uint64_t k[RS_I];
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
+        k[r] = (i < n) ? __ldcs(keys + i) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
+        uint32_t d = (i < n) ? ((uint32_t)(k[r] >> shift) & (nb - 1)) : 0xffffu;
+        // equal digits of a warp are counted once (skewed multisets)
         unsigned peers = __match_any_sync(0xffffffffu, d);
         int leader = __ffs(peers) - 1;
-        if (d < 256u && (int)(threadIdx.x & 31) == leader) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        if (d != 0xffffu && (int)(threadIdx.x & 31) == leader) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
-    counts[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    for (uint32_t d = threadIdx.x; d < nb; d += RS_T) counts[(uint64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
 template <bool VALS>
@@ -204,18 +213,19 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
                                                    uint64_t *__restrict__ kout,
                                                    const uint32_t *__restrict__ vin,
                                                    uint32_t *__restrict__ vout, uint64_t n,
-                                                   uint32_t shift, const uint32_t *__restrict__ offs,
+                                                   uint32_t shift, uint32_t nb, const uint32_t *__restrict__ offs,
                                                    uint64_t ntiles)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem);              // [8][256]
-    uint32_t *dstart = wcnt + RS_WARPS * 256;                          // [256]
-    uint32_t *dglob = dstart + 256;                                    // [256]
-    uint64_t *skeys = reinterpret_cast<uint64_t *>(dglob + 256);       // [4096]
+    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem);              // [8][512]
+    uint32_t *dstart = wcnt + RS_WARPS * RS_MAXB;                      // [512]
+    uint32_t *dglob = dstart + RS_MAXB;                                // [512]
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(dglob + RS_MAXB);   // [4096]
     uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + RS_TILE);   // [4096]
+    __shared__ uint32_t s_w[RS_WARPS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * 256; i += RS_T) wcnt[i] = 0;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB; i += RS_T) wcnt[i] = 0;
     __syncthreads();
 
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
@@ -235,47 +245,56 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
     for (int r = 0; r < RS_I; r++) {
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         bool ok = i < n;
-        uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & 255u) : 256u;
+        uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & (nb - 1)) : 0xffffu;
         unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t b = (d < 256) ? wcnt[warp * 256 + d] : 0;
+        uint32_t b = ok ? wcnt[warp * RS_MAXB + d] : 0;
         __syncwarp();
-        if (d < 256 && lane == __ffs(peers) - 1) wcnt[warp * 256 + d] = b + __popc(peers);
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp * RS_MAXB + d] = b + __popc(peers);
         __syncwarp();
         rank[r] = (uint16_t)(b + __popc(peers & lt));
     }
     __syncthreads();
     {
-        // per digit: warp-exclusive offsets and the tile total
-        const int d = threadIdx.x;
-        uint32_t acc = 0;
+        // per digit (two per thread): warp-exclusive offsets and tile totals,
+        // then an exclusive scan of the totals in digit order
+        uint32_t tot[2] = {0, 0};
 #pragma unroll
-        for (int w = 0; w < RS_WARPS; w++) {
-            uint32_t c = wcnt[w * 256 + d];
-            wcnt[w * 256 + d] = acc;
-            acc += c;
+        for (int h = 0; h < 2; h++) {
+            const uint32_t d = 2 * threadIdx.x + h;
+            if (d < nb) {
+                uint32_t acc = 0;
+#pragma unroll
+                for (int w = 0; w < RS_WARPS; w++) {
+                    uint32_t c = wcnt[w * RS_MAXB + d];
+                    wcnt[w * RS_MAXB + d] = acc;
+                    acc += c;
+                }
+                tot[h] = acc;
+                dglob[d] = offs[(uint64_t)d * ntiles + blockIdx.x];
+            }
         }
-        // exclusive scan of the totals across digits (256 threads)
-        uint32_t incl = acc;
+        const uint32_t pair = tot[0] + tot[1];
+        uint32_t incl = pair;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        __shared__ uint32_t s_w[RS_WARPS];
         if (lane == 31) s_w[warp] = incl;
         __syncthreads();
         uint32_t wpre = 0;
         for (int w = 0; w < warp; w++) wpre += s_w[w];
-        dstart[d] = wpre + incl - acc;
-        dglob[d] = offs[(uint64_t)d * ntiles + blockIdx.x];
+        const uint32_t ex = wpre + incl - pair;
+        if (2 * threadIdx.x < nb) dstart[2 * threadIdx.x] = ex;
+        if (2 * threadIdx.x + 1 < nb) dstart[2 * threadIdx.x + 1] = ex + tot[0];
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         if (i < n) {
-            uint32_t d = (uint32_t)(key[r] >> shift) & 255u;
-            uint32_t pos = dstart[d] + wcnt[warp * 256 + d] + rank[r];
+            uint32_t d = (uint32_t)(key[r] >> shift) & (nb - 1);
+            uint32_t pos = dstart[d] + wcnt[warp * RS_MAXB + d] + rank[r];
             skeys[pos] = key[r];
             if (VALS) svals[pos] = val[r];
         }
@@ -284,14 +303,14 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
     const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)RS_TILE ? (n - base) : RS_TILE);
     for (uint32_t k = threadIdx.x; k < cnt; k += RS_T) {
         uint64_t kk = skeys[k];
-        uint32_t d = (uint32_t)(kk >> shift) & 255u;
+        uint32_t d = (uint32_t)(kk >> shift) & (nb - 1);
         uint64_t g = (uint64_t)dglob[d] + (k - dstart[d]);
-        kout[g] = kk;
-        if (VALS) vout[g] = svals[k];
+        __stcs(kout + g, kk);
+        if (VALS) __stcs(vout + g, svals[k]);
     }
 }
 
-static constexpr size_t RS_SMEM = (RS_WARPS * 256 + 512) * 4 + RS_TILE * 8 + RS_TILE * 4;
+static constexpr size_t RS_SMEM = (RS_WARPS * RS_MAXB + 2 * RS_MAXB) * 4 + RS_TILE * 8 + RS_TILE * 4;
 
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt, uint64_t n,
@@ -306,7 +325,7 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         attr_done = true;
     }
     const bool vals = vals_in != nullptr;
-    uint32_t npass = (bits + 7) / 8;
+    const uint32_t npass = (bits + 8) / 9;  // digits of at most 9 bits
     if (npass == 0) {
         cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st);
         if (vals) cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, st);
@@ -315,25 +334,29 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
     const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const uint64_t *ksrc = keys_in;
     const uint32_t *vsrc = vals_in;
+    uint32_t shift = 0;
     for (uint32_t p = 0; p < npass; p++) {
+        // split the bits as evenly as possible: the first passes take the extra bit
+        const uint32_t db = bits / npass + (p < bits % npass ? 1u : 0u);
+        const uint32_t nb = 1u << db;
         bool to_out = ((npass - 1 - p) % 2) == 0;
         uint64_t *kdst = to_out ? keys_out : keys_alt;
         uint32_t *vdst = to_out ? vals_out : vals_alt;
-        uint32_t shift = 8 * p;
         {
             TraceScope ts_("rs_hist", n, st);
-            rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, tmp, ntiles);
+            rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles);
         }
-        exclusive_scan_u32(tmp, tmp, ntiles * 256, scan_tmp, ctr, st);
+        exclusive_scan_u32(tmp, tmp, ntiles * nb, scan_tmp, ctr, st);
         TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
         if (vals)
-            rs_scatter<true><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, vsrc, vdst, n, shift,
+            rs_scatter<true><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb,
                                                                      tmp, ntiles);
         else
             rs_scatter<false><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, nullptr, nullptr, n,
-                                                                      shift, tmp, ntiles);
+                                                                      shift, nb, tmp, ntiles);
         ksrc = kdst;
         vsrc = vdst;
+        shift += db;
     }
 }
 
