@@ -714,6 +714,272 @@ __global__ void gqf_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t
 }
 
 // ---------------------------------------------------------------------------
+// In-place bulk delete, the paper's even-odd regions (Sec. 7 with Sec. 5.4):
+// removing copies from a run only shifts the rest of its cluster left, never
+// past a home slot, so a delete is local to its cluster. One thread per
+// region of RQ quotients applies the region's groups largest first; even
+// regions run first, then odd ones. A read-only pre-check makes sure that
+// every affected cluster ends before the region after next, so that two
+// threads of a phase never touch the same slots or metadata words.
+// ---------------------------------------------------------------------------
+static constexpr long long RQ = 4096;  // quotients per delete region (a multiple of 64)
+
+struct GView {
+    Meta *meta;
+    uint8_t *rem;
+    long long N, nslots, nblk;
+};
+
+__device__ __forceinline__ bool gv_occ(const GView &g, long long y) { return (g.meta[y >> 6].occ >> (y & 63)) & 1ull; }
+__device__ __forceinline__ void gv_rend_put(const GView &g, long long i, bool v)
+{
+    unsigned long long &w = g.meta[i >> 6].rend;
+    if (v) w |= 1ull << (i & 63);
+    else w &= ~(1ull << (i & 63));
+}
+
+// first runend at or after slot i, or -1
+__device__ long long gv_next_runend(const GView &g, long long i)
+{
+    long long w = i >> 6;
+    if (i < 0 || w >= g.nblk) return -1;
+    unsigned long long bits = g.meta[w].rend & (~0ull << (i & 63));
+    while (!bits) {
+        if (++w >= g.nblk) return -1;
+        bits = g.meta[w].rend;
+    }
+    return 64 * w + __ffsll((long long)bits) - 1;
+}
+
+// last runend in [lo, hi], or -1
+__device__ long long gv_prev_runend(const GView &g, long long hi, long long lo)
+{
+    if (hi < lo) return -1;
+    long long w = hi >> 6;
+    const unsigned hb = (unsigned)(hi & 63);
+    unsigned long long bits = g.meta[w].rend & (hb == 63 ? ~0ull : ((1ull << (hb + 1)) - 1ull));
+    while (true) {
+        if (64 * w <= lo) bits &= ~0ull << (lo - 64 * w);
+        if (bits) return 64 * w + 63 - __clzll((long long)bits);
+        if (64 * w <= lo) return -1;
+        bits = g.meta[--w].rend;
+    }
+}
+
+// smallest occupied quotient in (y, lim], or -1
+__device__ long long gv_next_occ(const GView &g, long long y, long long lim)
+{
+    if (lim >= g.N) lim = g.N - 1;
+    const long long z = y + 1;
+    if (z > lim) return -1;
+    long long w = z >> 6;
+    unsigned long long bits = g.meta[w].occ & (~0ull << (z & 63));
+    while (true) {
+        if (bits) {
+            long long q = 64 * w + __ffsll((long long)bits) - 1;
+            return q <= lim ? q : -1;
+        }
+        if (64 * (w + 1) > lim) return -1;
+        bits = g.meta[++w].occ;
+    }
+}
+
+// end of the run of an occupied quotient y: offset of its block, then select
+__device__ long long gv_runend_of(const GView &g, long long y)
+{
+    const long long j = y >> 6;
+    const long long base = 64 * j + (long long)g.meta[j].off;
+    const unsigned k = (unsigned)(y & 63);
+    const unsigned long long upto = (k == 63) ? ~0ull : ((1ull << (k + 1)) - 1ull);
+    int d = __popcll(g.meta[j].occ & upto & ~1ull);
+    if (d == 0) return base;
+    long long w = base >> 6;
+    const unsigned bsh = (unsigned)(base & 63);
+    unsigned long long bits = (bsh == 63) ? 0ull : (g.meta[w].rend & (~0ull << (bsh + 1)));
+    while (true) {
+        int pc = __popcll(bits);
+        if (pc >= d) {
+            for (int t = 1; t < d; t++) bits &= bits - 1;
+            return 64 * w + __ffsll((long long)bits) - 1;
+        }
+        d -= pc;
+        if (++w >= g.nblk) return -1;
+        bits = g.meta[w].rend;
+    }
+}
+
+// offsets of the blocks j with 64j in [y, ylim) whose largest occupied
+// quotient <= 64j is y, given y's new and old run ends
+__device__ __forceinline__ void gv_fix_offsets(const GView &g, long long y, long long ylim, long long new_end,
+                                               long long old_end)
+{
+    long long jlo = (y + 63) >> 6;
+    long long hi = ylim - 1 < old_end ? ylim - 1 : old_end;
+    if (hi < 0) return;
+    long long jhi = hi >> 6;
+    if (jhi >= g.nblk) jhi = g.nblk - 1;
+    for (long long j = jlo; j <= jhi; j++) {
+        long long o = new_end - 64 * j;
+        g.meta[j].off = (unsigned)(o > 0 ? o : 0);
+    }
+}
+
+// remove min(c, d) copies of fingerprint fp; returns the number removed
+template <int R>
+__device__ uint64_t gv_delete(const GView &g, uint64_t fp, uint64_t d, unsigned long long *status)
+{
+    const long long x = (long long)(fp >> R);
+    const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
+    if (x >= g.N || !gv_occ(g, x)) return 0;
+    const long long e = gv_runend_of(g, x);
+    if (e < 0) {
+        atomicOr(status, ST_INTERNAL);
+        return 0;
+    }
+    const long long pr = gv_prev_runend(g, e - 1, x);
+    const long long s = pr >= 0 ? pr + 1 : x;
+    long long gpos = -1;
+    uint32_t glen = 0;
+    uint64_t c = 0;
+    for (long long p = s; p <= e;) {
+        const uint32_t val = rd_slot<R>(g.rem, (uint64_t)p);
+        uint64_t cc = 1;
+        uint32_t len = 1;
+        if (p + 2 <= e && rd_slot<R>(g.rem, (uint64_t)(p + 1)) == val) {
+            uint32_t nd = rd_slot<R>(g.rem, (uint64_t)(p + 2));
+            if (p + 2 + (long long)nd > e) nd = (uint32_t)(e - p - 2);
+            uint64_t acc = 0;
+            for (uint32_t t = 0; t < nd; t++) acc = (acc << R) | rd_slot<R>(g.rem, (uint64_t)(p + 3 + t));
+            cc = acc + 2;
+            len = 3 + nd;
+        }
+        if (val == v) {
+            gpos = p;
+            glen = len;
+            c = cc;
+            break;
+        }
+        if (val > v) break;
+        p += len;
+    }
+    if (gpos < 0) return 0;
+    const uint64_t rm = c < d ? c : d;
+    const uint64_t c2 = c - rm;
+    const uint32_t nlen = c2 ? enc_len(c2, R) : 0u;
+    if (c2) {
+        long long q = gpos;
+        wr_slot<R>(g.rem, (uint64_t)q++, v);
+        if (c2 > 1) {
+            const uint64_t xx = c2 - 2;
+            const uint32_t nd = ndig(xx, R);
+            wr_slot<R>(g.rem, (uint64_t)q++, v);
+            wr_slot<R>(g.rem, (uint64_t)q++, nd);
+            for (uint32_t t = 0; t < nd; t++)
+                wr_slot<R>(g.rem, (uint64_t)q++, (uint32_t)((xx >> (R * (nd - 1 - t))) & ((1u << R) - 1u)));
+        }
+    }
+    const long long delta = (long long)glen - (long long)nlen;
+    if (delta == 0) return rm;
+    // the rest of run x moves left by delta
+    for (long long q = gpos + glen; q <= e; q++) wr_slot<R>(g.rem, (uint64_t)(q - delta), rd_slot<R>(g.rem, (uint64_t)q));
+    const bool empty = (e - s + 1) == delta;
+    for (long long q = e - delta + 1; q <= e; q++) wr_slot<R>(g.rem, (uint64_t)q, 0u);  // vacated by run x
+    gv_rend_put(g, e, false);
+    long long new_prev_end;
+    if (!empty) {
+        gv_rend_put(g, e - delta, true);
+        new_prev_end = e - delta;
+    } else {
+        g.meta[x >> 6].occ &= ~(1ull << (x & 63));
+        new_prev_end = (s > x) ? s - 1 : x - 1;  // the run before x (any end < x when s == x)
+    }
+    long long old_prev_end = e;
+    long long y = x, y_new = new_prev_end, y_old = e;
+    // following runs of the cluster move to max(home, previous end + 1)
+    while (true) {
+        const long long yn = gv_next_occ(g, y, old_prev_end + 1);
+        gv_fix_offsets(g, y, yn >= 0 ? yn : (1ll << 62), y_new, y_old);
+        if (yn < 0) break;
+        const long long os = yn > old_prev_end + 1 ? yn : old_prev_end + 1;
+        const long long ns = yn > new_prev_end + 1 ? yn : new_prev_end + 1;
+        if (ns == os) break;
+        const long long oe = gv_next_runend(g, os);
+        if (oe < 0) {
+            atomicOr(status, ST_INTERNAL);
+            break;
+        }
+        const long long len = oe - os + 1;
+        for (long long q = 0; q < len; q++) wr_slot<R>(g.rem, (uint64_t)(ns + q), rd_slot<R>(g.rem, (uint64_t)(os + q)));
+        for (long long q = (ns + len > os ? ns + len : os); q <= oe; q++) wr_slot<R>(g.rem, (uint64_t)q, 0u);  // vacated
+        gv_rend_put(g, oe, false);
+        gv_rend_put(g, ns + len - 1, true);
+        old_prev_end = oe;
+        new_prev_end = ns + len - 1;
+        y = yn;
+        y_new = new_prev_end;
+        y_old = oe;
+    }
+    return rm;
+}
+
+// first group of every delete region (successor search)
+__global__ void gqf_region_ranges(const uint64_t *__restrict__ ufp, const uint32_t *pm, uint64_t N, uint32_t r,
+                                  uint64_t nreg, uint32_t *rlo)
+{
+    const uint64_t m = *pm;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= nreg;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t q0 = t * (uint64_t)RQ;
+        const uint64_t key = q0 >= N ? (N << r) : (q0 << r);
+        uint64_t lo = 0, hi = m;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (ufp[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        rlo[t] = (uint32_t)lo;
+    }
+}
+
+// read-only: does the cluster tail of every group end before the region after next?
+template <int R>
+__global__ void gqf_delete_precheck(GView g, const uint64_t *__restrict__ ufp, const uint32_t *pm,
+                                    unsigned long long *bad)
+{
+    const uint64_t m = *pm;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
+        const long long x = (long long)(ufp[i] >> R);
+        if (x >= g.N || !gv_occ(g, x)) continue;
+        long long limit = (x / RQ + 2) * RQ;
+        if (limit > g.nslots) limit = g.nslots;
+        long long prev = gv_runend_of(g, x), y = x;
+        while (prev >= 0 && prev < limit) {
+            const long long yn = gv_next_occ(g, y, prev + 1);
+            if (yn < 0) break;
+            prev = gv_next_runend(g, prev + 1);
+            y = yn;
+        }
+        if (prev < 0 || prev >= limit) atomicExch(bad, 1ull);
+    }
+}
+
+template <int R>
+__global__ void gqf_delete_phase(GView g, const uint64_t *__restrict__ ufp, const uint32_t *__restrict__ ustart,
+                                 const uint32_t *__restrict__ rlo, uint64_t nreg, int phase, uint32_t *removed,
+                                 unsigned long long *status)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t reg = 2 * i + (uint64_t)phase;
+        if (reg >= nreg) return;
+        for (uint32_t k = rlo[reg + 1]; k > rlo[reg]; k--) {
+            const uint32_t gi = k - 1;
+            const uint64_t rmv = gv_delete<R>(g, ufp[gi], ustart[gi + 1] - ustart[gi], status);
+            if (removed) removed[gi] = (uint32_t)rmv;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // per-key status after a batch
 // ---------------------------------------------------------------------------
 // pos: scanned group-start flags (pos[i + 1] - 1 = group of sorted element i)
@@ -886,7 +1152,7 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     piece(Q.flags, M + 1);
     piece(Q.removed, M);
     piece(Q.tile_state, Q.ntiles * 4 + 2);
-    piece(Q.tile_lo, Q.ntiles + 1);
+    piece(Q.tile_lo, (Q.ntiles > (Q.N + RQ - 1) / RQ ? Q.ntiles : (Q.N + RQ - 1) / RQ) + 1);
     piece(Q.radix_tmp, radix_tmp_words(M));
     piece(F->scan_tmp, scan_tmp_words(scan_n));
     scratch_bytes = bytes - table_bytes;
@@ -1030,9 +1296,46 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
     GqfState &Q = F->gqf;
     uint32_t *sidx = nullptr;
     gqf_prepare(F, keys, n, status != nullptr, st, &sidx);
-    int rc = gqf_merge(F, n, ~0ull, 1, 0, st);
-    if (rc) return rc;
-    Q.cur ^= 1;
+    int rc = FILTER_OK;
+    // small batches: in place, cluster by cluster; large ones: full merge
+    uint32_t m = 0;
+    if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
+    bool done = false;
+    if ((uint64_t)m * 4 <= Q.nslots) {
+        const uint64_t nreg = (Q.N + RQ - 1) / RQ;
+        GView g{reinterpret_cast<Meta *>(Q.meta[Q.cur]), Q.rem[Q.cur], (long long)Q.N, (long long)Q.nslots,
+                (long long)Q.nblk};
+        {
+            gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);
+            gqf_region_ranges<<<grid_for(nreg + 1, 256, 4), 256, 0, st>>>(Q.ufp, Q.flags + n, Q.N, Q.r, nreg, Q.tile_lo);
+        }
+        GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
+        {
+            gf::TraceScope ts_("gqf_delete_precheck", m, st);
+            if (Q.r == 8) gqf_delete_precheck<8><<<grid_for(m, 256, 8), 256, 0, st>>>(g, Q.ufp, Q.flags + n, &F->ctr->overflow);
+            else gqf_delete_precheck<16><<<grid_for(m, 256, 8), 256, 0, st>>>(g, Q.ufp, Q.flags + n, &F->ctr->overflow);
+        }
+        unsigned long long bad = 0;
+        if ((rc = read_dev(&F->ctr->overflow, &bad, st))) return rc;
+        if (!bad) {
+            const uint64_t half = (nreg + 1) / 2;
+            for (int ph = 0; ph < 2; ph++) {
+                gf::TraceScope ts_("gqf_delete_phase", half, st);
+                if (Q.r == 8)
+                    gqf_delete_phase<8><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, ph,
+                                                                                status ? Q.removed : nullptr, &F->ctr->status);
+                else
+                    gqf_delete_phase<16><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, ph,
+                                                                                 status ? Q.removed : nullptr, &F->ctr->status);
+            }
+            GF_CUDA(cudaGetLastError());
+            done = true;
+        }
+    }
+    if (!done) {
+        if ((rc = gqf_merge(F, n, ~0ull, 1, 0, st))) return rc;
+        Q.cur ^= 1;
+    }
     if (status) {
         {
             gf::TraceScope ts_("gqf_status_kernel", n, st);

@@ -92,7 +92,7 @@ extern "C" int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_s
     Q.flags = A.take<uint32_t>(M + 1);
     Q.removed = A.take<uint32_t>(M);
     Q.tile_state = A.take<unsigned long long>(Q.ntiles * 4 + 2);
-    Q.tile_lo = A.take<uint32_t>(Q.ntiles + 1);
+    Q.tile_lo = A.take<uint32_t>(Q.ntiles + 1);  // inserts only: the delete regions are never used here
     Q.radix_tmp = A.take<uint32_t>(radix_tmp_words(M));
     uint64_t scan_n = radix_tmp_words(M);
     if (M + 1 > scan_n) scan_n = M + 1;

@@ -192,3 +192,21 @@ def test_counting_config_2_28_zipf(gf, oracle):
     assert d is None, d
     del G
     torch.cuda.empty_cache()
+
+
+def test_inplace_delete_matches_oracle(gf, oracle):
+    """Deletes of a small fraction of the table take the in-place cluster path
+    (even-odd regions); image and statuses must equal the oracle's."""
+    w = W.gqf_uniform_workload(20, seed=1)
+    ins = w["insert"]
+    dele1 = np.concatenate([ins[::20], ins[:1000:20], W.uniform_keys(77, 3000)])  # repeats, absent keys
+    dele2 = np.concatenate([ins[1::37], ins[1::37]])
+    run_batches(gf, oracle, 20, 8, seed=1, batches=[ins], deletes=[dele1, dele2])
+
+
+def test_inplace_delete_small_tables_and_counters(gf, oracle):
+    q = 11
+    keys = W.uniform_keys(78, 1500)
+    ins = np.concatenate([keys, np.repeat(keys[:30], 300), np.repeat(keys[30:40], 3)])  # multi-digit counters
+    dele = [np.concatenate([np.repeat(keys[:30], 290), keys[30:35]]), np.repeat(keys[:10], 20), keys[100:130]]
+    run_batches(gf, oracle, q, 8, seed=4, batches=[ins], deletes=dele)
