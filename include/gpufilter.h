@@ -22,7 +22,7 @@
  *   bits 44.. of h (f bits, 0 and 1 moved to 2 and 3), b2 = b1 xor g(tag).
  *   nb = 2^log2_slots / B blocks of 32 bytes (B = 256 / f tags). Backing
  *   table: nbk buckets of 8 uint64 entries (min(b1,b2) << f | tag), nbk =
- *   max(8, ceil(ceil(N/100) / 8)) (Sec. 4.2 "backing table").
+ *   max(8, ceil(ceil(N/100) / 8)) (Sec. 4.1, "backing table").
  *   GQF (paper Sec. 5): p = q + r, fp = mix_p(fold_p(key) ^ seed mod 2^p),
  *   quotient = fp >> r, remainder = fp mod 2^r. N = 2^q home slots plus a
  *   tail of S = max(64, min(N, roundup64(1072 q))) slots. Per 64-slot block a
@@ -100,11 +100,11 @@ int filter_clear(filter_t *f, void *stream);
 /*
  * filter_insert: insert n keys (a multiset: duplicates are counted, Sec. 5 of
  * the paper, and stored as repeated tags by the TCF).
- *  TCF bulk mode: the phased deterministic batch insert (Sec. 4.2 shortcut,
- *  Sec. 4 two choices, Sec. 4.2 backing table, Sec. 4.3 sorted blocks).
+ *  TCF bulk mode: the phased deterministic batch insert (Sec. 4.1 shortcut,
+ *  Sec. 4 two choices, Sec. 4.1 backing table, Sec. 4.2 sorted blocks).
  *  TCF point mode: each key independently, Alg. 1 (CAS into an empty slot).
- *  GQF: sort, reduce to <fingerprint, count> (Sec. 5.5), merge the groups
- *  into the runs (Sec. 5.4). If the table cannot hold every group, the
+ *  GQF: sort, reduce to <fingerprint, count> (Sec. 5.4), merge the groups
+ *  into the runs (Sec. 5.3). If the table cannot hold every group, the
  *  longest prefix of the sorted groups that fits is kept.
  * d_keys: n uint64. d_status: NULL or n uint8 (FILTER_KEY_*). n <= max_batch.
  */
@@ -121,7 +121,7 @@ int filter_query(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_fou
                  void *stream);
 
 /*
- * filter_remove: delete one copy per key (Sec. 7 of the paper). Keys without a
+ * filter_remove: delete one copy per key (Sec. 6.4 of the paper). Keys without a
  * stored copy get FILTER_KEY_NOT_FOUND (for the TCF, deleting a key that was
  * never inserted may remove another key's aliasing fingerprint, as in every
  * fingerprint filter). n <= max_batch.

@@ -33,13 +33,13 @@
  *  12 zero bytes}, all blocks first, then the remainders (r/8 bytes each,
  *  little-endian).
  *
- *  Bulk insert (Sec. 5.4, 5.5): fingerprints are sorted and reduced to
+ *  Bulk insert (Sec. 5.3, 5.4): fingerprints are sorted and reduced to
  *  <fp, count> groups, which are inserted in ascending order by shifting the
  *  following runs right. If a group does not fit before the end of the tail,
  *  it and every later group of the batch are rejected (status 1), which keeps
  *  the longest prefix of the sorted batch that fits (R).
  *
- *  Bulk delete (Sec. 7): groups are removed in descending order ("larger
+ *  Bulk delete (Sec. 6.4): groups are removed in descending order ("larger
  *  items first"), shifting the following runs left but never before their
  *  home slot. A group of d deletes of a fingerprint with count c removes
  *  min(c, d) copies; the keys of the group are taken in batch order and the

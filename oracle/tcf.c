@@ -15,8 +15,8 @@
  *  pairing, so a fingerprint is the unordered pair {b1, b2} plus the tag and
  *  a query answer is the membership of that fingerprint.)
  *
- *  Deterministic bulk insert of one batch (Sec. 4.2 shortcut, Sec. 4
- *  power-of-two-choice, Sec. 4.2 backing table, Sec. 4.3 sorted blocks;
+ *  Deterministic bulk insert of one batch (Sec. 4.1 shortcut, Sec. 4
+ *  power-of-two-choice, Sec. 4.1 backing table, Sec. 4.2 sorted blocks;
  *  R: the phase order below makes the table a function of the batch).
  *  Candidates of a block are always taken in (tag, batch index) order.
  *   A  shortcut: block b takes its j-th candidate with b1 = b iff
@@ -28,7 +28,7 @@
  *      takes its j-th candidate iff fillB(b) + j < B.
  *   D  backing table: entry e = (min(b1, b2) << f) | tag lands in bucket
  *      ((mix64(e) >> 32) * nbk) >> 32 of nbk buckets of W = 8 entries,
- *      nbk = max(8, ceil(ceil(N / 100) / 8)) (Sec. 4.2 sizes it to 1/100 of
+ *      nbk = max(8, ceil(ceil(N / 100) / 8)) (Sec. 4.1 sizes it to 1/100 of
  *      the table; R: sorted buckets instead of double hashing). Bucket k takes
  *      its j-th candidate, in (e, batch index) order, iff fill(k) + j < W.
  *      The rest are rejected: status 1 (full).
@@ -37,7 +37,7 @@
  *
  *  Query: tag in block b1, or in block b2, or e in its bucket.
  *
- *  Deterministic bulk delete (Sec. 7 deletes one copy; R: phases as insert):
+ *  Deterministic bulk delete (Sec. 6.4 deletes one copy; R: phases as insert):
  *   1  block b1 removes one copy of the tag for each of its candidates, in
  *      (tag, batch index) order, while a copy is left;
  *   2  the keys still unmatched try b2 the same way;

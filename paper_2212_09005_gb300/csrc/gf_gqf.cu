@@ -3,7 +3,7 @@
 // Table (double-buffered): per 64-slot block a 32-byte metadata record
 // {occupieds, runends, offset}, and an array of r-bit remainders.
 //
-// Bulk insert / delete (Sec. 5.4-5.5, Sec. 7): fingerprints are computed,
+// Bulk insert / delete (Sec. 5.3-5.4, Sec. 6.4): fingerprints are computed,
 // radix-sorted and reduced to <fingerprint, count> groups (the paper's
 // map-reduce for skewed inputs). The groups are then merged into the table in
 // ONE pass over quotient tiles of TQ quotients instead of the paper's
@@ -693,7 +693,7 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
 }
 
 // first group of every tile: successor search of the tile's first fingerprint
-// in the sorted groups (paper Sec. 5.4, "the starts of buffers are set using
+// in the sorted groups (paper Sec. 5.3, "the starts of buffers are set using
 // successor search")
 __global__ void gqf_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t *pm, uint64_t m_limit,
                                 uint64_t N, uint32_t r, uint64_t ntiles, uint32_t *tlo)
@@ -714,7 +714,7 @@ __global__ void gqf_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t
 }
 
 // ---------------------------------------------------------------------------
-// In-place bulk delete, the paper's even-odd regions (Sec. 7 with Sec. 5.4):
+// In-place bulk delete, the paper's even-odd regions (Sec. 6.4 with Sec. 5.3):
 // removing copies from a run only shifts the rest of its cluster left, never
 // past a home slot, so a delete is local to its cluster. One thread per
 // region of RQ quotients applies the region's groups largest first; even

@@ -1,6 +1,6 @@
 // Generic device primitives: exclusive scan (single pass, decoupled
 // look-back) and LSD radix sort of 64-bit keys with optional 32-bit values.
-// The GQF sorts fingerprints before inserting them (paper Sec. 5.4, "Sorting
+// The GQF sorts fingerprints before inserting them (paper Sec. 5.3, "Sorting
 // hashes"); the TCF groups batches by block with the scan.
 #include <cstdio>
 #include <cstring>

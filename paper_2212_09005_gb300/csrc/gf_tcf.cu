@@ -1,14 +1,14 @@
 // Two-choice filter (TCF), paper Sec. 4, for sm_103a.
 //
 // Table: nb blocks of 32 bytes (one DRAM sector), B = 256 / f tags each, plus a
-// backing table of nbk buckets of 8 uint64 entries (Sec. 4.2 "Backing table").
+// backing table of nbk buckets of 8 uint64 entries (Sec. 4.1, "Backing table").
 //
 // Query (Sec. 4): probe both candidate blocks with two 16-byte loads each and a
 // SIMD compare (__vcmpeq2 / __vcmpeq4), then the backing bucket (L2-resident)
 // if the tag was in neither block.
 //
-// Bulk insert, deterministic mode (Sec. 4.2 shortcut + Sec. 4 two choices +
-// Sec. 4.2 backing table + Sec. 4.3 sorted blocks). Each phase groups its
+// Bulk insert, deterministic mode (Sec. 4.1 shortcut + Sec. 4 two choices +
+// Sec. 4.1 backing table + Sec. 4.2 sorted blocks). Each phase groups its
 // candidates by destination block with a counting sort (histogram in a
 // per-block counter array, exclusive scan, scatter), then one thread per
 // block takes the k smallest (tag, batch index) candidates that fit, merges
@@ -602,7 +602,7 @@ __global__ void __launch_bounds__(TPB) tcf_point_insert(const uint64_t *__restri
         x.load_l2(blocks, k.b1);
         int f1 = x.live();
         bool done = false;
-        if (f1 < (int)G.tsc) done = point_put<F>(blocks, k.b1, k.t, ctr);  // shortcut (Sec. 4.2)
+        if (f1 < (int)G.tsc) done = point_put<F>(blocks, k.b1, k.t, ctr);  // shortcut (Sec. 4.1)
         if (!done) {
             Blk<F> y;
             y.load_l2(blocks, k.b2);

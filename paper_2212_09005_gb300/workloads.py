@@ -12,7 +12,7 @@ number generators", OOPSLA 2014). Item i of stream `seed` is the SplitMix64
 output mix(seed + (i + 1) * golden_gamma), so any index range can be produced
 independently, on any machine, with identical results.
 
-Skewed multisets (the counting benchmark of Sec. 6, Table 4) are drawn from a
+Skewed multisets (the counting benchmark of Sec. 6, Table 5) are drawn from a
 Zipf law with the rejection-inversion sampler of Hoermann and Derflinger
 ("Rejection-inversion to generate variates from monotone discrete
 distributions", ACM TOMACS 1996), restated below from its published

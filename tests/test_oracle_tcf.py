@@ -1,7 +1,7 @@
 """Pins for the oracle TCF (paper Sec. 4): query answers equal fingerprint
 membership (brute force), conservation of the stored multiset, the placement
 rules (shortcut below 3B/4, two-choice by fill, other block, backing table),
-sorted blocks (Sec. 4.3), the false-positive closed form 2B/2^f (Sec. 4.1)
+sorted blocks (Sec. 4.2), the false-positive closed form 2B/2^f (Sec. 4.1)
 generalised to partial load, and deletes without false negatives."""
 import collections
 
@@ -48,7 +48,7 @@ def test_membership_equals_fingerprint_multiset(oracle, log2_slots, f):
         st = T.insert(batch)
         inserted.extend(batch[st == 0].tolist())
         blocks = T.blocks()
-        # Sec. 4.3: blocks hold sorted tags, EMPTY (0) padding at the end
+        # Sec. 4.2: blocks hold sorted tags, EMPTY (0) padding at the end
         for row in blocks[np.unique(T.keyinfo(batch)[0])]:
             k = int((row != 0).sum())
             assert (row[:k] != 0).all() and not row[k:].any()
@@ -185,7 +185,7 @@ def test_fpr_closed_form(oracle, f):
 
 
 def test_ninety_percent_load_small_backing_share(oracle):
-    """Sec. 4.2: with the backing table the TCF reaches 90% load; the share of
+    """Sec. 4.1: with the backing table the TCF reaches 90% load; the share of
     items in the backing table stays small (the paper reports < 0.07% for its
     point TCF; the phased bulk mode here is checked against 1%)."""
     T = oracle.TCF(18, 16, seed=2)
