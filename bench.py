@@ -76,6 +76,32 @@ def parse_args():
 
 
 # ---------------------------------------------------------------------------
+# ranks: one process per GPU, replicas of the whole step (weak scaling)
+# ---------------------------------------------------------------------------
+def rank_env():
+    """(rank, world, local_rank) from the launcher's environment."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(ops_per_step: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput in Gops/s: every rank did `steps` full steps."""
+    return ops_per_step * steps * world / (ms_max / 1e3) / 1e9
+
+
+# ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
 def make_inputs():
@@ -266,15 +292,12 @@ def run_ours(args, rank, world, device_index):
     clk = clocks.stop()
     gf.trace_enable(False)
     trace = gf.trace_summary()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device)
     if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        ms = float(t.item())
     checks = R.checks()
     ops = ops_per_step(inp)
-    value = ops * args.steps * world / (ms / 1e3) / 1e9
+    value = aggregate_rate(ops, args.steps, world, ms)
 
     # roofline of the dominant kernel, from the live trace of the timed region
     peak, peak_src = peaks()
@@ -355,12 +378,8 @@ def run_e2e(R, args, world, device):
     for _ in range(args.steps):
         step()
     torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([sec], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        sec = float(t.item())
-    v = ops_per_step(inp) * args.steps * world / sec / 1e9
+    sec = max_over_ranks(time.perf_counter() - t0, world, device)
+    v = aggregate_rate(ops_per_step(inp), args.steps, world, sec * 1e3)
     return {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 
@@ -423,9 +442,7 @@ def run_reference(args, rank, world):
 
 def main():
     args = parse_args()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     if world > 1:
         import torch
         import torch.distributed as dist
