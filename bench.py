@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--case", default="full", choices=["full", "profile"],
+                    help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
+                         "keys) that fits an ncu capture; its line is not the benchmark figure")
     return ap.parse_args()
 
 
@@ -104,16 +107,25 @@ def aggregate_rate(ops_per_step: int, steps: int, world: int, ms_max: float) -> 
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def make_inputs():
+PROFILE_WORKLOAD = ("reduced copy for ncu captures: TCF 2^24 slots f=16 bulk, 2^20-key batches, 2^22 + 2^22 "
+                    "queries; counting GQF 2^25 slots r=8, 3e7 Zipf(1.0) keys, 2^22 counts")
+
+
+def make_inputs(case: str = "full"):
     from paper_2212_09005_gb300 import workloads as W
 
-    t = W.tcf_workload()
-    g = W.gqf_zipf_workload()
+    if case == "profile":
+        t = W.tcf_workload(log2_slots=24, batch=1 << 20, n_query=1 << 22)
+        g = W.gqf_zipf_workload(q=25, n=30_000_000, n_query=1 << 22)
+    else:
+        t = W.tcf_workload()
+        g = W.gqf_zipf_workload()
     ins = t["insert"]
     probe = np.concatenate([ins[t["pos_idx"]], t["negatives"]])
     dels = ins[t["del_idx"]]
     return {
         "tcf_ins": ins, "tcf_batch": t["batch"], "tcf_probe": probe, "tcf_del": dels,
+        "tcf_log2": t["log2_slots"], "gqf_qbits": g["q"],
         "gqf_ins": g["insert"], "gqf_q": g["query"], "n_pos": len(t["pos_idx"]),
     }
 
@@ -215,8 +227,8 @@ class Runner:
         self.cnt = torch.zeros(len(inp["gqf_q"]), dtype=torch.int64, device=device)
         self.cnt2 = torch.zeros_like(self.cnt)
         self.B = inp["tcf_batch"]
-        self.tcf = gf.TCF(26, 16, gf.MODE_BULK, seed=2, max_batch=self.B)
-        self.gqf = gf.GQF(28, 8, seed=3, max_batch=len(inp["gqf_ins"]))
+        self.tcf = gf.TCF(inp["tcf_log2"], 16, gf.MODE_BULK, seed=2, max_batch=self.B)
+        self.gqf = gf.GQF(inp["gqf_qbits"], 8, seed=3, max_batch=len(inp["gqf_ins"]))
 
     def step(self, src=None):
         """One pass of the hot path. `src` maps input names to device tensors."""
@@ -270,7 +282,7 @@ def run_ours(args, rank, world, device_index):
 
     torch.cuda.set_device(device_index)
     device = torch.device("cuda", device_index)
-    inp = make_inputs()
+    inp = make_inputs(args.case)
     R = Runner(inp, device)
     stream = torch.cuda.current_stream()
     for _ in range(max(3, args.warmup)):
@@ -307,7 +319,7 @@ def run_ours(args, rank, world, device_index):
     for name, v in trace.items():
         bpu = BYTES_PER_UNIT.get(name)
         gbs = (bpu * v["units"] / (v["ms"] / 1e3) / 1e9) if (bpu and v["ms"] > 0) else None
-        kern.append({"kernel": name, "launches": v["launches"], "ms": round(v["ms"], 3),
+        kern.append({"kernel": name, "launches": v["launches"], "units": v["units"], "ms": round(v["ms"], 3),
                      "share": round(v["ms"] / tot_ms, 4) if tot_ms else None,
                      "achieved_gbs": round(gbs, 1) if gbs else None})
     kern.sort(key=lambda k: -k["ms"])
@@ -330,7 +342,7 @@ def run_ours(args, rank, world, device_index):
         e2e = run_e2e(R, args, world, device)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.case == "full":
         cpu = cpu_sample(inp)
 
     line = {
@@ -338,10 +350,10 @@ def run_ours(args, rank, world, device_index):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded SplitMix64 uniform keys, Zipf rejection-inversion keys)",
-        "config": {"workload": WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
+        "config": {"workload": WORKLOAD if args.case == "full" else PROFILE_WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "kernels": kern[:12], "checks": checks,
+        "cpu_baseline": cpu, "kernels": kern[:16], "checks": checks,
     }
     return line
 
