@@ -61,7 +61,18 @@ BYTES_PER_UNIT = {
     "tcf_bucket_remove": 132.0,
     "tcf_point_insert": 104.0,
     "tcf_point_remove": 104.0,
+    # filter groups
+    "tcf_group_prep": 32.0,            # key read + 24-byte prepared key write
+    "tcf_group_query_kernel": 73.0,
+    "gqf_group_fp_kernel": 16.0,
+    "gqf_merge_group_kernel": 3.0,
+    "gqf_group_count_kernel": 73.0,    # key + metadata sector + remainder sector + found byte
 }
+
+BATCHED_WORKLOAD = ("4096 filters: 2048 TCF f=16 bulk + 2048 counting GQF r=8, 2^e slots with e uniform in "
+                    "10..20, 85-95% load (7.2e8 keys in total); TCF keys inserted in 8 rounds, GQF keys in "
+                    "one batch; then every filter's own keys and as many fresh keys are queried; one group "
+                    "call per kind and operation")
 
 
 def parse_args():
@@ -72,7 +83,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--case", default="full", choices=["full", "profile"],
+    ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
+    ap.add_argument("--case", default="full", choices=["full", "profile", "batched"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
     return ap.parse_args()
@@ -311,7 +323,39 @@ def run_ours(args, rank, world, device_index):
     ops = ops_per_step(inp)
     value = aggregate_rate(ops, args.steps, world, ms)
 
-    # roofline of the dominant kernel, from the live trace of the timed region
+    kern, roof = roofline_from_trace(trace)
+    launches = sum(v["launches"] for v in trace.values())
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(R, args, world, device)
+
+    batched = None
+    if args.case == "full" and not args.no_batched:
+        del R
+        torch.cuda.empty_cache()
+        batched = run_batched(args, device)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu and args.case == "full":
+        cpu = cpu_sample(inp)
+
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic (seeded SplitMix64 uniform keys, Zipf rejection-inversion keys)",
+        "config": {"workload": WORKLOAD if args.case == "full" else PROFILE_WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
+                   "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
+        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+        "cpu_baseline": cpu, "kernels": kern[:16], "checks": checks, "batched": batched,
+    }
+    return line
+
+
+def roofline_from_trace(trace):
+    """Per-kernel shares and the roofline of the dominant kernel, from the live
+    CUDA-event trace of the timed region."""
     peak, peak_src = peaks()
     traffic = ncu_traffic()
     kern = []
@@ -331,31 +375,103 @@ def run_ours(args, rank, world, device_index):
         tr = None
         if name in traffic:
             u, b = traffic[name]
-            tr = b * per_launch_units / u if u else None
+            tr = round(b * per_launch_units / u) if u else None
         roof = {"bound": "hbm", "kernel": name, "achieved": top["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": round(top["achieved_gbs"] / peak, 4), "peak_source": peak_src,
                 "traffic": tr, "algorithmic_bytes_per_launch": BYTES_PER_UNIT[name] * per_launch_units}
-    launches = sum(v["launches"] for v in trace.values())
+    return kern, roof
 
-    e2e = None
-    if not args.no_e2e:
-        e2e = run_e2e(R, args, world, device)
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and args.case == "full":
-        cpu = cpu_sample(inp)
+# ---------------------------------------------------------------------------
+# batched filters (filter groups)
+# ---------------------------------------------------------------------------
+class BatchedRunner:
+    """One step: empty both groups; insert the TCF keys in rounds and the GQF
+    keys in one batch; query every filter's own keys and as many fresh keys."""
 
-    line = {
-        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic (seeded SplitMix64 uniform keys, Zipf rejection-inversion keys)",
-        "config": {"workload": WORKLOAD if args.case == "full" else PROFILE_WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
-                   "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
-        "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "kernels": kern[:16], "checks": checks,
-    }
-    return line
+    def __init__(self, w, device):
+        import torch
+
+        import paper_2212_09005_gb300 as gf
+        from paper_2212_09005_gb300 import workloads as W
+
+        self.torch, self.w = torch, w
+        off, keys, neg = w["offsets"], w["insert"], w["negatives"]
+        logs, seeds, nt = w["log2_slots"], w["hash_seeds"], w["n_tcf"]
+        to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
+        toff = off[: nt + 1]
+        goff = off[nt:] - off[nt]
+        self.toff, self.goff = to_dev(toff), to_dev(goff)
+        self.tkeys, self.tneg = to_dev(keys[: toff[-1]]), to_dev(neg[: toff[-1]])
+        self.gkeys, self.gneg = to_dev(keys[off[nt]:]), to_dev(neg[off[nt]:])
+        chunks = W.round_chunks(toff, w["tcf_rounds"])
+        self.rounds = []
+        for j in range(w["tcf_rounds"]):
+            lens = chunks[j, :, 1] - chunks[j, :, 0]
+            o = np.zeros(nt + 1, np.int64)
+            np.cumsum(lens, out=o[1:])
+            idx = np.concatenate([np.arange(a, b) for a, b in chunks[j]])
+            self.rounds.append((to_dev(o), to_dev(keys[idx])))
+        mt = max(int(r[1].numel()) for r in self.rounds)
+        self.T = gf.FilterGroup(gf.FILTER_TCF, logs[:nt], 16, seeds[:nt], max_total=mt)
+        self.G = gf.FilterGroup(gf.FILTER_GQF, logs[nt:], 8, seeds[nt:], max_total=int(self.gkeys.numel()))
+        u8 = lambda n: torch.zeros(n, dtype=torch.uint8, device=device)
+        self.tf, self.tfn = u8(self.tkeys.numel()), u8(self.tneg.numel())
+        self.gf_, self.gfn = u8(self.gkeys.numel()), u8(self.gneg.numel())
+        self.ops = int(off[-1]) * 3  # inserts, own-key queries, fresh-key queries
+
+    def step(self):
+        T, G = self.T, self.G
+        T.clear()
+        for o, k in self.rounds:
+            T.insert(o, k)
+        T.query(self.toff, self.tkeys, self.tf)
+        T.query(self.toff, self.tneg, self.tfn)
+        G.clear()
+        G.insert(self.goff, self.gkeys)
+        G.query(self.goff, self.gkeys, self.gf_)
+        G.query(self.goff, self.gneg, self.gfn)
+
+    def checks(self):
+        self.torch.cuda.synchronize()
+        st = self.T.stats(0)
+        return {"tcf_own_found": float(self.tf.float().mean().item()),
+                "tcf_failed_keys": st["failed_keys"],
+                "tcf_fpr": float(self.tfn.float().mean().item()),
+                "gqf_own_found": bool(self.gf_.all().item()),
+                "gqf_fpr": float(self.gfn.float().mean().item())}
+
+
+def run_batched(args, device):
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    R = BatchedRunner(W.batched_workload(), device)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        R.step()
+    torch.cuda.synchronize()
+    gf.trace_reset()
+    gf.trace_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        R.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    gf.trace_enable(False)
+    trace = gf.trace_summary()
+    ms = e0.elapsed_time(e1)
+    kern, roof = roofline_from_trace(trace)
+    out = {"workload": BATCHED_WORKLOAD, "value": round(aggregate_rate(R.ops, args.steps, 1, ms), 4), "unit": UNIT,
+           "ms_per_step": round(ms / args.steps, 3), "ops_per_step": R.ops,
+           "gpu_launches": sum(v["launches"] for v in trace.values()), "roofline": roof,
+           "kernels": kern[:12], "checks": R.checks()}
+    del R
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_e2e(R, args, world, device):
@@ -463,6 +579,16 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.case == "batched":
+        import torch
+
+        torch.cuda.set_device(local)
+        b = run_batched(args, torch.device("cuda", local))
+        line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": BATCHED_WORKLOAD}, "gpu_launches": b["gpu_launches"],
+                "roofline": b["roofline"], "kernels": b["kernels"], "checks": b["checks"]}
     else:
         line = run_ours(args, rank, world, local)
     if rank == 0 and line is not None:

@@ -8,9 +8,11 @@
  * default stream). All calls except filter_create, filter_destroy,
  * filter_get_stats, filter_export and filter_import are asynchronous: they
  * enqueue kernels on the stream and return; the caller's buffers must stay
- * valid until the stream reaches the call. Calls on one filter must be
- * ordered (same stream, or externally synchronised); different filters are
- * independent.
+ * valid until the stream reaches the call. Exceptions: a GQF insert
+ * synchronises the stream once to read whether the table overflowed, and a
+ * GQF remove once to read the number of distinct fingerprints (which picks
+ * the in-place or the merge path). Calls on one filter must be ordered (same
+ * stream, or externally synchronised); different filters are independent.
  *
  * Errors are returned synchronously for bad arguments, allocation failure
  * and unsupported operations. Conditions found on the device (a full table,
@@ -211,6 +213,131 @@ int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kern
 int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_seed, const void *d_table_in,
                               void *d_table_out, const uint64_t *d_keys, uint64_t n,
                               uint8_t *d_status, void *stream);
+
+/*
+ * ---- filter groups ----
+ * Many filters of one kind driven by one set of kernel launches per call: the
+ * number of launches of a group call does not grow with the number of
+ * members. The paper measures one filter per launch; groups serve workloads
+ * with thousands of small filters (one per user, shard or sample), where
+ * per-filter launches would be latency-bound. Each member's table is laid out
+ * and behaves exactly as a standalone filter with the same configuration that
+ * receives the same calls with its keys in the same order; its exported image
+ * is byte-identical to that filter's.
+ *
+ * filter_group_create: cfgs[0 .. n_filters) configure the members. All share
+ *   kind and tag_bits (TCF f / GQF r); TCF members use FILTER_MODE_BULK; each
+ *   has its own log2_slots and hash_seed (cfgs[i].max_batch is ignored).
+ *   max_total: the largest total key count of one insert or remove call (TCF
+ *   < 2^32, GQF < 2^30). One device allocation holds every member's table and
+ *   the shared scratch; the group owns it until filter_group_destroy.
+ *   Returns FILTER_ERR_ARG for mixed kinds or tag widths, point mode, a bad
+ *   member geometry (as filter_create), more than 2^32 TCF blocks in total, or
+ *   GQF member index bits + the largest q + r above 64; FILTER_ERR_OOM if the
+ *   allocation fails. Synchronises `stream`.
+ */
+typedef struct filter_group filter_group_t;
+
+int filter_group_create(const filter_config *cfgs, uint32_t n_filters, uint64_t max_total, void *stream,
+                        filter_group_t **out);
+
+/* filter_group_destroy: synchronise the device and free everything. NULL is a no-op. */
+int filter_group_destroy(filter_group_t *g);
+
+/* filter_group_clear: empty every member (asynchronous) and reset the statistics. */
+int filter_group_clear(filter_group_t *g, void *stream);
+
+/*
+ * Keys of a group call: member i's keys are d_keys[d_offsets[i] ..
+ * d_offsets[i + 1]), in the order the member sees them. d_offsets: device
+ * array of n_filters + 1 non-decreasing uint64 with d_offsets[0] = 0 and
+ * d_offsets[n_filters] = n_total; n_total is passed by value so that launch
+ * sizes are known without reading the device. Keys at or past n_total are
+ * never read. Per-key outputs (d_status, d_found, d_counts) are indexed like
+ * d_keys. Semantics per member are those of filter_insert, filter_remove,
+ * filter_query and filter_count.
+ *
+ * filter_group_insert / filter_group_remove: n_total <= max_total, else
+ *   FILTER_ERR_ARG. GQF inserts synchronise the stream once (overflow check);
+ *   a member whose keys do not fit is redone alone from its previous table,
+ *   keeping the longest prefix of its sorted groups that fits (as
+ *   filter_insert), with extra synchronisations. GQF removes always take the
+ *   merge path. All other group calls are asynchronous.
+ * filter_group_query: any n_total.
+ * filter_group_count: GQF groups only (TCF: FILTER_ERR_UNSUPPORTED); any n_total.
+ */
+int filter_group_insert(filter_group_t *g, const uint64_t *d_offsets, const uint64_t *d_keys, uint64_t n_total,
+                        uint8_t *d_status, void *stream);
+int filter_group_remove(filter_group_t *g, const uint64_t *d_offsets, const uint64_t *d_keys, uint64_t n_total,
+                        uint8_t *d_status, void *stream);
+int filter_group_query(filter_group_t *g, const uint64_t *d_offsets, const uint64_t *d_keys, uint64_t n_total,
+                       uint8_t *d_found, void *stream);
+int filter_group_count(filter_group_t *g, const uint64_t *d_offsets, const uint64_t *d_keys, uint64_t n_total,
+                       uint64_t *d_counts, void *stream);
+
+/*
+ * filter_group_get_stats: synchronise `stream` and read member `member`'s
+ * statistics. GQF members keep their own status word and failed-key count;
+ * in a TCF group these counters, and backing_used, are shared by all members.
+ * table_bytes and nslots are the member's; device_bytes is the whole group's.
+ */
+int filter_group_get_stats(filter_group_t *g, uint32_t member, void *stream, filter_stats *out);
+
+/* filter_group_export_size / filter_group_export: member `member`'s table
+ * image, in the filter_export layout of a standalone filter (synchronises). */
+int filter_group_export_size(filter_group_t *g, uint32_t member, uint64_t *nbytes);
+int filter_group_export(filter_group_t *g, uint32_t member, void *host_buf, uint64_t nbytes, void *stream);
+
+/*
+ * ---- serving loop ----
+ * Batches of host keys for many filters, run concurrently on several CUDA
+ * streams. The paper measures isolated bulk calls; this runtime serves a
+ * stream of requests (each a batch for one filter) as they arrive.
+ *
+ * filter_server_create: serve the given filters (created by filter_create on
+ *   the current device; the caller keeps ownership and must not use them
+ *   while the server runs) with n_workers workers (1..64). Each worker owns a
+ *   CUDA stream, a host thread and staging for max_keys keys: 16 bytes per key
+ *   on the device and as much pinned host memory. Requests are admitted by
+ *   free device memory: if the staging of all workers does not fit in the
+ *   free device memory, FILTER_ERR_OOM and nothing is created. Filter i is
+ *   served by worker i mod n_workers, which takes its requests in submission
+ *   order, so every filter applies its batches in submission order and each
+ *   batch's results equal those of the same per-filter sequence run alone.
+ *   Every filter's max_batch must be >= the batches submitted to it.
+ * filter_server_submit: enqueue one request and return at once with a
+ *   ticket. The key buffer (host memory, pageable or pinned) and the output
+ *   buffer must stay valid until the ticket is collected. host_out receives
+ *   n bytes of statuses (insert, remove) or found flags (query), or n uint64
+ *   counts (count, GQF only); NULL discards the results. FILTER_ERR_ARG for
+ *   a bad filter index or op, n > max_keys, or a server being destroyed.
+ * filter_server_wait: block until the request is done, then return
+ *   FILTER_OK with *op_rc = the operation's return code and *latency_s = the
+ *   seconds from submit to results in host_out. Each ticket is collected
+ *   once; an unknown or collected ticket gives FILTER_ERR_ARG.
+ * filter_server_destroy: finish every submitted request, stop the workers
+ *   and free the staging. The filters are left to the caller.
+ */
+#define FILTER_OP_INSERT 0
+#define FILTER_OP_QUERY 1
+#define FILTER_OP_REMOVE 2
+#define FILTER_OP_COUNT 3
+
+typedef struct filter_request {
+    uint32_t filter;            /* index into the server's filter list */
+    uint32_t op;                /* FILTER_OP_* */
+    const uint64_t *host_keys;  /* n keys, host memory */
+    uint64_t n;
+    void *host_out;             /* results, host memory, or NULL */
+} filter_request;
+
+typedef struct filter_server filter_server_t;
+
+int filter_server_create(filter_t *const *filters, uint32_t n_filters, uint32_t n_workers, uint64_t max_keys,
+                         filter_server_t **out);
+int filter_server_submit(filter_server_t *s, const filter_request *req, uint64_t *ticket);
+int filter_server_wait(filter_server_t *s, uint64_t ticket, int *op_rc, double *latency_s);
+int filter_server_destroy(filter_server_t *s);
 
 #ifdef __cplusplus
 }

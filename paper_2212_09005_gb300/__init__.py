@@ -15,7 +15,7 @@ import os
 import numpy as np
 
 __all__ = [
-    "Filter", "TCF", "GQF", "lib", "build", "FilterError",
+    "Filter", "TCF", "GQF", "FilterGroup", "FilterServer", "lib", "build", "FilterError",
     "FILTER_TCF", "FILTER_GQF", "MODE_BULK", "MODE_POINT",
     "KEY_OK", "KEY_FULL", "KEY_NOT_FOUND", "STATUS_FULL", "STATUS_TIMEOUT",
 ]
@@ -36,7 +36,13 @@ EXPORTS = [
     "filter_export", "filter_import", "filter_error_string",
     "filter_trace_enable", "filter_trace_reset", "filter_trace_summary",
     "filter_gqf_insert_noalloc",
+    "filter_group_create", "filter_group_destroy", "filter_group_clear", "filter_group_insert",
+    "filter_group_remove", "filter_group_query", "filter_group_count", "filter_group_get_stats",
+    "filter_group_export_size", "filter_group_export",
+    "filter_server_create", "filter_server_submit", "filter_server_wait", "filter_server_destroy",
 ]
+
+OP_INSERT, OP_QUERY, OP_REMOVE, OP_COUNT = 0, 1, 2, 3
 
 
 class FilterConfig(C.Structure):
@@ -48,6 +54,11 @@ class FilterStats(C.Structure):
     _fields_ = [("status_word", C.c_uint64), ("failed_keys", C.c_uint64),
                 ("backing_used", C.c_uint64), ("table_bytes", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("nslots", C.c_uint64)]
+
+
+class FilterRequest(C.Structure):
+    _fields_ = [("filter", C.c_uint32), ("op", C.c_uint32), ("host_keys", C.c_void_p), ("n", C.c_uint64),
+                ("host_out", C.c_void_p)]
 
 
 class TraceEntry(C.Structure):
@@ -90,6 +101,18 @@ def lib():
         L.filter_trace_reset.argtypes = []
         L.filter_trace_summary.argtypes = [C.c_uint32, C.POINTER(TraceEntry), C.POINTER(C.c_uint32)]
         L.filter_gqf_insert_noalloc.argtypes = [C.c_uint32, C.c_uint32, u64, vp, vp, vp, u64, vp, vp]
+        L.filter_group_create.argtypes = [C.POINTER(FilterConfig), C.c_uint32, u64, vp, C.POINTER(vp)]
+        L.filter_group_destroy.argtypes = [vp]
+        L.filter_group_clear.argtypes = [vp, vp]
+        for name in ("filter_group_insert", "filter_group_remove", "filter_group_query", "filter_group_count"):
+            getattr(L, name).argtypes = [vp, vp, vp, u64, vp, vp]
+        L.filter_group_get_stats.argtypes = [vp, C.c_uint32, vp, C.POINTER(FilterStats)]
+        L.filter_group_export_size.argtypes = [vp, C.c_uint32, C.POINTER(u64)]
+        L.filter_group_export.argtypes = [vp, C.c_uint32, vp, u64, vp]
+        L.filter_server_create.argtypes = [C.POINTER(vp), C.c_uint32, C.c_uint32, u64, C.POINTER(vp)]
+        L.filter_server_submit.argtypes = [vp, C.POINTER(FilterRequest), C.POINTER(u64)]
+        L.filter_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
+        L.filter_server_destroy.argtypes = [vp]
         L.filter_error_string.argtypes = [i32]
         L.filter_error_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -199,6 +222,121 @@ def TCF(log2_slots: int, tag_bits: int = 16, mode: int = MODE_BULK, seed: int = 
 
 def GQF(q: int, r: int = 8, seed: int = 0, max_batch: int = 1 << 22, stream=None) -> Filter:
     return Filter(FILTER_GQF, q, r, 0, seed, max_batch, stream)
+
+
+class FilterGroup:
+    """Many filters of one kind (all TCF bulk-mode or all GQF, one tag width),
+    driven by one set of kernel launches per call. Member i's keys of a call
+    are keys[offsets[i]:offsets[i + 1]] (offsets: int64 CUDA tensor of
+    n_filters + 1 entries)."""
+
+    def __init__(self, kind: int, log2_slots, tag_bits: int, seeds, max_total: int, stream=None):
+        log2_slots = [int(x) for x in log2_slots]
+        seeds = [int(x) & 0xFFFFFFFFFFFFFFFF for x in seeds]
+        if len(seeds) != len(log2_slots) or not log2_slots:
+            raise FilterError("need one seed per member")
+        self.n = len(log2_slots)
+        cfgs = (FilterConfig * self.n)()
+        for i, (lg, sd) in enumerate(zip(log2_slots, seeds)):
+            cfgs[i] = FilterConfig(kind, lg, tag_bits, MODE_BULK if kind == FILTER_TCF else 0, sd, 1)
+        h = C.c_void_p()
+        _check(lib().filter_group_create(cfgs, self.n, max(1, int(max_total)), _stream(stream), C.byref(h)),
+               "filter_group_create")
+        self._h = h
+        self.kind, self.tag_bits, self.log2_slots, self.seeds = kind, tag_bits, log2_slots, seeds
+        self.max_total = max(1, int(max_total))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().filter_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _call(self, name, offsets, keys, out, out_bytes, stream):
+        if offsets.numel() != self.n + 1:
+            raise FilterError(f"offsets must have {self.n + 1} entries")
+        _check(getattr(lib(), name)(self._h, _dptr(offsets, 8), _dptr(keys, 8), keys.numel(),
+                                    _dptr(out, out_bytes), _stream(stream)), name)
+
+    def insert(self, offsets, keys, status=None, stream=None):
+        self._call("filter_group_insert", offsets, keys, status, 1, stream)
+
+    def remove(self, offsets, keys, status=None, stream=None):
+        self._call("filter_group_remove", offsets, keys, status, 1, stream)
+
+    def query(self, offsets, keys, found, stream=None):
+        self._call("filter_group_query", offsets, keys, found, 1, stream)
+
+    def count(self, offsets, keys, counts, stream=None):
+        self._call("filter_group_count", offsets, keys, counts, 8, stream)
+
+    def clear(self, stream=None):
+        _check(lib().filter_group_clear(self._h, _stream(stream)), "filter_group_clear")
+
+    def stats(self, member: int, stream=None) -> dict:
+        s = FilterStats()
+        _check(lib().filter_group_get_stats(self._h, member, _stream(stream), C.byref(s)),
+               "filter_group_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in FilterStats._fields_}
+
+    def export(self, member: int, stream=None) -> np.ndarray:
+        n = C.c_uint64()
+        _check(lib().filter_group_export_size(self._h, member, C.byref(n)), "filter_group_export_size")
+        buf = np.zeros(n.value, np.uint8)
+        _check(lib().filter_group_export(self._h, member, buf.ctypes.data_as(C.c_void_p), n.value,
+                                         _stream(stream)), "filter_group_export")
+        return buf
+
+
+class FilterServer:
+    """Serves batches of host keys for many filters on `workers` CUDA streams.
+    Filter i's batches run in submission order on worker i mod workers."""
+
+    _OUT_DTYPE = {OP_INSERT: np.uint8, OP_QUERY: np.uint8, OP_REMOVE: np.uint8, OP_COUNT: np.uint64}
+
+    def __init__(self, filters, workers: int = 4, max_keys: int = 1 << 22):
+        self.filters = list(filters)  # keeps the filters alive while served
+        arr = (C.c_void_p * len(self.filters))(*[f._h.value for f in self.filters])
+        h = C.c_void_p()
+        _check(lib().filter_server_create(arr, len(self.filters), workers, max(1, int(max_keys)), C.byref(h)),
+               "filter_server_create")
+        self._h = h
+        self._pending = {}
+
+    def submit(self, filter_index: int, op: int, keys: np.ndarray, want_out: bool = True) -> int:
+        """Enqueue a batch; returns a ticket. The arrays are kept until wait()."""
+        keys = np.ascontiguousarray(keys, dtype=np.uint64)
+        out = np.zeros(keys.size, self._OUT_DTYPE[op]) if want_out else None
+        req = FilterRequest(filter_index, op, keys.ctypes.data_as(C.c_void_p), keys.size,
+                            out.ctypes.data_as(C.c_void_p) if out is not None else None)
+        t = C.c_uint64()
+        _check(lib().filter_server_submit(self._h, C.byref(req), C.byref(t)), "filter_server_submit")
+        self._pending[t.value] = (keys, out)
+        return t.value
+
+    def wait(self, ticket: int):
+        """Block until the batch is done: (results array or None, latency in seconds)."""
+        rc, lat = C.c_int(), C.c_double()
+        _check(lib().filter_server_wait(self._h, ticket, C.byref(rc), C.byref(lat)), "filter_server_wait")
+        _check(rc.value, "served operation")
+        keys, out = self._pending.pop(ticket)
+        return out, lat.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().filter_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def trace_enable(on: bool = True):

@@ -20,6 +20,7 @@
 // Count / query (Sec. 5.1 via the cited CQF): offset of the home block,
 // rank over occupieds, select over runends, then a scan of the run.
 #include <type_traits>
+#include <vector>
 
 #include "gf_internal.cuh"
 
@@ -101,6 +102,8 @@ struct MergeArgs {
     unsigned long long *ts;  // look-back state: [0] tile counter, then one status word per tile
     DevCounters *ctr;
     uint64_t N, nslots, nblk, ntiles;
+    uint64_t fmask;          // fingerprint bits of a sorted value (a group keeps its member index above them)
+    uint64_t tile0;          // group merge: global index of the filter's first tile
     uint32_t r;
     int del, dry;
 };
@@ -154,7 +157,7 @@ template <int R>
 __device__ __forceinline__ void new_group(const MergeSmem<R> &, const MergeArgs &a, long long Q0, uint32_t g,
                                           uint32_t &qoff, uint32_t &rem, uint64_t &cnt)
 {
-    const uint64_t f = a.ufp[g];
+    const uint64_t f = a.ufp[g] & a.fmask;
     qoff = (uint32_t)((long long)(f >> R) - Q0);
     rem = (uint32_t)(f & ((1ull << R) - 1ull));
     cnt = a.ustart[g + 1] - a.ustart[g];
@@ -274,17 +277,11 @@ __device__ __forceinline__ unsigned long long ld_vol(const unsigned long long *p
     return *(const volatile unsigned long long *)p;
 }
 
+// One tile of one filter. `tile` is the filter's own tile index; S.err is 0.
 template <int R>
-__global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
+__device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, const uint64_t tile)
 {
-    __shared__ MergeSmem<R> S;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        S.tile = (unsigned)atomicAdd(&a.ts[0], 1ull);
-        S.err = 0;
-    }
-    __syncthreads();
-    const uint64_t tile = S.tile;
     const long long Q0 = (long long)tile * TQ;
     const uint64_t j0 = tile * TBLK;
     const long long slot_end = min((long long)a.nslots, Q0 + TQ);
@@ -692,6 +689,45 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
     }
 }
 
+// Tiles are taken from a counter in launch order, so every tile a look-back
+// waits on has already been scheduled.
+template <int R>
+__global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
+{
+    __shared__ MergeSmem<R> S;
+    if (threadIdx.x == 0) {
+        S.tile = (unsigned)atomicAdd(&a.ts[0], 1ull);
+        S.err = 0;
+    }
+    __syncthreads();
+    merge_tile<R>(a, S, S.tile);
+}
+
+// Group merge: the tiles of all member filters, concatenated. tab[m] holds
+// member m's arguments with `ts` and `tlo` already offset to its first tile,
+// so the look-back of a member's tile stops at that member's first tile.
+template <int R>
+__global__ void __launch_bounds__(MT) gqf_merge_group_kernel(const MergeArgs *__restrict__ tab,
+                                                             const uint32_t *__restrict__ tile_member,
+                                                             unsigned long long *tctr)
+{
+    __shared__ MergeSmem<R> S;
+    __shared__ MergeArgs A;
+    if (threadIdx.x == 0) {
+        S.tile = (unsigned)atomicAdd(tctr, 1ull);
+        S.err = 0;
+    }
+    __syncthreads();
+    static_assert(sizeof(MergeArgs) % 8 == 0, "MergeArgs copies as 64-bit words");
+    {
+        const unsigned long long *src = reinterpret_cast<const unsigned long long *>(tab + tile_member[S.tile]);
+        unsigned long long *dst = reinterpret_cast<unsigned long long *>(&A);
+        for (int w = threadIdx.x; w < (int)(sizeof(MergeArgs) / 8); w += MT) dst[w] = src[w];
+    }
+    __syncthreads();
+    merge_tile<R>(A, S, S.tile - A.tile0);
+}
+
 // first group of every tile: successor search of the tile's first fingerprint
 // in the sorted groups (paper Sec. 5.3, "the starts of buffers are set using
 // successor search")
@@ -1009,6 +1045,83 @@ __global__ void gqf_account_full(DevCounters *ctr, const uint32_t *ustart, uint6
 // ---------------------------------------------------------------------------
 // count / query
 // ---------------------------------------------------------------------------
+// stored count of fingerprint fp (0 if absent)
+template <int R>
+__device__ __forceinline__ uint64_t count_fp(const uint64_t fp, const Meta *__restrict__ meta,
+                                             const uint8_t *__restrict__ rem, const uint64_t nblk)
+{
+    const uint64_t x = fp >> R;
+    const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
+    const uint64_t j = x >> 6;
+    const ulonglong2 or_ = __ldg(reinterpret_cast<const ulonglong2 *>(meta + j));
+    const unsigned long long occ = or_.x;
+    uint64_t c = 0;
+    if ((occ >> (x & 63)) & 1ull) {
+        const long long base = (long long)(64 * j) + (long long)__ldg(&meta[j].off);
+        const unsigned sh = (unsigned)(x & 63);
+        const unsigned long long upto = (sh == 63) ? ~0ull : ((1ull << (sh + 1)) - 1ull);
+        int d = __popcll(occ & upto & ~1ull);
+        long long end = base;
+        if (d > 0) {
+            long long w = base >> 6;
+            unsigned bsh = (unsigned)(base & 63);
+            unsigned long long bits = (bsh == 63) ? 0ull : (__ldg(&meta[w].rend) & (~0ull << (bsh + 1)));
+            while (true) {
+                int pc = __popcll(bits);
+                if (pc >= d) {
+                    for (int k = 1; k < d; k++) bits &= bits - 1;
+                    end = 64 * w + __ffsll((long long)bits) - 1;
+                    break;
+                }
+                d -= pc;
+                if (++w >= (long long)nblk) {
+                    end = -1;
+                    break;
+                }
+                bits = __ldg(&meta[w].rend);
+            }
+        }
+        if (end >= 0) {
+            // start: one past the last runend in [x, end - 1], else x
+            long long start = (long long)x;
+            long long p = end - 1;
+            while (p >= (long long)x) {
+                long long w = p >> 6;
+                unsigned long long bits = __ldg(&meta[w].rend);
+                unsigned pb = (unsigned)(p & 63);
+                bits &= (pb == 63) ? ~0ull : ((1ull << (pb + 1)) - 1ull);
+                if (64 * w < (long long)x) bits &= ~0ull << (x & 63);
+                if (bits) {
+                    start = 64 * w + 63 - __clzll((long long)bits) + 1;
+                    break;
+                }
+                p = 64 * w - 1;
+            }
+            long long q = start;
+            while (q <= end) {
+                uint32_t s = rd_slot<R>(rem, (uint64_t)q);
+                uint64_t cc = 1;
+                long long step = 1;
+                if (q + 2 <= end && rd_slot<R>(rem, (uint64_t)(q + 1)) == s) {
+                    uint32_t nd = rd_slot<R>(rem, (uint64_t)(q + 2));
+                    if (q + 2 + (long long)nd > end) nd = (uint32_t)(end - q - 2);
+                    uint64_t acc = 0;
+                    for (uint32_t dd = 0; dd < nd; dd++) acc = (acc << R) | rd_slot<R>(rem, (uint64_t)(q + 3 + dd));
+                    cc = acc + 2;
+                    step = 3 + nd;
+                }
+                if (s == v) {
+                    c = cc;
+                    break;
+                }
+                if (s > v) break;
+                q += step;
+            }
+        }
+    }
+    return c;
+}
+
 template <int R>
 __global__ void __launch_bounds__(256) gqf_count_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H,
                                                         const Meta *__restrict__ meta,
@@ -1016,76 +1129,7 @@ __global__ void __launch_bounds__(256) gqf_count_kernel(const uint64_t *__restri
                                                         uint64_t *counts, uint8_t *found)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t fp = fingerprint(__ldg(keys + i), H);
-        const uint64_t x = fp >> R;
-        const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
-        const uint64_t j = x >> 6;
-        const ulonglong2 or_ = __ldg(reinterpret_cast<const ulonglong2 *>(meta + j));
-        const unsigned long long occ = or_.x;
-        uint64_t c = 0;
-        if ((occ >> (x & 63)) & 1ull) {
-            const long long base = (long long)(64 * j) + (long long)__ldg(&meta[j].off);
-            const unsigned sh = (unsigned)(x & 63);
-            const unsigned long long upto = (sh == 63) ? ~0ull : ((1ull << (sh + 1)) - 1ull);
-            int d = __popcll(occ & upto & ~1ull);
-            long long end = base;
-            if (d > 0) {
-                long long w = base >> 6;
-                unsigned bsh = (unsigned)(base & 63);
-                unsigned long long bits = (bsh == 63) ? 0ull : (__ldg(&meta[w].rend) & (~0ull << (bsh + 1)));
-                while (true) {
-                    int pc = __popcll(bits);
-                    if (pc >= d) {
-                        for (int k = 1; k < d; k++) bits &= bits - 1;
-                        end = 64 * w + __ffsll((long long)bits) - 1;
-                        break;
-                    }
-                    d -= pc;
-                    if (++w >= (long long)nblk) {
-                        end = -1;
-                        break;
-                    }
-                    bits = __ldg(&meta[w].rend);
-                }
-            }
-            if (end >= 0) {
-                // start: one past the last runend in [x, end - 1], else x
-                long long start = (long long)x;
-                long long p = end - 1;
-                while (p >= (long long)x) {
-                    long long w = p >> 6;
-                    unsigned long long bits = __ldg(&meta[w].rend);
-                    unsigned pb = (unsigned)(p & 63);
-                    bits &= (pb == 63) ? ~0ull : ((1ull << (pb + 1)) - 1ull);
-                    if (64 * w < (long long)x) bits &= ~0ull << (x & 63);
-                    if (bits) {
-                        start = 64 * w + 63 - __clzll((long long)bits) + 1;
-                        break;
-                    }
-                    p = 64 * w - 1;
-                }
-                long long q = start;
-                while (q <= end) {
-                    uint32_t s = rd_slot<R>(rem, (uint64_t)q);
-                    uint64_t cc = 1;
-                    long long step = 1;
-                    if (q + 2 <= end && rd_slot<R>(rem, (uint64_t)(q + 1)) == s) {
-                        uint32_t nd = rd_slot<R>(rem, (uint64_t)(q + 2));
-                        if (q + 2 + (long long)nd > end) nd = (uint32_t)(end - q - 2);
-                        uint64_t acc = 0;
-                        for (uint32_t dd = 0; dd < nd; dd++) acc = (acc << R) | rd_slot<R>(rem, (uint64_t)(q + 3 + dd));
-                        cc = acc + 2;
-                        step = 3 + nd;
-                    }
-                    if (s == v) {
-                        c = cc;
-                        break;
-                    }
-                    if (s > v) break;
-                    q += step;
-                }
-            }
-        }
+        const uint64_t c = count_fp<R>(fingerprint(__ldg(keys + i), H), meta, rem, nblk);
         if (counts) counts[i] = c;
         if (found) found[i] = c ? 1 : 0;
     }
@@ -1217,6 +1261,8 @@ static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, 
     a.nslots = Q.nslots;
     a.nblk = Q.nblk;
     a.ntiles = Q.ntiles;
+    a.fmask = ~0ull;
+    a.tile0 = 0;
     a.r = Q.r;
     a.del = del;
     a.dry = dry;
@@ -1376,6 +1422,407 @@ int gqf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st)
         GF_CUDA(cudaMemcpyAsync(Q.rem[Q.cur], h + metaB, remB, cudaMemcpyHostToDevice, st));
     }
     GF_CUDA(cudaStreamSynchronize(st));
+    return FILTER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Filter groups: one sort, one reduction and one merge launch for the keys of
+// every member. Sort keys are member << pbits | fingerprint, so each member's
+// groups are contiguous and in fingerprint order; the merge runs over the
+// concatenated tiles of all members, each tile with its member's arguments,
+// and a member's first tile starts from an empty prefix. Each member thus
+// ends up exactly as a standalone filter given the same keys.
+// ---------------------------------------------------------------------------
+struct GqfMemberDev {
+    PHash H;
+    uint64_t N, nblk, tile0;
+    const Meta *meta[2];
+    const uint8_t *rem[2];
+};
+
+__global__ void gqf_group_fp_kernel(const uint64_t *__restrict__ keys, uint64_t n, const uint64_t *__restrict__ off,
+                                    uint32_t nmem, const GqfMemberDev *__restrict__ gm, uint32_t pbits, uint64_t *fp,
+                                    uint32_t *idx)
+{
+    MemberCursor c(off, nmem, n);
+    uint32_t cm = 0xffffffffu;
+    PHash H;
+    for (; c.valid(); c.next(off)) {
+        if (c.m != cm) {
+            cm = c.m;
+            H = gm[cm].H;
+        }
+        fp[c.i] = ((uint64_t)cm << pbits) | fingerprint(__ldg(keys + c.i), H);
+        if (idx) idx[c.i] = (uint32_t)c.i;
+    }
+}
+
+// first group of every tile of every member (successor search, as for one filter)
+__global__ void gqf_group_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t *pm,
+                                      const uint32_t *__restrict__ tile_member, const GqfMemberDev *__restrict__ gm,
+                                      uint32_t pbits, uint32_t r, uint64_t tiles, uint32_t *tlo)
+{
+    const uint64_t m = *pm;
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= tiles;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        if (t == tiles) {
+            tlo[t] = (uint32_t)m;
+            continue;
+        }
+        const uint32_t mb = tile_member[t];
+        const uint64_t q0 = (t - gm[mb].tile0) * TQ, N = gm[mb].N;
+        // a sum, not an or: N << r = 2^p may reach the member bits
+        const uint64_t key = ((uint64_t)mb << pbits) + ((q0 >= N ? N : q0) << r);
+        uint64_t lo = 0, hi = m;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi) >> 1;
+            if (ufp[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        tlo[t] = (uint32_t)lo;
+    }
+}
+
+__global__ void gqf_group_reset(DevCounters *mctr, uint32_t n)
+{
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x) {
+        mctr[m].overflow = 0;
+        mctr[m].gqf_end = -1;
+    }
+}
+
+// members whose merge passed the end of their table
+__global__ void gqf_group_overflow(const DevCounters *mctr, uint32_t n, DevCounters *gctr, uint32_t *list)
+{
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < n; m += gridDim.x * blockDim.x)
+        if (mctr[m].overflow) list[atomicAdd(&gctr->pend[0], 1u)] = m;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) gqf_group_count_kernel(const uint64_t *__restrict__ keys, uint64_t n,
+                                                              const uint64_t *__restrict__ off, uint32_t nmem,
+                                                              const GqfMemberDev *__restrict__ gm, int cur,
+                                                              uint64_t *counts, uint8_t *found)
+{
+    MemberCursor c(off, nmem, n);
+    uint32_t cm = 0xffffffffu;
+    PHash H;
+    const Meta *meta = nullptr;
+    const uint8_t *rem = nullptr;
+    uint64_t nblk = 0;
+    for (; c.valid(); c.next(off)) {
+        if (c.m != cm) {
+            cm = c.m;
+            H = gm[cm].H;
+            meta = gm[cm].meta[cur];
+            rem = gm[cm].rem[cur];
+            nblk = gm[cm].nblk;
+        }
+        const uint64_t cnt = count_fp<R>(fingerprint(__ldg(keys + c.i), H), meta, rem, nblk);
+        if (counts) counts[c.i] = cnt;
+        if (found) found[c.i] = cnt ? 1 : 0;
+    }
+}
+
+int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes_out, bool plan_only)
+{
+    const uint32_t n = GR->n, r = cfgs[0].tag_bits;
+    const uint64_t M = GR->max_total ? GR->max_total : 1;
+    if (M >= (1ull << 30)) return FILTER_ERR_ARG;
+    std::vector<filter> V(n);
+    std::vector<uint64_t> meta_off(n), rem_off(n), tile0(n);
+    uint64_t nblk_tot = 0, nslots_tot = 0, tiles = 0, ts_words = 2, tlo_words = 1;
+    uint32_t pbits = 0;
+    for (uint32_t m = 0; m < n; m++) {
+        if (cfgs[m].kind != FILTER_GQF || cfgs[m].tag_bits != r) return FILTER_ERR_ARG;
+        V[m].cfg = cfgs[m];
+        V[m].cfg.max_batch = M;
+        uint64_t tb = 0, sb = 0;
+        int rc = gqf_setup(&V[m], tb, sb, true);  // geometry only
+        if (rc != FILTER_OK) return rc;
+        const GqfState &Q = V[m].gqf;
+        meta_off[m] = nblk_tot;
+        rem_off[m] = nslots_tot;
+        tile0[m] = tiles;
+        nblk_tot += Q.nblk;
+        nslots_tot += Q.nslots;
+        tiles += Q.ntiles;
+        if (Q.p > pbits) pbits = Q.p;
+        const uint64_t nreg = (Q.N + RQ - 1) / RQ;
+        if (Q.ntiles * 4 + 2 > ts_words) ts_words = Q.ntiles * 4 + 2;
+        if ((Q.ntiles > nreg ? Q.ntiles : nreg) + 1 > tlo_words) tlo_words = (Q.ntiles > nreg ? Q.ntiles : nreg) + 1;
+    }
+    uint32_t mbits = 1;
+    while (mbits < 32 && (1ull << mbits) < n) mbits++;
+    if (pbits + mbits > 64 || tiles >= (1ull << 32)) return FILTER_ERR_ARG;
+    if (tiles + 2 > ts_words) ts_words = tiles + 2;
+    if (tiles + 1 > tlo_words) tlo_words = tiles + 1;
+    GR->tiles = tiles;
+    GR->pbits = pbits;
+    GR->mbits = mbits;
+    GqfState &Q = GR->gqf;
+    Q.r = r;
+    Q.nblk = nblk_tot;
+    Q.nslots = nslots_tot;
+    Q.ntiles = tiles;
+    uint64_t scan_n = radix_tmp_words(M);
+    if (M + 1 > scan_n) scan_n = M + 1;
+    uint64_t bytes = 0;
+    Arena &A = GR->arena;
+    auto piece = [&](auto *&ptr, uint64_t count) {
+        using T_ = typename std::remove_reference<decltype(*ptr)>::type;
+        bytes += (count * sizeof(T_) + 255) & ~255ull;
+        if (!plan_only) ptr = A.take<T_>(count);
+    };
+    for (int b = 0; b < 2; b++) {
+        piece(Q.meta[b], nblk_tot * 32);
+        piece(Q.rem[b], nslots_tot * (r / 8));
+    }
+    piece(Q.fp_a, M);
+    piece(Q.fp_b, M);
+    piece(Q.fp_c, M);
+    piece(Q.ufp, M);
+    piece(Q.idx_a, M);
+    piece(Q.idx_b, M);
+    piece(Q.idx_c, M);
+    piece(Q.ustart, M + 1);
+    piece(Q.flags, M + 1);
+    piece(Q.removed, M);
+    piece(Q.tile_state, ts_words);
+    piece(Q.tile_lo, tlo_words);
+    piece(Q.radix_tmp, radix_tmp_words(M));
+    piece(GR->scan_tmp, scan_tmp_words(scan_n));
+    piece(GR->mctr, (uint64_t)n);
+    piece(GR->d_tile_member, tiles);
+    piece(GR->d_ovf, (uint64_t)n);
+    {
+        MergeArgs *ma = nullptr;
+        GqfMemberDev *gd = nullptr;
+        piece(ma, 4ull * n);
+        piece(gd, (uint64_t)n);
+        GR->d_margs = ma;
+        GR->d_gmem = gd;
+    }
+    bytes_out = bytes;
+    if (plan_only) return FILTER_OK;
+    if (!Q.meta[1] || !Q.rem[1] || !Q.radix_tmp || !GR->scan_tmp || !GR->mctr || !GR->d_tile_member || !GR->d_ovf ||
+        !GR->d_margs || !GR->d_gmem)
+        return FILTER_ERR_INTERNAL;
+    Q.cur = 0;
+    GR->cur = 0;
+    // member views, merge arguments [cur][del][member], hash and table descriptors
+    std::vector<MergeArgs> margs(4ull * n);
+    std::vector<GqfMemberDev> gmem(n);
+    std::vector<uint32_t> tmem(tiles);
+    for (uint32_t m = 0; m < n; m++) {
+        filter &F = GR->members[m];
+        F.cfg = V[m].cfg;
+        F.gqf = V[m].gqf;
+        GqfState &S = F.gqf;
+        for (int b = 0; b < 2; b++) {
+            S.meta[b] = Q.meta[b] + meta_off[m] * 32;
+            S.rem[b] = Q.rem[b] + rem_off[m] * (r / 8);
+        }
+        S.cur = 0;
+        S.fp_a = Q.fp_a;
+        S.fp_b = Q.fp_b;
+        S.fp_c = Q.fp_c;
+        S.ufp = Q.ufp;
+        S.idx_a = Q.idx_a;
+        S.idx_b = Q.idx_b;
+        S.idx_c = Q.idx_c;
+        S.ustart = Q.ustart;
+        S.flags = Q.flags;
+        S.removed = Q.removed;
+        S.tile_state = Q.tile_state;
+        S.tile_lo = Q.tile_lo;
+        S.radix_tmp = Q.radix_tmp;
+        F.ctr = GR->mctr + m;
+        F.scan_tmp = GR->scan_tmp;
+        F.arena.base = GR->arena.base;  // marks the view valid; the group owns the memory
+        F.device = GR->device;
+        gmem[m].H = S.H;
+        gmem[m].N = S.N;
+        gmem[m].nblk = S.nblk;
+        gmem[m].tile0 = tile0[m];
+        for (int b = 0; b < 2; b++) {
+            gmem[m].meta[b] = reinterpret_cast<const Meta *>(S.meta[b]);
+            gmem[m].rem[b] = S.rem[b];
+        }
+        for (uint64_t t = 0; t < S.ntiles; t++) tmem[tile0[m] + t] = m;
+        for (int cur = 0; cur < 2; cur++)
+            for (int del = 0; del < 2; del++) {
+                MergeArgs &a = margs[(uint64_t)(cur * 2 + del) * n + m];
+                a.meta_old = reinterpret_cast<const Meta *>(S.meta[cur]);
+                a.rem_old = S.rem[cur];
+                a.meta_new = reinterpret_cast<Meta *>(S.meta[cur ^ 1]);
+                a.rem_new = S.rem[cur ^ 1];
+                a.ufp = Q.ufp;
+                a.ustart = Q.ustart;
+                a.pm = nullptr;
+                a.tlo = Q.tile_lo + tile0[m];
+                a.m_limit = ~0ull;
+                a.removed = del ? Q.removed : nullptr;
+                a.ts = Q.tile_state + tile0[m];
+                a.ctr = GR->mctr + m;
+                a.N = S.N;
+                a.nslots = S.nslots;
+                a.nblk = S.nblk;
+                a.ntiles = S.ntiles;
+                a.fmask = S.H.mask;
+                a.tile0 = tile0[m];
+                a.r = r;
+                a.del = del;
+                a.dry = 0;
+            }
+    }
+    GF_CUDA(cudaMemcpy(GR->d_margs, margs.data(), margs.size() * sizeof(MergeArgs), cudaMemcpyHostToDevice));
+    GF_CUDA(cudaMemcpy(GR->d_gmem, gmem.data(), gmem.size() * sizeof(GqfMemberDev), cudaMemcpyHostToDevice));
+    if (tiles) GF_CUDA(cudaMemcpy(GR->d_tile_member, tmem.data(), tiles * 4, cudaMemcpyHostToDevice));
+    return FILTER_OK;
+}
+
+static void group_set_cur(filter_group *GR, int cur)
+{
+    GR->cur = cur;
+    GR->gqf.cur = cur;
+    for (uint32_t m = 0; m < GR->n; m++) GR->members[m].gqf.cur = cur;
+}
+
+int gqf_group_clear(filter_group *GR, cudaStream_t st)
+{
+    GqfState &Q = GR->gqf;
+    for (int b = 0; b < 2; b++) {
+        GF_CUDA(cudaMemsetAsync(Q.meta[b], 0, Q.nblk * 32, st));
+        GF_CUDA(cudaMemsetAsync(Q.rem[b], 0, Q.nslots * (Q.r / 8), st));
+    }
+    GF_CUDA(cudaMemsetAsync(GR->mctr, 0, GR->n * sizeof(DevCounters), st));
+    GF_CUDA(cudaMemsetAsync(GR->ctr, 0, sizeof(DevCounters), st));
+    group_set_cur(GR, 0);
+    return FILTER_OK;
+}
+
+// fingerprints, sort, reduction to groups (count of groups in flags[n])
+static void group_prepare(filter_group *GR, const uint64_t *off, const uint64_t *keys, uint64_t n, bool need_idx,
+                          cudaStream_t st)
+{
+    GqfState &Q = GR->gqf;
+    const int g = grid_for(n, 256, 8);
+    {
+        gf::TraceScope ts_("gqf_group_fp_kernel", n, st);
+        gqf_group_fp_kernel<<<g, 256, 0, st>>>(keys, n, off, GR->n, static_cast<const GqfMemberDev *>(GR->d_gmem),
+                                               GR->pbits, Q.fp_a, need_idx ? Q.idx_a : nullptr);
+    }
+    radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, GR->pbits + GR->mbits,
+                   Q.radix_tmp, GR->scan_tmp, GR->ctr, st);
+    {
+        gf::TraceScope ts_("gqf_flags", n + 1, st);
+        gqf_flags<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(Q.fp_b, n, Q.flags);
+    }
+    exclusive_scan_u32(Q.flags, Q.flags, n + 1, GR->scan_tmp, GR->ctr, st);
+    {
+        gf::TraceScope ts_("gqf_compact", n, st);
+        gqf_compact<<<g, 256, 0, st>>>(Q.fp_b, n, Q.flags, Q.ufp, Q.ustart);
+    }
+}
+
+static int group_merge(filter_group *GR, uint64_t n, int del, cudaStream_t st)
+{
+    GqfState &Q = GR->gqf;
+    const int nb = GR->cur ^ 1;
+    GF_CUDA(cudaMemsetAsync(Q.tile_state, 0, (GR->tiles + 2) * 8, st));
+    GF_CUDA(cudaMemsetAsync(Q.meta[nb], 0, Q.nblk * 32, st));
+    {
+        gf::TraceScope ts_("gqf_group_reset", GR->n, st);
+        gqf_group_reset<<<grid_for(GR->n, 256, 1), 256, 0, st>>>(GR->mctr, GR->n);
+    }
+    {
+        gf::TraceScope ts_("gqf_group_tile_ranges", GR->tiles + 1, st);
+        gqf_group_tile_ranges<<<grid_for(GR->tiles + 1, 256, 4), 256, 0, st>>>(
+            Q.ufp, Q.flags + n, GR->d_tile_member, static_cast<const GqfMemberDev *>(GR->d_gmem), GR->pbits, Q.r,
+            GR->tiles, Q.tile_lo);
+    }
+    const MergeArgs *tab = static_cast<const MergeArgs *>(GR->d_margs) + (uint64_t)(GR->cur * 2 + del) * GR->n;
+    {
+        gf::TraceScope ts_("gqf_merge_group_kernel", Q.nslots, st);
+        if (Q.r == 8)
+            gqf_merge_group_kernel<8><<<(unsigned)GR->tiles, MT, 0, st>>>(tab, GR->d_tile_member, Q.tile_state);
+        else
+            gqf_merge_group_kernel<16><<<(unsigned)GR->tiles, MT, 0, st>>>(tab, GR->d_tile_member, Q.tile_state);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+int gqf_group_insert(filter_group *GR, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *status,
+                     cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = GR->gqf;
+    group_prepare(GR, off, keys, n, status != nullptr, st);
+    int rc = group_merge(GR, n, 0, st);
+    if (rc) return rc;
+    if (status) {
+        gf::TraceScope ts_("gqf_status_kernel", n, st);
+        gqf_status_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(n, Q.flags, Q.ustart, Q.idx_b, Q.removed, ~0ull, 0,
+                                                              status);
+    }
+    GF_CUDA(cudaMemsetAsync(&GR->ctr->pend[0], 0, 4, st));
+    {
+        gf::TraceScope ts_("gqf_group_overflow", GR->n, st);
+        gqf_group_overflow<<<grid_for(GR->n, 256, 1), 256, 0, st>>>(GR->mctr, GR->n, GR->ctr, GR->d_ovf);
+    }
+    GF_CUDA(cudaGetLastError());
+    unsigned novf = 0;
+    if ((rc = read_dev(&GR->ctr->pend[0], &novf, st))) return rc;
+    if (novf) {
+        // members that do not fit: redo them alone from their old table, which
+        // keeps the longest prefix of their sorted groups that fits
+        std::vector<uint32_t> list(novf);
+        GF_CUDA(cudaMemcpyAsync(list.data(), GR->d_ovf, novf * 4, cudaMemcpyDeviceToHost, st));
+        GF_CUDA(cudaStreamSynchronize(st));
+        for (uint32_t m : list) {
+            uint64_t o[2];
+            GF_CUDA(cudaMemcpyAsync(o, off + m, 16, cudaMemcpyDeviceToHost, st));
+            GF_CUDA(cudaStreamSynchronize(st));
+            filter &F = GR->members[m];
+            F.gqf.cur = GR->cur;
+            if ((rc = gqf_insert(&F, keys + o[0], o[1] - o[0], status ? status + o[0] : nullptr, st))) return rc;
+        }
+    }
+    group_set_cur(GR, GR->cur ^ 1);
+    return FILTER_OK;
+}
+
+int gqf_group_remove(filter_group *GR, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *status,
+                     cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = GR->gqf;
+    group_prepare(GR, off, keys, n, status != nullptr, st);
+    int rc = group_merge(GR, n, 1, st);
+    if (rc) return rc;
+    if (status) {
+        gf::TraceScope ts_("gqf_status_kernel", n, st);
+        gqf_status_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(n, Q.flags, Q.ustart, Q.idx_b, Q.removed, 0, 1, status);
+    }
+    GF_CUDA(cudaGetLastError());
+    group_set_cur(GR, GR->cur ^ 1);
+    return FILTER_OK;
+}
+
+int gqf_group_count(filter_group *GR, const uint64_t *off, const uint64_t *keys, uint64_t n, uint64_t *counts,
+                    uint8_t *found, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    const int g = grid_for(n, 256, 16);
+    const GqfMemberDev *gm = static_cast<const GqfMemberDev *>(GR->d_gmem);
+    {
+        gf::TraceScope ts_("gqf_group_count_kernel", n, st);
+        if (GR->gqf.r == 8) gqf_group_count_kernel<8><<<g, 256, 0, st>>>(keys, n, off, GR->n, gm, GR->cur, counts, found);
+        else gqf_group_count_kernel<16><<<g, 256, 0, st>>>(keys, n, off, GR->n, gm, GR->cur, counts, found);
+    }
+    GF_CUDA(cudaGetLastError());
     return FILTER_OK;
 }
 

@@ -130,6 +130,58 @@ __host__ __device__ __forceinline__ uint64_t tcf_bucket(uint64_t e, uint64_t nbk
 }
 
 // ---------------------------------------------------------------------------
+// Filter groups: member m of a group call owns keys [off[m], off[m + 1]).
+// ---------------------------------------------------------------------------
+// The member holding key i: the largest m with off[m] <= i (so empty members
+// are skipped). off has n + 1 entries.
+__device__ __forceinline__ uint32_t member_of(const uint64_t *off, uint32_t n, uint64_t i)
+{
+    uint32_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= i) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Keys of a group call are split into one contiguous chunk per CTA, visited
+// in steps of blockDim.x, so a thread finds its member once by binary search
+// and then only steps forward.
+struct MemberCursor {
+    uint64_t i, end;
+    uint32_t m;
+    __device__ __forceinline__ MemberCursor(const uint64_t *off, uint32_t n, uint64_t n_keys)
+    {
+        const uint64_t per = (((n_keys + gridDim.x - 1) / gridDim.x) + 31) & ~31ull;  // warp-aligned chunks
+        const uint64_t c0 = per * blockIdx.x;
+        end = c0 + per < n_keys ? c0 + per : n_keys;
+        i = c0 + threadIdx.x;
+        m = i < end ? member_of(off, n, i) : 0;
+    }
+    __device__ __forceinline__ bool valid() const { return i < end; }
+    __device__ __forceinline__ void next(const uint64_t *off)
+    {
+        i += blockDim.x;
+        if (i < end)
+            while (__ldg(off + m + 1) <= i) m++;
+    }
+};
+
+// geometry of one TCF group member
+struct TcfMember {
+    uint64_t nb, nbk, seed;
+    uint64_t block0, bucket0;  // its first block and bucket in the group's arrays
+};
+
+// one key of a TCF group call, hashed for its member
+struct TcfPrep {
+    uint32_t b1, b2;      // group-wide block indices
+    uint32_t bucket, t;   // group-wide backing bucket, tag
+    uint64_t e;           // backing entry (member-local block index << f | tag)
+};
+
+// ---------------------------------------------------------------------------
 // Scratch arena: one cudaMalloc per filter, carved into aligned pieces.
 // ---------------------------------------------------------------------------
 struct Arena {
@@ -236,7 +288,49 @@ struct filter {
     int device = 0;
 };
 
+// A group of filters of one kind sharing one allocation and one set of
+// launches per call. members[m] is a host-side view of member m whose table
+// pointers point into the group's arrays and whose scratch is the group's.
+struct filter_group {
+    uint32_t kind = 0, n = 0;
+    uint32_t bits = 0;          // TCF f / GQF r, shared by all members
+    uint64_t max_total = 0;
+    gf::Arena arena;
+    gf::DevCounters *ctr = nullptr;   // group-wide (TCF counters; GQF overflow list length)
+    gf::DevCounters *mctr = nullptr;  // GQF: one per member
+    uint64_t *scan_tmp = nullptr;
+    filter *members = nullptr;
+    int device = 0;
+    // TCF: concatenated blocks, buckets and fill bytes; G.nb / G.nbk are the totals
+    TcfState tcf;
+    gf::TcfMember *d_tmem = nullptr;
+    gf::TcfPrep *prep = nullptr;
+    // GQF: meta[b] / rem[b] are the concatenated regions of all members
+    GqfState gqf;
+    uint64_t tiles = 0;               // total merge tiles
+    uint32_t pbits = 0, mbits = 0;    // sort key = member << pbits | fingerprint
+    void *d_margs = nullptr;          // merge arguments [cur][del][member]
+    void *d_gmem = nullptr;           // per-member hash and table descriptors
+    uint32_t *d_tile_member = nullptr;
+    uint32_t *d_ovf = nullptr;        // members that overflowed in the last insert
+    int cur = 0;
+};
+
 namespace gf {
+int tcf_group_setup(filter_group *G, const filter_config *cfgs, uint64_t &bytes, bool plan_only);
+int tcf_group_clear(filter_group *G, cudaStream_t st);
+int tcf_group_op(filter_group *G, int op, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *out,
+                 cudaStream_t st);
+int gqf_group_setup(filter_group *G, const filter_config *cfgs, uint64_t &bytes, bool plan_only);
+int gqf_group_clear(filter_group *G, cudaStream_t st);
+int gqf_group_insert(filter_group *G, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *status,
+                     cudaStream_t st);
+int gqf_group_remove(filter_group *G, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *status,
+                     cudaStream_t st);
+int gqf_group_count(filter_group *G, const uint64_t *off, const uint64_t *keys, uint64_t n, uint64_t *counts,
+                    uint8_t *found, cudaStream_t st);
+enum GroupOp : int { GROUP_INSERT = 0, GROUP_REMOVE = 1, GROUP_QUERY = 2 };
+
 int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);
 int tcf_clear(filter *F, cudaStream_t st);
 int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);

@@ -22,6 +22,7 @@
 // or TOMBSTONE slot by an atomic compare-and-swap, retried a bounded number of
 // times; deletes swap the tag for TOMBSTONE.
 #include <type_traits>
+#include <vector>
 
 #include "gf_internal.cuh"
 
@@ -178,22 +179,37 @@ enum Src : int { SRC_KEYS = 0, SRC_PEND_U32 = 1, SRC_PEND_U64 = 2 };
 // how a candidate picks its destination
 enum Dst : int { DST_B1 = 0, DST_TARGET = 1, DST_ALT = 2, DST_B2 = 3, DST_BUCKET = 4 };
 
+// Key i of the call: hashed here, or (group calls) read from the prepared
+// keys, whose block indices already address the group's concatenated arrays.
+__device__ __forceinline__ KeyInfo key_at(const uint64_t *keys, const TcfPrep *prep, uint64_t i, const TcfGeom &G)
+{
+    if (prep) {
+        const uint2 bb = *reinterpret_cast<const uint2 *>(prep + i);
+        KeyInfo k;
+        k.b1 = bb.x;
+        k.b2 = bb.y;
+        k.t = prep[i].t;
+        return k;
+    }
+    return tcf_keyinfo(keys[i], G);
+}
+
 __device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t pend_word, const TcfGeom &G,
-                                            const uint8_t *fill)
+                                            const uint8_t *fill, const TcfPrep *prep, uint64_t i)
 {
     switch (dst) {
     case DST_B1: return k.b1;
     case DST_B2: return k.b2;
     case DST_TARGET: return fill[k.b1] <= fill[k.b2] ? k.b1 : k.b2;
     case DST_ALT: return pend_word >> 32;
-    default: return tcf_bucket(tcf_entry(k, G.f), G.nbk);
+    default: return prep ? (uint64_t)prep[i].bucket : tcf_bucket(tcf_entry(k, G.f), G.nbk);
     }
 }
 
 template <int SRC, int DST>
-__global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, uint64_t n_keys,
-                                                      const void *pend, const unsigned *npend, TcfGeom G,
-                                                      const uint8_t *fill, uint32_t *cnt)
+__global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, const TcfPrep *prep,
+                                                      uint64_t n_keys, const void *pend, const unsigned *npend,
+                                                      TcfGeom G, const uint8_t *fill, uint32_t *cnt)
 {
     const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
     for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TPB) {
@@ -203,15 +219,16 @@ __global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict
             pw = static_cast<const uint64_t *>(pend)[j];
             i = pw & 0xffffffffu;
         }
-        KeyInfo k = tcf_keyinfo(keys[i], G);
-        atomicAdd(&cnt[dest_of(DST, k, pw, G, fill)], 1u);
+        KeyInfo k = key_at(keys, prep, i, G);
+        atomicAdd(&cnt[dest_of(DST, k, pw, G, fill, prep, i)], 1u);
     }
 }
 
 // rec = (tag << 32) | batch index, or the backing entry with the index in recI
 template <int SRC, int DST>
-__global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restrict__ keys, uint64_t n_keys,
-                                                         const void *pend, const unsigned *npend, TcfGeom G,
+__global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restrict__ keys, const TcfPrep *prep,
+                                                         uint64_t n_keys, const void *pend, const unsigned *npend,
+                                                         TcfGeom G,
                                                          const uint8_t *fill, uint32_t *cnt,
                                                          const uint32_t *__restrict__ off, uint64_t *rec,
                                                          uint32_t *recI)
@@ -224,11 +241,11 @@ __global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restr
             pw = static_cast<const uint64_t *>(pend)[j];
             i = pw & 0xffffffffu;
         }
-        KeyInfo k = tcf_keyinfo(keys[i], G);
-        uint64_t d = dest_of(DST, k, pw, G, fill);
+        KeyInfo k = key_at(keys, prep, i, G);
+        uint64_t d = dest_of(DST, k, pw, G, fill, prep, i);
         uint32_t pos = off[d] + atomicSub(&cnt[d], 1u) - 1u;
         if (DST == DST_BUCKET) {
-            rec[pos] = tcf_entry(k, G.f);
+            rec[pos] = prep ? prep[i].e : tcf_entry(k, G.f);
             recI[pos] = (uint32_t)i;
         } else {
             rec[pos] = ((uint64_t)k.t << 32) | i;
@@ -246,7 +263,7 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
                                                         const uint32_t *__restrict__ off,
                                                         const uint64_t *__restrict__ rec, int phase,
                                                         uint32_t cap, uint32_t *pend32, uint64_t *pend64,
-                                                        unsigned *npend)
+                                                        unsigned *npend, const TcfPrep *prep)
 {
     constexpr int B = Blk<F>::B;
     for (uint64_t b = blockIdx.x * (uint64_t)TPB + threadIdx.x; b < G.nb; b += (uint64_t)gridDim.x * TPB) {
@@ -290,7 +307,8 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
             uint32_t i = (uint32_t)r;
             unsigned slot = atomicAdd(npend, 1u);
             if (phase == 1) {
-                uint64_t alt = b ^ tcf_g((uint32_t)(r >> 32), G.nb);
+                // the other block of the pair: b1 + b2 - b
+                uint64_t alt = prep ? (uint64_t)prep[i].b1 + prep[i].b2 - b : b ^ tcf_g((uint32_t)(r >> 32), G.nb);
                 pend64[slot] = (alt << 32) | i;
             } else {
                 pend32[slot] = i;
@@ -731,12 +749,48 @@ int tcf_clear(filter *F, cudaStream_t st)
     return FILTER_OK;
 }
 
-template <int F>
-static void tcf_bulk_insert(filter *FL, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+// Everything one bulk call touches: a filter's own table, or for a group the
+// concatenated arrays of all members (G.nb and G.nbk are then the totals)
+// with the keys prepared per member.
+struct TcfBulk {
+    TcfGeom G;
+    uint8_t *blocks;
+    uint64_t *bk;
+    uint8_t *fill;
+    uint32_t *cnt, *off;
+    uint64_t *rec;
+    uint32_t *pend0;
+    uint64_t *pend1;
+    uint32_t *pend2;
+    uint64_t *scan_tmp;
+    DevCounters *ctr;
+    const TcfPrep *prep;
+};
+
+static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep *prep)
 {
-    TcfState &T = FL->tcf;
+    TcfBulk W;
+    W.G = T.G;
+    W.blocks = T.blocks;
+    W.bk = T.bk;
+    W.fill = T.fill;
+    W.cnt = T.cnt;
+    W.off = T.off;
+    W.rec = T.rec;
+    W.pend0 = T.pend0;
+    W.pend1 = T.pend1;
+    W.pend2 = T.pend2;
+    W.scan_tmp = scan_tmp;
+    W.ctr = ctr;
+    W.prep = prep;
+    return W;
+}
+
+template <int F>
+static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
     const TcfGeom G = T.G;
-    DevCounters *ctr = FL->ctr;
+    DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
     const int gk = grid_for(n, TPB, 8);
     const int gb = grid_for(G.nb, TPB, 8);
@@ -745,57 +799,57 @@ static void tcf_bulk_insert(filter *FL, const uint64_t *keys, uint64_t n, uint8_
     // A: shortcut into b1
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt);
+        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
+        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
                                                                 T.rec, nullptr);
     }
     {
         gf::TraceScope ts_("tcf_block_insert", G.nb, st);
-        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 0, G.tsc, T.pend0, nullptr, &np[0]);
+        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 0, G.tsc, T.pend0, nullptr, &np[0], T.prep);
     }
     // B: the less full of b1, b2 under the post-A fills
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt);
+        tcf_group_hist<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt,
+        tcf_group_scatter<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt,
                                                                         T.off, T.rec, nullptr);
     }
     {
         gf::TraceScope ts_("tcf_block_insert", G.nb, st);
-        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 1, G.B, nullptr, T.pend1, &np[1]);
+        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 1, G.B, nullptr, T.pend1, &np[1], T.prep);
     }
     // C: the other block
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, n, T.pend1, &np[1], G, T.fill, T.cnt);
+        tcf_group_hist<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend1, &np[1], G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, n, T.pend1, &np[1], G, T.fill, T.cnt, T.off,
+        tcf_group_scatter<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend1, &np[1], G, T.fill, T.cnt, T.off,
                                                                      T.rec, nullptr);
     }
     {
         gf::TraceScope ts_("tcf_block_insert", G.nb, st);
-        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 2, G.B, T.pend2, nullptr, &np[2]);
+        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 2, G.B, T.pend2, nullptr, &np[2], T.prep);
     }
     // D: backing buckets
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt);
+        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt,
+        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt,
                                                                         T.off, T.rec, T.pend0);
     }
     {
@@ -805,11 +859,10 @@ static void tcf_bulk_insert(filter *FL, const uint64_t *keys, uint64_t n, uint8_
 }
 
 template <int F>
-static void tcf_bulk_remove(filter *FL, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
 {
-    TcfState &T = FL->tcf;
     const TcfGeom G = T.G;
-    DevCounters *ctr = FL->ctr;
+    DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
     const int gk = grid_for(n, TPB, 8);
     const int gb = grid_for(G.nb, TPB, 8);
@@ -818,12 +871,12 @@ static void tcf_bulk_remove(filter *FL, const uint64_t *keys, uint64_t n, uint8_
     // 1: primary block
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt);
+        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
+        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
                                                                 T.rec, nullptr);
     }
     {
@@ -833,12 +886,12 @@ static void tcf_bulk_remove(filter *FL, const uint64_t *keys, uint64_t n, uint8_
     // 2: secondary block
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt);
+        tcf_group_hist<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, n, T.pend0, &np[0], G, T.fill, T.cnt, T.off,
+        tcf_group_scatter<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt, T.off,
                                                                     T.rec, nullptr);
     }
     {
@@ -848,12 +901,12 @@ static void tcf_bulk_remove(filter *FL, const uint64_t *keys, uint64_t n, uint8_
     // 3: backing bucket; what is left is not found
     {
         gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt);
+        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt);
     }
-    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, FL->scan_tmp, ctr, st);
+    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, T.scan_tmp, ctr, st);
     {
         gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, n, T.pend2, &np[2], G, T.fill, T.cnt,
+        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt,
                                                                         T.off, T.rec, T.pend0);
     }
     {
@@ -875,8 +928,9 @@ int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        if (T.G.f == 16) tcf_bulk_insert<16>(F, keys, n, status, st);
-        else tcf_bulk_insert<8>(F, keys, n, status, st);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, nullptr);
+        if (T.G.f == 16) tcf_bulk_insert<16>(W, keys, n, status, st);
+        else tcf_bulk_insert<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -895,8 +949,9 @@ int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             else tcf_point_remove<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        if (T.G.f == 16) tcf_bulk_remove<16>(F, keys, n, status, st);
-        else tcf_bulk_remove<8>(F, keys, n, status, st);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, nullptr);
+        if (T.G.f == 16) tcf_bulk_remove<16>(W, keys, n, status, st);
+        else tcf_bulk_remove<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -942,6 +997,223 @@ int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st)
         }
     }
     GF_CUDA(cudaStreamSynchronize(st));
+    return FILTER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Filter groups: every member's keys in one set of launches. A member's keys
+// are hashed with its own geometry, then every phase runs over the
+// concatenated blocks and buckets of all members. Candidates of one block
+// all belong to its member and keep their batch order, so each member ends
+// up exactly as a standalone filter given the same keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ TcfGeom member_geom(const TcfMember &M, uint32_t f)
+{
+    TcfGeom G;
+    G.nb = M.nb;
+    G.nbk = M.nbk;
+    G.seed = M.seed;
+    G.f = f;
+    G.B = 256 / f;
+    G.tsc = 3 * G.B / 4;
+    G.tmask = (1u << f) - 1u;
+    return G;
+}
+
+__global__ void __launch_bounds__(TPB) tcf_group_prep(const uint64_t *__restrict__ keys, uint64_t n,
+                                                      const uint64_t *__restrict__ off, uint32_t nmem,
+                                                      const TcfMember *__restrict__ mem, uint32_t f,
+                                                      TcfPrep *__restrict__ out)
+{
+    MemberCursor c(off, nmem, n);
+    uint32_t cm = 0xffffffffu;
+    TcfMember M;
+    TcfGeom G;
+    for (; c.valid(); c.next(off)) {
+        if (c.m != cm) {
+            cm = c.m;
+            M = mem[cm];
+            G = member_geom(M, f);
+        }
+        const KeyInfo k = tcf_keyinfo(__ldg(keys + c.i), G);
+        const uint64_t e = tcf_entry(k, f);
+        TcfPrep p;
+        p.b1 = (uint32_t)(M.block0 + k.b1);
+        p.b2 = (uint32_t)(M.block0 + k.b2);
+        p.bucket = (uint32_t)(M.bucket0 + tcf_bucket(e, M.nbk));
+        p.t = k.t;
+        p.e = e;
+        out[c.i] = p;
+    }
+}
+
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_group_query_kernel(const uint64_t *__restrict__ keys, uint64_t n,
+                                                              const uint64_t *__restrict__ off, uint32_t nmem,
+                                                              const TcfMember *__restrict__ mem,
+                                                              const uint8_t *__restrict__ blocks,
+                                                              const uint64_t *__restrict__ bk,
+                                                              const DevCounters *ctr, uint8_t *__restrict__ out)
+{
+    const bool backing = ctr->backing != 0;
+    MemberCursor c(off, nmem, n);
+    uint32_t cm = 0xffffffffu;
+    TcfMember M;
+    TcfGeom G;
+    for (; c.valid(); c.next(off)) {
+        if (c.m != cm) {
+            cm = c.m;
+            M = mem[cm];
+            G = member_geom(M, F);
+        }
+        const KeyInfo k = tcf_keyinfo(__ldg(keys + c.i), G);
+        Blk<F> x, y;
+        x.load_ro(blocks, M.block0 + k.b1);
+        y.load_ro(blocks, M.block0 + k.b2);
+        bool hit = x.has(k.t) || y.has(k.t);
+        if (!hit && backing) {
+            const uint64_t e = tcf_entry(k, F);
+            const ulonglong2 *p =
+                reinterpret_cast<const ulonglong2 *>(bk + (M.bucket0 + tcf_bucket(e, M.nbk)) * BK_W);
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                ulonglong2 v = __ldg(p + s);
+                hit |= (v.x == e) | (v.y == e);
+            }
+        }
+        out[c.i] = hit ? 1 : 0;
+    }
+}
+
+int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes_out, bool plan_only)
+{
+    const uint32_t n = GR->n;
+    const uint32_t f = cfgs[0].tag_bits;
+    const uint64_t M = GR->max_total ? GR->max_total : 1;
+    if (M > 0xffffffffull) return FILTER_ERR_ARG;
+    std::vector<TcfMember> tm(n);
+    uint64_t nb_tot = 0, nbk_tot = 0;
+    for (uint32_t m = 0; m < n; m++) {
+        const filter_config &c = cfgs[m];
+        if (c.kind != FILTER_TCF || c.tag_bits != f || c.mode != FILTER_MODE_BULK) return FILTER_ERR_ARG;
+        filter V;
+        V.cfg = c;
+        V.cfg.max_batch = M;
+        uint64_t tb = 0, sb = 0;
+        int rc = tcf_setup(&V, tb, sb, true);  // geometry only
+        if (rc != FILTER_OK) return rc;
+        tm[m].nb = V.tcf.G.nb;
+        tm[m].nbk = V.tcf.G.nbk;
+        tm[m].seed = V.tcf.G.seed;
+        tm[m].block0 = nb_tot;
+        tm[m].bucket0 = nbk_tot;
+        nb_tot += V.tcf.G.nb;
+        nbk_tot += V.tcf.G.nbk;
+    }
+    if (nb_tot > 0xffffffffull || nbk_tot > 0xffffffffull) return FILTER_ERR_ARG;  // 32-bit indices
+    TcfState &T = GR->tcf;
+    T.mode = FILTER_MODE_BULK;
+    T.G.f = f;
+    T.G.B = 256 / f;
+    T.G.tsc = 3 * T.G.B / 4;
+    T.G.tmask = (1u << f) - 1u;
+    T.G.nb = nb_tot;
+    T.G.nbk = nbk_tot;
+    T.G.seed = 0;
+    const uint64_t groups = (nb_tot > nbk_tot ? nb_tot : nbk_tot) + 1;
+    uint64_t bytes = 0;
+    Arena &A = GR->arena;
+    auto piece = [&](auto *&ptr, uint64_t count) {
+        using T_ = typename std::remove_reference<decltype(*ptr)>::type;
+        bytes += (count * sizeof(T_) + 255) & ~255ull;
+        if (!plan_only) ptr = A.take<T_>(count);
+    };
+    piece(T.blocks, nb_tot * 32);
+    piece(T.bk, nbk_tot * BK_W);
+    piece(T.fill, nb_tot);
+    piece(T.cnt, groups);
+    piece(T.off, groups);
+    piece(T.rec, M);
+    piece(T.pend0, M);
+    piece(T.pend1, M);
+    piece(T.pend2, M);
+    piece(GR->prep, M);
+    piece(GR->d_tmem, (uint64_t)n);
+    piece(GR->scan_tmp, scan_tmp_words(groups));
+    T.rec2 = nullptr;
+    bytes_out = bytes;
+    if (plan_only) return FILTER_OK;
+    if (!T.blocks || !T.bk || !T.fill || !T.cnt || !T.off || !T.rec || !T.pend0 || !T.pend1 || !T.pend2 ||
+        !GR->prep || !GR->d_tmem || !GR->scan_tmp)
+        return FILTER_ERR_INTERNAL;
+    GF_CUDA(cudaMemcpy(GR->d_tmem, tm.data(), n * sizeof(TcfMember), cudaMemcpyHostToDevice));
+    // host views of the members: their slices of the group's arrays
+    for (uint32_t m = 0; m < n; m++) {
+        filter &V = GR->members[m];
+        V.cfg = cfgs[m];
+        V.cfg.max_batch = M;
+        uint64_t tb = 0, sb = 0;
+        tcf_setup(&V, tb, sb, true);
+        TcfState &S = V.tcf;
+        S.blocks = T.blocks + tm[m].block0 * 32;
+        S.bk = T.bk + tm[m].bucket0 * BK_W;
+        S.fill = T.fill + tm[m].block0;
+        S.cnt = T.cnt;
+        S.off = T.off;
+        S.rec = T.rec;
+        S.rec2 = nullptr;
+        S.pend0 = T.pend0;
+        S.pend1 = T.pend1;
+        S.pend2 = T.pend2;
+        V.ctr = GR->ctr;
+        V.scan_tmp = GR->scan_tmp;
+        V.arena.base = GR->arena.base;  // marks the view valid; the group owns the memory
+        V.device = GR->device;
+    }
+    return FILTER_OK;
+}
+
+int tcf_group_clear(filter_group *GR, cudaStream_t st)
+{
+    TcfState &T = GR->tcf;
+    const uint64_t groups = (T.G.nb > T.G.nbk ? T.G.nb : T.G.nbk) + 1;
+    GF_CUDA(cudaMemsetAsync(T.blocks, 0, T.G.nb * 32, st));
+    GF_CUDA(cudaMemsetAsync(T.bk, 0, T.G.nbk * BK_W * 8, st));
+    GF_CUDA(cudaMemsetAsync(T.fill, 0, T.G.nb, st));
+    GF_CUDA(cudaMemsetAsync(T.cnt, 0, groups * 4, st));
+    GF_CUDA(cudaMemsetAsync(GR->ctr, 0, sizeof(DevCounters), st));
+    return FILTER_OK;
+}
+
+int tcf_group_op(filter_group *GR, int op, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *out,
+                 cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    TcfState &T = GR->tcf;
+    if (op == GROUP_QUERY) {
+        const int g = grid_for(n, TPB, 16);
+        gf::TraceScope ts_("tcf_group_query_kernel", n, st);
+        if (T.G.f == 16)
+            tcf_group_query_kernel<16><<<g, TPB, 0, st>>>(keys, n, off, GR->n, GR->d_tmem, T.blocks, T.bk, GR->ctr, out);
+        else
+            tcf_group_query_kernel<8><<<g, TPB, 0, st>>>(keys, n, off, GR->n, GR->d_tmem, T.blocks, T.bk, GR->ctr, out);
+        GF_CUDA(cudaGetLastError());
+        return FILTER_OK;
+    }
+    if (out) GF_CUDA(cudaMemsetAsync(out, 0, n, st));
+    {
+        gf::TraceScope ts_("tcf_group_prep", n, st);
+        tcf_group_prep<<<grid_for(n, TPB, 8), TPB, 0, st>>>(keys, n, off, GR->n, GR->d_tmem, T.G.f, GR->prep);
+    }
+    const TcfBulk W = bulk_of(T, GR->scan_tmp, GR->ctr, GR->prep);
+    if (op == GROUP_INSERT) {
+        if (T.G.f == 16) tcf_bulk_insert<16>(W, nullptr, n, out, st);
+        else tcf_bulk_insert<8>(W, nullptr, n, out, st);
+    } else {
+        if (T.G.f == 16) tcf_bulk_remove<16>(W, nullptr, n, out, st);
+        else tcf_bulk_remove<8>(W, nullptr, n, out, st);
+    }
+    GF_CUDA(cudaGetLastError());
     return FILTER_OK;
 }
 

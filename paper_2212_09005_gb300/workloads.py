@@ -179,3 +179,168 @@ def gqf_zipf_workload(q: int = 28, n: int = 240_000_000, seed: int = 3, s: float
     keys = zipf_keys(seed, n, s, universe)
     qpos = sample_with_replacement(seed * 1000 + 3, n, n_query)
     return {"q": q, "r": 8, "insert": keys, "query": keys[qpos]}
+
+
+def batched_workload(n_filters: int = 4096, seed: int = 4, emin: int = 10, emax: int = 20,
+                     load_lo: float = 0.85, load_hi: float = 0.95, tcf_rounds: int = 8):
+    """Many small filters: the first half TCF (16-bit tags, bulk mode), the
+    second half GQF (8-bit remainders). Filter i has 2^e_i slots (TCF) or home
+    slots (GQF), e_i uniform over the integers emin..emax (stream seed), and
+    receives floor(L_i * 2^e_i) distinct uniform keys with L_i uniform in
+    [load_lo, load_hi) (stream seed + 1); its hash seed is item i of stream
+    seed + 3. Insert keys are consecutive ranges of stream seed + 2 in filter
+    order; the negatives, one fresh key per inserted key, are consecutive
+    ranges of stream seed + 1000. TCF filters take their keys in `tcf_rounds`
+    near-equal consecutive chunks (round j inserts chunk j of every TCF
+    filter); GQF filters take theirs in one batch."""
+    span = emax - emin + 1
+    e = (emin + (splitmix64(seed, 0, n_filters) % np.uint64(span))).astype(np.int64)
+    load = load_lo + (load_hi - load_lo) * uniform01(seed + 1, 0, n_filters)
+    n_keys = np.floor(load * np.power(2.0, e)).astype(np.int64)
+    off = np.zeros(n_filters + 1, dtype=np.int64)
+    np.cumsum(n_keys, out=off[1:])
+    total = int(off[-1])
+    return {
+        "n_filters": n_filters, "n_tcf": n_filters // 2, "log2_slots": e, "n_keys": n_keys,
+        "offsets": off, "hash_seeds": splitmix64(seed + 3, 0, n_filters),
+        "insert": uniform_keys(seed + 2, total), "negatives": uniform_keys(seed + 1000, total),
+        "tcf_rounds": tcf_rounds,
+    }
+
+
+def round_chunks(offsets: np.ndarray, rounds: int):
+    """Split each filter's key range [offsets[i], offsets[i+1]) into `rounds`
+    near-equal consecutive chunks: returns (round, member) -> (start, end)
+    as an int64 array of shape (rounds, n, 2)."""
+    off = np.asarray(offsets, dtype=np.int64)
+    n = off.size - 1
+    lens = off[1:] - off[:-1]
+    out = np.empty((rounds, n, 2), dtype=np.int64)
+    for j in range(rounds):
+        out[j, :, 0] = off[:-1] + (lens * j) // rounds
+        out[j, :, 1] = off[:-1] + (lens * (j + 1)) // rounds
+    return out
+
+
+def keys_at(seed: int, pos: np.ndarray) -> np.ndarray:
+    """Items at arbitrary positions `pos` of stream `seed`."""
+    with np.errstate(over="ignore"):
+        state = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (np.asarray(pos).astype(np.uint64) + np.uint64(1)) * _GAMMA
+    return _mix(state)
+
+
+def uniform_keys_range(seed: int, start: int, n: int) -> np.ndarray:
+    """Items start .. start+n-1 of stream `seed` (as uniform_keys, from an offset)."""
+    out = np.empty(n, dtype=np.uint64)
+    for s in range(0, n, _CHUNK):
+        c = min(_CHUNK, n - s)
+        out[s:s + c] = splitmix64(seed, start + s, c)
+    return out
+
+
+def serving_workload(n_filters: int = 64, log2_slots: int = 24, seed: int = 5, bmin: int = 10, bmax: int = 24,
+                     mix=(0.50, 0.45, 0.05), prefill: float = 0.5, stop_load: float = 0.9,
+                     filter_cap: float = 0.95, max_requests: int = 100000):
+    """A request stream for a filter server: n_filters filters of 2^log2_slots
+    slots, the first half TCF and the second half GQF, each pre-filled to
+    `prefill` with distinct uniform keys. Every inserted key is a fresh item of
+    stream seed + 2 (consecutive positions). Request j picks a filter uniformly
+    (stream seed + 10, item j), an operation by `mix` (insert, query, delete;
+    stream seed + 11) and a size 2^u with u uniform in [bmin, bmax] (stream
+    seed + 12; log-uniform sizes).
+      insert: fresh keys, capped at what keeps the filter at or below
+        filter_cap of its slots (a filter already there gets a query instead);
+      query: half of the keys drawn uniformly, with replacement, from the keys
+        the filter was ever given (stream seed + 3), half fresh keys of stream
+        seed + 1000;
+      delete: distinct keys drawn from the filter's live keys (inserted, not yet
+        deleted), capped at the live count (stream seed + 4, by rejection).
+    The stream ends once the live keys of all filters reach stop_load of all
+    slots, or after max_requests requests. Returns the prefill batches (one per
+    filter) and the requests as (filter, op, keys), op 0 insert, 1 query,
+    2 delete."""
+    slots = 1 << log2_slots
+    cap = int(filter_cap * slots)
+    pre = int(prefill * slots)
+    ranges = [[(f * pre, (f + 1) * pre)] for f in range(n_filters)]  # inserted stream positions
+    live = [pre] * n_filters
+    nxt = n_filters * pre
+    dead = np.zeros(1 << 20, np.uint8)                                # deleted positions, one bit each
+    prefill_batches = [uniform_keys_range(seed + 2, a, b - a) for (a, b), in ranges]
+    total_live = pre * n_filters
+    goal = int(stop_load * slots * n_filters)
+    pick = splitmix64(seed + 10, 0, max_requests) % np.uint64(n_filters)
+    opu = uniform01(seed + 11, 0, max_requests)
+    szu = uniform01(seed + 12, 0, max_requests)
+
+    def positions(f, u):
+        """Map u in [0, 1) to positions in filter f's inserted ranges."""
+        lens = np.array([b - a for a, b in ranges[f]], np.int64)
+        starts = np.array([a for a, b in ranges[f]], np.int64)
+        cum = np.concatenate([[0], np.cumsum(lens)])
+        r = np.minimum((u * cum[-1]).astype(np.int64), cum[-1] - 1)
+        k = np.searchsorted(cum, r, side="right") - 1
+        return starts[k] + (r - cum[k])
+
+    reqs = []
+    j = 0
+    while total_live < goal and j < max_requests:
+        f = int(pick[j])
+        u = opu[j]
+        op = 0 if u < mix[0] else (1 if u < mix[0] + mix[1] else 2)
+        want = max(1, int(2.0 ** (bmin + (bmax - bmin) * szu[j])))
+        size = want
+        if op == 0 and cap - live[f] <= 0:
+            op = 1
+        elif op == 0:
+            size = min(want, cap - live[f])
+        if op == 2 and live[f] == 0:
+            op = 1
+        elif op == 2:
+            size = min(want, live[f])
+        if op == 0:
+            keys = uniform_keys_range(seed + 2, nxt, size)
+            ranges[f].append((nxt, nxt + size))
+            nxt += size
+            live[f] += size
+            total_live += size
+        elif op == 1:
+            h = size // 2
+            pos = positions(f, uniform01(seed + 3, j << 25, h))
+            keys = np.concatenate([keys_at(seed + 2, pos), uniform_keys_range(seed + 1000, j << 25, size - h)])
+        else:
+            while (nxt >> 3) + 1 > dead.size:
+                dead = np.concatenate([dead, np.zeros(dead.size, np.uint8)])
+            got = np.zeros(0, np.int64)
+            attempt = 0
+            while got.size < size:
+                a_seed = (seed + 4) ^ ((attempt * _ATTEMPT_SALT) & 0xFFFFFFFFFFFFFFFF)
+                cand = positions(f, uniform01(a_seed, j << 25, 2 * (size - got.size) + 16))
+                alive = ((dead[cand >> 3] >> (cand & 7).astype(np.uint8)) & 1) == 0
+                cand = cand[alive]
+                if got.size:
+                    gs = np.sort(got)
+                    at = np.minimum(np.searchsorted(gs, cand), gs.size - 1)
+                    cand = cand[gs[at] != cand]
+                order = np.argsort(cand, kind="stable")       # first occurrence of each position
+                sc = cand[order]
+                first = np.ones(sc.size, bool)
+                first[1:] = sc[1:] != sc[:-1]
+                cand = cand[np.sort(order[first])]
+                got = np.concatenate([got, cand[: size - got.size]])
+                attempt += 1
+            np.bitwise_or.at(dead, got >> 3, (np.uint8(1) << (got & 7).astype(np.uint8)))
+            keys = keys_at(seed + 2, got)
+            live[f] -= size
+            total_live -= size
+        reqs.append((f, op, keys))
+        j += 1
+    return {"n_filters": n_filters, "n_tcf": n_filters // 2, "log2_slots": log2_slots,
+            "prefill": prefill_batches, "requests": reqs}
+
+
+def poisson_arrivals(seed: int, n: int, rate: float) -> np.ndarray:
+    """n arrival times (seconds) of a Poisson process of `rate` per second:
+    cumulative exponential gaps -ln(1 - u) / rate, u from stream `seed`."""
+    u = uniform01(seed, 0, n)
+    return np.cumsum(-np.log1p(-u) / rate)

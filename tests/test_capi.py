@@ -63,3 +63,39 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(gf, "_lib", None)
     with pytest.raises(gf.FilterError):
         gf.lib()
+
+
+def test_group_configurations_rejected_without_gpu(libpath):
+    """Group creation validates the member list before touching the device."""
+    import paper_2212_09005_gb300 as gf
+
+    lib = gf.lib()
+    h = ctypes.c_void_p()
+
+    def create(cfgs):
+        arr = (gf.FilterConfig * len(cfgs))(*cfgs)
+        return lib.filter_group_create(arr, len(cfgs), 1000, None, ctypes.byref(h))
+
+    tcf = gf.FilterConfig(gf.FILTER_TCF, 12, 16, gf.MODE_BULK, 1, 1)
+    gqf = gf.FilterConfig(gf.FILTER_GQF, 12, 8, 0, 1, 1)
+    assert create([tcf, gqf]) == 1                                              # mixed kinds
+    assert create([tcf, gf.FilterConfig(gf.FILTER_TCF, 12, 8, 0, 1, 1)]) == 1    # mixed tag widths
+    assert create([gf.FilterConfig(gf.FILTER_TCF, 12, 16, gf.MODE_POINT, 1, 1)]) == 1  # point mode
+    assert create([gf.FilterConfig(gf.FILTER_GQF, 40, 16, 0, 1, 1)]) == 1        # q + r beyond limits
+    assert lib.filter_group_create(None, 0, 1, None, ctypes.byref(h)) == 1
+    assert lib.filter_group_insert(None, None, None, 0, None, None) == 1
+    assert lib.filter_group_destroy(None) == 0
+
+
+def test_server_arguments_rejected_without_gpu(libpath):
+    import paper_2212_09005_gb300 as gf
+
+    lib = gf.lib()
+    h = ctypes.c_void_p()
+    assert lib.filter_server_create(None, 0, 1, 16, ctypes.byref(h)) == 1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.filter_server_create(arr, 1, 1, 16, ctypes.byref(h)) == 1  # null filter
+    t = ctypes.c_uint64()
+    assert lib.filter_server_submit(None, None, ctypes.byref(t)) == 1
+    assert lib.filter_server_wait(None, 1, None, None) == 1
+    assert lib.filter_server_destroy(None) == 0
