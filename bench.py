@@ -84,7 +84,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
-    ap.add_argument("--case", default="full", choices=["full", "profile", "batched"],
+    ap.add_argument("--case", default="full", choices=["full", "profile", "batched", "serving"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
     return ap.parse_args()
@@ -474,6 +474,84 @@ def run_batched(args, device):
     return out
 
 
+SERVING_WORKLOAD = ("serving loop: 64 filters of 2^24 slots (32 TCF f=16 bulk + 32 counting GQF r=8, "
+                    "2^30 slots in all) pre-filled to 50%; batches of 2^10..2^24 keys (log-uniform) for a "
+                    "uniformly chosen filter, 50/45/5 insert/query/delete, until 90% aggregate load; host "
+                    "keys in, host results out (page-locked buffers); 8 worker streams; Poisson arrivals at 0.5x and 0.8x of the "
+                    "back-to-back capacity")
+
+
+def run_serving(args, device):
+    """Capacity (every request submitted at once) and latency under Poisson
+    arrivals at 0.5x and 0.8x of that capacity, from the same pre-filled state."""
+    import time as _t
+
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    w = W.serving_workload()
+    reqs, nt, lg = w["requests"], w["n_tcf"], w["log2_slots"]
+    mb = max(max(len(b) for b in w["prefill"]), max(len(k) for _, _, k in reqs))
+    fs = [gf.TCF(lg, 16, gf.MODE_BULK, seed=5000 + i, max_batch=mb) if i < nt else
+          gf.GQF(lg, 8, seed=5000 + i, max_batch=mb) for i in range(w["n_filters"])]
+    pre = [torch.from_numpy(b.view(np.int64)).to(device) for b in w["prefill"]]
+
+    def prefill():
+        for f, b in zip(fs, pre):
+            f.clear()
+            f.insert(b)
+        torch.cuda.synchronize()
+
+    ops = sum(len(k) for _, _, k in reqs)
+    # request keys and results in page-locked host memory, as a server's
+    # receive buffers would be
+    kbuf = torch.empty(ops, dtype=torch.int64).pin_memory()
+    obuf = torch.empty(ops, dtype=torch.uint8).pin_memory()
+    kv, ov = kbuf.numpy().view(np.uint64), obuf.numpy()
+    spans, at = [], 0
+    for _, _, k in reqs:
+        kv[at:at + len(k)] = k
+        spans.append((at, at + len(k)))
+        at += len(k)
+    S = gf.FilterServer(fs, workers=8, max_keys=max(len(k) for _, _, k in reqs))
+
+    def run(arrivals):
+        prefill()
+        t0 = _t.perf_counter()
+        tickets = []
+        for j, (f, op, keys) in enumerate(reqs):
+            if arrivals is not None:
+                while _t.perf_counter() - t0 < arrivals[j]:
+                    pass
+            a, b = spans[j]
+            tickets.append(S.submit(f, op, kv[a:b], out=ov[a:b]))
+        lat = [S.wait(t)[1] for t in tickets]
+        sec = _t.perf_counter() - t0
+        return sec, np.array(lat)
+
+    run(None)  # warm-up
+    sec, lat = run(None)
+    cap = ops / sec
+    out = {"workload": SERVING_WORKLOAD, "requests": len(reqs), "ops": ops, "capacity_gops": round(cap / 1e9, 4),
+           "capacity_p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+           "capacity_p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "loads": []}
+    mean_ops = ops / len(reqs)
+    for frac in (0.5, 0.8):
+        rate = frac * cap / mean_ops
+        arr = W.poisson_arrivals(25, len(reqs), rate)
+        sec, lat = run(arr)
+        out["loads"].append({"load": frac, "offered_gops": round(frac * cap / 1e9, 4),
+                             "achieved_gops": round(ops / sec / 1e9, 4),
+                             "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                             "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)})
+    S.close()
+    del fs, pre, kbuf, obuf
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_e2e(R, args, world, device):
     """Same step through the C ABI with inputs in pinned host memory: every step
     copies its keys host->device and its results device->host."""
@@ -579,6 +657,16 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         line = run_reference(args, rank, world)
+    elif args.case == "serving":
+        import torch
+
+        torch.cuda.set_device(local)
+        sv = run_serving(args, torch.device("cuda", local))
+        hi = sv["loads"][-1]
+        line = {"metric": METRIC, "value": hi["achieved_gops"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+                "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": {"workload": SERVING_WORKLOAD},
+                "serving": sv}
     elif args.case == "batched":
         import torch
 

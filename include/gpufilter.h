@@ -307,7 +307,9 @@ int filter_group_export(filter_group_t *g, uint32_t member, void *host_buf, uint
  *   Every filter's max_batch must be >= the batches submitted to it.
  * filter_server_submit: enqueue one request and return at once with a
  *   ticket. The key buffer (host memory, pageable or pinned) and the output
- *   buffer must stay valid until the ticket is collected. host_out receives
+ *   buffer must stay valid until the ticket is collected. Page-locked buffers
+ *   (cudaHostAlloc / cudaHostRegister) are copied to and from the device
+ *   directly; pageable ones go through the worker's pinned staging. host_out receives
  *   n bytes of statuses (insert, remove) or found flags (query), or n uint64
  *   counts (count, GQF only); NULL discards the results. FILTER_ERR_ARG for
  *   a bad filter index or op, n > max_keys, or a server being destroyed.

@@ -308,10 +308,17 @@ class FilterServer:
         self._h = h
         self._pending = {}
 
-    def submit(self, filter_index: int, op: int, keys: np.ndarray, want_out: bool = True) -> int:
-        """Enqueue a batch; returns a ticket. The arrays are kept until wait()."""
+    def submit(self, filter_index: int, op: int, keys: np.ndarray, out: np.ndarray = None,
+               want_out: bool = True) -> int:
+        """Enqueue a batch; returns a ticket. The arrays are kept until wait().
+        `out` (optional) receives the results; page-locked arrays (e.g. numpy
+        views of pinned torch tensors) skip the staging copies."""
         keys = np.ascontiguousarray(keys, dtype=np.uint64)
-        out = np.zeros(keys.size, self._OUT_DTYPE[op]) if want_out else None
+        if out is not None:
+            if out.size < keys.size or out.dtype != self._OUT_DTYPE[op] or not out.flags.c_contiguous:
+                raise FilterError("out must be a contiguous array of n results of the op's type")
+        elif want_out:
+            out = np.zeros(keys.size, self._OUT_DTYPE[op])
         req = FilterRequest(filter_index, op, keys.ctypes.data_as(C.c_void_p), keys.size,
                             out.ctypes.data_as(C.c_void_p) if out is not None else None)
         t = C.c_uint64()

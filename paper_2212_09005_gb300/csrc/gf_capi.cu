@@ -18,7 +18,8 @@ static bool pointers_set(const filter *F)
     if (!F->ctr || !F->scan_tmp) return false;
     if (F->cfg.kind == FILTER_TCF) {
         const TcfState &T = F->tcf;
-        return T.blocks && T.bk && T.fill && T.cnt && T.off && T.rec && T.rec2 && T.pend0 && T.pend1 && T.pend2;
+        return T.blocks && T.bk && T.fill && T.cnt && T.off && T.rec && T.pend0 && T.pend1 && T.pend2 && T.tlist &&
+               T.tcount && T.dlist && T.seg;
     }
     const GqfState &Q = F->gqf;
     return Q.meta[0] && Q.meta[1] && Q.rem[0] && Q.rem[1] && Q.fp_a && Q.fp_b && Q.fp_c && Q.ufp && Q.idx_a &&

@@ -754,11 +754,15 @@ __global__ void gqf_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t
 // removing copies from a run only shifts the rest of its cluster left, never
 // past a home slot, so a delete is local to its cluster. One thread per
 // region of RQ quotients applies the region's groups largest first; even
-// regions run first, then odd ones. A read-only pre-check makes sure that
-// every affected cluster ends before the region after next, so that two
-// threads of a phase never touch the same slots or metadata words.
+// regions run first, then odd ones. A read-only pre-check measures how far
+// past its home slot every affected cluster reaches; RQ is then the smallest
+// power of two >= RQ_MIN covering that reach, so that every cluster touched
+// from region r ends before region r + 2 and two threads of a phase never
+// touch the same slots or metadata words. Reaches above RQ_MAX (long
+// clusters at high load) take the merge instead.
 // ---------------------------------------------------------------------------
-static constexpr long long RQ = 4096;  // quotients per delete region (a multiple of 64)
+static constexpr long long RQ_MIN = 256;     // quotients per delete region, smallest (a multiple of 64)
+static constexpr long long RQ_MAX = 1 << 16;
 
 struct GView {
     Meta *meta;
@@ -960,12 +964,12 @@ __device__ uint64_t gv_delete(const GView &g, uint64_t fp, uint64_t d, unsigned 
 
 // first group of every delete region (successor search)
 __global__ void gqf_region_ranges(const uint64_t *__restrict__ ufp, const uint32_t *pm, uint64_t N, uint32_t r,
-                                  uint64_t nreg, uint32_t *rlo)
+                                  uint64_t rq, uint64_t nreg, uint32_t *rlo)
 {
     const uint64_t m = *pm;
     for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t <= nreg;
          t += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t q0 = t * (uint64_t)RQ;
+        const uint64_t q0 = t * rq;
         const uint64_t key = q0 >= N ? (N << r) : (q0 << r);
         uint64_t lo = 0, hi = m;
         while (lo < hi) {
@@ -977,26 +981,28 @@ __global__ void gqf_region_ranges(const uint64_t *__restrict__ ufp, const uint32
     }
 }
 
-// read-only: does the cluster tail of every group end before the region after next?
+// read-only: the largest reach (cluster tail end - home slot + 1) over the
+// groups to delete, capped just above RQ_MAX
 template <int R>
 __global__ void gqf_delete_precheck(GView g, const uint64_t *__restrict__ ufp, const uint32_t *pm,
-                                    unsigned long long *bad)
+                                    unsigned long long *reach)
 {
     const uint64_t m = *pm;
+    unsigned long long mine = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < m; i += (uint64_t)gridDim.x * blockDim.x) {
         const long long x = (long long)(ufp[i] >> R);
         if (x >= g.N || !gv_occ(g, x)) continue;
-        long long limit = (x / RQ + 2) * RQ;
-        if (limit > g.nslots) limit = g.nslots;
         long long prev = gv_runend_of(g, x), y = x;
-        while (prev >= 0 && prev < limit) {
+        while (prev >= 0 && prev - x < RQ_MAX) {
             const long long yn = gv_next_occ(g, y, prev + 1);
             if (yn < 0) break;
             prev = gv_next_runend(g, prev + 1);
             y = yn;
         }
-        if (prev < 0 || prev >= limit) atomicExch(bad, 1ull);
+        const unsigned long long r = prev < 0 ? (unsigned long long)RQ_MAX + 1 : (unsigned long long)(prev - x + 1);
+        mine = r > mine ? r : mine;
     }
+    if (mine) atomicMax(reach, mine);
 }
 
 template <int R>
@@ -1196,7 +1202,7 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     piece(Q.flags, M + 1);
     piece(Q.removed, M);
     piece(Q.tile_state, Q.ntiles * 4 + 2);
-    piece(Q.tile_lo, (Q.ntiles > (Q.N + RQ - 1) / RQ ? Q.ntiles : (Q.N + RQ - 1) / RQ) + 1);
+    piece(Q.tile_lo, (Q.ntiles > (Q.N + RQ_MIN - 1) / RQ_MIN ? Q.ntiles : (Q.N + RQ_MIN - 1) / RQ_MIN) + 1);
     piece(Q.radix_tmp, radix_tmp_words(M));
     piece(F->scan_tmp, scan_tmp_words(scan_n));
     scratch_bytes = bytes - table_bytes;
@@ -1348,22 +1354,25 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
     if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
     bool done = false;
     if ((uint64_t)m * 4 <= Q.nslots) {
-        const uint64_t nreg = (Q.N + RQ - 1) / RQ;
         GView g{reinterpret_cast<Meta *>(Q.meta[Q.cur]), Q.rem[Q.cur], (long long)Q.N, (long long)Q.nslots,
                 (long long)Q.nblk};
-        {
-            gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);
-            gqf_region_ranges<<<grid_for(nreg + 1, 256, 4), 256, 0, st>>>(Q.ufp, Q.flags + n, Q.N, Q.r, nreg, Q.tile_lo);
-        }
         GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
         {
             gf::TraceScope ts_("gqf_delete_precheck", m, st);
             if (Q.r == 8) gqf_delete_precheck<8><<<grid_for(m, 256, 8), 256, 0, st>>>(g, Q.ufp, Q.flags + n, &F->ctr->overflow);
             else gqf_delete_precheck<16><<<grid_for(m, 256, 8), 256, 0, st>>>(g, Q.ufp, Q.flags + n, &F->ctr->overflow);
         }
-        unsigned long long bad = 0;
-        if ((rc = read_dev(&F->ctr->overflow, &bad, st))) return rc;
-        if (!bad) {
+        unsigned long long reach = 0;
+        if ((rc = read_dev(&F->ctr->overflow, &reach, st))) return rc;
+        uint64_t rq = RQ_MIN;
+        while ((unsigned long long)rq < reach) rq <<= 1;
+        if (rq <= (uint64_t)RQ_MAX) {
+            const uint64_t nreg = (Q.N + rq - 1) / rq;
+            {
+                gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);
+                gqf_region_ranges<<<grid_for(nreg + 1, 256, 4), 256, 0, st>>>(Q.ufp, Q.flags + n, Q.N, Q.r, rq, nreg,
+                                                                             Q.tile_lo);
+            }
             const uint64_t half = (nreg + 1) / 2;
             for (int ph = 0; ph < 2; ph++) {
                 gf::TraceScope ts_("gqf_delete_phase", half, st);
@@ -1548,7 +1557,7 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
         nslots_tot += Q.nslots;
         tiles += Q.ntiles;
         if (Q.p > pbits) pbits = Q.p;
-        const uint64_t nreg = (Q.N + RQ - 1) / RQ;
+        const uint64_t nreg = (Q.N + RQ_MIN - 1) / RQ_MIN;
         if (Q.ntiles * 4 + 2 > ts_words) ts_words = Q.ntiles * 4 + 2;
         if ((Q.ntiles > nreg ? Q.ntiles : nreg) + 1 > tlo_words) tlo_words = (Q.ntiles > nreg ? Q.ntiles : nreg) + 1;
     }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "../../include/gpufilter.h"
@@ -41,8 +42,12 @@ struct DevCounters {
     unsigned int pend[8];         // TCF: pending-list lengths per phase
     unsigned int tile_ctr[4];     // dynamic tile counters
     long long gqf_end;            // GQF merge: end of the last run (dry runs)
-    unsigned long long pad[5];
+    unsigned int touched[4];      // TCF sparse phases: touched destinations (cursor must follow)
+    unsigned int cursor[4];       // TCF sparse phases: records placed so far
+    unsigned long long pad[1];
 };
+static_assert(offsetof(DevCounters, cursor) == offsetof(DevCounters, touched) + sizeof(DevCounters::touched),
+              "touched and cursor are cleared together");
 
 // ---------------------------------------------------------------------------
 // Hashing (paper Sec. 5.1 fingerprint h; Sec. 4 block/tag hash). Bijective:
@@ -251,10 +256,15 @@ struct TcfState {
     uint32_t *cnt;     // max(nb, nbk) + 1, kept zero between phases
     uint32_t *off;     // max(nb, nbk) + 1
     uint64_t *rec;     // max_batch
-    uint64_t *rec2;    // max_batch
     uint32_t *pend0;   // max_batch
     uint64_t *pend1;   // max_batch
     uint32_t *pend2;   // max_batch
+    // sparse phases: destinations touched per CTA chunk, then the dense list
+    // of touched destinations with their record segments
+    uint32_t *tlist;   // max_batch
+    uint32_t *tcount;  // one per CTA of a phase launch
+    uint32_t *dlist;   // max_batch
+    uint64_t *seg;     // max_batch: start << 32 | count
 };
 
 struct GqfState {

@@ -182,12 +182,17 @@ size_t radix_tmp_words(uint64_t n)
     return tiles * RS_MAXB + 1;
 }
 
+// Per-tile digit counts. Each warp counts into its own shared histogram
+// with plain shared atomics (equal digits inside one warp serialise on one
+// address, which is cheaper than ranking them), then the warps' counts are
+// summed per digit.
 __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ keys, uint64_t n, uint32_t shift,
                                                 uint32_t nb, uint32_t *counts, uint64_t ntiles)
 {
-    __shared__ uint32_t h[RS_MAXB];
-    for (uint32_t d = threadIdx.x; d < nb; d += RS_T) h[d] = 0;
+    __shared__ uint32_t h[RS_WARPS][RS_MAXB];
+    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB; i += RS_T) (&h[0][0])[i] = 0;
     __syncthreads();
+    const int warp = threadIdx.x >> 5;
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
     uint64_t k[RS_I];
 #pragma unroll
@@ -198,34 +203,43 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
         uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
-        uint32_t d = (i < n) ? ((uint32_t)(k[r] >> shift) & (nb - 1)) : 0xffffu;
-        // equal digits of a warp are counted once (skewed multisets)
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        int leader = __ffs(peers) - 1;
-        if (d != 0xffffu && (int)(threadIdx.x & 31) == leader) atomicAdd(&h[d], (uint32_t)__popc(peers));
+        if (i < n) atomicAdd(&h[warp][(uint32_t)(k[r] >> shift) & (nb - 1)], 1u);
     }
     __syncthreads();
-    for (uint32_t d = threadIdx.x; d < nb; d += RS_T) counts[(uint64_t)d * ntiles + blockIdx.x] = h[d];
+    for (uint32_t d = threadIdx.x; d < nb; d += RS_T) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) c += h[w][d];
+        counts[(uint64_t)d * ntiles + blockIdx.x] = c;
+    }
 }
 
+// Scatter of one pass. Keys are ranked inside each warp (match_any groups
+// equal digits; a per-warp 16-bit counter per digit carries the rank across
+// the warp's 16 rounds), the per-digit warp offsets and the tile's digit
+// starts come from a scan in shared memory, and the keys are staged in digit
+// order together with their global index, so that the copy-out writes runs
+// of consecutive addresses and needs no further lookups. Shared memory and
+// registers are sized for 3 CTAs per SM (2 with values).
 template <bool VALS>
-__global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ kin,
-                                                   uint64_t *__restrict__ kout,
-                                                   const uint32_t *__restrict__ vin,
-                                                   uint32_t *__restrict__ vout, uint64_t n,
-                                                   uint32_t shift, uint32_t nb, const uint32_t *__restrict__ offs,
-                                                   uint64_t ntiles)
+__global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t *__restrict__ kin,
+                                                      uint64_t *__restrict__ kout,
+                                                      const uint32_t *__restrict__ vin,
+                                                      uint32_t *__restrict__ vout, uint64_t n,
+                                                      uint32_t shift, uint32_t nb, const uint32_t *__restrict__ offs,
+                                                      uint64_t ntiles)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint32_t *wcnt = reinterpret_cast<uint32_t *>(smem);              // [8][512]
-    uint32_t *dstart = wcnt + RS_WARPS * RS_MAXB;                      // [512]
-    uint32_t *dglob = dstart + RS_MAXB;                                // [512]
-    uint64_t *skeys = reinterpret_cast<uint64_t *>(dglob + RS_MAXB);   // [4096]
-    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + RS_TILE);   // [4096]
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(smem);           // [RS_TILE] keys in digit order
+    uint32_t *sg = reinterpret_cast<uint32_t *>(skeys + RS_TILE);   // [RS_TILE] their global index
+    uint32_t *svals = sg + RS_TILE;                                 // [RS_TILE] values (VALS)
+    uint32_t *gdelta = svals + (VALS ? RS_TILE : 0);                // [RS_MAXB] global start - tile start
+    uint16_t *wcnt = reinterpret_cast<uint16_t *>(gdelta + RS_MAXB); // [RS_WARPS][RS_MAXB]
+    uint16_t *dstart = wcnt + RS_WARPS * RS_MAXB;                   // [RS_MAXB] tile start of each digit
     __shared__ uint32_t s_w[RS_WARPS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB; i += RS_T) wcnt[i] = 0;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB / 2; i += RS_T) reinterpret_cast<uint32_t *>(wcnt)[i] = 0;
     __syncthreads();
 
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
@@ -249,7 +263,7 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
         unsigned peers = __match_any_sync(0xffffffffu, d);
         uint32_t b = ok ? wcnt[warp * RS_MAXB + d] : 0;
         __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) wcnt[warp * RS_MAXB + d] = b + __popc(peers);
+        if (ok && lane == __ffs(peers) - 1) wcnt[warp * RS_MAXB + d] = (uint16_t)(b + __popc(peers));
         __syncwarp();
         rank[r] = (uint16_t)(b + __popc(peers & lt));
     }
@@ -266,11 +280,10 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
 #pragma unroll
                 for (int w = 0; w < RS_WARPS; w++) {
                     uint32_t c = wcnt[w * RS_MAXB + d];
-                    wcnt[w * RS_MAXB + d] = acc;
+                    wcnt[w * RS_MAXB + d] = (uint16_t)acc;
                     acc += c;
                 }
                 tot[h] = acc;
-                dglob[d] = offs[(uint64_t)d * ntiles + blockIdx.x];
             }
         }
         const uint32_t pair = tot[0] + tot[1];
@@ -285,8 +298,15 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
         uint32_t wpre = 0;
         for (int w = 0; w < warp; w++) wpre += s_w[w];
         const uint32_t ex = wpre + incl - pair;
-        if (2 * threadIdx.x < nb) dstart[2 * threadIdx.x] = ex;
-        if (2 * threadIdx.x + 1 < nb) dstart[2 * threadIdx.x + 1] = ex + tot[0];
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const uint32_t d = 2 * threadIdx.x + h;
+            const uint32_t st = h ? ex + tot[0] : ex;
+            if (d < nb) {
+                dstart[d] = (uint16_t)st;
+                gdelta[d] = offs[(uint64_t)d * ntiles + blockIdx.x] - st;
+            }
+        }
     }
     __syncthreads();
 #pragma unroll
@@ -294,23 +314,30 @@ __global__ void __launch_bounds__(RS_T) rs_scatter(const uint64_t *__restrict__ 
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)(key[r] >> shift) & (nb - 1);
-            uint32_t pos = dstart[d] + wcnt[warp * RS_MAXB + d] + rank[r];
+            uint32_t pos = (uint32_t)dstart[d] + wcnt[warp * RS_MAXB + d] + rank[r];
             skeys[pos] = key[r];
+            sg[pos] = gdelta[d] + pos;
             if (VALS) svals[pos] = val[r];
         }
     }
     __syncthreads();
     const uint32_t cnt = (uint32_t)((n - base) < (uint64_t)RS_TILE ? (n - base) : RS_TILE);
-    for (uint32_t k = threadIdx.x; k < cnt; k += RS_T) {
-        uint64_t kk = skeys[k];
-        uint32_t d = (uint32_t)(kk >> shift) & (nb - 1);
-        uint64_t g = (uint64_t)dglob[d] + (k - dstart[d]);
-        __stcs(kout + g, kk);
-        if (VALS) __stcs(vout + g, svals[k]);
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        const uint32_t k = r * RS_T + threadIdx.x;
+        if (k < cnt) {
+            const uint32_t g = sg[k];
+            __stcs(kout + g, skeys[k]);
+            if (VALS) __stcs(vout + g, svals[k]);
+        }
     }
 }
 
-static constexpr size_t RS_SMEM = (RS_WARPS * RS_MAXB + 2 * RS_MAXB) * 4 + RS_TILE * 8 + RS_TILE * 4;
+template <bool VALS>
+static constexpr size_t rs_smem()
+{
+    return RS_TILE * 8 + RS_TILE * 4 + (VALS ? RS_TILE * 4 : 0) + RS_MAXB * 4 + RS_WARPS * RS_MAXB * 2 + RS_MAXB * 2;
+}
 
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt, uint64_t n,
@@ -320,8 +347,8 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
     if (n == 0) return;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
-        cudaFuncSetAttribute(rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
+        cudaFuncSetAttribute(rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
         attr_done = true;
     }
     const bool vals = vals_in != nullptr;
@@ -349,10 +376,10 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         exclusive_scan_u32(tmp, tmp, ntiles * nb, scan_tmp, ctr, st);
         TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
         if (vals)
-            rs_scatter<true><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb,
+            rs_scatter<true><<<(unsigned)ntiles, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb,
                                                                      tmp, ntiles);
         else
-            rs_scatter<false><<<(unsigned)ntiles, RS_T, RS_SMEM, st>>>(ksrc, kdst, nullptr, nullptr, n,
+            rs_scatter<false><<<(unsigned)ntiles, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n,
                                                                       shift, nb, tmp, ntiles);
         ksrc = kdst;
         vsrc = vdst;

@@ -8,7 +8,8 @@
 // flight: a batch's results are the same alone and in the mix. Workers run
 // concurrently on their own streams and pinned staging buffers; a worker
 // handles one request at a time (host keys -> pinned staging -> device, the
-// filter operation, results -> pinned staging -> caller's buffer).
+// filter operation, results -> pinned staging -> caller's buffer); page-locked
+// caller buffers skip the staging copies.
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -67,14 +68,29 @@ namespace {
 
 static int out_bytes(uint32_t op) { return op == FILTER_OP_COUNT ? 8 : 1; }
 
+// page-locked host memory can be copied to and from the device directly
+static bool page_locked(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
 static int run_one(filter_server *S, Worker &W, const filter_request &r)
 {
     filter_t *f = S->filters[r.filter];
     const uint64_t n = r.n;
     const size_t ob = (size_t)out_bytes(r.op) * n;
     if (n) {
-        std::memcpy(W.h_keys, r.host_keys, n * 8);
-        GF_CUDA(cudaMemcpyAsync(W.d_keys, W.h_keys, n * 8, cudaMemcpyHostToDevice, W.stream));
+        const uint64_t *src = r.host_keys;
+        if (!page_locked(src)) {  // pageable: through the worker's pinned staging
+            std::memcpy(W.h_keys, src, n * 8);
+            src = W.h_keys;
+        }
+        GF_CUDA(cudaMemcpyAsync(W.d_keys, src, n * 8, cudaMemcpyHostToDevice, W.stream));
     }
     int rc;
     switch (r.op) {
@@ -94,9 +110,11 @@ static int run_one(filter_server *S, Worker &W, const filter_request &r)
         rc = FILTER_ERR_ARG;
     }
     if (rc != FILTER_OK) return rc;
-    if (n && r.host_out) GF_CUDA(cudaMemcpyAsync(W.h_out, W.d_out, ob, cudaMemcpyDeviceToHost, W.stream));
+    const bool direct = n && r.host_out && page_locked(r.host_out);
+    if (n && r.host_out)
+        GF_CUDA(cudaMemcpyAsync(direct ? r.host_out : W.h_out, W.d_out, ob, cudaMemcpyDeviceToHost, W.stream));
     GF_CUDA(cudaStreamSynchronize(W.stream));
-    if (n && r.host_out) std::memcpy(r.host_out, W.h_out, ob);
+    if (n && r.host_out && !direct) std::memcpy(r.host_out, W.h_out, ob);
     return FILTER_OK;
 }
 

@@ -113,6 +113,47 @@ struct Blk {
             return c >> 3;
         }
     }
+    // bit s set where slot s holds tag t
+    __device__ __forceinline__ uint32_t eq_slots(uint32_t t) const
+    {
+        uint32_t sm = 0;
+        if (F == 16) {
+            const uint32_t tt = t | (t << 16);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t m = __vcmpeq2(w[k], tt);
+                sm |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * k);
+            }
+        } else {
+            const uint32_t tt = t * 0x01010101u;
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint32_t m = __vcmpeq4(w[k], tt);
+                sm |= ((m & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u)) << (4 * k);
+            }
+        }
+        return sm;
+    }
+    // bits of word k below bit position bp of the 256-bit block
+    static __device__ __forceinline__ uint32_t low_bits(int k, int bp)
+    {
+        const int lo = bp - 32 * k;
+        return lo >= 32 ? 0xffffffffu : (lo <= 0 ? 0u : ((1u << lo) - 1u));
+    }
+    // slot pos is removed: slots above it move down by one, the last becomes EMPTY
+    __device__ __forceinline__ void delete_at(int pos)
+    {
+        const int bp = pos * F;
+        uint32_t nw[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t sh = k < 7 ? __funnelshift_r(w[k], w[k + 1], F) : (w[7] >> F);
+            const uint32_t lo = low_bits(k, bp);
+            nw[k] = (w[k] & lo) | (sh & ~lo);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) w[k] = nw[k];
+    }
     // pack B tags (ascending, zero padded) from an array
     __device__ __forceinline__ void pack(const uint32_t *t)
     {
@@ -124,6 +165,44 @@ struct Blk {
         }
     }
 };
+
+// sort up to 8 records held in registers (absent ones are ~0 and sort last):
+// a 19-comparator network of depth 6, or 5 comparators for the first 4
+// when no lane of the warp has more; r8[0] is consumed by shifting the rest
+// down, which keeps the array in registers
+__device__ __forceinline__ void cswap(uint64_t &a, uint64_t &b)
+{
+    const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+    a = lo;
+    b = hi;
+}
+__device__ __forceinline__ void sort4(uint64_t (&r)[8])
+{
+    cswap(r[0], r[1]); cswap(r[2], r[3]);
+    cswap(r[0], r[2]); cswap(r[1], r[3]);
+    cswap(r[1], r[2]);
+}
+__device__ __forceinline__ void sort8(uint64_t (&r)[8])
+{
+    cswap(r[0], r[2]); cswap(r[1], r[3]); cswap(r[4], r[6]); cswap(r[5], r[7]);
+    cswap(r[0], r[4]); cswap(r[1], r[5]); cswap(r[2], r[6]); cswap(r[3], r[7]);
+    cswap(r[0], r[1]); cswap(r[2], r[3]); cswap(r[4], r[5]); cswap(r[6], r[7]);
+    cswap(r[2], r[4]); cswap(r[3], r[5]);
+    cswap(r[1], r[4]); cswap(r[3], r[6]);
+    cswap(r[1], r[2]); cswap(r[3], r[4]); cswap(r[5], r[6]);
+}
+__device__ __forceinline__ void shift_down(uint64_t (&r)[8])
+{
+#pragma unroll
+    for (int q = 0; q < 7; q++) r[q] = r[q + 1];
+    r[7] = ~0ull;
+}
+__device__ __forceinline__ void sort_small(uint64_t (&r)[8], uint32_t cnt)
+{
+    const uint32_t wmax = __reduce_max_sync(__activemask(), cnt);
+    if (wmax > 4) sort8(r);
+    else if (wmax > 1) sort4(r);
+}
 
 // keep the `have` smallest values seen so far in a[0..have), ascending, at most k
 __device__ __forceinline__ int topk_push(uint64_t *a, int have, int k, uint64_t v)
@@ -206,13 +285,36 @@ __device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t 
     }
 }
 
-template <int SRC, int DST>
+// A CTA's share of a sparse phase's candidates: one contiguous, warp-aligned
+// chunk (the touched destinations it finds are listed from the chunk's start)
+__device__ __forceinline__ void cta_chunk(uint64_t n, uint64_t &c0, uint64_t &c1)
+{
+    const uint64_t per = (((n + gridDim.x - 1) / gridDim.x) + 31) & ~31ull;
+    c0 = per * blockIdx.x;
+    if (c0 > n) c0 = n;
+    c1 = c0 + per < n ? c0 + per : n;
+}
+
+// Dense phases count every candidate per destination; sparse phases (few
+// candidates, as in the later phases) also list each destination the first
+// time it is hit, per CTA chunk, in tlist[c0 ..] with the count in tcount.
+template <int SRC, int DST, bool SPARSE>
 __global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, const TcfPrep *prep,
                                                       uint64_t n_keys, const void *pend, const unsigned *npend,
-                                                      TcfGeom G, const uint8_t *fill, uint32_t *cnt)
+                                                      TcfGeom G, const uint8_t *fill, uint32_t *cnt,
+                                                      uint32_t *tlist, uint32_t *tcount)
 {
     const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
-    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TPB) {
+    __shared__ unsigned s_n;
+    uint64_t c0 = 0, c1 = n, step = (uint64_t)gridDim.x * TPB, j = blockIdx.x * (uint64_t)TPB + threadIdx.x;
+    if (SPARSE) {
+        if (threadIdx.x == 0) s_n = 0;
+        __syncthreads();
+        cta_chunk(n, c0, c1);
+        step = TPB;
+        j = c0 + threadIdx.x;
+    }
+    for (; j < c1; j += step) {
         uint64_t pw = 0, i = j;
         if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[j];
         if (SRC == SRC_PEND_U64) {
@@ -220,7 +322,65 @@ __global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict
             i = pw & 0xffffffffu;
         }
         KeyInfo k = key_at(keys, prep, i, G);
-        atomicAdd(&cnt[dest_of(DST, k, pw, G, fill, prep, i)], 1u);
+        const uint64_t d = dest_of(DST, k, pw, G, fill, prep, i);
+        if (SPARSE) {
+            if (atomicAdd(&cnt[d], 1u) == 0u) tlist[c0 + atomicAdd(&s_n, 1u)] = (uint32_t)d;
+        } else {
+            atomicAdd(&cnt[d], 1u);
+        }
+    }
+    if (SPARSE) {
+        __syncthreads();
+        if (threadIdx.x == 0) tcount[blockIdx.x] = s_n;
+    }
+}
+
+// Sparse phases: every touched destination gets a contiguous segment of the
+// record array (CTA-wide scan of the counts, one atomic per 256 destinations)
+// and an entry in the dense touched list. Same grid as the histogram.
+__global__ void __launch_bounds__(TPB) tcf_alloc(const unsigned *npend, uint64_t n_keys,
+                                                 const uint32_t *__restrict__ tlist,
+                                                 const uint32_t *__restrict__ tcount, const uint32_t *cnt,
+                                                 uint32_t *off, uint32_t *dlist, uint64_t *seg, unsigned *cursor,
+                                                 unsigned *nlist)
+{
+    __shared__ uint32_t s_w[TPB / 32];
+    __shared__ uint32_t s_base, s_lbase;
+    const uint64_t n = npend ? (uint64_t)*npend : n_keys;
+    uint64_t c0, c1;
+    cta_chunk(n, c0, c1);
+    const uint32_t m = tcount[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t j0 = 0; j0 < m; j0 += TPB) {
+        const uint32_t j = j0 + threadIdx.x;
+        const uint32_t d = j < m ? tlist[c0 + j] : 0u;
+        const uint32_t c = j < m ? cnt[d] : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        uint32_t pre = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < TPB / 32; w++) {
+            if (w < warp) pre += s_w[w];
+            tot += s_w[w];
+        }
+        if (threadIdx.x == 0) {
+            s_base = atomicAdd(cursor, tot);
+            s_lbase = atomicAdd(nlist, m - j0 < (uint32_t)TPB ? m - j0 : (uint32_t)TPB);
+        }
+        __syncthreads();
+        if (j < m) {
+            const uint32_t start = s_base + pre + incl - c;
+            off[d] = start;
+            dlist[s_lbase + threadIdx.x] = d;
+            seg[s_lbase + threadIdx.x] = ((uint64_t)start << 32) | c;
+        }
+        __syncthreads();
     }
 }
 
@@ -258,60 +418,116 @@ __global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restr
 // ---------------------------------------------------------------------------
 // phase 0 (A): cap = 3B/4, rejects -> pend_u32; phase 1 (B): cap = B, rejects
 // -> pend_u64 (alt block << 32 | index); phase 2 (C): cap = B, rejects -> pend_u32
+// The blocks of a phase: every block with the scanned offsets (dense phases),
+// or only the touched ones with their segments (sparse phases, dlist set).
+struct PhaseDst {
+    const uint32_t *off;     // dense: nb + 1 scanned offsets
+    const uint32_t *dlist;   // sparse: touched destinations
+    const uint64_t *seg;     // sparse: start << 32 | count
+    const unsigned *nlist;   // sparse: number of touched destinations
+};
+
+__device__ __forceinline__ uint64_t phase_count(const PhaseDst &P, uint64_t dense_n)
+{
+    return P.dlist ? (uint64_t)*P.nlist : dense_n;
+}
+
+// destination j of the phase with its record range [s, e)
+__device__ __forceinline__ uint64_t phase_dst(const PhaseDst &P, uint64_t j, uint32_t &s, uint32_t &e)
+{
+    if (P.dlist) {
+        const uint64_t sg = P.seg[j];
+        s = (uint32_t)(sg >> 32);
+        e = s + (uint32_t)sg;
+        return P.dlist[j];
+    }
+    s = P.off[j];
+    e = P.off[j + 1];
+    return j;
+}
+
+// A warp reserves room for all its lanes' entries of a pending list with one
+// atomic; lane l's entries start at the returned position. Every lane of the
+// warp must call it.
+__device__ __forceinline__ uint32_t warp_reserve(unsigned *counter, uint32_t mine)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t base = 0;
+    if (lane == 31 && total) base = atomicAdd(counter, total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + incl - mine;
+}
+
+// The grid-stride loops of the per-block kernels step whole warps, so that
+// every lane reaches warp_reserve in every iteration.
 template <int F>
-__global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill,
-                                                        const uint32_t *__restrict__ off,
+__global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
                                                         const uint64_t *__restrict__ rec, int phase,
                                                         uint32_t cap, uint32_t *pend32, uint64_t *pend64,
                                                         unsigned *npend, const TcfPrep *prep)
 {
     constexpr int B = Blk<F>::B;
-    for (uint64_t b = blockIdx.x * (uint64_t)TPB + threadIdx.x; b < G.nb; b += (uint64_t)gridDim.x * TPB) {
-        const uint32_t s = off[b], e = off[b + 1];
-        if (s == e) continue;
-        const uint32_t cnt = e - s;
-        const uint32_t f0 = fill[b];
-        const uint32_t k = cap > f0 ? min(cnt, cap - f0) : 0u;
-        uint64_t a[MAXSEL];
-        int have = 0;
-        uint64_t thr = 0;  // records <= thr are accepted
-        if (k > 0) {
-            for (uint32_t j = s; j < e; j++) have = topk_push(a, have, (int)k, rec[j]);
-            thr = a[k - 1];
-            Blk<F> blk;
-            blk.load(blocks, b);
-            uint32_t t_out[B];
-            int ia = 0, ib = 0;
+    const uint64_t nd = phase_count(P, G.nb);
+    const uint64_t stride = (uint64_t)gridDim.x * TPB;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
+        const uint64_t j = j0 + (threadIdx.x & 31);
+        uint32_t s = 0, e = 0, k = 0;
+        uint64_t b = 0, thr = 0;  // records <= thr are accepted
+        if (j < nd) {
+            b = phase_dst(P, j, s, e);
+            if (s != e) {
+                const uint32_t cnt = e - s;
+                const uint32_t f0 = fill[b];
+                k = cap > f0 ? min(cnt, cap - f0) : 0u;
+                if (k > 0) {
+                    uint64_t a[MAXSEL];
+                    int have = 0;
+                    for (uint32_t q = s; q < e; q++) have = topk_push(a, have, (int)k, rec[q]);
+                    thr = a[k - 1];
+                    Blk<F> blk;
+                    blk.load(blocks, b);
+                    uint32_t t_out[B];
+                    int ia = 0, ib = 0;
 #pragma unroll
-            for (int p = 0; p < B; p++) {
-                uint32_t ta = (ia < (int)f0) ? blk.tag(ia) : 0xffffffffu;
-                uint32_t tb = (ib < (int)k) ? (uint32_t)(a[ib] >> 32) : 0xffffffffu;
-                if (ta == 0xffffffffu && tb == 0xffffffffu) {
-                    t_out[p] = 0;
-                } else if (ta <= tb) {
-                    t_out[p] = ta;
-                    ia++;
-                } else {
-                    t_out[p] = tb;
-                    ib++;
+                    for (int p = 0; p < B; p++) {
+                        uint32_t ta = (ia < (int)f0) ? blk.tag(ia) : 0xffffffffu;
+                        uint32_t tb = (ib < (int)k) ? (uint32_t)(a[ib] >> 32) : 0xffffffffu;
+                        if (ta == 0xffffffffu && tb == 0xffffffffu) {
+                            t_out[p] = 0;
+                        } else if (ta <= tb) {
+                            t_out[p] = ta;
+                            ia++;
+                        } else {
+                            t_out[p] = tb;
+                            ib++;
+                        }
+                    }
+                    blk.pack(t_out);
+                    blk.store(blocks, b);
+                    fill[b] = (uint8_t)(f0 + k);
                 }
             }
-            blk.pack(t_out);
-            blk.store(blocks, b);
-            fill[b] = (uint8_t)(f0 + k);
         }
-        if (k == cnt) continue;
-        for (uint32_t j = s; j < e; j++) {
-            uint64_t r = rec[j];
+        const uint32_t nrej = (e - s) - k;
+        uint32_t slot = warp_reserve(npend, nrej);
+        if (nrej == 0) continue;
+        for (uint32_t q = s; q < e; q++) {
+            const uint64_t r = rec[q];
             if (k > 0 && r <= thr) continue;
-            uint32_t i = (uint32_t)r;
-            unsigned slot = atomicAdd(npend, 1u);
+            const uint32_t i = (uint32_t)r;
             if (phase == 1) {
                 // the other block of the pair: b1 + b2 - b
                 uint64_t alt = prep ? (uint64_t)prep[i].b1 + prep[i].b2 - b : b ^ tcf_g((uint32_t)(r >> 32), G.nb);
-                pend64[slot] = (alt << 32) | i;
+                pend64[slot++] = (alt << 32) | i;
             } else {
-                pend32[slot] = i;
+                pend32[slot++] = i;
             }
         }
     }
@@ -319,14 +535,15 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
 
 // backing buckets: candidates (entry in rec, index in recI) taken in (entry,
 // index) order while there is room; the rest are FULL
-__global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk,
-                                                         const uint32_t *__restrict__ off,
+__global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk, PhaseDst P,
                                                          const uint64_t *__restrict__ rec,
                                                          const uint32_t *__restrict__ recI, uint8_t *status,
                                                          DevCounters *ctr)
 {
-    for (uint64_t q = blockIdx.x * (uint64_t)TPB + threadIdx.x; q < G.nbk; q += (uint64_t)gridDim.x * TPB) {
-        const uint32_t s = off[q], e = off[q + 1];
+    const uint64_t nd = phase_count(P, G.nbk);
+    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < nd; j += (uint64_t)gridDim.x * TPB) {
+        uint32_t s, e;
+        const uint64_t q = phase_dst(P, j, s, e);
         if (s == e) continue;
         uint64_t cur[BK_W];
         int used = 0;
@@ -392,117 +609,127 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk
 // the c smallest (tag, index) candidates with that tag remove one copy each.
 // ---------------------------------------------------------------------------
 template <int F>
-__global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill,
-                                                        const uint32_t *__restrict__ off,
+__global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
                                                         const uint64_t *__restrict__ rec, uint32_t *pend32,
                                                         unsigned *npend)
 {
     constexpr int B = Blk<F>::B;
-    for (uint64_t b = blockIdx.x * (uint64_t)TPB + threadIdx.x; b < G.nb; b += (uint64_t)gridDim.x * TPB) {
-        const uint32_t s = off[b], e = off[b + 1];
-        if (s == e) continue;
-        const uint32_t f0 = fill[b];
-        Blk<F> blk;
-        blk.load(blocks, b);
-        if (e - s <= 8) {
-            // small segment: sort the candidates, then each takes the first
-            // remaining copy of its tag; the block stays sorted
-            uint64_t r8[8];
-            int c = 0;
-            for (uint32_t j = s; j < e; j++) {
-                uint64_t v = rec[j];
-                int q = c++;
-                while (q > 0 && r8[q - 1] > v) {
-                    r8[q] = r8[q - 1];
-                    q--;
-                }
-                r8[q] = v;
-            }
-            uint32_t gone = 0;
-            for (int q = 0; q < c; q++) {
-                const uint32_t t = (uint32_t)(r8[q] >> 32);
-                int hit = -1;
-#pragma unroll
-                for (int p = 0; p < B; p++)
-                    if (hit < 0 && p < (int)f0 && !((gone >> p) & 1u) && blk.tag(p) == t) hit = p;
-                if (hit >= 0) gone |= 1u << hit;
-                else pend32[atomicAdd(npend, 1u)] = (uint32_t)r8[q];
-            }
-            if (gone) {
-                uint32_t t_out[B];
-                int o = 0;
-#pragma unroll
-                for (int p = 0; p < B; p++)
-                    if (p < (int)f0 && !((gone >> p) & 1u)) t_out[o++] = blk.tag(p);
-                for (int p = o; p < B; p++) t_out[p] = 0;
-                blk.pack(t_out);
-                blk.store(blocks, b);
-                fill[b] = (uint8_t)o;
-            }
-            continue;
-        }
-        uint32_t tags[B];
-#pragma unroll
-        for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
-        // per distinct stored tag: threshold record (the c-th smallest with that tag)
-        uint32_t dt[B];
-        uint32_t dc[B];
+    const uint64_t nd = phase_count(P, G.nb);
+    const uint64_t stride = (uint64_t)gridDim.x * TPB;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
+        const uint64_t j = j0 + (threadIdx.x & 31);
+        uint32_t s = 0, e = 0, nunm = 0, unm = 0;
+        bool fast = false;
+        uint64_t r8[8];  // fast path: the candidates, sorted
+        // general path: per distinct stored tag, the copies, the candidates
+        // that matched and the largest matched record
+        uint32_t dt[B], dc[B], used[B];
         uint64_t thr[B];
-        uint32_t used[B];
-        int nd = 0;
-        for (int p = 0; p < (int)f0; p++) {
-            if (nd > 0 && dt[nd - 1] == tags[p]) {
-                dc[nd - 1]++;
-            } else {
-                dt[nd] = tags[p];
-                dc[nd] = 1;
-                nd++;
+        int ndt = 0;
+        if (j < nd) {
+            const uint64_t b = phase_dst(P, j, s, e);
+            if (s != e) {
+                const uint32_t f0 = fill[b];
+                Blk<F> blk;
+                blk.load(blocks, b);
+                int removed = 0;
+                if (e - s <= 8) {
+                    // few candidates: sort them in registers; each takes the
+                    // first remaining copy of its tag, so the block stays sorted
+                    fast = true;
+                    const uint32_t c = e - s;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) r8[q] = (uint32_t)q < c ? rec[s + q] : ~0ull;
+                    sort_small(r8, c);
+                    uint64_t w8[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) w8[q] = r8[q];
+                    for (uint32_t q = 0; q < c; q++) {
+                        const uint32_t sm = blk.eq_slots((uint32_t)(w8[0] >> 32));
+                        if (sm) {
+                            blk.delete_at(__ffs(sm) - 1);
+                            removed++;
+                        } else {
+                            unm |= 1u << q;
+                            nunm++;
+                        }
+                        shift_down(w8);
+                    }
+                    if (removed) {
+                        blk.store(blocks, b);
+                        fill[b] = (uint8_t)(f0 - removed);
+                    }
+                } else {
+                    uint32_t tags[B];
+#pragma unroll
+                    for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
+                    for (int p = 0; p < (int)f0; p++) {
+                        if (ndt > 0 && dt[ndt - 1] == tags[p]) {
+                            dc[ndt - 1]++;
+                        } else {
+                            dt[ndt] = tags[p];
+                            dc[ndt] = 1;
+                            ndt++;
+                        }
+                    }
+                    for (int d = 0; d < ndt; d++) {
+                        uint64_t a[MAXSEL];
+                        int have = 0;
+                        uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
+                        for (uint32_t q = s; q < e; q++) {
+                            uint64_t r = rec[q];
+                            if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
+                        }
+                        used[d] = (uint32_t)have;
+                        thr[d] = have ? a[have - 1] : 0;
+                    }
+                    // rebuild the block without the removed copies
+                    uint32_t t_out[B];
+                    int o = 0;
+                    for (int d = 0; d < ndt; d++) {
+                        for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = dt[d];
+                        removed += (int)used[d];
+                    }
+                    for (int p = o; p < B; p++) t_out[p] = 0;
+                    if (removed) {
+                        blk.pack(t_out);
+                        blk.store(blocks, b);
+                        fill[b] = (uint8_t)(f0 - removed);
+                    }
+                    nunm = (e - s) - (uint32_t)removed;
+                }
             }
-        }
-        for (int d = 0; d < nd; d++) {
-            uint64_t a[MAXSEL];
-            int have = 0;
-            uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
-            for (uint32_t j = s; j < e; j++) {
-                uint64_t r = rec[j];
-                if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
-            }
-            used[d] = (uint32_t)have;
-            thr[d] = have ? a[have - 1] : 0;
-        }
-        // rebuild the block without the removed copies
-        uint32_t t_out[B];
-        int o = 0, removed = 0;
-        for (int d = 0; d < nd; d++) {
-            for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = dt[d];
-            removed += (int)used[d];
-        }
-        for (int p = o; p < B; p++) t_out[p] = 0;
-        if (removed) {
-            blk.pack(t_out);
-            blk.store(blocks, b);
-            fill[b] = (uint8_t)(f0 - removed);
         }
         // unmatched candidates go on
-        for (uint32_t j = s; j < e; j++) {
-            uint64_t r = rec[j];
-            uint32_t t = (uint32_t)(r >> 32);
-            bool matched = false;
-            for (int d = 0; d < nd; d++)
-                if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
-            if (!matched) pend32[atomicAdd(npend, 1u)] = (uint32_t)r;
+        uint32_t slot = warp_reserve(npend, nunm);
+        if (nunm == 0) continue;
+        if (fast) {
+            for (uint32_t q = 0; q < e - s; q++) {
+                if ((unm >> q) & 1u) pend32[slot++] = (uint32_t)r8[0];
+                shift_down(r8);
+            }
+        } else {
+            for (uint32_t q = s; q < e; q++) {
+                const uint64_t r = rec[q];
+                const uint32_t t = (uint32_t)(r >> 32);
+                bool matched = false;
+                for (int d = 0; d < ndt; d++)
+                    if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
+                if (!matched) pend32[slot++] = (uint32_t)r;
+            }
         }
     }
 }
 
-__global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk,
-                                                         const uint32_t *__restrict__ off,
+__global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk, PhaseDst P,
                                                          const uint64_t *__restrict__ rec,
                                                          const uint32_t *__restrict__ recI, uint8_t *status,
                                                          DevCounters *ctr)
 {
-    for (uint64_t q = blockIdx.x * (uint64_t)TPB + threadIdx.x; q < G.nbk; q += (uint64_t)gridDim.x * TPB) {
-        const uint32_t s = off[q], e = off[q + 1];
+    const uint64_t nd = phase_count(P, G.nbk);
+    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < nd; j += (uint64_t)gridDim.x * TPB) {
+        uint32_t s, e;
+        const uint64_t q = phase_dst(P, j, s, e);
         if (s == e) continue;
         // distinct stored entries (the bucket is sorted) with their copy counts
         uint64_t dv[BK_W];
@@ -728,10 +955,13 @@ int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     piece(T.cnt, groups);
     piece(T.off, groups);
     piece(T.rec, M);
-    piece(T.rec2, M);
     piece(T.pend0, M);
     piece(T.pend1, M);
     piece(T.pend2, M);
+    piece(T.tlist, M);
+    piece(T.tcount, (uint64_t)sm_count() * 8);
+    piece(T.dlist, M);
+    piece(T.seg, M);
     piece(F->scan_tmp, scan_tmp_words(groups));
     scratch_bytes = bytes - table_bytes;
     return FILTER_OK;
@@ -762,6 +992,8 @@ struct TcfBulk {
     uint32_t *pend0;
     uint64_t *pend1;
     uint32_t *pend2;
+    uint32_t *tlist, *tcount, *dlist;
+    uint64_t *seg;
     uint64_t *scan_tmp;
     DevCounters *ctr;
     const TcfPrep *prep;
@@ -780,10 +1012,64 @@ static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, 
     W.pend0 = T.pend0;
     W.pend1 = T.pend1;
     W.pend2 = T.pend2;
+    W.tlist = T.tlist;
+    W.tcount = T.tcount;
+    W.dlist = T.dlist;
+    W.seg = T.seg;
     W.scan_tmp = scan_tmp;
     W.ctr = ctr;
     W.prep = prep;
     return W;
+}
+
+// CTAs of the grouping launches of a phase (the same for histogram and
+// segment allocation, whose chunks must agree)
+static int group_grid(uint64_t n) { return grid_for(n, TPB, 8); }
+
+// Groups one phase's candidates by destination. The first phase of a call
+// (all keys, most blocks hit) is dense: per-destination counts, an exclusive
+// scan over all destinations, then the scatter. Later phases see few
+// candidates and are sparse: only the touched destinations get a segment and
+// a list entry (slot: the phase's counters), so their per-destination kernel
+// visits those alone. `recI` (bucket phases) receives the batch indices.
+template <int SRC, int DST>
+static PhaseDst group_phase(const TcfBulk &T, const uint64_t *keys, uint64_t n, const void *pend,
+                            const unsigned *npend, int slot, uint32_t *recI, cudaStream_t st)
+{
+    const TcfGeom G = T.G;
+    const int gk = group_grid(n);
+    constexpr bool SPARSE = SRC != SRC_KEYS;
+    const uint64_t ndst = (DST == DST_BUCKET ? G.nbk : G.nb);
+    PhaseDst P{nullptr, nullptr, nullptr, nullptr};
+    {
+        gf::TraceScope ts_("tcf_group_hist", n, st);
+        tcf_group_hist<SRC, DST, SPARSE><<<gk, TPB, 0, st>>>(keys, T.prep, n, pend, npend, G, T.fill, T.cnt, T.tlist,
+                                                             T.tcount);
+    }
+    if (SPARSE) {
+        gf::TraceScope ts_("tcf_alloc", n, st);
+        tcf_alloc<<<gk, TPB, 0, st>>>(npend, n, T.tlist, T.tcount, T.cnt, T.off, T.dlist, T.seg, &T.ctr->cursor[slot],
+                                      &T.ctr->touched[slot]);
+        P.dlist = T.dlist;
+        P.seg = T.seg;
+        P.nlist = &T.ctr->touched[slot];
+    } else {
+        exclusive_scan_u32(T.cnt, T.off, ndst + 1, T.scan_tmp, T.ctr, st);
+        P.off = T.off;
+    }
+    {
+        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        tcf_group_scatter<SRC, DST><<<gk, TPB, 0, st>>>(keys, T.prep, n, pend, npend, G, T.fill, T.cnt, T.off, T.rec,
+                                                        recI);
+    }
+    return P;
+}
+
+// per-destination grid: dense phases visit every destination, sparse ones at
+// most one per candidate
+static int dst_grid(const PhaseDst &P, uint64_t n, uint64_t ndst)
+{
+    return grid_for(P.dlist ? (n < ndst ? n : ndst) : ndst, TPB, 8);
 }
 
 template <int F>
@@ -792,69 +1078,34 @@ static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     const TcfGeom G = T.G;
     DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
-    const int gk = grid_for(n, TPB, 8);
-    const int gb = grid_for(G.nb, TPB, 8);
-    const int gq = grid_for(G.nbk, TPB, 8);
     cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
+    cudaMemsetAsync(ctr->touched, 0, sizeof(ctr->touched) + sizeof(ctr->cursor), st);  // adjacent fields
     // A: shortcut into b1
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
-                                                                T.rec, nullptr);
-    }
+    PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_insert", G.nb, st);
-        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 0, G.tsc, T.pend0, nullptr, &np[0], T.prep);
+        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc, T.pend0,
+                                                                   nullptr, &np[0], T.prep);
     }
     // B: the less full of b1, b2 under the post-A fills
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_TARGET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt,
-                                                                        T.off, T.rec, nullptr);
-    }
+    P = group_phase<SRC_PEND_U32, DST_TARGET>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_insert", G.nb, st);
-        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 1, G.B, nullptr, T.pend1, &np[1], T.prep);
+        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
+                                                                   T.pend1, &np[1], T.prep);
     }
     // C: the other block
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend1, &np[1], G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U64, DST_ALT><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend1, &np[1], G, T.fill, T.cnt, T.off,
-                                                                     T.rec, nullptr);
-    }
+    P = group_phase<SRC_PEND_U64, DST_ALT>(T, keys, n, T.pend1, &np[1], 2, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_insert", G.nb, st);
-        tcf_block_insert<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, 2, G.B, T.pend2, nullptr, &np[2], T.prep);
+        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
+                                                                   nullptr, &np[2], T.prep);
     }
     // D: backing buckets
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt,
-                                                                        T.off, T.rec, T.pend0);
-    }
+    P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
     {
         gf::TraceScope ts_("tcf_bucket_insert", G.nbk, st);
-        tcf_bucket_insert<<<gq, TPB, 0, st>>>(G, T.bk, T.off, T.rec, T.pend0, status, ctr);
+        tcf_bucket_insert<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr);
     }
 }
 
@@ -864,54 +1115,25 @@ static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     const TcfGeom G = T.G;
     DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
-    const int gk = grid_for(n, TPB, 8);
-    const int gb = grid_for(G.nb, TPB, 8);
-    const int gq = grid_for(G.nbk, TPB, 8);
     cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
+    cudaMemsetAsync(ctr->touched, 0, sizeof(ctr->touched) + sizeof(ctr->cursor), st);  // adjacent fields
     // 1: primary block
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_KEYS, DST_B1><<<gk, TPB, 0, st>>>(keys, T.prep, n, nullptr, nullptr, G, T.fill, T.cnt, T.off,
-                                                                T.rec, nullptr);
-    }
+    PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_remove", G.nb, st);
-        tcf_block_remove<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, T.pend0, &np[0]);
+        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0]);
     }
     // 2: secondary block
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nb + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_B2><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend0, &np[0], G, T.fill, T.cnt, T.off,
-                                                                    T.rec, nullptr);
-    }
+    P = group_phase<SRC_PEND_U32, DST_B2>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_remove", G.nb, st);
-        tcf_block_remove<F><<<gb, TPB, 0, st>>>(G, T.blocks, T.fill, T.off, T.rec, T.pend2, &np[2]);
+        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2]);
     }
     // 3: backing bucket; what is left is not found
-    {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
-        tcf_group_hist<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt);
-    }
-    exclusive_scan_u32(T.cnt, T.off, G.nbk + 1, T.scan_tmp, ctr, st);
-    {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
-        tcf_group_scatter<SRC_PEND_U32, DST_BUCKET><<<gk, TPB, 0, st>>>(keys, T.prep, n, T.pend2, &np[2], G, T.fill, T.cnt,
-                                                                        T.off, T.rec, T.pend0);
-    }
+    P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
     {
         gf::TraceScope ts_("tcf_bucket_remove", G.nbk, st);
-        tcf_bucket_remove<<<gq, TPB, 0, st>>>(G, T.bk, T.off, T.rec, T.pend0, status, ctr);
+        tcf_bucket_remove<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr);
     }
 }
 
@@ -1137,14 +1359,17 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     piece(T.pend0, M);
     piece(T.pend1, M);
     piece(T.pend2, M);
+    piece(T.tlist, M);
+    piece(T.tcount, (uint64_t)sm_count() * 8);
+    piece(T.dlist, M);
+    piece(T.seg, M);
     piece(GR->prep, M);
     piece(GR->d_tmem, (uint64_t)n);
     piece(GR->scan_tmp, scan_tmp_words(groups));
-    T.rec2 = nullptr;
     bytes_out = bytes;
     if (plan_only) return FILTER_OK;
     if (!T.blocks || !T.bk || !T.fill || !T.cnt || !T.off || !T.rec || !T.pend0 || !T.pend1 || !T.pend2 ||
-        !GR->prep || !GR->d_tmem || !GR->scan_tmp)
+        !T.tlist || !T.tcount || !T.dlist || !T.seg || !GR->prep || !GR->d_tmem || !GR->scan_tmp)
         return FILTER_ERR_INTERNAL;
     GF_CUDA(cudaMemcpy(GR->d_tmem, tm.data(), n * sizeof(TcfMember), cudaMemcpyHostToDevice));
     // host views of the members: their slices of the group's arrays
@@ -1161,10 +1386,13 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
         S.cnt = T.cnt;
         S.off = T.off;
         S.rec = T.rec;
-        S.rec2 = nullptr;
         S.pend0 = T.pend0;
         S.pend1 = T.pend1;
         S.pend2 = T.pend2;
+        S.tlist = T.tlist;
+        S.tcount = T.tcount;
+        S.dlist = T.dlist;
+        S.seg = T.seg;
         V.ctr = GR->ctr;
         V.scan_tmp = GR->scan_tmp;
         V.arena.base = GR->arena.base;  // marks the view valid; the group owns the memory
