@@ -46,9 +46,7 @@ BYTES_PER_UNIT = {
     "rs_scatter_kv": 24.0,       # key + index read and write
     "rs_hist": 8.0,              # key read
     "scan_kernel": 8.0,          # u32 read + write
-    "gqf_fp_kernel": 16.0,       # key read + fingerprint write
-    "gqf_flags": 12.0,           # fingerprint read + flag write
-    "gqf_compact": 12.0,         # fingerprint + position read
+    "rle_kernel": 8.0,           # sorted fingerprint read (group writes not counted)
     "gqf_merge_kernel": 3.0,     # per slot: old table read + new table write (r = 8: 1.5 B/slot each)
     "gqf_count_kernel": 80.0,    # key + metadata sector + remainder sector + count
     "gqf_status_kernel": 13.0,
@@ -242,21 +240,29 @@ class Runner:
         self.tcf = gf.TCF(inp["tcf_log2"], 16, gf.MODE_BULK, seed=2, max_batch=self.B)
         self.gqf = gf.GQF(inp["gqf_qbits"], 8, seed=3, max_batch=len(inp["gqf_ins"]))
 
-    def step(self, src=None):
-        """One pass of the hot path. `src` maps input names to device tensors."""
+    def step(self, src=None, wait=None):
+        """One pass of the hot path. `src` maps input names to device tensors;
+        `wait(name, k)` (optional) is called before input `name` (batch k) is
+        first used, so that its host->device copy can still be in flight."""
         d = src or self.d
+        w = wait or (lambda name, k=0: None)
         tcf, gqf, B = self.tcf, self.gqf, self.B
         tcf.clear()
         ins = d["tcf_ins"]
-        for s in range(0, ins.numel(), B):
+        for k, s in enumerate(range(0, ins.numel(), B)):
+            w("tcf_ins", k)
             tcf.insert(ins[s:s + B])
+        w("tcf_probe")
         tcf.query(d["tcf_probe"], self.found)
         dl = d["tcf_del"]
-        for s in range(0, dl.numel(), B):
+        for k, s in enumerate(range(0, dl.numel(), B)):
+            w("tcf_del", k)
             tcf.remove(dl[s:s + B])
         tcf.query(d["tcf_probe"], self.found2)
         gqf.clear()
+        w("gqf_ins")
         gqf.insert(d["gqf_ins"])
+        w("gqf_q")
         gqf.count(d["gqf_q"], self.cnt)
         gqf.remove(d["gqf_q"])
         gqf.count(d["gqf_q"], self.cnt2)
@@ -325,6 +331,8 @@ def run_ours(args, rank, world, device_index):
 
     kern, roof = roofline_from_trace(trace)
     launches = sum(v["launches"] for v in trace.values())
+    gather = query_vs_gather(kern, {"tcf_query_kernel": R.tcf.stats()["table_bytes"],
+                                    "gqf_count_kernel": R.gqf.stats()["table_bytes"]}, device)
 
     e2e = None
     if not args.no_e2e:
@@ -348,9 +356,47 @@ def run_ours(args, rank, world, device_index):
         "config": {"workload": WORKLOAD if args.case == "full" else PROFILE_WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "kernels": kern[:16], "checks": checks, "batched": batched,
+        "cpu_baseline": cpu, "random_gather": gather, "kernels": kern[:16], "checks": checks, "batched": batched,
     }
     return line
+
+
+def gather_peak(footprint_bytes: int, device, sectors_per_key: int = 2, n: int = 1 << 24) -> float:
+    """Throughput (GB/s of 8 + 32 * spk + 1 bytes per key) of random 32-byte
+    gathers over a table of the given footprint: the query access pattern
+    without filter arithmetic, timed with CUDA events (best of 5)."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+
+    table = torch.zeros(footprint_bytes, dtype=torch.uint8, device=device)
+    keys = torch.randint(-(1 << 62), 1 << 62, (n,), dtype=torch.int64, device=device)
+    out = torch.empty(n, dtype=torch.uint8, device=device)
+    for _ in range(3):
+        gf.calibrate_gather(table, keys, out, sectors_per_key)
+    best = float("inf")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(5):
+        e0.record()
+        gf.calibrate_gather(table, keys, out, sectors_per_key)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del table, keys, out
+    return (8 + 32 * sectors_per_key + 1) * n / (best / 1e3) / 1e9
+
+
+def query_vs_gather(kern, footprints, device):
+    """The query kernels against the random-gather roofline at their table footprint."""
+    out = {}
+    for name, fp in footprints.items():
+        k = next((x for x in kern if x["kernel"] == name), None)
+        if k is None or not k["achieved_gbs"]:
+            continue
+        g = gather_peak(fp, device)
+        out[name] = {"footprint_mib": round(fp / 2**20, 1), "gather_gbs": round(g, 1),
+                     "kernel_gbs": k["achieved_gbs"], "frac": round(k["achieved_gbs"] / g, 4)}
+    return out
 
 
 def roofline_from_trace(trace):
@@ -465,10 +511,12 @@ def run_batched(args, device):
     trace = gf.trace_summary()
     ms = e0.elapsed_time(e1)
     kern, roof = roofline_from_trace(trace)
+    gather = query_vs_gather(kern, {"tcf_group_query_kernel": sum(R.T.export_size(m) for m in range(R.T.n)),
+                                    "gqf_group_count_kernel": sum(R.G.export_size(m) for m in range(R.G.n))}, device)
     out = {"workload": BATCHED_WORKLOAD, "value": round(aggregate_rate(R.ops, args.steps, 1, ms), 4), "unit": UNIT,
            "ms_per_step": round(ms / args.steps, 3), "ops_per_step": R.ops,
            "gpu_launches": sum(v["launches"] for v in trace.values()), "roofline": roof,
-           "kernels": kern[:12], "checks": R.checks()}
+           "random_gather": gather, "kernels": kern[:12], "checks": R.checks()}
     del R
     torch.cuda.empty_cache()
     return out
@@ -554,27 +602,38 @@ def run_serving(args, device):
 
 def run_e2e(R, args, world, device):
     """Same step through the C ABI with inputs in pinned host memory: every step
-    copies its keys host->device and its results device->host."""
+    copies its keys host->device and its results device->host. The copies in
+    run on a second stream in the order the step consumes them, each batch
+    behind an event, so they overlap the work on the earlier batches."""
     import torch
     import torch.distributed as dist
 
     inp = R.inp
+    B = R.B
     names = ("tcf_ins", "tcf_probe", "tcf_del", "gqf_ins", "gqf_q")
     hostb = {k: torch.from_numpy(np.ascontiguousarray(inp[k]).view(np.int64)).pin_memory() for k in names}
     devb = {k: torch.empty(hostb[k].shape, dtype=torch.int64, device=device) for k in names}
-    out_found = torch.empty(R.found.shape, dtype=torch.uint8).pin_memory()
-    out_cnt = torch.empty(R.cnt.shape, dtype=torch.int64).pin_memory()
+    outs = [(torch.empty(t.shape, dtype=t.dtype).pin_memory(), t) for t in (R.found, R.found2, R.cnt, R.cnt2)]
     h2d = sum(hostb[k].numel() * 8 for k in names)
-    d2h = 2 * (out_found.numel() + out_cnt.numel() * 8)
+    d2h = sum(h.numel() * h.element_size() for h, _ in outs)
+    main = torch.cuda.current_stream(device)
+    cs = torch.cuda.Stream(device)
 
     def step():
-        for k in names:
-            devb[k].copy_(hostb[k], non_blocking=True)
-        R.step(devb)
-        out_found.copy_(R.found, non_blocking=True)
-        out_cnt.copy_(R.cnt, non_blocking=True)
-        out_found.copy_(R.found2, non_blocking=True)
-        out_cnt.copy_(R.cnt2, non_blocking=True)
+        ev = {}
+        cs.wait_stream(main)  # the previous step is done with the device inputs
+        with torch.cuda.stream(cs):
+            for k in names:
+                batched = k in ("tcf_ins", "tcf_del")
+                n = hostb[k].numel()
+                for j, s in enumerate(range(0, n, B if batched else max(n, 1))):
+                    e = min(n, s + (B if batched else n))
+                    devb[k][s:e].copy_(hostb[k][s:e], non_blocking=True)
+                    ev[(k, j)] = torch.cuda.Event()
+                    ev[(k, j)].record(cs)
+        R.step(devb, wait=lambda name, k=0: main.wait_event(ev[(name, k)]))
+        for h, t in outs:
+            h.copy_(t, non_blocking=True)
 
     step()
     torch.cuda.synchronize()
@@ -586,7 +645,8 @@ def run_e2e(R, args, world, device):
     torch.cuda.synchronize()
     sec = max_over_ranks(time.perf_counter() - t0, world, device)
     v = aggregate_rate(ops_per_step(inp), args.steps, world, sec * 1e3)
-    return {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    return {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "overlap": "host->device copies on a second stream, each batch behind an event"}
 
 
 # ---------------------------------------------------------------------------

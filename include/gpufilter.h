@@ -180,6 +180,19 @@ int filter_trace_reset(void);
 int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kernels);
 
 /*
+ * filter_calibrate_gather: a measurement utility, not a filter operation.
+ * For each of n keys, reads the key, `sectors_per_key` pseudo-random 32-byte
+ * sectors of the table d_table (table_bytes bytes, 16-byte aligned, at most
+ * 2^32 sectors; sector choice from mix64 of the key) and writes one byte to
+ * d_out[i]: the memory pattern of a filter query without the filter
+ * arithmetic. Timing it gives the random-access throughput the query kernels
+ * are compared with at the same table footprint. Asynchronous on `stream`;
+ * FILTER_ERR_ARG for null or misaligned pointers or an empty table.
+ */
+int filter_calibrate_gather(const void *d_table, uint64_t table_bytes, const uint64_t *d_keys, uint64_t n,
+                            uint32_t sectors_per_key, uint8_t *d_out, void *stream);
+
+/*
  * filter_gqf_insert_noalloc: a GQF bulk insert (the same work as
  * filter_insert on a GQF) that allocates no device memory at all. The paper
  * has no counterpart; this exists for callers that must not call cudaMalloc:

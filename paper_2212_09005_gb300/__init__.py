@@ -40,6 +40,7 @@ EXPORTS = [
     "filter_group_remove", "filter_group_query", "filter_group_count", "filter_group_get_stats",
     "filter_group_export_size", "filter_group_export",
     "filter_server_create", "filter_server_submit", "filter_server_wait", "filter_server_destroy",
+    "filter_calibrate_gather",
 ]
 
 OP_INSERT, OP_QUERY, OP_REMOVE, OP_COUNT = 0, 1, 2, 3
@@ -113,6 +114,7 @@ def lib():
         L.filter_server_submit.argtypes = [vp, C.POINTER(FilterRequest), C.POINTER(u64)]
         L.filter_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
         L.filter_server_destroy.argtypes = [vp]
+        L.filter_calibrate_gather.argtypes = [vp, u64, vp, u64, C.c_uint32, vp, vp]
         L.filter_error_string.argtypes = [i32]
         L.filter_error_string.restype = C.c_char_p
         for name in EXPORTS:
@@ -284,6 +286,11 @@ class FilterGroup:
                "filter_group_get_stats")
         return {k: int(getattr(s, k)) for k, _ in FilterStats._fields_}
 
+    def export_size(self, member: int) -> int:
+        n = C.c_uint64()
+        _check(lib().filter_group_export_size(self._h, member, C.byref(n)), "filter_group_export_size")
+        return n.value
+
     def export(self, member: int, stream=None) -> np.ndarray:
         n = C.c_uint64()
         _check(lib().filter_group_export_size(self._h, member, C.byref(n)), "filter_group_export_size")
@@ -363,6 +370,13 @@ def trace_summary() -> dict:
     _check(lib().filter_trace_summary(n.value, arr, C.byref(n)), "filter_trace_summary")
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "units": int(arr[i].units),
                                    "ms": float(arr[i].ms)} for i in range(n.value)}
+
+
+def calibrate_gather(table, keys, out, sectors_per_key: int = 2, stream=None):
+    """Random 32-byte gathers over `table` (a CUDA tensor), one result byte per key."""
+    _check(lib().filter_calibrate_gather(_dptr(table), table.numel() * table.element_size(), _dptr(keys, 8),
+                                         keys.numel(), sectors_per_key, _dptr(out, 1), _stream(stream)),
+           "filter_calibrate_gather")
 
 
 NOALLOC_MAX_KEYS = 65536

@@ -54,38 +54,6 @@ __host__ __device__ __forceinline__ uint32_t ndig(uint64_t v, uint32_t r)
 __host__ __device__ __forceinline__ uint32_t enc_len(uint64_t c, uint32_t r) { return c == 1 ? 1u : 3u + ndig(c - 2, r); }
 
 // ---------------------------------------------------------------------------
-// fingerprints, group flags, compaction
-// ---------------------------------------------------------------------------
-__global__ void gqf_fp_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H, uint64_t *fp, uint32_t *idx)
-{
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        fp[i] = fingerprint(keys[i], H);
-        if (idx) idx[i] = (uint32_t)i;
-    }
-}
-
-// flags[i] = 1 where a new fingerprint starts; flags[n] = 0
-__global__ void gqf_flags(const uint64_t *__restrict__ fp, uint64_t n, uint32_t *flags)
-{
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i <= n; i += (uint64_t)gridDim.x * blockDim.x)
-        flags[i] = (i < n && (i == 0 || fp[i] != fp[i - 1])) ? 1u : 0u;
-}
-
-// after the scan, pos[i] = number of group starts before i, pos[n] = m
-__global__ void gqf_compact(const uint64_t *__restrict__ fp, uint64_t n, const uint32_t *__restrict__ pos,
-                            uint64_t *ufp, uint32_t *ustart)
-{
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        if (i == 0 || fp[i] != fp[i - 1]) {
-            uint32_t u = pos[i];
-            ufp[u] = fp[i];
-            ustart[u] = (uint32_t)i;
-        }
-        if (i == 0) ustart[pos[n]] = (uint32_t)n;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // The merge kernel
 // ---------------------------------------------------------------------------
 struct MergeArgs {
@@ -599,6 +567,16 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
         e = v > xA ? v : xA;
     }
     const long long e_thread_in = e;
+    // runend bits go to the staged words when inside the staged window,
+    // else straight to the new metadata
+    auto flush_rend = [&](long long w, unsigned long long bits) {
+        if (!bits) return;
+        const long long wi = w - wbase;
+        if ((64 * w + 63) - w0 < OUTBUF && wi >= 0 && wi < RWORDS) atomicOr(&S.rend[wi], bits);
+        else atomicOr(&a.meta_new[w].rend, bits);
+    };
+    long long rw = -1;
+    unsigned long long rbits = 0;
     uint32_t newbyte = 0;
     long long first_end = -1;
 #pragma unroll
@@ -610,16 +588,19 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
         const long long end = start + L - 1;
         S.qstart[tid * QPT + c] = (int)(start - Q0);
         if (end < (long long)a.nslots) {
-            const long long wi = (end >> 6) - wbase;
-            if (end - w0 < OUTBUF && wi >= 0 && wi < RWORDS)
-                atomicOr(&S.rend[wi], 1ull << (end & 63));
-            else
-                atomicOr(&a.meta_new[end >> 6].rend, 1ull << (end & 63));
+            // a thread's run ends increase: OR them into one word at a time
+            if ((end >> 6) != rw) {
+                flush_rend(rw, rbits);
+                rw = end >> 6;
+                rbits = 0;
+            }
+            rbits |= 1ull << (end & 63);
         }
         e = end;
         newbyte |= 1u << c;
         if (c == 0) first_end = end;
     }
+    flush_rend(rw, rbits);
     S.newocc[tid] = (unsigned char)newbyte;
     if ((tid & 7) == 0) {
         const uint64_t j = j0 + (tid >> 3);
@@ -692,7 +673,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
 // Tiles are taken from a counter in launch order, so every tile a look-back
 // waits on has already been scheduled.
 template <int R>
-__global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
+__global__ void __launch_bounds__(MT, 5) gqf_merge_kernel(MergeArgs a)
 {
     __shared__ MergeSmem<R> S;
     if (threadIdx.x == 0) {
@@ -707,7 +688,7 @@ __global__ void __launch_bounds__(MT) gqf_merge_kernel(MergeArgs a)
 // member m's arguments with `ts` and `tlo` already offset to its first tile,
 // so the look-back of a member's tile stops at that member's first tile.
 template <int R>
-__global__ void __launch_bounds__(MT) gqf_merge_group_kernel(const MergeArgs *__restrict__ tab,
+__global__ void __launch_bounds__(MT, 5) gqf_merge_group_kernel(const MergeArgs *__restrict__ tab,
                                                              const uint32_t *__restrict__ tile_member,
                                                              unsigned long long *tctr)
 {
@@ -1024,13 +1005,13 @@ __global__ void gqf_delete_phase(GView g, const uint64_t *__restrict__ ufp, cons
 // ---------------------------------------------------------------------------
 // per-key status after a batch
 // ---------------------------------------------------------------------------
-// pos: scanned group-start flags (pos[i + 1] - 1 = group of sorted element i)
-__global__ void gqf_status_kernel(uint64_t n, const uint32_t *__restrict__ pos, const uint32_t *__restrict__ ustart,
+// run_of[i] = group of sorted element i
+__global__ void gqf_status_kernel(uint64_t n, const uint32_t *__restrict__ run_of, const uint32_t *__restrict__ ustart,
                                   const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ removed,
                                   uint64_t m_keep, int del, uint8_t *status)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t g = pos[i + 1] - 1;
+        uint32_t g = run_of[i];
         uint8_t s;
         if (del) s = (i - ustart[g]) < removed[g] ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;
         else s = (g < m_keep) ? FILTER_KEY_OK : FILTER_KEY_FULL;
@@ -1191,11 +1172,12 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     table_bytes = bytes;
     uint64_t scan_n = radix_tmp_words(M);
     if (M + 1 > scan_n) scan_n = M + 1;
-    piece(Q.fp_a, M);
+    Q.fp_a = nullptr;  // the sort hashes the keys in its first pass
+    
     piece(Q.fp_b, M);
     piece(Q.fp_c, M);
     piece(Q.ufp, M);
-    piece(Q.idx_a, M);
+    Q.idx_a = nullptr;  // the first pass takes the positions as its values
     piece(Q.idx_b, M);
     piece(Q.idx_c, M);
     piece(Q.ustart, M + 1);
@@ -1227,22 +1209,11 @@ static void gqf_prepare(filter *F, const uint64_t *keys, uint64_t n, bool need_i
                         uint32_t **sorted_idx)
 {
     GqfState &Q = F->gqf;
-    const int g = grid_for(n, 256, 8);
-    {
-        gf::TraceScope ts_("gqf_fp_kernel", n, st);
-        gqf_fp_kernel<<<g, 256, 0, st>>>(keys, n, Q.H, Q.fp_a, need_idx ? Q.idx_a : nullptr);
-    }
-    radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp,
-                   F->scan_tmp, F->ctr, st);
-    {
-        gf::TraceScope ts_("gqf_flags", n + 1, st);
-        gqf_flags<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(Q.fp_b, n, Q.flags);
-    }
-    exclusive_scan_u32(Q.flags, Q.flags, n + 1, F->scan_tmp, F->ctr, st);
-    {
-        gf::TraceScope ts_("gqf_compact", n, st);
-        gqf_compact<<<g, 256, 0, st>>>(Q.fp_b, n, Q.flags, Q.ufp, Q.ustart);
-    }
+    // fingerprints are computed by the sort's first pass
+    radix_sort_u64(keys, Q.fp_b, Q.fp_c, nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp, F->scan_tmp, F->ctr, st,
+                   &Q.H, need_idx);
+    // groups: flags[n] = their number; flags[i] = the group of sorted element i (statuses only)
+    rle_sorted_u64(Q.fp_b, n, Q.ufp, Q.ustart, need_idx ? Q.flags : nullptr, Q.flags + n, F->scan_tmp, F->ctr, st);
     *sorted_idx = Q.idx_b;
 }
 
@@ -1724,15 +1695,7 @@ static void group_prepare(filter_group *GR, const uint64_t *off, const uint64_t 
     }
     radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, GR->pbits + GR->mbits,
                    Q.radix_tmp, GR->scan_tmp, GR->ctr, st);
-    {
-        gf::TraceScope ts_("gqf_flags", n + 1, st);
-        gqf_flags<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(Q.fp_b, n, Q.flags);
-    }
-    exclusive_scan_u32(Q.flags, Q.flags, n + 1, GR->scan_tmp, GR->ctr, st);
-    {
-        gf::TraceScope ts_("gqf_compact", n, st);
-        gqf_compact<<<g, 256, 0, st>>>(Q.fp_b, n, Q.flags, Q.ufp, Q.ustart);
-    }
+    rle_sorted_u64(Q.fp_b, n, Q.ufp, Q.ustart, need_idx ? Q.flags : nullptr, Q.flags + n, GR->scan_tmp, GR->ctr, st);
 }
 
 static int group_merge(filter_group *GR, uint64_t n, int del, cudaStream_t st)

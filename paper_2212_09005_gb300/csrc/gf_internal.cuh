@@ -179,11 +179,13 @@ struct TcfMember {
     uint64_t block0, bucket0;  // its first block and bucket in the group's arrays
 };
 
-// one key of a TCF group call, hashed for its member
+// the keys of a TCF group call, hashed for their members, as separate arrays
+// so that each phase reads only what it needs (bt null: keys not prepared)
 struct TcfPrep {
-    uint32_t b1, b2;      // group-wide block indices
-    uint32_t bucket, t;   // group-wide backing bucket, tag
-    uint64_t e;           // backing entry (member-local block index << f | tag)
+    uint64_t *bt;       // b1 << 32 | tag, b1 group-wide
+    uint32_t *b2;       // group-wide
+    uint32_t *bucket;   // group-wide backing bucket
+    uint64_t *e;        // backing entry (member-local block index << f | tag)
 };
 
 // ---------------------------------------------------------------------------
@@ -211,13 +213,22 @@ size_t scan_tmp_words(uint64_t n);
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint64_t *tmp,
                         DevCounters *ctr, cudaStream_t st);
 
+// Run-length encoding of a sorted array: uniq[g] / start[g] for each run g,
+// start[m] = n and *m_out = m (the number of runs); run_of[i] (optional) =
+// the run of element i. tmp: scan_tmp_words(n) words.
+void rle_sorted_u64(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *start, uint32_t *run_of,
+                    uint32_t *m_out, uint64_t *tmp, DevCounters *ctr, cudaStream_t st);
+
 // LSD radix sort of 64-bit keys on bits [0, bits), optional 32-bit values.
 // Result lands in keys_out / vals_out. `tmp` holds radix_tmp_words(n) words.
+// With `fp`, keys_in holds raw keys and the sort is of their fingerprints
+// under *fp (computed in the first pass; keys_in is only read); iota_vals
+// then makes the values the input positions.
 size_t radix_tmp_words(uint64_t n);
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt,
                     uint64_t n, uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp,
-                    DevCounters *ctr, cudaStream_t st);
+                    DevCounters *ctr, cudaStream_t st, const PHash *fp = nullptr, bool iota_vals = false);
 
 // Kernel tracing: a TraceScope around a launch records CUDA events before and
 // after it when tracing is on.
@@ -314,7 +325,7 @@ struct filter_group {
     // TCF: concatenated blocks, buckets and fill bytes; G.nb / G.nbk are the totals
     TcfState tcf;
     gf::TcfMember *d_tmem = nullptr;
-    gf::TcfPrep *prep = nullptr;
+    gf::TcfPrep prep{nullptr, nullptr, nullptr, nullptr};
     // GQF: meta[b] / rem[b] are the concatenated regions of all members
     GqfState gqf;
     uint64_t tiles = 0;               // total merge tiles

@@ -81,11 +81,11 @@ extern "C" int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_s
     Q.rem[1] = reinterpret_cast<uint8_t *>(tout) + metaB;
     Q.cur = 0;
     F.ctr = A.take<DevCounters>(1);
-    Q.fp_a = A.take<uint64_t>(M);
+    Q.fp_a = nullptr;
     Q.fp_b = A.take<uint64_t>(M);
     Q.fp_c = A.take<uint64_t>(M);
     Q.ufp = A.take<uint64_t>(M);
-    Q.idx_a = A.take<uint32_t>(M);
+    Q.idx_a = nullptr;
     Q.idx_b = A.take<uint32_t>(M);
     Q.idx_c = A.take<uint32_t>(M);
     Q.ustart = A.take<uint32_t>(M + 1);

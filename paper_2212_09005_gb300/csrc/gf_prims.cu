@@ -51,6 +51,46 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
     return *(const volatile unsigned long long *)p;
 }
 
+// Warp 0 of tile `tile`: publish the tile's total, look back over 32
+// predecessors at a time for the exclusive prefix, publish the inclusive one.
+// All 32 lanes call it and get the prefix. A wait that reaches SPIN_LIMIT
+// records ST_TIMEOUT and gives up (prefix then incomplete).
+__device__ uint32_t lookback_prefix(unsigned long long *st, uint64_t tile, uint32_t total,
+                                    unsigned long long *status)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t prefix = 0;
+    if (tile == 0) {
+        if (lane == 0) atomicExch(&st[0], (2ull << 32) | total);
+        return 0;
+    }
+    if (lane == 0) atomicExch(&st[tile], (1ull << 32) | total);
+    int64_t jtop = (int64_t)tile - 1;
+    uint32_t spins = 0;
+    while (true) {
+        const int64_t j = jtop - lane;
+        unsigned long long w2 = 2ull << 32;  // before tile 0: inclusive prefix 0
+        if (j >= 0) {
+            w2 = ld_volatile(&st[j]);
+            while ((w2 >> 32) == 0 && ++spins <= SPIN_LIMIT) w2 = ld_volatile(&st[j]);
+        }
+        const uint32_t flag = (uint32_t)(w2 >> 32);
+        if (__ballot_sync(0xffffffffu, flag == 0)) {
+            if (lane == 0) atomicOr(status, ST_TIMEOUT);
+            break;
+        }
+        const unsigned incl_mask = __ballot_sync(0xffffffffu, flag == 2);
+        const int L = incl_mask ? __ffs(incl_mask) - 1 : 31;
+        uint32_t part = (lane <= L) ? (uint32_t)w2 : 0u;
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        prefix += part;
+        if (incl_mask) break;
+        jtop -= 32;
+    }
+    if (lane == 0) atomicExch(&st[tile], (2ull << 32) | (uint32_t)(prefix + total));
+    return prefix;
+}
+
 __global__ void __launch_bounds__(SCAN_T) scan_kernel(const uint32_t *in, uint32_t *out, uint64_t n,
                                                       unsigned long long *tmp,
                                                       unsigned long long *status)
@@ -104,37 +144,9 @@ __global__ void __launch_bounds__(SCAN_T) scan_kernel(const uint32_t *in, uint32
             if (lane >= o) wi += y;
         }
         if (lane < SCAN_T / 32) s_warp[lane] = wi - w;
-        // tile total sits in lane 7; look back over 32 predecessors at a time
+        // tile total sits in lane 7
         const uint32_t total = __shfl_sync(0xffffffffu, wi, SCAN_T / 32 - 1);
-        uint32_t prefix = 0;
-        if (tile == 0) {
-            if (lane == 0) atomicExch(&st[0], (2ull << 32) | total);
-        } else {
-            if (lane == 0) atomicExch(&st[tile], (1ull << 32) | total);
-            int64_t jtop = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            while (true) {
-                const int64_t j = jtop - lane;
-                unsigned long long w2 = 2ull << 32;  // before tile 0: inclusive prefix 0
-                if (j >= 0) {
-                    w2 = ld_volatile(&st[j]);
-                    while ((w2 >> 32) == 0 && ++spins <= SPIN_LIMIT) w2 = ld_volatile(&st[j]);
-                }
-                const uint32_t flag = (uint32_t)(w2 >> 32);
-                if (__ballot_sync(0xffffffffu, flag == 0)) {
-                    if (lane == 0) atomicOr(status, ST_TIMEOUT);
-                    break;
-                }
-                const unsigned incl_mask = __ballot_sync(0xffffffffu, flag == 2);
-                const int L = incl_mask ? __ffs(incl_mask) - 1 : 31;
-                uint32_t part = (lane <= L) ? (uint32_t)w2 : 0u;
-                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                prefix += part;
-                if (incl_mask) break;
-                jtop -= 32;
-            }
-            if (lane == 0) atomicExch(&st[tile], (2ull << 32) | (uint32_t)(prefix + total));
-        }
+        const uint32_t prefix = lookback_prefix(st, tile, total, status);
         if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
@@ -163,6 +175,99 @@ void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Run-length encoding of a sorted array in one pass: each run's first key and
+// start, the number of runs, and optionally each element's run index. Run
+// starts are counted per tile and ranked by the same decoupled look-back as
+// the scan.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(SCAN_T) rle_kernel(const uint64_t *__restrict__ keys, uint64_t n,
+                                                     uint64_t *__restrict__ uniq, uint32_t *__restrict__ start,
+                                                     uint32_t *__restrict__ run_of, uint32_t *m_out,
+                                                     unsigned long long *tmp, unsigned long long *status)
+{
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_warp[SCAN_T / 32];
+    __shared__ uint32_t s_prefix;
+    if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&tmp[0], 1ull);
+    __syncthreads();
+    const uint64_t tile = s_tile;
+    const uint64_t base = tile * SCAN_TILE + (uint64_t)threadIdx.x * SCAN_I;
+    uint64_t k[SCAN_I];
+    if (base + SCAN_I <= n) {
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(keys + base);
+#pragma unroll
+        for (int q = 0; q < SCAN_I / 2; q++) {
+            const ulonglong2 v = __ldcs(p + q);
+            k[2 * q] = v.x;
+            k[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < SCAN_I; q++) k[q] = (base + q < n) ? keys[base + q] : 0ull;
+    }
+    uint64_t prev = (base > 0 && base - 1 < n) ? keys[base - 1] : ~k[0];
+    uint32_t starts = 0;  // bit q: element base + q starts a run
+#pragma unroll
+    for (int q = 0; q < SCAN_I; q++) {
+        if (base + q < n && k[q] != prev) starts |= 1u << q;
+        prev = k[q];
+    }
+    const uint32_t sum = __popc(starts);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < SCAN_T / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < SCAN_T / 32) s_warp[lane] = wi - w;
+        const uint32_t total = __shfl_sync(0xffffffffu, wi, SCAN_T / 32 - 1);
+        const uint32_t prefix = lookback_prefix(tmp + 1, tile, total, status);
+        if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    uint32_t g = s_prefix + s_warp[warp] + (incl - sum);  // runs started before this thread's elements
+#pragma unroll
+    for (int q = 0; q < SCAN_I; q++) {
+        if ((starts >> q) & 1u) {
+            uniq[g] = k[q];
+            start[g] = (uint32_t)(base + q);
+            g++;
+        }
+        if (run_of && base + q < n) run_of[base + q] = g - 1;
+        if (base + q == n - 1) {
+            *m_out = g;
+            start[g] = (uint32_t)n;
+        }
+    }
+}
+
+void rle_sorted_u64(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *start, uint32_t *run_of,
+                    uint32_t *m_out, uint64_t *tmp, DevCounters *ctr, cudaStream_t st)
+{
+    if (n == 0) {
+        cudaMemsetAsync(m_out, 0, 4, st);
+        cudaMemsetAsync(start, 0, 4, st);
+        return;
+    }
+    const uint64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    cudaMemsetAsync(tmp, 0, (tiles + 1) * sizeof(uint64_t), st);
+    TraceScope ts_("rle_kernel", n, st);
+    rle_kernel<<<(unsigned)tiles, SCAN_T, 0, st>>>(keys, n, uniq, start, run_of, m_out, (unsigned long long *)tmp,
+                                                  &ctr->status);
+}
+
+// ---------------------------------------------------------------------------
 // LSD radix sort with digits of up to 9 bits (the fewest passes that cover the
 // key bits, e.g. 4 x 9 bits for 36-bit fingerprints). Per pass: per-tile digit
 // histograms, one exclusive scan over the digit-major count matrix, then a
@@ -186,8 +291,11 @@ size_t radix_tmp_words(uint64_t n)
 // with plain shared atomics (equal digits inside one warp serialise on one
 // address, which is cheaper than ranking them), then the warps' counts are
 // summed per digit.
+// FP: the input holds raw keys and the sorted values are their fingerprints
+// under H (first pass of a fingerprint sort: no separate hashing pass).
+template <bool FP>
 __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ keys, uint64_t n, uint32_t shift,
-                                                uint32_t nb, uint32_t *counts, uint64_t ntiles)
+                                                uint32_t nb, uint32_t *counts, uint64_t ntiles, PHash H)
 {
     __shared__ uint32_t h[RS_WARPS][RS_MAXB];
     for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB; i += RS_T) (&h[0][0])[i] = 0;
@@ -199,6 +307,7 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
     for (int r = 0; r < RS_I; r++) {
         uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
         k[r] = (i < n) ? __ldcs(keys + i) : 0;
+        if (FP) k[r] = fingerprint(k[r], H);
     }
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
@@ -216,26 +325,26 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
 
 // Scatter of one pass. Keys are ranked inside each warp (match_any groups
 // equal digits; a per-warp 16-bit counter per digit carries the rank across
-// the warp's 16 rounds), the per-digit warp offsets and the tile's digit
-// starts come from a scan in shared memory, and the keys are staged in digit
-// order together with their global index, so that the copy-out writes runs
-// of consecutive addresses and needs no further lookups. Shared memory and
-// registers are sized for 3 CTAs per SM (2 with values).
-template <bool VALS>
+// the warp's 16 rounds). A scan in shared memory turns the counters into one
+// tile position per (warp, digit), the keys are staged in digit order, and
+// the copy-out writes runs of consecutive addresses, taking each key's
+// global position from its digit's offset. Shared memory and registers are
+// sized for 3 CTAs per SM (2 with values).
+// FP: as for rs_hist; the values (VALS) are then the input positions.
+template <bool VALS, bool FP>
 __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t *__restrict__ kin,
-                                                      uint64_t *__restrict__ kout,
-                                                      const uint32_t *__restrict__ vin,
-                                                      uint32_t *__restrict__ vout, uint64_t n,
-                                                      uint32_t shift, uint32_t nb, const uint32_t *__restrict__ offs,
-                                                      uint64_t ntiles)
+                                                                 uint64_t *__restrict__ kout,
+                                                                 const uint32_t *__restrict__ vin,
+                                                                 uint32_t *__restrict__ vout, uint64_t n,
+                                                                 uint32_t shift, uint32_t nb,
+                                                                 const uint32_t *__restrict__ offs, uint64_t ntiles,
+                                                                 PHash H)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    uint64_t *skeys = reinterpret_cast<uint64_t *>(smem);           // [RS_TILE] keys in digit order
-    uint32_t *sg = reinterpret_cast<uint32_t *>(skeys + RS_TILE);   // [RS_TILE] their global index
-    uint32_t *svals = sg + RS_TILE;                                 // [RS_TILE] values (VALS)
-    uint32_t *gdelta = svals + (VALS ? RS_TILE : 0);                // [RS_MAXB] global start - tile start
-    uint16_t *wcnt = reinterpret_cast<uint16_t *>(gdelta + RS_MAXB); // [RS_WARPS][RS_MAXB]
-    uint16_t *dstart = wcnt + RS_WARPS * RS_MAXB;                   // [RS_MAXB] tile start of each digit
+    uint64_t *skeys = reinterpret_cast<uint64_t *>(smem);              // [RS_TILE] keys in digit order
+    uint32_t *svals = reinterpret_cast<uint32_t *>(skeys + RS_TILE);   // [RS_TILE] values (VALS)
+    uint32_t *gdelta = svals + (VALS ? RS_TILE : 0);                   // [RS_MAXB] global start - tile start
+    uint16_t *wcnt = reinterpret_cast<uint16_t *>(gdelta + RS_MAXB);    // [RS_WARPS][RS_MAXB]
     __shared__ uint32_t s_w[RS_WARPS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -253,7 +362,8 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         bool ok = i < n;
         key[r] = ok ? __ldcs(kin + i) : 0;
-        if (VALS) val[r] = ok ? __ldcs(vin + i) : 0;
+        if (FP) key[r] = fingerprint(key[r], H);
+        if (VALS) val[r] = ok ? (FP ? (uint32_t)i : __ldcs(vin + i)) : 0;
     }
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
@@ -270,7 +380,8 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
     __syncthreads();
     {
         // per digit (two per thread): warp-exclusive offsets and tile totals,
-        // then an exclusive scan of the totals in digit order
+        // then an exclusive scan of the totals in digit order; finally every
+        // (warp, digit) counter becomes that warp's first tile position
         uint32_t tot[2] = {0, 0};
 #pragma unroll
         for (int h = 0; h < 2; h++) {
@@ -303,8 +414,9 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
             const uint32_t d = 2 * threadIdx.x + h;
             const uint32_t st = h ? ex + tot[0] : ex;
             if (d < nb) {
-                dstart[d] = (uint16_t)st;
                 gdelta[d] = offs[(uint64_t)d * ntiles + blockIdx.x] - st;
+#pragma unroll
+                for (int w = 0; w < RS_WARPS; w++) wcnt[w * RS_MAXB + d] = (uint16_t)(wcnt[w * RS_MAXB + d] + st);
             }
         }
     }
@@ -314,9 +426,8 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         if (i < n) {
             uint32_t d = (uint32_t)(key[r] >> shift) & (nb - 1);
-            uint32_t pos = (uint32_t)dstart[d] + wcnt[warp * RS_MAXB + d] + rank[r];
+            uint32_t pos = (uint32_t)wcnt[warp * RS_MAXB + d] + rank[r];
             skeys[pos] = key[r];
-            sg[pos] = gdelta[d] + pos;
             if (VALS) svals[pos] = val[r];
         }
     }
@@ -326,8 +437,9 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
     for (int r = 0; r < RS_I; r++) {
         const uint32_t k = r * RS_T + threadIdx.x;
         if (k < cnt) {
-            const uint32_t g = sg[k];
-            __stcs(kout + g, skeys[k]);
+            const uint64_t kk = skeys[k];
+            const uint32_t g = gdelta[(uint32_t)(kk >> shift) & (nb - 1)] + k;
+            __stcs(kout + g, kk);
             if (VALS) __stcs(vout + g, svals[k]);
         }
     }
@@ -336,28 +448,31 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
 template <bool VALS>
 static constexpr size_t rs_smem()
 {
-    return RS_TILE * 8 + RS_TILE * 4 + (VALS ? RS_TILE * 4 : 0) + RS_MAXB * 4 + RS_WARPS * RS_MAXB * 2 + RS_MAXB * 2;
+    return RS_TILE * 8 + (VALS ? RS_TILE * 4 : 0) + RS_MAXB * 4 + RS_WARPS * RS_MAXB * 2;
 }
 
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt, uint64_t n,
                     uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp, DevCounters *ctr,
-                    cudaStream_t st)
+                    cudaStream_t st, const PHash *fp, bool iota_vals)
 {
     if (n == 0) return;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
-        cudaFuncSetAttribute(rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
         attr_done = true;
     }
-    const bool vals = vals_in != nullptr;
-    const uint32_t npass = (bits + 8) / 9;  // digits of at most 9 bits
+    const bool vals = vals_in != nullptr || (fp && iota_vals);
+    const uint32_t npass = (bits + 8) / 9;  // digits of at most 9 bits (a fingerprint sort has p >= 7 bits)
     if (npass == 0) {
         cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st);
-        if (vals) cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, st);
+        if (vals_in) cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, st);
         return;
     }
+    const PHash H = fp ? *fp : PHash{0, 0, 0, 0};
     const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const uint64_t *ksrc = keys_in;
     const uint32_t *vsrc = vals_in;
@@ -366,24 +481,51 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         // split the bits as evenly as possible: the first passes take the extra bit
         const uint32_t db = bits / npass + (p < bits % npass ? 1u : 0u);
         const uint32_t nb = 1u << db;
+        const bool hash = fp && p == 0;
         bool to_out = ((npass - 1 - p) % 2) == 0;
         uint64_t *kdst = to_out ? keys_out : keys_alt;
         uint32_t *vdst = to_out ? vals_out : vals_alt;
         {
             TraceScope ts_("rs_hist", n, st);
-            rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles);
+            if (hash) rs_hist<true><<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles, H);
+            else rs_hist<false><<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles, H);
         }
         exclusive_scan_u32(tmp, tmp, ntiles * nb, scan_tmp, ctr, st);
         TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
-        if (vals)
-            rs_scatter<true><<<(unsigned)ntiles, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb,
-                                                                     tmp, ntiles);
-        else
-            rs_scatter<false><<<(unsigned)ntiles, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n,
-                                                                      shift, nb, tmp, ntiles);
+        const unsigned g = (unsigned)ntiles;
+        if (vals) {
+            if (hash) rs_scatter<true, true><<<g, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, ntiles, H);
+            else rs_scatter<true, false><<<g, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, ntiles, H);
+        } else {
+            if (hash) rs_scatter<false, true><<<g, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, ntiles, H);
+            else rs_scatter<false, false><<<g, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, ntiles, H);
+        }
         ksrc = kdst;
         vsrc = vdst;
         shift += db;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Random-access calibration: the memory pattern of a filter query (a key
+// read, `spk` random 32-byte sectors of a table, one result byte) without
+// any filter arithmetic. Its throughput is the random-gather roofline at a
+// given table footprint.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) gather32_kernel(const uint4 *__restrict__ table, uint64_t nsect,
+                                                       const uint64_t *__restrict__ keys, uint64_t n, uint32_t spk,
+                                                       uint8_t *__restrict__ out)
+{
+    for (uint64_t i = blockIdx.x * 256ull + threadIdx.x; i < n; i += (uint64_t)gridDim.x * 256) {
+        uint64_t h = mix64(__ldg(keys + i));
+        uint32_t acc = 0;
+        for (uint32_t k = 0; k < spk; k++) {
+            const uint64_t sct = (h & 0xffffffffull) * nsect >> 32;  // sector index in [0, nsect)
+            const uint4 a = __ldg(table + 2 * sct), b = __ldg(table + 2 * sct + 1);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+            h = mix64(h + k + 1);
+        }
+        out[i] = (uint8_t)acc;
     }
 }
 
@@ -497,3 +639,22 @@ int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kern
 namespace gf {
 
 }  // namespace gf
+
+extern "C" int filter_calibrate_gather(const void *d_table, uint64_t table_bytes, const uint64_t *d_keys, uint64_t n,
+                                       uint32_t sectors_per_key, uint8_t *d_out, void *stream)
+{
+    const uint64_t nsect = table_bytes / 32;
+    if (!d_table || nsect == 0 || nsect > 0xffffffffull || (n && (!d_keys || !d_out)) ||
+        (reinterpret_cast<uintptr_t>(d_table) & 15u))
+        return FILTER_ERR_ARG;
+    if (n == 0) return FILTER_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    {
+        gf::TraceScope ts_("gather32_kernel", n, st);
+        gf::gather32_kernel<<<gf::grid_for(n, 256, 16), 256, 0, st>>>(static_cast<const uint4 *>(d_table), nsect, d_keys,
+                                                                      n, sectors_per_key, d_out);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+

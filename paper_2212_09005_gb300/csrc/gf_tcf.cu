@@ -259,29 +259,31 @@ enum Src : int { SRC_KEYS = 0, SRC_PEND_U32 = 1, SRC_PEND_U64 = 2 };
 enum Dst : int { DST_B1 = 0, DST_TARGET = 1, DST_ALT = 2, DST_B2 = 3, DST_BUCKET = 4 };
 
 // Key i of the call: hashed here, or (group calls) read from the prepared
-// keys, whose block indices already address the group's concatenated arrays.
-__device__ __forceinline__ KeyInfo key_at(const uint64_t *keys, const TcfPrep *prep, uint64_t i, const TcfGeom &G)
+// keys, whose block indices already address the group's concatenated arrays;
+// b2 is read only by the destinations that need it.
+template <int DST>
+__device__ __forceinline__ KeyInfo key_at(const uint64_t *keys, const TcfPrep &P, uint64_t i, const TcfGeom &G)
 {
-    if (prep) {
-        const uint2 bb = *reinterpret_cast<const uint2 *>(prep + i);
+    if (P.bt) {
+        const uint64_t v = P.bt[i];
         KeyInfo k;
-        k.b1 = bb.x;
-        k.b2 = bb.y;
-        k.t = prep[i].t;
+        k.b1 = v >> 32;
+        k.t = (uint32_t)v;
+        k.b2 = (DST == DST_TARGET || DST == DST_B2) ? P.b2[i] : 0;
         return k;
     }
     return tcf_keyinfo(keys[i], G);
 }
 
 __device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t pend_word, const TcfGeom &G,
-                                            const uint8_t *fill, const TcfPrep *prep, uint64_t i)
+                                            const uint8_t *fill, const TcfPrep &P, uint64_t i)
 {
     switch (dst) {
     case DST_B1: return k.b1;
     case DST_B2: return k.b2;
     case DST_TARGET: return fill[k.b1] <= fill[k.b2] ? k.b1 : k.b2;
     case DST_ALT: return pend_word >> 32;
-    default: return prep ? (uint64_t)prep[i].bucket : tcf_bucket(tcf_entry(k, G.f), G.nbk);
+    default: return P.bt ? (uint64_t)P.bucket[i] : tcf_bucket(tcf_entry(k, G.f), G.nbk);
     }
 }
 
@@ -299,7 +301,7 @@ __device__ __forceinline__ void cta_chunk(uint64_t n, uint64_t &c0, uint64_t &c1
 // candidates, as in the later phases) also list each destination the first
 // time it is hit, per CTA chunk, in tlist[c0 ..] with the count in tcount.
 template <int SRC, int DST, bool SPARSE>
-__global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, const TcfPrep *prep,
+__global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, const TcfPrep prep,
                                                       uint64_t n_keys, const void *pend, const unsigned *npend,
                                                       TcfGeom G, const uint8_t *fill, uint32_t *cnt,
                                                       uint32_t *tlist, uint32_t *tcount)
@@ -321,12 +323,12 @@ __global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict
             pw = static_cast<const uint64_t *>(pend)[j];
             i = pw & 0xffffffffu;
         }
-        KeyInfo k = key_at(keys, prep, i, G);
+        KeyInfo k = key_at<DST>(keys, prep, i, G);
         const uint64_t d = dest_of(DST, k, pw, G, fill, prep, i);
         if (SPARSE) {
             if (atomicAdd(&cnt[d], 1u) == 0u) tlist[c0 + atomicAdd(&s_n, 1u)] = (uint32_t)d;
         } else {
-            atomicAdd(&cnt[d], 1u);
+            atomicAdd(&cnt[d], 1u);  // no result used: a reduction the L2 applies without a reply
         }
     }
     if (SPARSE) {
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(TPB) tcf_alloc(const unsigned *npend, uint64_t
 
 // rec = (tag << 32) | batch index, or the backing entry with the index in recI
 template <int SRC, int DST>
-__global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restrict__ keys, const TcfPrep *prep,
+__global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restrict__ keys, const TcfPrep prep,
                                                          uint64_t n_keys, const void *pend, const unsigned *npend,
                                                          TcfGeom G,
                                                          const uint8_t *fill, uint32_t *cnt,
@@ -401,11 +403,11 @@ __global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restr
             pw = static_cast<const uint64_t *>(pend)[j];
             i = pw & 0xffffffffu;
         }
-        KeyInfo k = key_at(keys, prep, i, G);
+        KeyInfo k = key_at<DST>(keys, prep, i, G);
         uint64_t d = dest_of(DST, k, pw, G, fill, prep, i);
         uint32_t pos = off[d] + atomicSub(&cnt[d], 1u) - 1u;
         if (DST == DST_BUCKET) {
-            rec[pos] = prep ? prep[i].e : tcf_entry(k, G.f);
+            rec[pos] = prep.bt ? prep.e[i] : tcf_entry(k, G.f);
             recI[pos] = (uint32_t)i;
         } else {
             rec[pos] = ((uint64_t)k.t << 32) | i;
@@ -471,7 +473,7 @@ template <int F>
 __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
                                                         const uint64_t *__restrict__ rec, int phase,
                                                         uint32_t cap, uint32_t *pend32, uint64_t *pend64,
-                                                        unsigned *npend, const TcfPrep *prep)
+                                                        unsigned *npend, const TcfPrep prep)
 {
     constexpr int B = Blk<F>::B;
     const uint64_t nd = phase_count(P, G.nb);
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
             const uint32_t i = (uint32_t)r;
             if (phase == 1) {
                 // the other block of the pair: b1 + b2 - b
-                uint64_t alt = prep ? (uint64_t)prep[i].b1 + prep[i].b2 - b : b ^ tcf_g((uint32_t)(r >> 32), G.nb);
+                uint64_t alt = prep.bt ? (prep.bt[i] >> 32) + prep.b2[i] - b : b ^ tcf_g((uint32_t)(r >> 32), G.nb);
                 pend64[slot++] = (alt << 32) | i;
             } else {
                 pend32[slot++] = i;
@@ -996,10 +998,10 @@ struct TcfBulk {
     uint64_t *seg;
     uint64_t *scan_tmp;
     DevCounters *ctr;
-    const TcfPrep *prep;
+    TcfPrep prep;
 };
 
-static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep *prep)
+static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep &prep)
 {
     TcfBulk W;
     W.G = T.G;
@@ -1150,7 +1152,7 @@ int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, nullptr);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr});
         if (T.G.f == 16) tcf_bulk_insert<16>(W, keys, n, status, st);
         else tcf_bulk_insert<8>(W, keys, n, status, st);
     }
@@ -1171,7 +1173,7 @@ int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             else tcf_point_remove<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, nullptr);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr});
         if (T.G.f == 16) tcf_bulk_remove<16>(W, keys, n, status, st);
         else tcf_bulk_remove<8>(W, keys, n, status, st);
     }
@@ -1244,8 +1246,7 @@ __device__ __forceinline__ TcfGeom member_geom(const TcfMember &M, uint32_t f)
 
 __global__ void __launch_bounds__(TPB) tcf_group_prep(const uint64_t *__restrict__ keys, uint64_t n,
                                                       const uint64_t *__restrict__ off, uint32_t nmem,
-                                                      const TcfMember *__restrict__ mem, uint32_t f,
-                                                      TcfPrep *__restrict__ out)
+                                                      const TcfMember *__restrict__ mem, uint32_t f, TcfPrep out)
 {
     MemberCursor c(off, nmem, n);
     uint32_t cm = 0xffffffffu;
@@ -1259,13 +1260,10 @@ __global__ void __launch_bounds__(TPB) tcf_group_prep(const uint64_t *__restrict
         }
         const KeyInfo k = tcf_keyinfo(__ldg(keys + c.i), G);
         const uint64_t e = tcf_entry(k, f);
-        TcfPrep p;
-        p.b1 = (uint32_t)(M.block0 + k.b1);
-        p.b2 = (uint32_t)(M.block0 + k.b2);
-        p.bucket = (uint32_t)(M.bucket0 + tcf_bucket(e, M.nbk));
-        p.t = k.t;
-        p.e = e;
-        out[c.i] = p;
+        out.bt[c.i] = ((M.block0 + k.b1) << 32) | k.t;
+        out.b2[c.i] = (uint32_t)(M.block0 + k.b2);
+        out.bucket[c.i] = (uint32_t)(M.bucket0 + tcf_bucket(e, M.nbk));
+        out.e[c.i] = e;
     }
 }
 
@@ -1363,13 +1361,17 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     piece(T.tcount, (uint64_t)sm_count() * 8);
     piece(T.dlist, M);
     piece(T.seg, M);
-    piece(GR->prep, M);
+    piece(GR->prep.bt, M);
+    piece(GR->prep.b2, M);
+    piece(GR->prep.bucket, M);
+    piece(GR->prep.e, M);
     piece(GR->d_tmem, (uint64_t)n);
     piece(GR->scan_tmp, scan_tmp_words(groups));
     bytes_out = bytes;
     if (plan_only) return FILTER_OK;
     if (!T.blocks || !T.bk || !T.fill || !T.cnt || !T.off || !T.rec || !T.pend0 || !T.pend1 || !T.pend2 ||
-        !T.tlist || !T.tcount || !T.dlist || !T.seg || !GR->prep || !GR->d_tmem || !GR->scan_tmp)
+        !T.tlist || !T.tcount || !T.dlist || !T.seg || !GR->prep.bt || !GR->prep.b2 || !GR->prep.bucket ||
+        !GR->prep.e || !GR->d_tmem || !GR->scan_tmp)
         return FILTER_ERR_INTERNAL;
     GF_CUDA(cudaMemcpy(GR->d_tmem, tm.data(), n * sizeof(TcfMember), cudaMemcpyHostToDevice));
     // host views of the members: their slices of the group's arrays

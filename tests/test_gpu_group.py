@@ -293,3 +293,46 @@ def test_batched_workload_full_size_sampled(gf, oracle):
         O = oracle.GQF(int(logs[nt + m]), 8, seed=int(seeds[nt + m]))
         O.insert(gk[goff[m]:goff[m + 1]])
         assert first_diff(G.export(m), O.export()) is None, m
+
+
+def test_tcf_group_calls_capture_in_a_cuda_graph(gf, oracle):
+    """TCF group inserts and queries enqueue no host synchronisation, so a
+    sequence of them can be captured once in a CUDA graph and replayed; the
+    replay gives the same tables and answers as the oracle."""
+    import torch
+
+    w = W.batched_workload(n_filters=24, seed=43, emin=10, emax=12, tcf_rounds=2)
+    logs, seeds, keys, off = w["log2_slots"], w["hash_seeds"], w["insert"], w["offsets"]
+    n = len(logs)
+    chunks = W.round_chunks(off, 2)
+    calls = [call_arrays(keys, chunks[j]) for j in range(2)]
+    G = gf.FilterGroup(gf.FILTER_TCF, logs, 16, seeds, max_total=len(keys))
+    d_calls = [(dev_off(o), dev_u64(k)) for o, k in calls]
+    d_q = dev_u64(keys)
+    d_qo = dev_off(off)
+    found = zeros_u8(len(keys))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        G.clear(stream=s)  # the first call of each kernel happens outside the capture
+        G.insert(*d_calls[0], stream=s)
+        G.query(d_qo, d_q, found, stream=s)
+        s.synchronize()
+        with torch.cuda.graph(graph, stream=s):
+            G.clear(stream=s)
+            for o, k in d_calls:
+                G.insert(o, k, stream=s)
+            G.query(d_qo, d_q, found, stream=s)
+    found.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    O = [oracle.TCF(int(logs[m]), 16, seed=int(seeds[m])) for m in range(n)]
+    for j in range(2):
+        o, k = calls[j]
+        for m in range(n):
+            O[m].insert(k[o[m]:o[m + 1]])
+    check_images(G, O)
+    fh = host(found)
+    for m in range(n):
+        assert np.array_equal(fh[off[m]:off[m + 1]], O[m].query(keys[off[m]:off[m + 1]])), m
