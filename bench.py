@@ -46,6 +46,7 @@ BYTES_PER_UNIT = {
     "rs_scatter_kv": 24.0,       # key + index read and write
     "rs_hist": 8.0,              # key read
     "scan_kernel": 8.0,          # u32 read + write
+    "gqf_fp_kernel": 16.0,       # key read + fingerprint write
     "rle_kernel": 8.0,           # sorted fingerprint read (group writes not counted)
     "gqf_merge_kernel": 3.0,     # per slot: old table read + new table write (r = 8: 1.5 B/slot each)
     "gqf_count_kernel": 80.0,    # key + metadata sector + remainder sector + count
@@ -582,9 +583,19 @@ def run_serving(args, device):
     run(None)  # warm-up
     sec, lat = run(None)
     cap = ops / sec
+    # where the time goes: summed latency per filter kind and operation
+    brk = {}
+    for (f, op, keys), l in zip(reqs, lat):
+        k = ("tcf" if f < nt else "gqf") + "_" + ("insert", "query", "delete")[op]
+        b = brk.setdefault(k, [0, 0, 0.0])
+        b[0] += 1
+        b[1] += len(keys)
+        b[2] += float(l)
+    breakdown = {k: {"requests": v[0], "keys": v[1], "latency_s_sum": round(v[2], 3)} for k, v in brk.items()}
     out = {"workload": SERVING_WORKLOAD, "requests": len(reqs), "ops": ops, "capacity_gops": round(cap / 1e9, 4),
            "capacity_p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-           "capacity_p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "loads": []}
+           "capacity_p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "capacity_breakdown": breakdown,
+           "loads": []}
     mean_ops = ops / len(reqs)
     for frac in (0.5, 0.8):
         rate = frac * cap / mean_ops

@@ -22,7 +22,7 @@ static bool pointers_set(const filter *F)
                T.tcount && T.dlist && T.seg;
     }
     const GqfState &Q = F->gqf;
-    return Q.meta[0] && Q.meta[1] && Q.rem[0] && Q.rem[1] && Q.fp_b && Q.fp_c && Q.ufp &&
+    return Q.meta[0] && Q.meta[1] && Q.rem[0] && Q.rem[1] && Q.fp_a && Q.fp_b && Q.fp_c && Q.ufp && Q.idx_a &&
            Q.idx_b && Q.idx_c && Q.ustart && Q.flags && Q.removed && Q.tile_state && Q.tile_lo && Q.radix_tmp;
 }
 

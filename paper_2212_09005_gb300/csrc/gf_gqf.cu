@@ -54,6 +54,17 @@ __host__ __device__ __forceinline__ uint32_t ndig(uint64_t v, uint32_t r)
 __host__ __device__ __forceinline__ uint32_t enc_len(uint64_t c, uint32_t r) { return c == 1 ? 1u : 3u + ndig(c - 2, r); }
 
 // ---------------------------------------------------------------------------
+// fingerprints
+// ---------------------------------------------------------------------------
+__global__ void gqf_fp_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H, uint64_t *fp, uint32_t *idx)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        fp[i] = fingerprint(keys[i], H);
+        if (idx) idx[i] = (uint32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The merge kernel
 // ---------------------------------------------------------------------------
 struct MergeArgs {
@@ -744,6 +755,10 @@ __global__ void gqf_tile_ranges(const uint64_t *__restrict__ ufp, const uint32_t
 // ---------------------------------------------------------------------------
 static constexpr long long RQ_MIN = 256;     // quotients per delete region, smallest (a multiple of 64)
 static constexpr long long RQ_MAX = 1 << 16;
+// In-place batches are worth it only while each region thread has few groups
+// to apply one after another; past that the merge, whose cost does not grow
+// with the batch, is faster. Limit on the mean groups per region.
+static constexpr uint64_t GROUPS_PER_REGION = 8;
 
 struct GView {
     Meta *meta;
@@ -943,6 +958,285 @@ __device__ uint64_t gv_delete(const GView &g, uint64_t fp, uint64_t d, unsigned 
     return rm;
 }
 
+// ---------------------------------------------------------------------------
+// In-place bulk insert over even-odd regions (the paper's Sec. 5.3 scheme):
+// one thread per region inserts the region's groups in ascending order, each
+// by rewriting its run and moving the following runs of the cluster right
+// (the mirror of the delete above; the result is the same canonical layout
+// as the merge). A read-only pre-check bounds, per region, how far the
+// region's inserts can push data: the Delta-th empty slot after its last
+// group, Delta being the exact number of slots the region adds. When every
+// region's bound ends before the region after next (and before the end of
+// the table), two threads of a phase never touch the same slots or words,
+// and every value a thread reads outside its own region belongs to a region
+// that is idle in that phase.
+// ---------------------------------------------------------------------------
+// largest occupied quotient in [lo, x), or -1
+__device__ long long gv_prev_occ_from(const GView &g, long long x, long long lo)
+{
+    long long z = x - 1;
+    if (z < lo) return -1;
+    long long w = z >> 6;
+    unsigned long long bits = g.meta[w].occ & (((z & 63) == 63) ? ~0ull : ((1ull << ((z & 63) + 1)) - 1ull));
+    while (true) {
+        if (64 * w < lo) bits &= ~0ull << (lo - 64 * w);
+        if (bits) return 64 * w + 63 - __clzll((long long)bits);
+        if (64 * w <= lo) return -1;
+        bits = g.meta[--w].occ;
+    }
+}
+
+// End of the run of the largest occupied quotient < x, for x in the region
+// starting at r0, from the region's own metadata (-1: it ends before r0).
+// A run that reaches into the region from the left is known from the offset
+// of the region's first block, which the region alone may change.
+__device__ long long gv_prev_end_in(const GView &g, long long x, long long r0)
+{
+    const long long y = gv_prev_occ_from(g, x, r0);
+    if (y >= 0) return gv_runend_of(g, y);
+    const long long b0 = r0 >> 6;
+    if (gv_occ(g, r0)) {
+        // x == r0 and r0 has a run: the chain before it ends just before it starts
+        const long long e = gv_runend_of(g, r0);
+        const long long pr = gv_prev_runend(g, e - 1, r0);
+        return pr >= 0 ? pr : -1;
+    }
+    const long long off = (long long)g.meta[b0].off;
+    if (off > 0) return r0 + off;
+    if ((g.meta[b0].rend & 1ull) != 0) return r0;
+    return -1;
+}
+
+// one group (value v, count c) of R-bit slots at position pos
+template <int R>
+__device__ __forceinline__ void gv_put_group(const GView &g, long long pos, uint32_t v, uint64_t c)
+{
+    wr_slot<R>(g.rem, (uint64_t)pos++, v);
+    if (c == 1) return;
+    const uint64_t xx = c - 2;
+    const uint32_t nd = ndig(xx, R);
+    wr_slot<R>(g.rem, (uint64_t)pos++, v);
+    wr_slot<R>(g.rem, (uint64_t)pos++, nd);
+    for (uint32_t t = 0; t < nd; t++)
+        wr_slot<R>(g.rem, (uint64_t)pos++, (uint32_t)((xx >> (R * (nd - 1 - t))) & ((1u << R) - 1u)));
+}
+
+// the group of run [p, e] starting at p: value, count, encoded length
+template <int R>
+__device__ __forceinline__ uint32_t gv_group_at(const GView &g, long long p, long long e, uint32_t &val, uint64_t &cc)
+{
+    val = rd_slot<R>(g.rem, (uint64_t)p);
+    cc = 1;
+    if (p + 2 <= e && rd_slot<R>(g.rem, (uint64_t)(p + 1)) == val) {
+        uint32_t nd = rd_slot<R>(g.rem, (uint64_t)(p + 2));
+        if (p + 2 + (long long)nd > e) nd = (uint32_t)(e - p - 2);
+        uint64_t acc = 0;
+        for (uint32_t t = 0; t < nd; t++) acc = (acc << R) | rd_slot<R>(g.rem, (uint64_t)(p + 3 + t));
+        cc = acc + 2;
+        return 3 + nd;
+    }
+    return 1;
+}
+
+// Where group (x, v) goes: run start s, old run end e (s - 1 when x has no
+// run), insertion point p, and the old count and length of v's group (0 when
+// v is new). False on an inconsistent table.
+template <int R>
+__device__ bool gv_locate(const GView &g, long long x, uint32_t v, long long r0, long long &s, long long &e,
+                          long long &p, uint64_t &c_old, uint32_t &ol)
+{
+    c_old = 0;
+    ol = 0;
+    if (gv_occ(g, x)) {
+        e = gv_runend_of(g, x);
+        if (e < 0) return false;
+        const long long pr = gv_prev_runend(g, e - 1, x);
+        s = pr >= 0 ? pr + 1 : x;
+        p = s;
+        while (p <= e) {
+            uint32_t val;
+            uint64_t cc;
+            const uint32_t len = gv_group_at<R>(g, p, e, val, cc);
+            if (val == v) {
+                c_old = cc;
+                ol = len;
+                break;
+            }
+            if (val > v) break;
+            p += len;
+        }
+    } else {
+        const long long pe = gv_prev_end_in(g, x, r0);
+        s = x > pe + 1 ? x : pe + 1;
+        e = s - 1;
+        p = s;
+    }
+    return true;
+}
+
+// add c copies of fingerprint fp; false on an inconsistent table
+template <int R>
+__device__ bool gv_insert(const GView &g, uint64_t fp, uint64_t c, long long r0)
+{
+    const long long x = (long long)(fp >> R);
+    const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
+    const bool had = gv_occ(g, x);
+    long long s, e, p;
+    uint64_t c_old;
+    uint32_t ol;
+    if (!gv_locate<R>(g, x, v, r0, s, e, p, c_old, ol)) return false;
+    const uint64_t cn = c_old + c;
+    const uint32_t nl = enc_len(cn, R);
+    const long long delta = (long long)nl - (long long)ol;
+    if (delta == 0) {
+        gv_put_group<R>(g, p, v, cn);
+        return true;
+    }
+    // the following runs of the cluster move to max(home, previous end + 1);
+    // find the last one that moves (all runs between x and it move)
+    long long old_prev_end = e, new_prev_end = e + delta, y = x;
+    long long cy = -1, cos = 0, coe = 0, cns = 0;
+    while (true) {
+        const long long yn = gv_next_occ(g, y, new_prev_end + 1);
+        if (yn < 0) break;
+        const long long os = yn > old_prev_end + 1 ? yn : old_prev_end + 1;
+        const long long ns = yn > new_prev_end + 1 ? yn : new_prev_end + 1;
+        if (ns == os) break;
+        const long long oe = gv_next_runend(g, os);
+        if (oe < 0) return false;
+        cy = yn;
+        cos = os;
+        coe = oe;
+        cns = ns;
+        old_prev_end = oe;
+        new_prev_end = ns + (oe - os);
+        y = yn;
+    }
+    if (new_prev_end >= g.nslots) return false;
+    // move them, last first: each moves right and lands right after the one
+    // before it, so the one before is found from the untouched bits below
+    long long ny = -1, first_moved = -1;
+    while (cy >= 0) {
+        const long long len = coe - cos + 1, ne = cns + len - 1;
+        for (long long q = len - 1; q >= 0; q--)
+            wr_slot<R>(g.rem, (uint64_t)(cns + q), rd_slot<R>(g.rem, (uint64_t)(cos + q)));
+        gv_rend_put(g, coe, false);
+        gv_rend_put(g, ne, true);
+        const long long yl = ny >= 0 ? ny : gv_next_occ(g, cy, ne);
+        gv_fix_offsets(g, cy, yl >= 0 ? yl : (1ll << 62), ne, ne);
+        first_moved = cy;
+        const long long py = gv_prev_occ_from(g, cy, x + 1);
+        if (py < 0) break;
+        const long long poe = gv_prev_runend(g, cos - 1, x);       // its old end
+        if (poe < py) return false;
+        const long long ppr = gv_prev_runend(g, poe - 1, x);       // the end of the run before it, if >= x
+        const long long pst = py > ppr + 1 ? py : ppr + 1;
+        const long long pns = cns - (poe - pst + 1);
+        if (pns <= pst) return false;
+        ny = cy;
+        cy = py;
+        cos = pst;
+        coe = poe;
+        cns = pns;
+    }
+    // the run of x: its tail after the group moves right, the group is written
+    for (long long q = e; q >= p + (long long)ol; q--)
+        wr_slot<R>(g.rem, (uint64_t)(q + delta), rd_slot<R>(g.rem, (uint64_t)q));
+    gv_put_group<R>(g, p, v, cn);
+    if (had) gv_rend_put(g, e, false);
+    gv_rend_put(g, e + delta, true);
+    if (!had) g.meta[x >> 6].occ |= 1ull << (x & 63);
+    const long long ylim0 = first_moved >= 0 ? first_moved : gv_next_occ(g, x, e + delta);
+    gv_fix_offsets(g, x, ylim0 >= 0 ? ylim0 : (1ll << 62), e + delta, e + delta);
+    return true;
+}
+
+// Where data pushed right by `need` slots from quotient x stops: the need-th
+// empty slot at or after the chain that covers x (-1 when it would pass
+// `limit`). r0: the start of x's region.
+__device__ long long gv_push_end(const GView &g, long long x, long long need, long long r0, long long limit)
+{
+    long long pos = x;
+    long long E = gv_prev_end_in(g, x + 1, r0);  // end of the run of the largest occupied quotient <= x
+    if (E >= pos) {
+        long long y = pos;
+        while (true) {
+            const long long yn = gv_next_occ(g, y, E + 1);
+            if (yn < 0) break;
+            E = gv_next_runend(g, E + 1);
+            if (E < 0 || E > limit) return -1;
+            y = yn;
+        }
+        pos = E + 1;
+    }
+    while (need > 0) {
+        if (pos > limit) return -1;
+        const long long yn = gv_next_occ(g, pos - 1, limit);
+        const long long gap = (yn < 0 ? limit + 1 : yn) - pos;  // empty slots before the next run
+        if (gap >= need) return pos + need - 1;
+        if (yn < 0) return -1;
+        need -= gap;
+        E = gv_runend_of(g, yn);
+        long long y = yn;
+        while (E >= 0 && E <= limit) {
+            const long long y2 = gv_next_occ(g, y, E + 1);
+            if (y2 < 0) break;
+            E = gv_next_runend(g, E + 1);
+            y = y2;
+        }
+        if (E < 0 || E > limit) return -1;
+        pos = E + 1;
+    }
+    return pos - 1;
+}
+
+// read-only: per region, the slots its groups add, and whether the data they
+// push stays before the region after next (two slots of margin) and before
+// the table's end
+template <int R>
+__global__ void gqf_insert_precheck(GView g, const uint64_t *__restrict__ ufp, const uint32_t *__restrict__ ustart,
+                                    const uint32_t *__restrict__ rlo, uint64_t nreg, uint64_t rq,
+                                    unsigned long long *bad)
+{
+    for (uint64_t reg = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; reg < nreg;
+         reg += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t k0 = rlo[reg], k1 = rlo[reg + 1];
+        if (k0 == k1) continue;
+        const long long r0 = (long long)(reg * rq);
+        long long limit = (long long)((reg + 2) * rq) - 2;
+        if (limit > g.nslots - 1) limit = g.nslots - 1;
+        long long need = 0;
+        for (uint32_t k = k0; k < k1; k++) {
+            const uint64_t fp = ufp[k];
+            long long s, e, p;
+            uint64_t c_old;
+            uint32_t ol;
+            if (!gv_locate<R>(g, (long long)(fp >> R), (uint32_t)(fp & ((1ull << R) - 1ull)), r0, s, e, p, c_old, ol)) {
+                atomicExch(bad, 1ull);
+                return;
+            }
+            need += (long long)enc_len(c_old + (uint64_t)(ustart[k + 1] - ustart[k]), R) - (long long)ol;
+        }
+        // the data all of them push stops, at the latest, where the data pushed
+        // from the last one stops
+        if (gv_push_end(g, (long long)(ufp[k1 - 1] >> R), need, r0, limit) < 0) atomicExch(bad, 1ull);
+    }
+}
+
+template <int R>
+__global__ void gqf_insert_phase(GView g, const uint64_t *__restrict__ ufp, const uint32_t *__restrict__ ustart,
+                                 const uint32_t *__restrict__ rlo, uint64_t nreg, uint64_t rq, int phase,
+                                 unsigned long long *status)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t reg = 2 * i + (uint64_t)phase;
+        if (reg >= nreg) return;
+        const long long r0 = (long long)(reg * rq);
+        for (uint32_t k = rlo[reg]; k < rlo[reg + 1]; k++)
+            if (!gv_insert<R>(g, ufp[k], ustart[k + 1] - ustart[k], r0)) atomicOr(status, ST_INTERNAL);
+    }
+}
+
 // first group of every delete region (successor search)
 __global__ void gqf_region_ranges(const uint64_t *__restrict__ ufp, const uint32_t *pm, uint64_t N, uint32_t r,
                                   uint64_t rq, uint64_t nreg, uint32_t *rlo)
@@ -1134,6 +1428,13 @@ static uint64_t tail_slots(uint32_t q)
     return s;
 }
 
+// entries of the range array: one per merge tile or per smallest region, plus one
+uint64_t gqf_tile_lo_words(const GqfState &Q)
+{
+    const uint64_t nreg = (Q.N + RQ_MIN - 1) / RQ_MIN;
+    return (Q.ntiles > nreg ? Q.ntiles : nreg) + 1;
+}
+
 int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only)
 {
     const filter_config &c = F->cfg;
@@ -1172,23 +1473,24 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     table_bytes = bytes;
     uint64_t scan_n = radix_tmp_words(M);
     if (M + 1 > scan_n) scan_n = M + 1;
-    Q.fp_a = nullptr;  // the sort hashes the keys in its first pass
+    piece(Q.fp_a, M);
     
     piece(Q.fp_b, M);
     piece(Q.fp_c, M);
     piece(Q.ufp, M);
-    Q.idx_a = nullptr;  // the first pass takes the positions as its values
+    piece(Q.idx_a, M);
     piece(Q.idx_b, M);
     piece(Q.idx_c, M);
     piece(Q.ustart, M + 1);
     piece(Q.flags, M + 1);
     piece(Q.removed, M);
     piece(Q.tile_state, Q.ntiles * 4 + 2);
-    piece(Q.tile_lo, (Q.ntiles > (Q.N + RQ_MIN - 1) / RQ_MIN ? Q.ntiles : (Q.N + RQ_MIN - 1) / RQ_MIN) + 1);
+    piece(Q.tile_lo, gqf_tile_lo_words(Q));
     piece(Q.radix_tmp, radix_tmp_words(M));
     piece(F->scan_tmp, scan_tmp_words(scan_n));
     scratch_bytes = bytes - table_bytes;
     Q.cur = 0;
+    Q.merge_only = false;
     return FILTER_OK;
 }
 
@@ -1209,9 +1511,12 @@ static void gqf_prepare(filter *F, const uint64_t *keys, uint64_t n, bool need_i
                         uint32_t **sorted_idx)
 {
     GqfState &Q = F->gqf;
-    // fingerprints are computed by the sort's first pass
-    radix_sort_u64(keys, Q.fp_b, Q.fp_c, nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp, F->scan_tmp, F->ctr, st,
-                   &Q.H, need_idx);
+    {
+        gf::TraceScope ts_("gqf_fp_kernel", n, st);
+        gqf_fp_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(keys, n, Q.H, Q.fp_a, need_idx ? Q.idx_a : nullptr);
+    }
+    radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp,
+                   F->scan_tmp, F->ctr, st);
     // groups: flags[n] = their number; flags[i] = the group of sorted element i (statuses only)
     rle_sorted_u64(Q.fp_b, n, Q.ufp, Q.ustart, need_idx ? Q.flags : nullptr, Q.flags + n, F->scan_tmp, F->ctr, st);
     *sorted_idx = Q.idx_b;
@@ -1269,13 +1574,80 @@ static int read_dev(const T *d, T *h, cudaStream_t st)
     return FILTER_OK;
 }
 
+// Small batches go in place over even-odd regions; `done` is false when the
+// pre-check found, at every region size tried, a region whose inserts could
+// reach the region after next (or the table's end).
+static int gqf_insert_in_place(filter *F, uint64_t n, uint32_t m, cudaStream_t st, bool &done)
+{
+    GqfState &Q = F->gqf;
+    done = false;
+    GView g{reinterpret_cast<Meta *>(Q.meta[Q.cur]), Q.rem[Q.cur], (long long)Q.N, (long long)Q.nslots,
+            (long long)Q.nblk};
+    int rc = FILTER_OK;
+    // a few region sizes, growing fourfold; dense batches go to the merge
+    for (uint64_t rq = RQ_MIN; rq <= (uint64_t)RQ_MAX / 4 && (uint64_t)m * rq <= GROUPS_PER_REGION * Q.N; rq <<= 2) {
+        const uint64_t nreg = (Q.N + rq - 1) / rq;
+        {
+            gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);
+            gqf_region_ranges<<<grid_for(nreg + 1, 256, 4), 256, 0, st>>>(Q.ufp, Q.flags + n, Q.N, Q.r, rq, nreg,
+                                                                         Q.tile_lo);
+        }
+        GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
+        {
+            gf::TraceScope ts_("gqf_insert_precheck", nreg, st);
+            if (Q.r == 8)
+                gqf_insert_precheck<8><<<grid_for(nreg, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq,
+                                                                               &F->ctr->overflow);
+            else
+                gqf_insert_precheck<16><<<grid_for(nreg, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq,
+                                                                                &F->ctr->overflow);
+        }
+        unsigned long long bad = 0;
+        if ((rc = read_dev(&F->ctr->overflow, &bad, st))) return rc;
+        if (bad) continue;
+        const uint64_t half = (nreg + 1) / 2;
+        for (int ph = 0; ph < 2; ph++) {
+            gf::TraceScope ts_("gqf_insert_phase", half, st);
+            if (Q.r == 8)
+                gqf_insert_phase<8><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq, ph,
+                                                                            &F->ctr->status);
+            else
+                gqf_insert_phase<16><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq,
+                                                                             ph, &F->ctr->status);
+        }
+        GF_CUDA(cudaGetLastError());
+        done = true;
+        return FILTER_OK;
+    }
+    return FILTER_OK;
+}
+
 int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
 {
     if (n == 0) return FILTER_OK;
     GqfState &Q = F->gqf;
     uint32_t *sidx = nullptr;
     gqf_prepare(F, keys, n, status != nullptr, st, &sidx);
-    int rc = gqf_merge(F, n, ~0ull, 0, 0, st);
+    int rc;
+    // small batches: in place, region by region; larger ones: the merge
+    {
+        uint32_t m = 0;
+        if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
+        if ((uint64_t)m * RQ_MIN <= GROUPS_PER_REGION * Q.N && !Q.merge_only) {
+            bool done = false;
+            if ((rc = gqf_insert_in_place(F, n, m, st, done))) return rc;
+            if (done) {
+                if (status) {
+                    gf::TraceScope ts_("gqf_status_kernel", n, st);
+                    gqf_status_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(n, Q.flags, Q.ustart, sidx, Q.removed,
+                                                                          ~0ull, 0, status);
+                }
+                GF_CUDA(cudaGetLastError());
+                return FILTER_OK;
+            }
+        }
+    }
+    rc = gqf_merge(F, n, ~0ull, 0, 0, st);
     if (rc) return rc;
     unsigned long long ovf = 0;
     if ((rc = read_dev(&F->ctr->overflow, &ovf, st))) return rc;
@@ -1324,7 +1696,7 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
     uint32_t m = 0;
     if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
     bool done = false;
-    if ((uint64_t)m * 4 <= Q.nslots) {
+    if ((uint64_t)m * RQ_MIN <= GROUPS_PER_REGION * Q.N) {
         GView g{reinterpret_cast<Meta *>(Q.meta[Q.cur]), Q.rem[Q.cur], (long long)Q.N, (long long)Q.nslots,
                 (long long)Q.nblk};
         GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
@@ -1337,7 +1709,7 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
         if ((rc = read_dev(&F->ctr->overflow, &reach, st))) return rc;
         uint64_t rq = RQ_MIN;
         while ((unsigned long long)rq < reach) rq <<= 1;
-        if (rq <= (uint64_t)RQ_MAX) {
+        if (rq <= (uint64_t)RQ_MAX && (uint64_t)m * rq <= GROUPS_PER_REGION * Q.N) {
             const uint64_t nreg = (Q.N + rq - 1) / rq;
             {
                 gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);
@@ -1528,9 +1900,8 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
         nslots_tot += Q.nslots;
         tiles += Q.ntiles;
         if (Q.p > pbits) pbits = Q.p;
-        const uint64_t nreg = (Q.N + RQ_MIN - 1) / RQ_MIN;
         if (Q.ntiles * 4 + 2 > ts_words) ts_words = Q.ntiles * 4 + 2;
-        if ((Q.ntiles > nreg ? Q.ntiles : nreg) + 1 > tlo_words) tlo_words = (Q.ntiles > nreg ? Q.ntiles : nreg) + 1;
+        if (gqf_tile_lo_words(Q) > tlo_words) tlo_words = gqf_tile_lo_words(Q);
     }
     uint32_t mbits = 1;
     while (mbits < 32 && (1ull << mbits) < n) mbits++;
@@ -1599,6 +1970,7 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
         F.cfg = V[m].cfg;
         F.gqf = V[m].gqf;
         GqfState &S = F.gqf;
+        S.merge_only = true;  // a member redone alone must land in the other buffer, like the group
         for (int b = 0; b < 2; b++) {
             S.meta[b] = Q.meta[b] + meta_off[m] * 32;
             S.rem[b] = Q.rem[b] + rem_off[m] * (r / 8);

@@ -221,14 +221,11 @@ void rle_sorted_u64(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *
 
 // LSD radix sort of 64-bit keys on bits [0, bits), optional 32-bit values.
 // Result lands in keys_out / vals_out. `tmp` holds radix_tmp_words(n) words.
-// With `fp`, keys_in holds raw keys and the sort is of their fingerprints
-// under *fp (computed in the first pass; keys_in is only read); iota_vals
-// then makes the values the input positions.
 size_t radix_tmp_words(uint64_t n);
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt,
                     uint64_t n, uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp,
-                    DevCounters *ctr, cudaStream_t st, const PHash *fp = nullptr, bool iota_vals = false);
+                    DevCounters *ctr, cudaStream_t st);
 
 // Kernel tracing: a TraceScope around a launch records CUDA events before and
 // after it when tracing is on.
@@ -285,6 +282,7 @@ struct GqfState {
     uint8_t *meta[2];  // nblk * 32
     uint8_t *rem[2];   // nslots * r/8
     int cur;           // which buffer holds the table
+    bool merge_only;   // inserts always merge into the other buffer (no in-place path)
     // scratch
     uint64_t *fp_a, *fp_b, *fp_c;  // max_batch
     uint32_t *idx_a, *idx_b, *idx_c;
@@ -361,6 +359,7 @@ uint64_t tcf_image_bytes(const filter *F);
 int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st);
 
 int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);
+uint64_t gqf_tile_lo_words(const GqfState &Q);
 int gqf_clear(filter *F, cudaStream_t st);
 int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
 int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);

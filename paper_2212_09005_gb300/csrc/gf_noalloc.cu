@@ -80,19 +80,20 @@ extern "C" int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_s
     Q.meta[1] = reinterpret_cast<uint8_t *>(tout);
     Q.rem[1] = reinterpret_cast<uint8_t *>(tout) + metaB;
     Q.cur = 0;
+    Q.merge_only = true;  // the input image is read only: the result goes to the output image
     F.ctr = A.take<DevCounters>(1);
-    Q.fp_a = nullptr;
+    Q.fp_a = A.take<uint64_t>(M);
     Q.fp_b = A.take<uint64_t>(M);
     Q.fp_c = A.take<uint64_t>(M);
     Q.ufp = A.take<uint64_t>(M);
-    Q.idx_a = nullptr;
+    Q.idx_a = A.take<uint32_t>(M);
     Q.idx_b = A.take<uint32_t>(M);
     Q.idx_c = A.take<uint32_t>(M);
     Q.ustart = A.take<uint32_t>(M + 1);
     Q.flags = A.take<uint32_t>(M + 1);
     Q.removed = A.take<uint32_t>(M);
     Q.tile_state = A.take<unsigned long long>(Q.ntiles * 4 + 2);
-    Q.tile_lo = A.take<uint32_t>(Q.ntiles + 1);  // inserts only: the delete regions are never used here
+    Q.tile_lo = A.take<uint32_t>(gqf_tile_lo_words(Q));
     Q.radix_tmp = A.take<uint32_t>(radix_tmp_words(M));
     uint64_t scan_n = radix_tmp_words(M);
     if (M + 1 > scan_n) scan_n = M + 1;

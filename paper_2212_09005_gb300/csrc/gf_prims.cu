@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(SCAN_T) rle_kernel(const uint64_t *__restrict_
     }
     __syncthreads();
     uint32_t g = s_prefix + s_warp[warp] + (incl - sum);  // runs started before this thread's elements
+    uint32_t rv[SCAN_I];
 #pragma unroll
     for (int q = 0; q < SCAN_I; q++) {
         if ((starts >> q) & 1u) {
@@ -244,10 +245,21 @@ __global__ void __launch_bounds__(SCAN_T) rle_kernel(const uint64_t *__restrict_
             start[g] = (uint32_t)(base + q);
             g++;
         }
-        if (run_of && base + q < n) run_of[base + q] = g - 1;
+        rv[q] = g - 1;
         if (base + q == n - 1) {
             *m_out = g;
             start[g] = (uint32_t)n;
+        }
+    }
+    if (run_of) {
+        if (base + SCAN_I <= n) {
+            uint4 *p = reinterpret_cast<uint4 *>(run_of + base);
+#pragma unroll
+            for (int q = 0; q < SCAN_I / 4; q++) p[q] = make_uint4(rv[4 * q], rv[4 * q + 1], rv[4 * q + 2], rv[4 * q + 3]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < SCAN_I; q++)
+                if (base + q < n) run_of[base + q] = rv[q];
         }
     }
 }
@@ -291,11 +303,8 @@ size_t radix_tmp_words(uint64_t n)
 // with plain shared atomics (equal digits inside one warp serialise on one
 // address, which is cheaper than ranking them), then the warps' counts are
 // summed per digit.
-// FP: the input holds raw keys and the sorted values are their fingerprints
-// under H (first pass of a fingerprint sort: no separate hashing pass).
-template <bool FP>
 __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ keys, uint64_t n, uint32_t shift,
-                                                uint32_t nb, uint32_t *counts, uint64_t ntiles, PHash H)
+                                                uint32_t nb, uint32_t *counts, uint64_t ntiles)
 {
     __shared__ uint32_t h[RS_WARPS][RS_MAXB];
     for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB; i += RS_T) (&h[0][0])[i] = 0;
@@ -307,7 +316,6 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
     for (int r = 0; r < RS_I; r++) {
         uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
         k[r] = (i < n) ? __ldcs(keys + i) : 0;
-        if (FP) k[r] = fingerprint(k[r], H);
     }
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
@@ -330,15 +338,13 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
 // the copy-out writes runs of consecutive addresses, taking each key's
 // global position from its digit's offset. Shared memory and registers are
 // sized for 3 CTAs per SM (2 with values).
-// FP: as for rs_hist; the values (VALS) are then the input positions.
-template <bool VALS, bool FP>
+template <bool VALS>
 __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t *__restrict__ kin,
                                                                  uint64_t *__restrict__ kout,
                                                                  const uint32_t *__restrict__ vin,
                                                                  uint32_t *__restrict__ vout, uint64_t n,
                                                                  uint32_t shift, uint32_t nb,
-                                                                 const uint32_t *__restrict__ offs, uint64_t ntiles,
-                                                                 PHash H)
+                                                                 const uint32_t *__restrict__ offs, uint64_t ntiles)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     uint64_t *skeys = reinterpret_cast<uint64_t *>(smem);              // [RS_TILE] keys in digit order
@@ -362,8 +368,7 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         bool ok = i < n;
         key[r] = ok ? __ldcs(kin + i) : 0;
-        if (FP) key[r] = fingerprint(key[r], H);
-        if (VALS) val[r] = ok ? (FP ? (uint32_t)i : __ldcs(vin + i)) : 0;
+        if (VALS) val[r] = ok ? __ldcs(vin + i) : 0;
     }
 #pragma unroll
     for (int r = 0; r < RS_I; r++) {
@@ -454,25 +459,22 @@ static constexpr size_t rs_smem()
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt, uint64_t n,
                     uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp, DevCounters *ctr,
-                    cudaStream_t st, const PHash *fp, bool iota_vals)
+                    cudaStream_t st)
 {
     if (n == 0) return;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(rs_scatter<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
-        cudaFuncSetAttribute(rs_scatter<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
-        cudaFuncSetAttribute(rs_scatter<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
-        cudaFuncSetAttribute(rs_scatter<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
         attr_done = true;
     }
-    const bool vals = vals_in != nullptr || (fp && iota_vals);
-    const uint32_t npass = (bits + 8) / 9;  // digits of at most 9 bits (a fingerprint sort has p >= 7 bits)
+    const bool vals = vals_in != nullptr;
+    const uint32_t npass = (bits + 8) / 9;  // digits of at most 9 bits
     if (npass == 0) {
         cudaMemcpyAsync(keys_out, keys_in, n * 8, cudaMemcpyDeviceToDevice, st);
-        if (vals_in) cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, st);
+        if (vals) cudaMemcpyAsync(vals_out, vals_in, n * 4, cudaMemcpyDeviceToDevice, st);
         return;
     }
-    const PHash H = fp ? *fp : PHash{0, 0, 0, 0};
     const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const uint64_t *ksrc = keys_in;
     const uint32_t *vsrc = vals_in;
@@ -481,25 +483,21 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         // split the bits as evenly as possible: the first passes take the extra bit
         const uint32_t db = bits / npass + (p < bits % npass ? 1u : 0u);
         const uint32_t nb = 1u << db;
-        const bool hash = fp && p == 0;
         bool to_out = ((npass - 1 - p) % 2) == 0;
         uint64_t *kdst = to_out ? keys_out : keys_alt;
         uint32_t *vdst = to_out ? vals_out : vals_alt;
         {
             TraceScope ts_("rs_hist", n, st);
-            if (hash) rs_hist<true><<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles, H);
-            else rs_hist<false><<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles, H);
+            rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles);
         }
         exclusive_scan_u32(tmp, tmp, ntiles * nb, scan_tmp, ctr, st);
         TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
-        const unsigned g = (unsigned)ntiles;
-        if (vals) {
-            if (hash) rs_scatter<true, true><<<g, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, ntiles, H);
-            else rs_scatter<true, false><<<g, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, ntiles, H);
-        } else {
-            if (hash) rs_scatter<false, true><<<g, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, ntiles, H);
-            else rs_scatter<false, false><<<g, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, ntiles, H);
-        }
+        if (vals)
+            rs_scatter<true><<<(unsigned)ntiles, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb,
+                                                                            tmp, ntiles);
+        else
+            rs_scatter<false><<<(unsigned)ntiles, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n,
+                                                                              shift, nb, tmp, ntiles);
         ksrc = kdst;
         vsrc = vdst;
         shift += db;

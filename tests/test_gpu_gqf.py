@@ -197,9 +197,24 @@ def test_counting_config_2_28_zipf(gf, oracle):
 def test_inplace_delete_matches_oracle(gf, oracle):
     """Deletes of a small fraction of the table take the in-place cluster path
     (even-odd regions); image and statuses must equal the oracle's."""
+    ins = W.uniform_keys(1, int(0.4 * (1 << 20)))  # 40% load: short clusters
+    dele1 = np.concatenate([ins[::80], ins[:1000:20], W.uniform_keys(77, 3000)])  # repeats, absent keys
+    dele2 = np.concatenate([ins[1::37], ins[1::37]])
+    gf.trace_reset()
+    gf.trace_enable(True)
+    try:
+        run_batches(gf, oracle, 20, 8, seed=1, batches=[ins], deletes=[dele1, dele2])
+        assert "gqf_delete_phase" in gf.trace_summary(), "the deletes should have been applied in place"
+    finally:
+        gf.trace_enable(False)
+
+
+def test_deletes_at_high_load(gf, oracle):
+    """At 90% load the clusters are long; whichever path the library takes,
+    image and statuses must equal the oracle's."""
     w = W.gqf_uniform_workload(20, seed=1)
     ins = w["insert"]
-    dele1 = np.concatenate([ins[::20], ins[:1000:20], W.uniform_keys(77, 3000)])  # repeats, absent keys
+    dele1 = np.concatenate([ins[::80], ins[:1000:20], W.uniform_keys(77, 3000)])
     dele2 = np.concatenate([ins[1::37], ins[1::37]])
     run_batches(gf, oracle, 20, 8, seed=1, batches=[ins], deletes=[dele1, dele2])
 
@@ -210,3 +225,66 @@ def test_inplace_delete_small_tables_and_counters(gf, oracle):
     ins = np.concatenate([keys, np.repeat(keys[:30], 300), np.repeat(keys[30:40], 3)])  # multi-digit counters
     dele = [np.concatenate([np.repeat(keys[:30], 290), keys[30:35]]), np.repeat(keys[:10], 20), keys[100:130]]
     run_batches(gf, oracle, q, 8, seed=4, batches=[ins], deletes=dele)
+
+
+def _inplace_used(gf):
+    return "gqf_insert_phase" in gf.trace_summary()
+
+
+@pytest.mark.parametrize("q,r,load", [(12, 8, 0.3), (14, 8, 0.6), (13, 16, 0.5), (12, 8, 0.85), (16, 8, 0.7)])
+def test_inplace_insert_matches_oracle(gf, oracle, q, r, load):
+    """Small batches into a filled table go in place over even-odd regions (the
+    paper's Sec. 5.3 scheme); the image must stay byte-identical to the oracle's
+    after every batch, with new fingerprints, repeats of stored ones (counters
+    growing past one and two digits) and new quotients at every load."""
+    n_fill = int(load * (1 << q))
+    base = W.uniform_keys(1700 + q, n_fill)
+    nf, na = (1 << q) // 80, (1 << q) // 640  # a few groups per delete region of 256 quotients
+    extra = W.uniform_keys(1800 + q, 6 * nf)
+    batches = [base]  # the merge fills the table
+    for j in range(6):
+        fresh = extra[j * nf:(j + 1) * nf]
+        again = base[j * na:(j + 1) * na]
+        hot = np.full(300 * (j + 1), base[7], dtype=np.uint64)  # one counter keeps growing
+        batches.append(np.concatenate([fresh, again, hot, fresh[:10]]))
+    O = oracle.GQF(q, r, seed=q)
+    G = gf.GQF(q, r, seed=q, max_batch=max(len(b) for b in batches))
+    gf.trace_reset()
+    gf.trace_enable(True)
+    try:
+        for k, b in enumerate(batches):
+            st_o = O.insert(b)
+            st = zeros_u8(len(b))
+            G.insert(dev_u64(b), st)
+            assert np.array_equal(host(st), st_o), k
+            d = first_diff(G.export(), O.export())
+            assert d is None, (k, d)
+        used = _inplace_used(gf)
+    finally:
+        gf.trace_enable(False)
+    if load <= 0.7:
+        assert used, "small batches should have been inserted in place"
+    probe = np.concatenate([base[:3000], extra, W.uniform_keys(1900 + q, 3000)])
+    c = zeros_u64(len(probe))
+    G.count(dev_u64(probe), c)
+    assert np.array_equal(host(c), O.count(probe))
+
+
+def test_inplace_insert_and_delete_alternating(gf, oracle):
+    """In-place inserts and deletes, alternating on one table, keep it equal to
+    the oracle's."""
+    q, r = 13, 8
+    keys = W.uniform_keys(2100, 6000)
+    O = oracle.GQF(q, r, seed=5)
+    G = gf.GQF(q, r, seed=5, max_batch=6000)
+    O.insert(keys[:4000])
+    G.insert(dev_u64(keys[:4000]))
+    for j in range(8):
+        ins = np.concatenate([keys[4000 + 200 * j:4000 + 200 * (j + 1)], keys[j * 30:(j + 1) * 30]])
+        dl = keys[1000 + 150 * j:1000 + 150 * (j + 1)]
+        for op, b in (("insert", ins), ("remove", dl)):
+            st_o = getattr(O, op)(b)
+            st = zeros_u8(len(b))
+            getattr(G, op)(dev_u64(b), st)
+            assert np.array_equal(host(st), st_o), (j, op)
+            assert first_diff(G.export(), O.export()) is None, (j, op)
