@@ -292,6 +292,8 @@ static constexpr int RS_I = 16;
 static constexpr int RS_TILE = RS_T * RS_I;
 static constexpr int RS_WARPS = RS_T / 32;
 static constexpr int RS_MAXB = 512;  // buckets of the widest digit
+static_assert(RS_MAXB == 2 * RS_T, "the scatter's scan gives each thread two digits");
+static_assert(RS_TILE < (1 << 16), "tile positions fit the 16-bit counters");
 
 size_t radix_tmp_words(uint64_t n)
 {
@@ -331,13 +333,16 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
     }
 }
 
-// Scatter of one pass. Keys are ranked inside each warp (match_any groups
-// equal digits; a per-warp 16-bit counter per digit carries the rank across
-// the warp's 16 rounds). A scan in shared memory turns the counters into one
-// tile position per (warp, digit), the keys are staged in digit order, and
-// the copy-out writes runs of consecutive addresses, taking each key's
-// global position from its digit's offset. Shared memory and registers are
-// sized for 3 CTAs per SM (2 with values).
+// Scatter of one pass. Keys are ranked inside each warp: a round's lanes
+// with equal digits are found with one ballot per digit bit, or with
+// match_any when the round is a single run of one digit (long runs of equal
+// keys, which the earlier passes of a skewed key set produce); a per-warp
+// 16-bit counter per digit carries the rank across the warp's 16 rounds. A
+// scan in shared memory, two digits per thread on packed counter pairs, turns
+// the counters into one tile position per (warp, digit), the keys are staged
+// in digit order, and the copy-out writes runs of consecutive addresses,
+// taking each key's global position from its digit's offset. Shared memory
+// and registers are sized for 3 CTAs per SM (2 with values).
 template <bool VALS>
 __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t *__restrict__ kin,
                                                                  uint64_t *__restrict__ kout,
@@ -354,7 +359,7 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
     __shared__ uint32_t s_w[RS_WARPS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB / 2; i += RS_T) reinterpret_cast<uint32_t *>(wcnt)[i] = 0;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB / 8; i += RS_T) reinterpret_cast<uint4 *>(wcnt)[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
 
     const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
@@ -375,7 +380,18 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         bool ok = i < n;
         uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & (nb - 1)) : 0xffffu;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned peers;
+        const uint32_t dprev = __shfl_up_sync(0xffffffffu, d, 1);
+        if (__ballot_sync(0xffffffffu, lane == 0 || d != dprev) == 1u) {
+            peers = __match_any_sync(0xffffffffu, d);  // one run: the cheap case of match_any
+        } else {
+            peers = __ballot_sync(0xffffffffu, ok);
+            if (!ok) peers = ~peers;
+            for (uint32_t bit = 0; (1u << bit) < nb; bit++) {
+                const unsigned m = __ballot_sync(0xffffffffu, (d >> bit) & 1u);
+                peers &= ((d >> bit) & 1u) ? m : ~m;
+            }
+        }
         uint32_t b = ok ? wcnt[warp * RS_MAXB + d] : 0;
         __syncwarp();
         if (ok && lane == __ffs(peers) - 1) wcnt[warp * RS_MAXB + d] = (uint16_t)(b + __popc(peers));
@@ -384,25 +400,16 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
     }
     __syncthreads();
     {
-        // per digit (two per thread): warp-exclusive offsets and tile totals,
-        // then an exclusive scan of the totals in digit order; finally every
+        // thread t owns digits 2t and 2t + 1, whose per-warp counters share one
+        // 32-bit word (counts stay below 2^16, so the halves add without carry):
+        // tile totals, an exclusive scan of them in digit order, then every
         // (warp, digit) counter becomes that warp's first tile position
-        uint32_t tot[2] = {0, 0};
+        uint32_t *wc32 = reinterpret_cast<uint32_t *>(wcnt);
+        uint32_t acc = 0;
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t d = 2 * threadIdx.x + h;
-            if (d < nb) {
-                uint32_t acc = 0;
-#pragma unroll
-                for (int w = 0; w < RS_WARPS; w++) {
-                    uint32_t c = wcnt[w * RS_MAXB + d];
-                    wcnt[w * RS_MAXB + d] = (uint16_t)acc;
-                    acc += c;
-                }
-                tot[h] = acc;
-            }
-        }
-        const uint32_t pair = tot[0] + tot[1];
+        for (int w = 0; w < RS_WARPS; w++) acc += wc32[w * (RS_MAXB / 2) + threadIdx.x];
+        const uint32_t t0 = acc & 0xffffu, t1 = acc >> 16;
+        const uint32_t pair = t0 + t1;
         uint32_t incl = pair;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -413,17 +420,17 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         __syncthreads();
         uint32_t wpre = 0;
         for (int w = 0; w < warp; w++) wpre += s_w[w];
-        const uint32_t ex = wpre + incl - pair;
+        const uint32_t st0 = wpre + incl - pair, st1 = st0 + t0;
+        uint32_t run = st0 | (st1 << 16);
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const uint32_t d = 2 * threadIdx.x + h;
-            const uint32_t st = h ? ex + tot[0] : ex;
-            if (d < nb) {
-                gdelta[d] = offs[(uint64_t)d * ntiles + blockIdx.x] - st;
-#pragma unroll
-                for (int w = 0; w < RS_WARPS; w++) wcnt[w * RS_MAXB + d] = (uint16_t)(wcnt[w * RS_MAXB + d] + st);
-            }
+        for (int w = 0; w < RS_WARPS; w++) {
+            const uint32_t c = wc32[w * (RS_MAXB / 2) + threadIdx.x];
+            wc32[w * (RS_MAXB / 2) + threadIdx.x] = run;
+            run += c;
         }
+        const uint32_t d0 = 2 * threadIdx.x;
+        if (d0 < nb) gdelta[d0] = offs[(uint64_t)d0 * ntiles + blockIdx.x] - st0;
+        if (d0 + 1 < nb) gdelta[d0 + 1] = offs[(uint64_t)(d0 + 1) * ntiles + blockIdx.x] - st1;
     }
     __syncthreads();
 #pragma unroll
@@ -536,10 +543,14 @@ struct TraceRec {
     const char *name;
     uint64_t units;
     cudaEvent_t a, b;
+    int dev_slot;  // >= 0: the units are the device counter g_units_dev[dev_slot]
 };
 static std::vector<TraceRec> g_trace;
 static std::vector<cudaEvent_t> g_event_pool;
 static std::mutex g_trace_mu;
+static constexpr int TRACE_DEV_SLOTS = 1 << 16;
+static unsigned long long *g_units_dev = nullptr;  // zeroed on enable and reset
+static int g_units_used = 0;
 
 static cudaEvent_t pool_event()
 {
@@ -553,14 +564,22 @@ static cudaEvent_t pool_event()
     return e;
 }
 
-int trace_open(const char *name, uint64_t units, cudaStream_t st)
+int trace_open(const char *name, uint64_t units, cudaStream_t st, bool dev_units)
 {
     std::lock_guard<std::mutex> g(g_trace_mu);
     if (g_trace.size() >= (1u << 20)) return -1;
-    TraceRec r{name, units, pool_event(), pool_event()};
+    TraceRec r{name, units, pool_event(), pool_event(), -1};
+    if (dev_units && g_units_dev && g_units_used < TRACE_DEV_SLOTS) r.dev_slot = g_units_used++;
     cudaEventRecord(r.a, st);
     g_trace.push_back(r);
     return (int)g_trace.size() - 1;
+}
+
+unsigned long long *trace_units(int slot)
+{
+    std::lock_guard<std::mutex> g(g_trace_mu);
+    if (slot < 0 || slot >= (int)g_trace.size() || g_trace[slot].dev_slot < 0) return nullptr;
+    return g_units_dev + g_trace[slot].dev_slot;
 }
 
 void trace_close(int slot, cudaStream_t st)
@@ -576,6 +595,8 @@ static void trace_clear_locked()
         g_event_pool.push_back(r.b);
     }
     g_trace.clear();
+    if (g_units_dev && g_units_used) cudaMemset(g_units_dev, 0, sizeof(unsigned long long) * g_units_used);
+    g_units_used = 0;
 }
 
 static char g_last_err[256];
@@ -593,6 +614,22 @@ extern "C" {
 
 int filter_trace_enable(int on)
 {
+    if (on) {
+        std::lock_guard<std::mutex> g(gf::g_trace_mu);
+        if (!gf::g_units_dev) {
+            void *p = nullptr;
+            if (cudaMalloc(&p, sizeof(unsigned long long) * gf::TRACE_DEV_SLOTS) != cudaSuccess) {
+                cudaGetLastError();
+                return FILTER_ERR_OOM;
+            }
+            if (cudaMemset(p, 0, sizeof(unsigned long long) * gf::TRACE_DEV_SLOTS) != cudaSuccess) {
+                cudaFree(p);
+                return FILTER_ERR_CUDA;
+            }
+            gf::g_units_dev = static_cast<unsigned long long *>(p);
+            gf::g_units_used = 0;
+        }
+    }
     gf::g_trace_on = on != 0;
     return FILTER_OK;
 }
@@ -609,8 +646,14 @@ int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kern
 {
     std::lock_guard<std::mutex> g(gf::g_trace_mu);
     std::vector<filter_trace_entry> acc;
-    for (auto &r : gf::g_trace) {
+    std::vector<unsigned long long> dev_units(gf::g_units_used);
+    for (auto &r : gf::g_trace)
         if (cudaEventSynchronize(r.b) != cudaSuccess) return FILTER_ERR_CUDA;
+    if (gf::g_units_used &&
+        cudaMemcpy(dev_units.data(), gf::g_units_dev, sizeof(unsigned long long) * gf::g_units_used,
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+        return FILTER_ERR_CUDA;
+    for (auto &r : gf::g_trace) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) return FILTER_ERR_CUDA;
         filter_trace_entry *e = nullptr;
@@ -624,7 +667,7 @@ int filter_trace_summary(uint32_t cap, filter_trace_entry *out, uint32_t *n_kern
             e = &acc.back();
         }
         e->launches++;
-        e->units += r.units;
+        e->units += r.dev_slot >= 0 ? dev_units[r.dev_slot] : r.units;
         e->ms += ms;
     }
     if (n_kernels) *n_kernels = (uint32_t)acc.size();
