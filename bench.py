@@ -54,10 +54,14 @@ BYTES_PER_UNIT = {
     "tcf_query_kernel": 73.0,    # key + two 32-byte blocks + found byte
     "tcf_group_hist": 8.0,       # key read
     "tcf_group_scatter": 16.0,   # key read + record write
-    "tcf_block_insert": 69.0,    # per block: offsets + fill + 32-byte block read and write
-    "tcf_block_remove": 69.0,
-    "tcf_bucket_insert": 132.0,  # per bucket: offsets + 64-byte bucket read and write
-    "tcf_bucket_remove": 132.0,
+    "tcf_group_hist_sparse": 12.0,     # per candidate (counted on the device): pending entry + key read
+    "tcf_group_scatter_sparse": 20.0,  # per candidate: pending entry + key read + record write
+    "tcf_alloc": 24.0,           # per touched destination: list + count read, offset + list + segment write
+    "tcf_block_insert": 74.0,    # per block with candidates (counted on the device): offsets + fill
+                                 # read and write + 32-byte block read and write (records not counted)
+    "tcf_block_remove": 74.0,
+    "tcf_bucket_insert": 136.0,  # per bucket with candidates: segment + 64-byte bucket read and write
+    "tcf_bucket_remove": 136.0,
     "tcf_point_insert": 104.0,
     "tcf_point_remove": 104.0,
     # filter groups

@@ -162,10 +162,13 @@ const char *filter_error_string(int code);
 /*
  * Kernel tracing (process-wide, off by default). While on, every kernel the
  * library launches is bracketed by two CUDA events on its stream and recorded
- * with its name and its work units (keys, slots or blocks, per kernel).
+ * with its name and its work units (keys, slots or blocks, per kernel; the
+ * sparse TCF phases count theirs on the device, in a 512 KB buffer that the
+ * first filter_trace_enable(1) allocates).
  * filter_trace_summary synchronises the recorded events and returns, per
  * kernel name, the launch count, the summed units and the summed device time
  * in milliseconds. Enabling costs two event records per launch.
+ * filter_trace_enable returns FILTER_ERR_OOM if that buffer cannot be allocated.
  */
 typedef struct filter_trace_entry {
     char name[48];

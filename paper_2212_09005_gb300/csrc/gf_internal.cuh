@@ -228,17 +228,21 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
                     DevCounters *ctr, cudaStream_t st);
 
 // Kernel tracing: a TraceScope around a launch records CUDA events before and
-// after it when tracing is on.
+// after it when tracing is on. Launches whose work is only known on the device
+// (the sparse phases) open the scope with dev_units and pass units() to the
+// kernel, which adds its work units there (a null pointer when not tracing).
 extern bool g_trace_on;
-int trace_open(const char *name, uint64_t units, cudaStream_t st);
+int trace_open(const char *name, uint64_t units, cudaStream_t st, bool dev_units);
 void trace_close(int slot, cudaStream_t st);
+unsigned long long *trace_units(int slot);
 struct TraceScope {
     int slot;
     cudaStream_t st;
-    TraceScope(const char *name, uint64_t units, cudaStream_t s) : slot(-1), st(s)
+    TraceScope(const char *name, uint64_t units, cudaStream_t s, bool dev_units = false) : slot(-1), st(s)
     {
-        if (g_trace_on) slot = trace_open(name, units, s);
+        if (g_trace_on) slot = trace_open(name, units, s, dev_units);
     }
+    unsigned long long *units() const { return slot >= 0 ? trace_units(slot) : nullptr; }
     ~TraceScope()
     {
         if (slot >= 0) trace_close(slot, st);

@@ -287,6 +287,13 @@ __device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t 
     }
 }
 
+// Traced launches whose work is only known on the device record it here
+// (units is null when tracing is off)
+__device__ __forceinline__ void note_units(unsigned long long *units, uint64_t v)
+{
+    if (units && blockIdx.x == 0 && threadIdx.x == 0) *units = v;
+}
+
 // A CTA's share of a sparse phase's candidates: one contiguous, warp-aligned
 // chunk (the touched destinations it finds are listed from the chunk's start)
 __device__ __forceinline__ void cta_chunk(uint64_t n, uint64_t &c0, uint64_t &c1)
@@ -304,9 +311,10 @@ template <int SRC, int DST, bool SPARSE>
 __global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict__ keys, const TcfPrep prep,
                                                       uint64_t n_keys, const void *pend, const unsigned *npend,
                                                       TcfGeom G, const uint8_t *fill, uint32_t *cnt,
-                                                      uint32_t *tlist, uint32_t *tcount)
+                                                      uint32_t *tlist, uint32_t *tcount, unsigned long long *units)
 {
     const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
+    note_units(units, n);
     __shared__ unsigned s_n;
     uint64_t c0 = 0, c1 = n, step = (uint64_t)gridDim.x * TPB, j = blockIdx.x * (uint64_t)TPB + threadIdx.x;
     if (SPARSE) {
@@ -344,7 +352,7 @@ __global__ void __launch_bounds__(TPB) tcf_alloc(const unsigned *npend, uint64_t
                                                  const uint32_t *__restrict__ tlist,
                                                  const uint32_t *__restrict__ tcount, const uint32_t *cnt,
                                                  uint32_t *off, uint32_t *dlist, uint64_t *seg, unsigned *cursor,
-                                                 unsigned *nlist)
+                                                 unsigned *nlist, unsigned long long *units)
 {
     __shared__ uint32_t s_w[TPB / 32];
     __shared__ uint32_t s_base, s_lbase;
@@ -352,6 +360,7 @@ __global__ void __launch_bounds__(TPB) tcf_alloc(const unsigned *npend, uint64_t
     uint64_t c0, c1;
     cta_chunk(n, c0, c1);
     const uint32_t m = tcount[blockIdx.x];
+    if (units && threadIdx.x == 0 && m) atomicAdd(units, (unsigned long long)m);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t j0 = 0; j0 < m; j0 += TPB) {
         const uint32_t j = j0 + threadIdx.x;
@@ -393,9 +402,10 @@ __global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restr
                                                          TcfGeom G,
                                                          const uint8_t *fill, uint32_t *cnt,
                                                          const uint32_t *__restrict__ off, uint64_t *rec,
-                                                         uint32_t *recI)
+                                                         uint32_t *recI, unsigned long long *units)
 {
     const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
+    note_units(units, n);
     for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TPB) {
         uint64_t pw = 0, i = j;
         if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[j];
@@ -473,17 +483,23 @@ template <int F>
 __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
                                                         const uint64_t *__restrict__ rec, int phase,
                                                         uint32_t cap, uint32_t *pend32, uint64_t *pend64,
-                                                        unsigned *npend, const TcfPrep prep)
+                                                        unsigned *npend, const TcfPrep prep,
+                                                        unsigned long long *units)
 {
     constexpr int B = Blk<F>::B;
     const uint64_t nd = phase_count(P, G.nb);
+    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
     const uint64_t stride = (uint64_t)gridDim.x * TPB;
     for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
         const uint64_t j = j0 + (threadIdx.x & 31);
         uint32_t s = 0, e = 0, k = 0;
         uint64_t b = 0, thr = 0;  // records <= thr are accepted
+        if (j < nd) b = phase_dst(P, j, s, e);
+        if (units && !P.dlist) {
+            const unsigned t = __ballot_sync(0xffffffffu, s != e);
+            if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
+        }
         if (j < nd) {
-            b = phase_dst(P, j, s, e);
             if (s != e) {
                 const uint32_t cnt = e - s;
                 const uint32_t f0 = fill[b];
@@ -540,9 +556,10 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
 __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk, PhaseDst P,
                                                          const uint64_t *__restrict__ rec,
                                                          const uint32_t *__restrict__ recI, uint8_t *status,
-                                                         DevCounters *ctr)
+                                                         DevCounters *ctr, unsigned long long *units)
 {
     const uint64_t nd = phase_count(P, G.nbk);
+    note_units(units, nd);  // units: buckets with candidates
     for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < nd; j += (uint64_t)gridDim.x * TPB) {
         uint32_t s, e;
         const uint64_t q = phase_dst(P, j, s, e);
@@ -613,10 +630,11 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk
 template <int F>
 __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
                                                         const uint64_t *__restrict__ rec, uint32_t *pend32,
-                                                        unsigned *npend)
+                                                        unsigned *npend, unsigned long long *units)
 {
     constexpr int B = Blk<F>::B;
     const uint64_t nd = phase_count(P, G.nb);
+    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
     const uint64_t stride = (uint64_t)gridDim.x * TPB;
     for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
         const uint64_t j = j0 + (threadIdx.x & 31);
@@ -628,8 +646,13 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
         uint32_t dt[B], dc[B], used[B];
         uint64_t thr[B];
         int ndt = 0;
+        uint64_t b = 0;
+        if (j < nd) b = phase_dst(P, j, s, e);
+        if (units && !P.dlist) {
+            const unsigned t = __ballot_sync(0xffffffffu, s != e);
+            if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
+        }
         if (j < nd) {
-            const uint64_t b = phase_dst(P, j, s, e);
             if (s != e) {
                 const uint32_t f0 = fill[b];
                 Blk<F> blk;
@@ -726,9 +749,10 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
 __global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk, PhaseDst P,
                                                          const uint64_t *__restrict__ rec,
                                                          const uint32_t *__restrict__ recI, uint8_t *status,
-                                                         DevCounters *ctr)
+                                                         DevCounters *ctr, unsigned long long *units)
 {
     const uint64_t nd = phase_count(P, G.nbk);
+    note_units(units, nd);  // units: buckets with candidates
     for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < nd; j += (uint64_t)gridDim.x * TPB) {
         uint32_t s, e;
         const uint64_t q = phase_dst(P, j, s, e);
@@ -1044,14 +1068,14 @@ static PhaseDst group_phase(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     const uint64_t ndst = (DST == DST_BUCKET ? G.nbk : G.nb);
     PhaseDst P{nullptr, nullptr, nullptr, nullptr};
     {
-        gf::TraceScope ts_("tcf_group_hist", n, st);
+        gf::TraceScope ts_(SPARSE ? "tcf_group_hist_sparse" : "tcf_group_hist", n, st, SPARSE);
         tcf_group_hist<SRC, DST, SPARSE><<<gk, TPB, 0, st>>>(keys, T.prep, n, pend, npend, G, T.fill, T.cnt, T.tlist,
-                                                             T.tcount);
+                                                             T.tcount, ts_.units());
     }
     if (SPARSE) {
-        gf::TraceScope ts_("tcf_alloc", n, st);
+        gf::TraceScope ts_("tcf_alloc", 0, st, true);
         tcf_alloc<<<gk, TPB, 0, st>>>(npend, n, T.tlist, T.tcount, T.cnt, T.off, T.dlist, T.seg, &T.ctr->cursor[slot],
-                                      &T.ctr->touched[slot]);
+                                      &T.ctr->touched[slot], ts_.units());
         P.dlist = T.dlist;
         P.seg = T.seg;
         P.nlist = &T.ctr->touched[slot];
@@ -1060,9 +1084,9 @@ static PhaseDst group_phase(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
         P.off = T.off;
     }
     {
-        gf::TraceScope ts_("tcf_group_scatter", n, st);
+        gf::TraceScope ts_(SPARSE ? "tcf_group_scatter_sparse" : "tcf_group_scatter", n, st, SPARSE);
         tcf_group_scatter<SRC, DST><<<gk, TPB, 0, st>>>(keys, T.prep, n, pend, npend, G, T.fill, T.cnt, T.off, T.rec,
-                                                        recI);
+                                                        recI, ts_.units());
     }
     return P;
 }
@@ -1085,29 +1109,29 @@ static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     // A: shortcut into b1
     PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_insert", G.nb, st);
+        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
         tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc, T.pend0,
-                                                                   nullptr, &np[0], T.prep);
+                                                                   nullptr, &np[0], T.prep, ts_.units());
     }
     // B: the less full of b1, b2 under the post-A fills
     P = group_phase<SRC_PEND_U32, DST_TARGET>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_insert", G.nb, st);
+        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
         tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
-                                                                   T.pend1, &np[1], T.prep);
+                                                                   T.pend1, &np[1], T.prep, ts_.units());
     }
     // C: the other block
     P = group_phase<SRC_PEND_U64, DST_ALT>(T, keys, n, T.pend1, &np[1], 2, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_insert", G.nb, st);
+        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
         tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
-                                                                   nullptr, &np[2], T.prep);
+                                                                   nullptr, &np[2], T.prep, ts_.units());
     }
     // D: backing buckets
     P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
     {
-        gf::TraceScope ts_("tcf_bucket_insert", G.nbk, st);
-        tcf_bucket_insert<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr);
+        gf::TraceScope ts_("tcf_bucket_insert", 0, st, true);
+        tcf_bucket_insert<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr, ts_.units());
     }
 }
 
@@ -1122,20 +1146,20 @@ static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     // 1: primary block
     PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_remove", G.nb, st);
-        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0]);
+        gf::TraceScope ts_("tcf_block_remove", 0, st, true);
+        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0], ts_.units());
     }
     // 2: secondary block
     P = group_phase<SRC_PEND_U32, DST_B2>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_remove", G.nb, st);
-        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2]);
+        gf::TraceScope ts_("tcf_block_remove", 0, st, true);
+        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2], ts_.units());
     }
     // 3: backing bucket; what is left is not found
     P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
     {
-        gf::TraceScope ts_("tcf_bucket_remove", G.nbk, st);
-        tcf_bucket_remove<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr);
+        gf::TraceScope ts_("tcf_bucket_remove", 0, st, true);
+        tcf_bucket_remove<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr, ts_.units());
     }
 }
 
