@@ -8,11 +8,11 @@
  * default stream). All calls except filter_create, filter_destroy,
  * filter_get_stats, filter_export and filter_import are asynchronous: they
  * enqueue kernels on the stream and return; the caller's buffers must stay
- * valid until the stream reaches the call. Exceptions: a GQF insert
- * synchronises the stream once to read whether the table overflowed, and a
- * GQF remove once to read the number of distinct fingerprints (which picks
- * the in-place or the merge path). Calls on one filter must be ordered (same
- * stream, or externally synchronised); different filters are independent.
+ * valid until the stream reaches the call. Exceptions: GQF inserts and
+ * removes synchronise the stream to read the number of distinct fingerprints
+ * (which picks the in-place or the merge path) and, after a merge, whether
+ * the table overflowed. Calls on one filter must be ordered (same stream, or
+ * externally synchronised); different filters are independent.
  *
  * Errors are returned synchronously for bad arguments, allocation failure
  * and unsupported operations. Conditions found on the device (a full table,

@@ -192,6 +192,56 @@ def test_counting_config_2_28_zipf(gf, oracle):
     assert d is None, d
     del G
     torch.cuda.empty_cache()
+    # the same batch without statuses (no sorted indices)
+    G2 = gf.GQF(28, 8, seed=3, max_batch=len(keys))
+    G2.insert(dev_u64(keys))
+    d = first_diff(G2.export(), img)
+    assert d is None, d
+    del G2
+    torch.cuda.empty_cache()
+
+
+def _no_status_rounds(gf, oracle, q, r, seed, rounds):
+    """Inserts and removes without per-key statuses (the benchmark's calls:
+    no sorted indices travel with the fingerprints); the image must equal the
+    oracle's after every call."""
+    O = oracle.GQF(q, r, seed=seed)
+    G = gf.GQF(q, r, seed=seed, max_batch=max(len(b) for _, b in rounds))
+    for op, b in rounds:
+        if op == "ins":
+            O.insert(b)
+            G.insert(dev_u64(b))
+        else:
+            O.remove(b)
+            G.remove(dev_u64(b))
+        d = first_diff(G.export(), O.export())
+        assert d is None, (op, len(b), d)
+    return O, G
+
+
+def test_no_status_zipf_batches_match_oracle(gf, oracle):
+    """Skewed batches of about 2^20 keys without statuses: heavy keys repeat
+    thousands of times inside one sort tile and across tiles; a ragged length,
+    then a remove of a skewed batch."""
+    q = 22
+    keys = W.zipf_keys(31, (1 << 20) + 77, 1.0, 1 << 24)
+    more = W.zipf_keys(32, (1 << 20) + 4096, 1.2, 1 << 24)
+    dele = np.concatenate([keys[: 1 << 19], more[: (1 << 19) + 5]])
+    O, G = _no_status_rounds(gf, oracle, q, 8, 31, [("ins", keys), ("ins", more), ("rem", dele)])
+    u, c = np.unique(np.concatenate([keys, more]), return_counts=True)
+    probe = u[::97]
+    got = zeros_u64(len(probe))
+    G.count(dev_u64(probe), got)
+    assert np.array_equal(host(got), O.count(probe))
+
+
+def test_no_status_extremes_match_oracle(gf, oracle):
+    """Exactly 2^20 keys of one value (one group of 2^20 copies), 2^20
+    distinct keys, and 16-bit remainders."""
+    same = np.full(1 << 20, 12345, np.uint64)
+    distinct = W.uniform_keys(33, 1 << 20)
+    _no_status_rounds(gf, oracle, 22, 8, 7, [("ins", same), ("ins", distinct), ("rem", same[: (1 << 20) - 1])])
+    _no_status_rounds(gf, oracle, 21, 16, 8, [("ins", W.zipf_keys(34, (1 << 20) + 1, 1.0, 1 << 22))])
 
 
 def test_inplace_delete_matches_oracle(gf, oracle):
