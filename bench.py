@@ -48,7 +48,8 @@ BYTES_PER_UNIT = {
     "scan_kernel": 8.0,          # u32 read + write
     "gqf_fp_kernel": 16.0,       # key read + fingerprint write
     "rle_kernel": 8.0,           # sorted fingerprint read (group writes not counted)
-    "gqf_merge_kernel": 3.0,     # per slot: old table read + new table write (r = 8: 1.5 B/slot each)
+    "gqf_merge_kernel": 1.0,     # unit = algorithmic byte, counted on the device: old table read + new
+                                 # table write (r / 8 + 1 / 2 B per slot each) + 12 B per group read
     "gqf_count_kernel": 80.0,    # key + metadata sector + remainder sector + count
     "gqf_status_kernel": 13.0,
     "tcf_query_kernel": 73.0,    # key + two 32-byte blocks + found byte
@@ -60,6 +61,8 @@ BYTES_PER_UNIT = {
     "tcf_block_insert": 74.0,    # per block with candidates (counted on the device): offsets + fill
                                  # read and write + 32-byte block read and write (records not counted)
     "tcf_block_remove": 74.0,
+    "tcf_block_insert_sparse": 74.0,
+    "tcf_block_remove_sparse": 74.0,
     "tcf_bucket_insert": 136.0,  # per bucket with candidates: segment + 64-byte bucket read and write
     "tcf_bucket_remove": 136.0,
     "tcf_point_insert": 104.0,
@@ -68,7 +71,7 @@ BYTES_PER_UNIT = {
     "tcf_group_prep": 32.0,            # key read + 24-byte prepared key write
     "tcf_group_query_kernel": 73.0,
     "gqf_group_fp_kernel": 16.0,
-    "gqf_merge_group_kernel": 3.0,
+    "gqf_merge_group_kernel": 1.0,
     "gqf_group_count_kernel": 73.0,    # key + metadata sector + remainder sector + found byte
 }
 

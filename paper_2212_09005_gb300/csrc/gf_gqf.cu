@@ -32,6 +32,7 @@ static constexpr int TQ = MT * QPT;     // quotients per tile
 static constexpr int TBLK = TQ / 64;    // blocks per tile
 static constexpr int OLDBUF = 3072;     // staged old slots
 static constexpr int OUTBUF = 3072;     // staged new slots
+static constexpr int MERGE_CTAS = 5;    // resident merge CTAs per SM
 static constexpr int RWORDS = OUTBUF / 64 + 2;
 static constexpr long long NEG_INF = -(1ll << 60);
 
@@ -460,7 +461,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
         xA = pA;
         xB = pB;
     }
-    // 8. decoupled look-back over tiles, CTA-wide: 256 predecessors per round.
+    // 8. decoupled look-back over tiles, CTA-wide: MT predecessors per round.
     // One status word per tile: bits 62-63 flag (1 aggregate, 2 inclusive end);
     // aggregate payload (A - Q0 + 1) << 31 | B, with 0 in the A field for a tile
     // without runs; inclusive payload P + 1. A tile whose aggregate does not fit
@@ -683,13 +684,26 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
 
 // Tiles are taken from a counter in launch order, so every tile a look-back
 // waits on has already been scheduled.
+// Traced launches record their algorithmic bytes on the device: the old
+// table read and the new one written (r / 8 + 1 / 2 bytes per slot each) and
+// 12 bytes (fingerprint and start) per group read.
 template <int R>
-__global__ void __launch_bounds__(MT, 5) gqf_merge_kernel(MergeArgs a)
+__device__ __forceinline__ void merge_units(unsigned long long *units, uint64_t slots, uint64_t groups)
+{
+    *units = (unsigned long long)(slots * (2 * R / 8 + 1) + 12 * groups);
+}
+
+template <int R>
+__global__ void __launch_bounds__(MT, MERGE_CTAS) gqf_merge_kernel(MergeArgs a, unsigned long long *units)
 {
     __shared__ MergeSmem<R> S;
     if (threadIdx.x == 0) {
         S.tile = (unsigned)atomicAdd(&a.ts[0], 1ull);
         S.err = 0;
+        if (units && S.tile == 0) {
+            const uint64_t m = *a.pm;
+            merge_units<R>(units, a.nslots, m < a.m_limit ? m : a.m_limit);
+        }
     }
     __syncthreads();
     merge_tile<R>(a, S, S.tile);
@@ -699,15 +713,17 @@ __global__ void __launch_bounds__(MT, 5) gqf_merge_kernel(MergeArgs a)
 // member m's arguments with `ts` and `tlo` already offset to its first tile,
 // so the look-back of a member's tile stops at that member's first tile.
 template <int R>
-__global__ void __launch_bounds__(MT, 5) gqf_merge_group_kernel(const MergeArgs *__restrict__ tab,
+__global__ void __launch_bounds__(MT, MERGE_CTAS) gqf_merge_group_kernel(const MergeArgs *__restrict__ tab,
                                                              const uint32_t *__restrict__ tile_member,
-                                                             unsigned long long *tctr)
+                                                             unsigned long long *tctr, uint64_t slots,
+                                                             const uint32_t *pm, unsigned long long *units)
 {
     __shared__ MergeSmem<R> S;
     __shared__ MergeArgs A;
     if (threadIdx.x == 0) {
         S.tile = (unsigned)atomicAdd(tctr, 1ull);
         S.err = 0;
+        if (units && S.tile == 0) merge_units<R>(units, slots, *pm);
     }
     __syncthreads();
     static_assert(sizeof(MergeArgs) % 8 == 0, "MergeArgs copies as 64-bit words");
@@ -1558,9 +1574,9 @@ static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, 
                                                                        Q.ntiles, Q.tile_lo);
     }
     {
-        gf::TraceScope ts_("gqf_merge_kernel", Q.nslots, st);
-        if (Q.r == 8) gqf_merge_kernel<8><<<(unsigned)Q.ntiles, MT, 0, st>>>(a);
-        else gqf_merge_kernel<16><<<(unsigned)Q.ntiles, MT, 0, st>>>(a);
+        gf::TraceScope ts_("gqf_merge_kernel", 0, st, true);
+        if (Q.r == 8) gqf_merge_kernel<8><<<(unsigned)Q.ntiles, MT, 0, st>>>(a, ts_.units());
+        else gqf_merge_kernel<16><<<(unsigned)Q.ntiles, MT, 0, st>>>(a, ts_.units());
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -2088,11 +2104,13 @@ static int group_merge(filter_group *GR, uint64_t n, int del, cudaStream_t st)
     }
     const MergeArgs *tab = static_cast<const MergeArgs *>(GR->d_margs) + (uint64_t)(GR->cur * 2 + del) * GR->n;
     {
-        gf::TraceScope ts_("gqf_merge_group_kernel", Q.nslots, st);
+        gf::TraceScope ts_("gqf_merge_group_kernel", 0, st, true);
         if (Q.r == 8)
-            gqf_merge_group_kernel<8><<<(unsigned)GR->tiles, MT, 0, st>>>(tab, GR->d_tile_member, Q.tile_state);
+            gqf_merge_group_kernel<8><<<(unsigned)GR->tiles, MT, 0, st>>>(tab, GR->d_tile_member, Q.tile_state,
+                                                                          Q.nslots, Q.flags + n, ts_.units());
         else
-            gqf_merge_group_kernel<16><<<(unsigned)GR->tiles, MT, 0, st>>>(tab, GR->d_tile_member, Q.tile_state);
+            gqf_merge_group_kernel<16><<<(unsigned)GR->tiles, MT, 0, st>>>(tab, GR->d_tile_member, Q.tile_state,
+                                                                           Q.nslots, Q.flags + n, ts_.units());
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;

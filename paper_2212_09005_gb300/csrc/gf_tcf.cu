@@ -154,6 +154,58 @@ struct Blk {
 #pragma unroll
         for (int k = 0; k < 8; k++) w[k] = nw[k];
     }
+    // Merge k new tags (the high words of r[0 .. k), ascending) into the f0
+    // sorted tags of the block (f0 + k <= B, k <= 8) with a bitonic merge on
+    // packed lanes: empty lanes become the largest tag value, the new tags go
+    // descending into the top lanes, and log2(B) half-cleaner stages of SIMD
+    // min / max sort the lanes ascending; lanes from f0 + k on are cleared.
+    // Equal tags are indistinguishable, so the result equals the stable merge.
+    __device__ __forceinline__ void merge_new(uint32_t f0, uint32_t k, const uint64_t (&r)[8])
+    {
+#pragma unroll
+        for (int q = 0; q < 8; q++) w[q] |= ~low_bits(q, (int)(f0 * F));
+#pragma unroll
+        for (int m = 0; m < 8; m++) {
+            if (m < (int)k) {
+                constexpr int LPW = 32 / F;  // lanes per word
+                const int L = B - 1 - m;
+                const int sh = (L % LPW) * F;
+                const uint32_t lane_mask = (F == 16 ? 0xffffu : 0xffu) << sh;
+                w[L / LPW] = (w[L / LPW] & ~lane_mask) | ((uint32_t)(r[m] >> 32) << sh);
+            }
+        }
+        // word-level half-cleaners: distances of 4, 2 and 1 words
+#pragma unroll
+        for (int dw = 4; dw >= 1; dw >>= 1) {
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                if ((q & dw) == 0) {
+                    const uint32_t a = w[q], c = w[q + dw];
+                    w[q] = F == 16 ? __vminu2(a, c) : __vminu4(a, c);
+                    w[q + dw] = F == 16 ? __vmaxu2(a, c) : __vmaxu4(a, c);
+                }
+            }
+        }
+        // lane-level half-cleaners inside each word
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            uint32_t x = w[q];
+            if (F == 8) {  // lanes two apart: swap the 16-bit halves
+                const uint32_t y = __byte_perm(x, 0u, 0x1032u);
+                x = __byte_perm(__vminu4(x, y), __vmaxu4(x, y), 0x7610u);
+            }
+            if (F == 16) {  // lanes one apart: the two halves
+                const uint32_t y = __byte_perm(x, 0u, 0x1032u);
+                x = __byte_perm(__vminu2(x, y), __vmaxu2(x, y), 0x7610u);
+            } else {        // lanes one apart: bytes 0/1 and 2/3
+                const uint32_t y = __byte_perm(x, 0u, 0x2301u);
+                x = __byte_perm(__vminu4(x, y), __vmaxu4(x, y), 0x7250u);
+            }
+            w[q] = x;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) w[q] &= low_bits(q, (int)((f0 + k) * F));
+    }
     // pack B tags (ascending, zero padded) from an array
     __device__ __forceinline__ void pack(const uint32_t *t)
     {
@@ -168,8 +220,8 @@ struct Blk {
 
 // sort up to 8 records held in registers (absent ones are ~0 and sort last):
 // a 19-comparator network of depth 6, or 5 comparators for the first 4
-// when no lane of the warp has more; r8[0] is consumed by shifting the rest
-// down, which keeps the array in registers
+// when no lane of the warp has more; callers index the array only in
+// unrolled loops, which keeps it in registers
 __device__ __forceinline__ void cswap(uint64_t &a, uint64_t &b)
 {
     const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
@@ -190,12 +242,6 @@ __device__ __forceinline__ void sort8(uint64_t (&r)[8])
     cswap(r[2], r[4]); cswap(r[3], r[5]);
     cswap(r[1], r[4]); cswap(r[3], r[6]);
     cswap(r[1], r[2]); cswap(r[3], r[4]); cswap(r[5], r[6]);
-}
-__device__ __forceinline__ void shift_down(uint64_t (&r)[8])
-{
-#pragma unroll
-    for (int q = 0; q < 7; q++) r[q] = r[q + 1];
-    r[7] = ~0ull;
 }
 __device__ __forceinline__ void sort_small(uint64_t (&r)[8], uint32_t cnt)
 {
@@ -504,13 +550,28 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
                 const uint32_t cnt = e - s;
                 const uint32_t f0 = fill[b];
                 k = cap > f0 ? min(cnt, cap - f0) : 0u;
-                if (k > 0) {
+                if (k > 0 && cnt <= 8) {
+                    // few candidates: all loads in flight at once, a sorting
+                    // network in registers, a bitonic merge into the block
+                    Blk<F> blk;
+                    blk.load(blocks, b);
+                    uint64_t r8[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) r8[q] = q < (int)cnt ? rec[s + q] : ~0ull;
+                    sort_small(r8, cnt);
+#pragma unroll
+                    for (int q = 0; q < 8; q++)
+                        if (q == (int)k - 1) thr = r8[q];
+                    blk.merge_new(f0, k, r8);
+                    blk.store(blocks, b);
+                    fill[b] = (uint8_t)(f0 + k);
+                } else if (k > 0) {
+                    Blk<F> blk;
+                    blk.load(blocks, b);
                     uint64_t a[MAXSEL];
                     int have = 0;
                     for (uint32_t q = s; q < e; q++) have = topk_push(a, have, (int)k, rec[q]);
                     thr = a[k - 1];
-                    Blk<F> blk;
-                    blk.load(blocks, b);
                     uint32_t t_out[B];
                     int ia = 0, ib = 0;
 #pragma unroll
@@ -666,19 +727,18 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
 #pragma unroll
                     for (int q = 0; q < 8; q++) r8[q] = (uint32_t)q < c ? rec[s + q] : ~0ull;
                     sort_small(r8, c);
-                    uint64_t w8[8];
 #pragma unroll
-                    for (int q = 0; q < 8; q++) w8[q] = r8[q];
-                    for (uint32_t q = 0; q < c; q++) {
-                        const uint32_t sm = blk.eq_slots((uint32_t)(w8[0] >> 32));
-                        if (sm) {
-                            blk.delete_at(__ffs(sm) - 1);
-                            removed++;
-                        } else {
-                            unm |= 1u << q;
-                            nunm++;
+                    for (int q = 0; q < 8; q++) {
+                        if ((uint32_t)q < c) {
+                            const uint32_t sm = blk.eq_slots((uint32_t)(r8[q] >> 32));
+                            if (sm) {
+                                blk.delete_at(__ffs(sm) - 1);
+                                removed++;
+                            } else {
+                                unm |= 1u << q;
+                                nunm++;
+                            }
                         }
-                        shift_down(w8);
                     }
                     if (removed) {
                         blk.store(blocks, b);
@@ -729,10 +789,9 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
         uint32_t slot = warp_reserve(npend, nunm);
         if (nunm == 0) continue;
         if (fast) {
-            for (uint32_t q = 0; q < e - s; q++) {
-                if ((unm >> q) & 1u) pend32[slot++] = (uint32_t)r8[0];
-                shift_down(r8);
-            }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if ((unm >> q) & 1u) pend32[slot++] = (uint32_t)r8[q];
         } else {
             for (uint32_t q = s; q < e; q++) {
                 const uint64_t r = rec[q];
@@ -1116,14 +1175,14 @@ static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     // B: the less full of b1, b2 under the post-A fills
     P = group_phase<SRC_PEND_U32, DST_TARGET>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
+        gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
         tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
                                                                    T.pend1, &np[1], T.prep, ts_.units());
     }
     // C: the other block
     P = group_phase<SRC_PEND_U64, DST_ALT>(T, keys, n, T.pend1, &np[1], 2, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
+        gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
         tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
                                                                    nullptr, &np[2], T.prep, ts_.units());
     }
@@ -1152,7 +1211,7 @@ static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     // 2: secondary block
     P = group_phase<SRC_PEND_U32, DST_B2>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
-        gf::TraceScope ts_("tcf_block_remove", 0, st, true);
+        gf::TraceScope ts_("tcf_block_remove_sparse", 0, st, true);
         tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2], ts_.units());
     }
     // 3: backing bucket; what is left is not found
