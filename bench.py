@@ -364,7 +364,7 @@ def run_ours(args, rank, world, device_index):
         "config": {"workload": WORKLOAD if args.case == "full" else PROFILE_WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "random_gather": gather, "kernels": kern[:16], "checks": checks, "batched": batched,
+        "cpu_baseline": cpu, "random_gather": gather, "kernels": kern, "checks": checks, "batched": batched,
     }
     return line
 
@@ -524,7 +524,7 @@ def run_batched(args, device):
     out = {"workload": BATCHED_WORKLOAD, "value": round(aggregate_rate(R.ops, args.steps, 1, ms), 4), "unit": UNIT,
            "ms_per_step": round(ms / args.steps, 3), "ops_per_step": R.ops,
            "gpu_launches": sum(v["launches"] for v in trace.values()), "roofline": roof,
-           "random_gather": gather, "kernels": kern[:12], "checks": R.checks()}
+           "random_gather": gather, "kernels": kern, "checks": R.checks()}
     del R
     torch.cuda.empty_cache()
     return out

@@ -43,6 +43,7 @@ int grid_for(uint64_t work, int threads, int per_sm)
 static constexpr int SCAN_T = 256;
 static constexpr int SCAN_I = 16;
 static constexpr uint64_t SCAN_TILE = SCAN_T * SCAN_I;
+static_assert(SCAN_TILE <= 65536, "positions inside a tile fit 16 bits");
 
 size_t scan_tmp_words(uint64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 2; }
 
@@ -187,7 +188,9 @@ __global__ void __launch_bounds__(SCAN_T) rle_kernel(const uint64_t *__restrict_
 {
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_warp[SCAN_T / 32];
-    __shared__ uint32_t s_prefix;
+    __shared__ uint32_t s_prefix, s_total;
+    __shared__ uint64_t s_key[SCAN_TILE];  // the tile's groups in order: first key,
+    __shared__ uint16_t s_pos[SCAN_TILE];  // and start within the tile
     if (threadIdx.x == 0) s_tile = (uint32_t)atomicAdd(&tmp[0], 1ull);
     __syncthreads();
     const uint64_t tile = s_tile;
@@ -233,23 +236,34 @@ __global__ void __launch_bounds__(SCAN_T) rle_kernel(const uint64_t *__restrict_
         if (lane < SCAN_T / 32) s_warp[lane] = wi - w;
         const uint32_t total = __shfl_sync(0xffffffffu, wi, SCAN_T / 32 - 1);
         const uint32_t prefix = lookback_prefix(tmp + 1, tile, total, status);
-        if (lane == 0) s_prefix = prefix;
+        if (lane == 0) {
+            s_prefix = prefix;
+            s_total = total;
+        }
     }
     __syncthreads();
-    uint32_t g = s_prefix + s_warp[warp] + (incl - sum);  // runs started before this thread's elements
+    // groups are staged in shared memory in order, then written as whole lines
+    uint32_t lg = s_warp[warp] + (incl - sum);  // the tile's runs started before this thread's elements
+    const uint32_t g0 = s_prefix;
     uint32_t rv[SCAN_I];
 #pragma unroll
     for (int q = 0; q < SCAN_I; q++) {
         if ((starts >> q) & 1u) {
-            uniq[g] = k[q];
-            start[g] = (uint32_t)(base + q);
-            g++;
+            s_key[lg] = k[q];
+            s_pos[lg] = (uint16_t)(threadIdx.x * SCAN_I + q);
+            lg++;
         }
-        rv[q] = g - 1;
+        rv[q] = g0 + lg - 1;
         if (base + q == n - 1) {
-            *m_out = g;
-            start[g] = (uint32_t)n;
+            *m_out = g0 + lg;
+            start[g0 + lg] = (uint32_t)n;
         }
+    }
+    __syncthreads();
+    const uint32_t tot = s_total;
+    for (uint32_t x = threadIdx.x; x < tot; x += SCAN_T) {
+        uniq[g0 + x] = s_key[x];
+        start[g0 + x] = (uint32_t)(tile * SCAN_TILE) + s_pos[x];
     }
     if (run_of) {
         if (base + SCAN_I <= n) {
