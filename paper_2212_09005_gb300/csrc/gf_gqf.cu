@@ -55,17 +55,6 @@ __host__ __device__ __forceinline__ uint32_t ndig(uint64_t v, uint32_t r)
 __host__ __device__ __forceinline__ uint32_t enc_len(uint64_t c, uint32_t r) { return c == 1 ? 1u : 3u + ndig(c - 2, r); }
 
 // ---------------------------------------------------------------------------
-// fingerprints
-// ---------------------------------------------------------------------------
-__global__ void gqf_fp_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H, uint64_t *fp, uint32_t *idx)
-{
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        fp[i] = fingerprint(keys[i], H);
-        if (idx) idx[i] = (uint32_t)i;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // The merge kernel
 // ---------------------------------------------------------------------------
 struct MergeArgs {
@@ -1527,12 +1516,9 @@ static void gqf_prepare(filter *F, const uint64_t *keys, uint64_t n, bool need_i
                         uint32_t **sorted_idx)
 {
     GqfState &Q = F->gqf;
-    {
-        gf::TraceScope ts_("gqf_fp_kernel", n, st);
-        gqf_fp_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(keys, n, Q.H, Q.fp_a, need_idx ? Q.idx_a : nullptr);
-    }
+    fingerprint_for_sort(keys, n, Q.H, Q.fp_a, need_idx ? Q.idx_a : nullptr, Q.p, Q.radix_tmp, st);
     radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp,
-                   F->scan_tmp, F->ctr, st);
+                   F->scan_tmp, F->ctr, st, true);
     // groups: flags[n] = their number; flags[i] = the group of sorted element i (statuses only)
     rle_sorted_u64(Q.fp_b, n, Q.ufp, Q.ustart, need_idx ? Q.flags : nullptr, Q.flags + n, F->scan_tmp, F->ctr, st);
     *sorted_idx = Q.idx_b;

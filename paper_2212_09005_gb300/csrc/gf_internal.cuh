@@ -222,10 +222,17 @@ void rle_sorted_u64(const uint64_t *keys, uint64_t n, uint64_t *uniq, uint32_t *
 // LSD radix sort of 64-bit keys on bits [0, bits), optional 32-bit values.
 // Result lands in keys_out / vals_out. `tmp` holds radix_tmp_words(n) words.
 size_t radix_tmp_words(uint64_t n);
+// first_hist_done: tmp already holds the first pass's per-tile histogram
+// (from fingerprint_for_sort)
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt,
                     uint64_t n, uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp,
-                    DevCounters *ctr, cudaStream_t st);
+                    DevCounters *ctr, cudaStream_t st, bool first_hist_done = false);
+// fp[i] = fingerprint(keys[i], H) (idx[i] = i when idx is set), with the
+// per-tile histogram of the lowest digit that radix_sort_u64(.., bits, tmp)
+// takes for its first pass
+void fingerprint_for_sort(const uint64_t *keys, uint64_t n, const PHash &H, uint64_t *fp, uint32_t *idx,
+                          uint32_t bits, uint32_t *tmp, cudaStream_t st);
 
 // Kernel tracing: a TraceScope around a launch records CUDA events before and
 // after it when tracing is on. Launches whose work is only known on the device

@@ -347,6 +347,44 @@ __global__ void __launch_bounds__(RS_T) rs_hist(const uint64_t *__restrict__ key
     }
 }
 
+// The same first-pass histogram fused with the fingerprinting that feeds
+// the sort: keys are hashed (H), the fingerprints written (with their batch
+// indices when wanted) and counted by their lowest digit, so that the sort's
+// first pass needs no histogram pass of its own.
+__global__ void __launch_bounds__(RS_T) rs_fp_hist(const uint64_t *__restrict__ keys, uint64_t n, PHash H,
+                                                   uint64_t *__restrict__ fp, uint32_t *__restrict__ idx, uint32_t nb,
+                                                   uint32_t *counts, uint64_t ntiles)
+{
+    __shared__ uint32_t h[RS_WARPS][RS_MAXB];
+    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXB; i += RS_T) (&h[0][0])[i] = 0;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+    uint64_t k[RS_I];
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
+        k[r] = (i < n) ? __ldcs(keys + i) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_I; r++) {
+        uint64_t i = base + (uint64_t)r * RS_T + threadIdx.x;
+        if (i < n) {
+            const uint64_t f = fingerprint(k[r], H);
+            fp[i] = f;
+            if (idx) idx[i] = (uint32_t)i;
+            atomicAdd(&h[warp][(uint32_t)f & (nb - 1)], 1u);
+        }
+    }
+    __syncthreads();
+    for (uint32_t d = threadIdx.x; d < nb; d += RS_T) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; w++) c += h[w][d];
+        counts[(uint64_t)d * ntiles + blockIdx.x] = c;
+    }
+}
+
 // Scatter of one pass. Keys are ranked inside each warp: a round's lanes
 // with equal digits are found with one ballot per digit bit, or with
 // match_any when the round is a single run of one digit (long runs of equal
@@ -477,10 +515,26 @@ static constexpr size_t rs_smem()
     return RS_TILE * 8 + (VALS ? RS_TILE * 4 : 0) + RS_MAXB * 4 + RS_WARPS * RS_MAXB * 2;
 }
 
+static uint32_t first_digit_bits(uint32_t bits)
+{
+    const uint32_t npass = (bits + 8) / 9;
+    return npass ? bits / npass + (bits % npass ? 1u : 0u) : 0u;
+}
+
+void fingerprint_for_sort(const uint64_t *keys, uint64_t n, const PHash &H, uint64_t *fp, uint32_t *idx,
+                          uint32_t bits, uint32_t *tmp, cudaStream_t st)
+{
+    if (n == 0) return;
+    const uint32_t db = first_digit_bits(bits);
+    const uint64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
+    TraceScope ts_("rs_fp_hist", n, st);
+    rs_fp_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(keys, n, H, fp, idx, 1u << db, tmp, ntiles);
+}
+
 void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_alt,
                     const uint32_t *vals_in, uint32_t *vals_out, uint32_t *vals_alt, uint64_t n,
                     uint32_t bits, uint32_t *tmp, uint64_t *scan_tmp, DevCounters *ctr,
-                    cudaStream_t st)
+                    cudaStream_t st, bool first_hist_done)
 {
     if (n == 0) return;
     static bool attr_done = false;
@@ -507,7 +561,7 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         bool to_out = ((npass - 1 - p) % 2) == 0;
         uint64_t *kdst = to_out ? keys_out : keys_alt;
         uint32_t *vdst = to_out ? vals_out : vals_alt;
-        {
+        if (p > 0 || !first_hist_done) {
             TraceScope ts_("rs_hist", n, st);
             rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ksrc, n, shift, nb, tmp, ntiles);
         }
