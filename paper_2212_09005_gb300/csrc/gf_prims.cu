@@ -395,7 +395,7 @@ __global__ void __launch_bounds__(RS_T) rs_fp_hist(const uint64_t *__restrict__ 
 // in digit order, and the copy-out writes runs of consecutive addresses,
 // taking each key's global position from its digit's offset. Shared memory
 // and registers are sized for 3 CTAs per SM (2 with values).
-template <bool VALS>
+template <bool VALS, int DB>
 __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t *__restrict__ kin,
                                                                  uint64_t *__restrict__ kout,
                                                                  const uint32_t *__restrict__ vin,
@@ -436,6 +436,17 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         const uint32_t dprev = __shfl_up_sync(0xffffffffu, d, 1);
         if (__ballot_sync(0xffffffffu, lane == 0 || d != dprev) == 1u) {
             peers = __match_any_sync(0xffffffffu, d);  // one run: the cheap case of match_any
+        } else if (DB > 0) {
+            // digit width known at compile time: accumulate the lanes that
+            // differ in validity or in any digit bit, one ballot per bit
+            const uint32_t sok = ok ? ~0u : 0u;
+            uint32_t x = __ballot_sync(0xffffffffu, ok) ^ sok;
+#pragma unroll
+            for (int bit = 0; bit < DB; bit++) {
+                const uint32_t sb = (uint32_t)((int32_t)(d << (31 - bit)) >> 31);
+                x |= __ballot_sync(0xffffffffu, sb != 0u) ^ sb;
+            }
+            peers = ~x;
         } else {
             peers = __ballot_sync(0xffffffffu, ok);
             if (!ok) peers = ~peers;
@@ -515,6 +526,20 @@ static constexpr size_t rs_smem()
     return RS_TILE * 8 + (VALS ? RS_TILE * 4 : 0) + RS_MAXB * 4 + RS_WARPS * RS_MAXB * 2;
 }
 
+// the scatter specialised for the common digit widths (36-bit fingerprints:
+// 9 bits; 40-bit group keys: 8 bits), else the generic loop
+template <bool VALS>
+static void launch_scatter(uint32_t db, uint64_t ntiles, const uint64_t *ks, uint64_t *kd, const uint32_t *vs,
+                           uint32_t *vd, uint64_t n, uint32_t shift, uint32_t nb, const uint32_t *offs,
+                           cudaStream_t st)
+{
+    const unsigned g = (unsigned)ntiles;
+    const size_t sm = rs_smem<VALS>();
+    if (db == 9) rs_scatter<VALS, 9><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
+    else if (db == 8) rs_scatter<VALS, 8><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
+    else rs_scatter<VALS, 0><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
+}
+
 static uint32_t first_digit_bits(uint32_t bits)
 {
     const uint32_t npass = (bits + 8) / 9;
@@ -539,8 +564,12 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
     if (n == 0) return;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaFuncSetAttribute(rs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
-        cudaFuncSetAttribute(rs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<true, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
+        cudaFuncSetAttribute(rs_scatter<false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
         attr_done = true;
     }
     const bool vals = vals_in != nullptr;
@@ -568,11 +597,9 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         exclusive_scan_u32(tmp, tmp, ntiles * nb, scan_tmp, ctr, st);
         TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
         if (vals)
-            rs_scatter<true><<<(unsigned)ntiles, RS_T, rs_smem<true>(), st>>>(ksrc, kdst, vsrc, vdst, n, shift, nb,
-                                                                            tmp, ntiles);
+            launch_scatter<true>(db, ntiles, ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, st);
         else
-            rs_scatter<false><<<(unsigned)ntiles, RS_T, rs_smem<false>(), st>>>(ksrc, kdst, nullptr, nullptr, n,
-                                                                              shift, nb, tmp, ntiles);
+            launch_scatter<false>(db, ntiles, ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, st);
         ksrc = kdst;
         vsrc = vdst;
         shift += db;
