@@ -121,6 +121,20 @@ struct MergeSmem {
     unsigned int tile, kold, oldlen, err;
 };
 
+// a new group's quotient offset from Q0, remainder and batch count, from its
+// sorted value f and its start and end in the batch
+template <int R>
+__device__ __forceinline__ void decode_group(const MergeArgs &a, long long Q0, uint64_t fv, uint32_t s0, uint32_t s1,
+                                             uint32_t &qoff, uint32_t &rem, uint64_t &cnt)
+{
+    const uint64_t f = fv & a.fmask;
+    qoff = (uint32_t)((long long)(f >> R) - Q0);
+    rem = (uint32_t)(f & ((1ull << R) - 1ull));
+    cnt = s1 - s0;
+}
+
+static constexpr int GB = 4;  // groups a thread loads before using them
+
 // new group g: quotient offset from Q0, remainder and batch count
 template <int R>
 __device__ __forceinline__ void new_group(const MergeSmem<R> &, const MergeArgs &a, long long Q0, uint32_t g,
@@ -349,18 +363,44 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
     }
     __syncthreads();
     const bool old_ok = S.err == 0;
-    for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
-        uint32_t qo, rm;
-        uint64_t cn;
-        new_group<R>(S, a, Q0, (uint32_t)g, qo, rm, cn);
-        atomicMin(&S.qfirst[qo], (unsigned)g);
-        if (!a.del) {
-            atomicAdd(&S.Lq[qo], enc_len(cn, R));
-        } else if (a.removed) {
-            const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
-            if (!ho) a.removed[g] = 0;  // nothing stored to delete
+    for (uint64_t g0 = S.glo + tid; g0 < S.ghi; g0 += GB * MT) {
+        // the loads of GB groups first, so that they are in flight together
+        uint64_t fv[GB];
+        uint32_t s0[GB], s1[GB];
+#pragma unroll
+        for (int u = 0; u < GB; u++) {
+            const uint64_t g = g0 + (uint64_t)u * MT;
+            if (g < S.ghi) {
+                fv[u] = a.ufp[g];
+                s0[u] = a.ustart[g];
+                s1[u] = a.ustart[g + 1];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GB; u++) {
+            const uint64_t g = g0 + (uint64_t)u * MT;
+            if (g < S.ghi) {
+                uint32_t qo, rm;
+                uint64_t cn;
+                decode_group<R>(a, Q0, fv[u], s0[u], s1[u], qo, rm, cn);
+                atomicMin(&S.qfirst[qo], (unsigned)g);
+                if (!a.del) {
+                    atomicAdd(&S.Lq[qo], enc_len(cn, R));
+                } else if (a.removed) {
+                    const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
+                    if (!ho) a.removed[g] = 0;  // nothing stored to delete
+                }
+            }
         }
     }
+    // 5 and 6 concern old runs only: a tile without any (kold is the same for
+    // every thread) goes straight to the placement
+    if (kold == 0) {
+        if (tid == 0) {
+            S.os0 = 0;
+            S.oldlen = 0;
+        }
+    } else {
     if (tid == 0) {
         // 5. staged window of the old runs
         if (kold > 0 && S.err == 0) {
@@ -412,6 +452,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
             S.Lq[y] = merge_run<R, false>(S, a, o, true, gf, ge, 0, Q0);
         }
     }
+    }  // kold > 0
     __syncthreads();
 
     // 7. placement: thread tid owns quotients 8 tid .. 8 tid + 7
@@ -615,7 +656,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
 
     // 10. write the runs: old-only runs are copied, mixed runs merged, and the
     // groups of new-only runs encoded by one thread each
-    for (int y = tid; y < TQ; y += MT) {
+    for (int y = tid; kold > 0 && y < TQ; y += MT) {
         const unsigned L = S.Lq[y];
         if (!L) continue;
         const bool ho = old_ok && ((S.occ[y >> 6] >> (y & 63)) & 1ull);
@@ -643,20 +684,36 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
         }
     }
     if (!a.del) {
-        for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
-            uint32_t qo, rm;
-            uint64_t cn;
-            new_group<R>(S, a, Q0, (uint32_t)g, qo, rm, cn);
-            const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
-            if (ho) continue;  // written by the merge above
-            long long pos = Q0 + S.qstart[qo];
-            for (uint32_t h = S.qfirst[qo]; h < (uint32_t)g; h++) {
-                uint32_t q2, r2;
-                uint64_t c2;
-                new_group<R>(S, a, Q0, h, q2, r2, c2);
-                pos += enc_len(c2, R);
+        for (uint64_t g0 = S.glo + tid; g0 < S.ghi; g0 += GB * MT) {
+            uint64_t fv[GB];
+            uint32_t s0[GB], s1[GB];
+#pragma unroll
+            for (int u = 0; u < GB; u++) {
+                const uint64_t g = g0 + (uint64_t)u * MT;
+                if (g < S.ghi) {
+                    fv[u] = a.ufp[g];
+                    s0[u] = a.ustart[g];
+                    s1[u] = a.ustart[g + 1];
+                }
             }
-            put_group<R>(S, a, pos, rm, cn);
+#pragma unroll
+            for (int u = 0; u < GB; u++) {
+                const uint64_t g = g0 + (uint64_t)u * MT;
+                if (g >= S.ghi) continue;
+                uint32_t qo, rm;
+                uint64_t cn;
+                decode_group<R>(a, Q0, fv[u], s0[u], s1[u], qo, rm, cn);
+                const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
+                if (ho) continue;  // written by the merge above
+                long long pos = Q0 + S.qstart[qo];
+                for (uint32_t h = S.qfirst[qo]; h < (uint32_t)g; h++) {
+                    uint32_t q2, r2;
+                    uint64_t c2;
+                    new_group<R>(S, a, Q0, h, q2, r2, c2);
+                    pos += enc_len(c2, R);
+                }
+                put_group<R>(S, a, pos, rm, cn);
+            }
         }
     }
     __syncthreads();
