@@ -121,6 +121,10 @@ struct MergeSmem {
     unsigned int tile, kold, oldlen, err;
 };
 
+static_assert(offsetof(MergeSmem<8>, out) % 4 == 0 && offsetof(MergeSmem<16>, out) % 4 == 0 &&
+                  OUTBUF % 4 == 0,
+              "the staged output is cleared in 32-bit words");
+
 // a new group's quotient offset from Q0, remainder and batch count, from its
 // sorted value f and its start and end in the batch
 template <int R>
@@ -269,8 +273,13 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
     const uint64_t j0 = tile * TBLK;
     const long long slot_end = min((long long)a.nslots, Q0 + TQ);
 
-    // 1. old occupieds of the tile
+    // 1. old occupieds of the tile; 4a. its new group range (precomputed by
+    // successor search), loaded alongside
     if (tid < TBLK) S.occ[tid] = (j0 + tid < a.nblk) ? a.meta_old[j0 + tid].occ : 0ull;
+    if (tid == TBLK) {
+        S.glo = a.tlo[tile];
+        S.ghi = a.tlo[tile + 1];
+    }
     __syncthreads();
     const uint32_t mybyte = (uint32_t)(S.occ[tid >> 3] >> ((tid & 7) * 8)) & 0xffu;
 
@@ -291,11 +300,6 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
             S.kpre[MT] = pre + incl;
             S.kold = pre + incl;
         }
-    }
-    // 4a. new group range of the tile (precomputed by successor search)
-    if (tid == 0) {
-        S.glo = a.tlo[tile];
-        S.ghi = a.tlo[tile + 1];
     }
     __syncthreads();
     const uint32_t kold = S.kold;
@@ -598,7 +602,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
     // 9. starts, runends, occupieds and offsets (thread tid: its 8 quotients)
     const long long w0 = S.w0, w1 = S.w1;
     const long long staged = (w1 - w0) < OUTBUF ? (w1 - w0) : OUTBUF;
-    for (int p = tid; p < OUTBUF; p += MT) S.out[p] = 0;
+    for (int p = tid; p < OUTBUF * (int)sizeof(S.out[0]) / 4; p += MT) reinterpret_cast<uint32_t *>(S.out)[p] = 0u;
     for (int p = tid; p < RWORDS; p += MT) S.rend[p] = 0ull;
     for (long long p = w0 + OUTBUF + tid; p < w1; p += MT) wr_slot<R>(a.rem_new, (uint64_t)p, 0u);
     __syncthreads();
@@ -1472,9 +1476,10 @@ __global__ void __launch_bounds__(256) gqf_count_kernel(const uint64_t *__restri
                                                         uint64_t *counts, uint8_t *found)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t c = count_fp<R>(fingerprint(__ldg(keys + i), H), meta, rem, nblk);
-        if (counts) counts[i] = c;
-        if (found) found[i] = c ? 1 : 0;
+        // keys and answers stream past the L2, which keeps the table
+        const uint64_t c = count_fp<R>(fingerprint(__ldcs(keys + i), H), meta, rem, nblk);
+        if (counts) __stcs(reinterpret_cast<unsigned long long *>(counts + i), (unsigned long long)c);
+        if (found) __stcs(found + i, (uint8_t)(c ? 1 : 0));
     }
 }
 
@@ -1929,9 +1934,9 @@ __global__ void __launch_bounds__(256) gqf_group_count_kernel(const uint64_t *__
             rem = gm[cm].rem[cur];
             nblk = gm[cm].nblk;
         }
-        const uint64_t cnt = count_fp<R>(fingerprint(__ldg(keys + c.i), H), meta, rem, nblk);
-        if (counts) counts[c.i] = cnt;
-        if (found) found[c.i] = cnt ? 1 : 0;
+        const uint64_t cnt = count_fp<R>(fingerprint(__ldcs(keys + c.i), H), meta, rem, nblk);
+        if (counts) __stcs(reinterpret_cast<unsigned long long *>(counts + c.i), (unsigned long long)cnt);
+        if (found) __stcs(found + c.i, (uint8_t)(cnt ? 1 : 0));
     }
 }
 

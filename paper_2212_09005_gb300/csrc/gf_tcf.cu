@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restri
 {
     const bool backing = ctr->backing != 0;
     for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
-        KeyInfo k = tcf_keyinfo(__ldg(keys + i), G);
+        KeyInfo k = tcf_keyinfo(__ldcs(keys + i), G);  // keys and answers stream past the L2
         Blk<F> x, y;
         x.load_ro(blocks, k.b1);
         y.load_ro(blocks, k.b2);
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restri
                 hit |= (v.x == e) | (v.y == e);
             }
         }
-        out[i] = hit ? 1 : 0;
+        __stcs(out + i, (uint8_t)(hit ? 1 : 0));
     }
 }
 
@@ -1341,7 +1341,7 @@ __global__ void __launch_bounds__(TPB) tcf_group_prep(const uint64_t *__restrict
             M = mem[cm];
             G = member_geom(M, f);
         }
-        const KeyInfo k = tcf_keyinfo(__ldg(keys + c.i), G);
+        const KeyInfo k = tcf_keyinfo(__ldcs(keys + c.i), G);
         const uint64_t e = tcf_entry(k, f);
         out.bt[c.i] = ((M.block0 + k.b1) << 32) | k.t;
         out.b2[c.i] = (uint32_t)(M.block0 + k.b2);
@@ -1369,7 +1369,7 @@ __global__ void __launch_bounds__(TPB) tcf_group_query_kernel(const uint64_t *__
             M = mem[cm];
             G = member_geom(M, F);
         }
-        const KeyInfo k = tcf_keyinfo(__ldg(keys + c.i), G);
+        const KeyInfo k = tcf_keyinfo(__ldcs(keys + c.i), G);
         Blk<F> x, y;
         x.load_ro(blocks, M.block0 + k.b1);
         y.load_ro(blocks, M.block0 + k.b2);
@@ -1384,7 +1384,7 @@ __global__ void __launch_bounds__(TPB) tcf_group_query_kernel(const uint64_t *__
                 hit |= (v.x == e) | (v.y == e);
             }
         }
-        out[c.i] = hit ? 1 : 0;
+        __stcs(out + c.i, (uint8_t)(hit ? 1 : 0));
     }
 }
 
