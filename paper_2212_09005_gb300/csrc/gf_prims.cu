@@ -386,7 +386,9 @@ __global__ void __launch_bounds__(RS_T) rs_fp_hist(const uint64_t *__restrict__ 
 }
 
 // Scatter of one pass. Keys are ranked inside each warp: a round's lanes
-// with equal digits are found with one ballot per digit bit, or with
+// with equal digits are found with one ballot per digit bit (DB > 0: the
+// digit width is a compile-time constant and the lanes that differ are
+// accumulated with one ballot and one logic operation per bit), or with
 // match_any when the round is a single run of one digit (long runs of equal
 // keys, which the earlier passes of a skewed key set produce); a per-warp
 // 16-bit counter per digit carries the rank across the warp's 16 rounds. A
