@@ -90,7 +90,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
-    ap.add_argument("--case", default="full", choices=["full", "profile", "batched", "serving"],
+    ap.add_argument("--case", default="full", choices=["full", "profile", "batched", "serving", "kmer"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
     return ap.parse_args()
@@ -530,6 +530,76 @@ def run_batched(args, device):
     return out
 
 
+KMER_WORKLOAD = ("k-mer counting: counting GQF 2^28 slots r=8; one batch of 2e8 canonical 28-mers of synthetic "
+                 "100-base reads (random genome of 2^25 bases, about 6x k-mer coverage, 0.5% substitution errors), "
+                 "then 2^24 count queries on k-mers sampled from the batch")
+KMER_N = 200_000_000
+PAPER_KMER_2_28 = 507.373  # M k-mers/s, the paper's GQF counting table at 2^28 slots (other hardware)
+
+
+def run_kmer(args, device):
+    """GQF counting insert of synthetic k-mers: the paper's k-mer count column
+    (Table of GQF counting inserts), on generated reads."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    kmers = W.kmer_workload(KMER_N)
+    qpos = W.sample_with_replacement(6 * 1000 + 3, len(kmers), 1 << 24)
+    kd = torch.from_numpy(kmers.view(np.int64)).to(device)
+    qd = torch.from_numpy(kmers[qpos].view(np.int64)).to(device)
+    cnt = torch.zeros(len(qpos), dtype=torch.int64, device=device)
+    G = gf.GQF(28, 8, seed=6, max_batch=len(kmers))
+    stream = torch.cuda.current_stream()
+
+    ins_ev = []
+
+    def step(timed=False):
+        G.clear()
+        if timed:
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        G.insert(kd)
+        if timed:
+            b.record(stream)
+            ins_ev.append((a, b))
+        G.count(qd, cnt)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    gf.trace_reset()
+    gf.trace_enable(True)
+    clocks = ClockSampler(device.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step(timed=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    gf.trace_enable(False)
+    trace = gf.trace_summary()
+    ms = e0.elapsed_time(e1)
+    kern, roof = roofline_from_trace(trace)
+    ins_ms = sum(a.elapsed_time(b) for a, b in ins_ev) / len(ins_ev)
+    st = G.stats()
+    c = cnt.cpu().numpy()
+    out = {"workload": KMER_WORKLOAD, "value": round(aggregate_rate(len(kmers) + len(qpos), args.steps, 1, ms), 4),
+           "unit": UNIT, "ms_per_step": round(ms / args.steps, 3), "ops_per_step": len(kmers) + len(qpos),
+           "insert_mkmers_per_s": round(len(kmers) / ins_ms / 1e3, 1),
+           "paper_kmer_count_2_28_mkmers_per_s": PAPER_KMER_2_28,
+           "clocks": clk, "gpu_launches": sum(v["launches"] for v in trace.values()), "roofline": roof,
+           "kernels": kern,
+           "checks": {"counts_positive": bool((c >= 1).all()), "failed_keys": st["failed_keys"],
+                      "status_word": st["status_word"]}}
+    del G, kd, qd, cnt
+    torch.cuda.empty_cache()
+    return out
+
+
 SERVING_WORKLOAD = ("serving loop: 64 filters of 2^24 slots (32 TCF f=16 bulk + 32 counting GQF r=8, "
                     "2^30 slots in all) pre-filled to 50%; batches of 2^10..2^24 keys (log-uniform) for a "
                     "uniformly chosen filter, 50/45/5 insert/query/delete, until 90% aggregate load; host "
@@ -775,6 +845,16 @@ def main():
                 "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": {"workload": SERVING_WORKLOAD},
                 "serving": sv}
+    elif args.case == "kmer":
+        import torch
+
+        torch.cuda.set_device(local)
+        km = run_kmer(args, torch.device("cuda", local))
+        line = {"metric": METRIC, "value": km["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": km["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": KMER_WORKLOAD}, "clocks": km["clocks"], "gpu_launches": km["gpu_launches"],
+                "roofline": km["roofline"], "kmer": km}
     elif args.case == "batched":
         import torch
 

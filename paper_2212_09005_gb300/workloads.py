@@ -339,6 +339,149 @@ def serving_workload(n_filters: int = 64, log2_slots: int = 24, seed: int = 5, b
             "prefill": prefill_batches, "requests": reqs}
 
 
+# ---------------------------------------------------------------------------
+# Synthetic k-mer counting workload (stand-in for the sequencing reads the
+# paper counts k-mers of, Sec. 6: the real dataset is not available here).
+# A random genome of `genome_len` bases; reads of `read_len` bases start at
+# uniform positions; each base of a read is replaced by a different random base
+# with probability `error_rate` (substitution errors); every k-mer of every
+# read is packed 2 bits per base (A=0, C=1, G=2, T=3, first base most
+# significant) and taken in canonical form, the smaller of the k-mer and its
+# reverse complement. Genomic k-mers repeat about coverage times, erroneous
+# ones are mostly unique, as in real reads.
+# ---------------------------------------------------------------------------
+
+def _bases(seed: int, start: int, n: int) -> np.ndarray:
+    """n bases (0..3) from stream `seed`, 32 per 64-bit draw."""
+    words = splitmix64(seed, start // 32, (start % 32 + n + 31) // 32)
+    b = ((words[:, None] >> (2 * np.arange(32, dtype=np.uint64))[None, :]) & np.uint64(3)).astype(np.uint8)
+    return b.reshape(-1)[start % 32: start % 32 + n]
+
+
+def revcomp_kmer(x: np.ndarray, k: int) -> np.ndarray:
+    """Reverse complement of 2-bit packed k-mers (complement: 3 - base)."""
+    x = np.asarray(x, dtype=np.uint64)
+    out = np.zeros_like(x)
+    for j in range(k):
+        out = (out << np.uint64(2)) | (np.uint64(3) - ((x >> np.uint64(2 * j)) & np.uint64(3)))
+    return out
+
+
+def kmers_of_reads(reads: np.ndarray, k: int) -> np.ndarray:
+    """Canonical k-mers of every read (rows of 2-bit base codes), read by read."""
+    n_reads, length = reads.shape
+    w = length - k + 1
+    fwd = np.zeros((n_reads, w), np.uint64)
+    rev = np.zeros((n_reads, w), np.uint64)
+    r64 = reads.astype(np.uint64)
+    c64 = np.uint64(3) - r64  # complements
+    t = np.empty((n_reads, w), np.uint64)
+    two = np.uint64(2)
+    for j in range(k):
+        np.left_shift(fwd, two, out=fwd)
+        np.bitwise_or(fwd, r64[:, j:j + w], out=fwd)
+        np.left_shift(c64[:, j:j + w], np.uint64(2 * j), out=t)
+        np.bitwise_or(rev, t, out=rev)
+    np.minimum(fwd, rev, out=fwd)
+    return fwd.reshape(-1)
+
+
+def _genome_kmers(genome: np.ndarray, k: int) -> np.ndarray:
+    """k-mer at every position of a base array: the bases packed 32 to a word,
+    first base in the top bits, and each k-mer cut from two adjacent words."""
+    n = genome.size
+    nw = (n + 31) // 32 + 1
+    b = np.zeros(nw * 32, np.uint64)
+    b[:n] = genome
+    words = np.bitwise_or.reduce(b.reshape(nw, 32) << (np.uint64(62) - np.uint64(2) * np.arange(32, dtype=np.uint64)),
+                                 axis=1)
+    i = np.arange(n - k + 1, dtype=np.int64)
+    w = i >> 5
+    off = ((i & 31) * 2).astype(np.uint64)
+    hi = words[w] << off
+    lo = np.where(off > 0, words[w + 1] >> ((np.uint64(64) - off) & np.uint64(63)), np.uint64(0))
+    return (hi | lo) >> np.uint64(64 - 2 * k)
+
+
+_PAIR_MASKS = [(np.uint64(0x3333333333333333), 2), (np.uint64(0x0F0F0F0F0F0F0F0F), 4),
+               (np.uint64(0x00FF00FF00FF00FF), 8), (np.uint64(0x0000FFFF0000FFFF), 16)]
+
+
+def _revcomp_fast(x: np.ndarray, k: int) -> np.ndarray:
+    """revcomp_kmer by bit operations: complement every base (xor 3), reverse
+    the order of the 32 two-bit groups of the word, shift back to 2k bits."""
+    y = np.asarray(x, dtype=np.uint64) ^ np.uint64((1 << (2 * k)) - 1 if k < 32 else 0xFFFFFFFFFFFFFFFF)
+    for m, sh in _PAIR_MASKS:
+        y = ((y >> np.uint64(sh)) & m) | ((y & m) << np.uint64(sh))
+    y = (y >> np.uint64(32)) | (y << np.uint64(32))
+    return y >> np.uint64(64 - 2 * k)
+
+
+def _read_starts(seed: int, r0: int, m: int, read_len: int, genome_len: int) -> np.ndarray:
+    return (splitmix64(seed + 1, r0, m) % np.uint64(genome_len - read_len + 1)).astype(np.int64)
+
+
+def _error_hits(seed: int, r0: int, m: int, read_len: int, error_rate: float) -> np.ndarray:
+    u = (splitmix64(seed + 2, r0 * read_len, m * read_len) >> np.uint64(11)).astype(np.float64) * (1.0 / (1 << 53))
+    return (u < error_rate).reshape(m, read_len)
+
+
+def _error_shift(seed: int, r0: int, m: int, read_len: int) -> np.ndarray:
+    """1..3: how far (mod 4) a substituted base moves from the true one."""
+    return (_bases(seed + 3, r0 * read_len, m * read_len).reshape(m, read_len) % 3) + 1
+
+
+def synthetic_reads(n_reads: int, seed: int = 6, read_len: int = 100, genome_len: int = 1 << 25,
+                    error_rate: float = 0.005, r0: int = 0) -> np.ndarray:
+    """Reads r0 .. r0 + n_reads - 1 of the k-mer workload as rows of base codes."""
+    genome = _bases(seed, 0, genome_len)
+    starts = _read_starts(seed, r0, n_reads, read_len, genome_len)
+    reads = genome[starts[:, None] + np.arange(read_len)[None, :]]
+    hit = _error_hits(seed, r0, n_reads, read_len, error_rate)
+    return np.where(hit, (reads + _error_shift(seed, r0, n_reads, read_len)) & 3, reads).astype(np.uint8)
+
+
+def kmer_workload(n_kmers: int, seed: int = 6, k: int = 28, read_len: int = 100, genome_len: int = 1 << 25,
+                  error_rate: float = 0.005, chunk_reads: int = 1 << 18):
+    """Canonical k-mers (uint64, 2k bits) of the first ceil(n_kmers / (read_len
+    - k + 1)) reads of `synthetic_reads`, in read order, truncated to n_kmers.
+    Streams: genome = seed, read starts = seed + 1, error positions = seed + 2,
+    substituted bases = seed + 3. Equal to kmers_of_reads(synthetic_reads(..));
+    computed faster from the k-mers at every genome position, each sequencing
+    error flipping the bits of its base in the up to k k-mers that cover it."""
+    assert 1 <= k <= 32 and read_len >= k
+    genome = _bases(seed, 0, genome_len)
+    G = genome_len - k + 1
+    fwd_g = _genome_kmers(genome, k)
+    rev_g = _revcomp_fast(fwd_g, k)
+    per = read_len - k + 1
+    n_reads = (n_kmers + per - 1) // per
+    out = np.empty(n_reads * per, np.uint64)
+    cols = np.arange(per)
+    for r0 in range(0, n_reads, chunk_reads):
+        m = min(chunk_reads, n_reads - r0)
+        starts = _read_starts(seed, r0, m, read_len, genome_len)
+        idx = starts[:, None] + cols[None, :]
+        fwd = fwd_g[idx]
+        rev = rev_g[idx]
+        er, ep = np.nonzero(_error_hits(seed, r0, m, read_len, error_rate))
+        if er.size:
+            old = genome[starts[er] + ep].astype(np.uint64)
+            new = (old + _error_shift(seed, r0, m, read_len)[er, ep].astype(np.uint64)) & np.uint64(3)
+            delta = old ^ new
+            for o in range(k):  # the error is base o of k-mer ep - o: one k-mer per error, no repeats
+                kk = ep - o
+                ok = (kk >= 0) & (kk < per)
+                if not ok.any():
+                    continue
+                ri, ki, d = er[ok], kk[ok], delta[ok]
+                fwd[ri, ki] ^= d << np.uint64(2 * (k - 1 - o))
+                rev[ri, ki] ^= d << np.uint64(2 * o)
+        np.minimum(fwd, rev, out=fwd)
+        out[r0 * per:(r0 + m) * per] = fwd.reshape(-1)
+    return out[:n_kmers]
+
+
 def poisson_arrivals(seed: int, n: int, rate: float) -> np.ndarray:
     """n arrival times (seconds) of a Poisson process of `rate` per second:
     cumulative exponential gaps -ln(1 - u) / rate, u from stream `seed`."""

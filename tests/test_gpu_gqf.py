@@ -244,6 +244,23 @@ def test_no_status_extremes_match_oracle(gf, oracle):
     _no_status_rounds(gf, oracle, 21, 16, 8, [("ins", W.zipf_keys(34, (1 << 20) + 1, 1.0, 1 << 22))])
 
 
+def test_kmer_counting_matches_oracle(gf, oracle):
+    """Canonical 28-mers of synthetic reads (repeats near the coverage, unique
+    error k-mers) counted in one batch and in two: table image equal to the
+    oracle's, and every k-mer's count equal to the oracle's and at least its
+    true multiplicity (56-bit k-mers, 26-bit fingerprints)."""
+    q, r = 18, 8
+    kmers = W.kmer_workload(150000, seed=21, genome_len=1 << 14)
+    _no_status_rounds(gf, oracle, q, r, 21, [("ins", kmers)])
+    O, G = _no_status_rounds(gf, oracle, q, r, 21, [("ins", kmers[:70001]), ("ins", kmers[70001:])])
+    u, c = np.unique(kmers, return_counts=True)
+    got = zeros_u64(len(u))
+    G.count(dev_u64(u), got)
+    got = host(got)
+    assert np.array_equal(got, O.count(u))
+    assert (got >= c.astype(np.uint64)).all()
+
+
 def test_inplace_delete_matches_oracle(gf, oracle):
     """Deletes of a small fraction of the table take the in-place cluster path
     (even-odd regions); image and statuses must equal the oracle's."""
