@@ -142,6 +142,30 @@ int filter_count(filter_t *f, const uint64_t *d_keys, uint64_t n, uint64_t *d_co
 /* filter_get_stats: synchronise `stream`, then read the status word and counters. */
 int filter_get_stats(filter_t *f, void *stream, filter_stats *out);
 
+/*
+ * filter_get_device_view: describe the filter's current table for the
+ * device-side point queries of include/gpufilter_device.cuh (a caller's own
+ * kernels call gf_device_tcf_contains / gf_device_gqf_count with the view
+ * passed by value). The view holds device pointers owned by the filter and is
+ * valid until the next insert, remove, clear or import on it; a GQF update
+ * switches table buffers, so take the view again after one. Host only, does
+ * not touch the device. Group members are not covered.
+ */
+typedef struct filter_device_view {
+    uint32_t kind;       /* FILTER_TCF or FILTER_GQF */
+    uint32_t tag_bits;   /* TCF: tag bits f; GQF: remainder bits r */
+    uint32_t q;          /* GQF: quotient bits; TCF: 0 */
+    uint32_t reserved;
+    uint64_t seed;       /* the filter's hash seed (filter_config.hash_seed) */
+    const void *table;   /* TCF: nb blocks of 32 bytes; GQF: the 32-byte metadata records */
+    const void *aux;     /* TCF: the backing buckets (8 uint64 each); GQF: the remainders */
+    uint64_t n_blocks;   /* TCF: nb (a power of two); GQF: metadata records */
+    uint64_t n_aux;      /* TCF: backing buckets; GQF: slots */
+    const unsigned long long *backing_used;  /* TCF: device count of backing entries; GQF: NULL */
+} filter_device_view;
+
+int filter_get_device_view(filter_t *f, filter_device_view *out);
+
 /* filter_export_size: bytes of the table image (see the layout above). */
 int filter_export_size(filter_t *f, uint64_t *nbytes);
 

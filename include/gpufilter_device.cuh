@@ -1,0 +1,202 @@
+/*
+ * gpufilter_device.cuh - device-side point queries for filters built by the
+ * library, callable from the caller's own CUDA kernels (header only).
+ *
+ * The paper's filters are also used from inside GPU applications, one key
+ * per thread, next to the bulk API (Sec. 4: point operations; Sec. 6). This
+ * header lets a kernel written elsewhere query a TCF or count a key in a GQF
+ * that the C ABI built and filled:
+ *
+ *   host:    filter_device_view v;  filter_get_device_view(f, &v);
+ *            pass v by value to the kernel
+ *   device:  bool hit  = gf_device_tcf_contains(v, key);
+ *            uint64_t c = gf_device_gqf_count(v, key);
+ *
+ * Both functions read only. A view describes the table as it is when
+ * filter_get_device_view returns; it must be taken again after any insert,
+ * remove, clear or import on the filter (a GQF update switches between two
+ * table buffers), and the filter must not be updated while kernels use it.
+ * The functions restate the library's hashing and table layouts; a GPU test
+ * checks them against filter_query / filter_count on the same keys.
+ */
+#pragma once
+
+#include <stdint.h>
+
+#include "gpufilter.h"
+
+namespace gf_device {
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x)
+{
+    x ^= x >> 33;
+    x *= 0xff51afd7ed558ccdull;
+    x ^= x >> 33;
+    x *= 0xc4ceb9fe1a85ec53ull;
+    x ^= x >> 33;
+    return x;
+}
+
+// The GQF fingerprint: the key folded to p bits (xor of its p-bit chunks),
+// xored with the seed, then xor-shift / odd-multiply rounds mod 2^p.
+__device__ __forceinline__ uint64_t gqf_fingerprint(uint64_t key, uint32_t p, uint64_t seed)
+{
+    const uint64_t mask = p >= 64 ? ~0ull : ((1ull << p) - 1ull);
+    const uint32_t s = (p + 1) / 2;
+    uint64_t x = key;
+    if (p < 64) {
+        uint64_t r = 0;
+        while (x) {
+            r ^= x & mask;
+            x >>= p;
+        }
+        x = r;
+    }
+    x ^= seed & mask;
+    x ^= x >> s;
+    x = (x * 0xff51afd7ed558ccdull) & mask;
+    x ^= x >> s;
+    x = (x * 0xc4ceb9fe1a85ec53ull) & mask;
+    x ^= x >> s;
+    return x;
+}
+
+// does the 32-byte block hold tag t (f = 8 or 16 bits per tag)?
+__device__ __forceinline__ bool tcf_block_has(const uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
+    const uint4 lo = __ldg(p), hi = __ldg(p + 1);
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    uint32_t m = 0;
+    if (f == 16) {
+        const uint32_t tt = t | (t << 16);
+#pragma unroll
+        for (int k = 0; k < 8; k++) m |= __vcmpeq2(w[k], tt);
+    } else {
+        const uint32_t tt = t * 0x01010101u;
+#pragma unroll
+        for (int k = 0; k < 8; k++) m |= __vcmpeq4(w[k], tt);
+    }
+    return m != 0;
+}
+
+template <int R>
+__device__ __forceinline__ uint32_t gqf_slot(const uint8_t *rem, uint64_t i)
+{
+    if (R == 8) return rem[i];
+    return reinterpret_cast<const uint16_t *>(rem)[i];
+}
+
+// Count of fingerprint fp: the quotient's home block gives the offset of the
+// first run end at or after it; the run of quotient x ends at the d-th run
+// end from there, where d counts the occupied quotients of the block up to x;
+// it starts one past the previous run end (or at x). Inside the run, groups
+// are [rem] or [rem, rem, n, n base-2^R digits of count - 2], ascending.
+template <int R>
+__device__ uint64_t gqf_count_fp(uint64_t fp, const uint8_t *meta, const uint8_t *rem, uint64_t nblk)
+{
+    // metadata record of block j: occupieds u64, runends u64, offset u32, 12 bytes unused
+    auto occ_of = [&](uint64_t j) { return __ldg(reinterpret_cast<const unsigned long long *>(meta + 32 * j)); };
+    auto rend_of = [&](uint64_t j) { return __ldg(reinterpret_cast<const unsigned long long *>(meta + 32 * j + 8)); };
+    auto off_of = [&](uint64_t j) { return __ldg(reinterpret_cast<const unsigned int *>(meta + 32 * j + 16)); };
+    const uint64_t x = fp >> R;
+    const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
+    const uint64_t j = x >> 6;
+    if (j >= nblk) return 0;
+    const unsigned long long occ = occ_of(j);
+    if (!((occ >> (x & 63)) & 1ull)) return 0;
+    const long long base = (long long)(64 * j) + (long long)off_of(j);
+    const unsigned sh = (unsigned)(x & 63);
+    const unsigned long long upto = (sh == 63) ? ~0ull : ((1ull << (sh + 1)) - 1ull);
+    int d = __popcll(occ & upto & ~1ull);
+    long long end = base;
+    if (d > 0) {
+        long long w = base >> 6;
+        const unsigned bsh = (unsigned)(base & 63);
+        unsigned long long bits = (bsh == 63) ? 0ull : (rend_of((uint64_t)w) & (~0ull << (bsh + 1)));
+        while (true) {
+            const int pc = __popcll(bits);
+            if (pc >= d) {
+                for (int k = 1; k < d; k++) bits &= bits - 1;
+                end = 64 * w + __ffsll((long long)bits) - 1;
+                break;
+            }
+            d -= pc;
+            if (++w >= (long long)nblk) return 0;
+            bits = rend_of((uint64_t)w);
+        }
+    }
+    long long start = (long long)x;
+    for (long long p = end - 1; p >= (long long)x;) {
+        const long long w = p >> 6;
+        unsigned long long bits = rend_of((uint64_t)w);
+        const unsigned pb = (unsigned)(p & 63);
+        bits &= (pb == 63) ? ~0ull : ((1ull << (pb + 1)) - 1ull);
+        if (64 * w < (long long)x) bits &= ~0ull << (x & 63);
+        if (bits) {
+            start = 64 * w + 63 - __clzll((long long)bits) + 1;
+            break;
+        }
+        p = 64 * w - 1;
+    }
+    for (long long q = start; q <= end;) {
+        const uint32_t s = gqf_slot<R>(rem, (uint64_t)q);
+        uint64_t c = 1;
+        long long step = 1;
+        if (q + 2 <= end && gqf_slot<R>(rem, (uint64_t)(q + 1)) == s) {
+            uint32_t nd = gqf_slot<R>(rem, (uint64_t)(q + 2));
+            if (q + 2 + (long long)nd > end) nd = (uint32_t)(end - q - 2);
+            uint64_t acc = 0;
+            for (uint32_t k = 0; k < nd; k++) acc = (acc << R) | gqf_slot<R>(rem, (uint64_t)(q + 3 + k));
+            c = acc + 2;
+            step = 3 + nd;
+        }
+        if (s == v) return c;
+        if (s > v) return 0;
+        q += step;
+    }
+    return 0;
+}
+
+}  // namespace gf_device
+
+// Is key in the TCF (a false positive with the filter's rate, never a false
+// negative for an inserted key)? Tag t and block pair (b1, b2 = b1 xor g(t))
+// from one 64-bit hash; the backing bucket is read only when some key was
+// stored there.
+__device__ __forceinline__ bool gf_device_tcf_contains(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    const uint64_t nb = v.n_blocks;
+    const uint64_t h = mix64(key ^ v.seed);
+    uint32_t t = (uint32_t)((h >> 44) & ((1u << v.tag_bits) - 1u));
+    if (t < 2) t += 2;
+    const uint64_t b1 = h & (nb - 1);
+    uint64_t g = mix64((uint64_t)t) & (nb - 1);
+    if (!g) g = 1;
+    const uint64_t b2 = b1 ^ g;
+    const uint8_t *blocks = static_cast<const uint8_t *>(v.table);
+    if (tcf_block_has(blocks, b1, t, v.tag_bits) || tcf_block_has(blocks, b2, t, v.tag_bits)) return true;
+    if (!v.backing_used || *v.backing_used == 0) return false;
+    const uint64_t e = ((b1 < b2 ? b1 : b2) << v.tag_bits) | t;
+    const uint64_t bucket = ((mix64(e) >> 32) * v.n_aux) >> 32;
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(static_cast<const uint64_t *>(v.aux) + bucket * 8);
+#pragma unroll
+    for (int s = 0; s < 4; s++) {
+        const ulonglong2 w = __ldg(p + s);
+        if (w.x == e || w.y == e) return true;
+    }
+    return false;
+}
+
+// How many copies of key the GQF counts (0 if absent; at least the true
+// count, exactly it when distinct keys have distinct fingerprints).
+__device__ __forceinline__ uint64_t gf_device_gqf_count(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    const uint32_t r = v.tag_bits;
+    const uint64_t fp = gqf_fingerprint(key, v.q + r, v.seed);
+    const uint8_t *meta = static_cast<const uint8_t *>(v.table);
+    const uint8_t *rem = static_cast<const uint8_t *>(v.aux);
+    return r == 8 ? gqf_count_fp<8>(fp, meta, rem, v.n_blocks) : gqf_count_fp<16>(fp, meta, rem, v.n_blocks);
+}

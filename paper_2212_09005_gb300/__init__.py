@@ -32,7 +32,7 @@ STATUS_FULL, STATUS_TIMEOUT, STATUS_INTERNAL = 1 << ERR_FULL, 1 << ERR_TIMEOUT, 
 # entry points declared in include/gpufilter.h
 EXPORTS = [
     "filter_create", "filter_destroy", "filter_clear", "filter_insert", "filter_query",
-    "filter_remove", "filter_count", "filter_get_stats", "filter_export_size",
+    "filter_remove", "filter_count", "filter_get_stats", "filter_get_device_view", "filter_export_size",
     "filter_export", "filter_import", "filter_error_string",
     "filter_trace_enable", "filter_trace_reset", "filter_trace_summary",
     "filter_gqf_insert_noalloc",
@@ -55,6 +55,14 @@ class FilterStats(C.Structure):
     _fields_ = [("status_word", C.c_uint64), ("failed_keys", C.c_uint64),
                 ("backing_used", C.c_uint64), ("table_bytes", C.c_uint64),
                 ("device_bytes", C.c_uint64), ("nslots", C.c_uint64)]
+
+
+class FilterDeviceView(C.Structure):
+    """The filter_device_view of include/gpufilter.h (pass it by value to a
+    kernel that includes include/gpufilter_device.cuh)."""
+    _fields_ = [("kind", C.c_uint32), ("tag_bits", C.c_uint32), ("q", C.c_uint32), ("reserved", C.c_uint32),
+                ("seed", C.c_uint64), ("table", C.c_void_p), ("aux", C.c_void_p), ("n_blocks", C.c_uint64),
+                ("n_aux", C.c_uint64), ("backing_used", C.c_void_p)]
 
 
 class FilterRequest(C.Structure):
@@ -196,6 +204,13 @@ class Filter:
 
     def clear(self, stream=None):
         _check(lib().filter_clear(self._h, _stream(stream)), "filter_clear")
+
+    def device_view(self) -> "FilterDeviceView":
+        """Table pointers and geometry for device-side point queries; take it
+        again after any update of the filter."""
+        v = FilterDeviceView()
+        _check(lib().filter_get_device_view(self._h, C.byref(v)), "filter_get_device_view")
+        return v
 
     # ---- synchronous helpers ----
     def stats(self, stream=None) -> dict:

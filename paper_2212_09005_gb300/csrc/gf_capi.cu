@@ -137,6 +137,31 @@ int filter_get_stats(filter_t *f, void *stream, filter_stats *out)
     return FILTER_OK;
 }
 
+int filter_get_device_view(filter_t *f, filter_device_view *out)
+{
+    if (!valid(f) || !out) return FILTER_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    out->kind = f->cfg.kind;
+    out->tag_bits = f->cfg.tag_bits;
+    out->seed = f->cfg.hash_seed;
+    if (f->cfg.kind == FILTER_TCF) {
+        const TcfState &T = f->tcf;
+        out->table = T.blocks;
+        out->aux = T.bk;
+        out->n_blocks = T.G.nb;
+        out->n_aux = T.G.nbk;
+        out->backing_used = &f->ctr->backing;
+    } else {
+        const GqfState &Q = f->gqf;
+        out->q = Q.q;
+        out->table = Q.meta[Q.cur];
+        out->aux = Q.rem[Q.cur];
+        out->n_blocks = Q.nblk;
+        out->n_aux = Q.nslots;
+    }
+    return FILTER_OK;
+}
+
 int filter_export_size(filter_t *f, uint64_t *nbytes)
 {
     if (!valid(f) || !nbytes) return FILTER_ERR_ARG;

@@ -1,0 +1,29 @@
+// A caller's own kernel using the device-side point queries of
+// include/gpufilter_device.cuh on filters built through the C ABI: one key
+// per thread, the view passed by value.
+#include <cuda_runtime.h>
+
+#include "gpufilter_device.cuh"
+
+__global__ void device_query_kernel(filter_device_view v, const uint64_t *keys, uint64_t n, uint8_t *found,
+                                    uint64_t *counts)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (v.kind == FILTER_TCF) {
+            found[i] = gf_device_tcf_contains(v, keys[i]) ? 1 : 0;
+        } else {
+            const uint64_t c = gf_device_gqf_count(v, keys[i]);
+            if (counts) counts[i] = c;
+            if (found) found[i] = c ? 1 : 0;
+        }
+    }
+}
+
+extern "C" int device_query_example(const filter_device_view *v, const uint64_t *keys, uint64_t n, uint8_t *found,
+                                    uint64_t *counts, void *stream)
+{
+    if (!v || n == 0) return 0;
+    const unsigned grid = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    device_query_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, found, counts);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
