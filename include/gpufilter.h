@@ -149,19 +149,22 @@ int filter_get_stats(filter_t *f, void *stream, filter_stats *out);
  * passed by value). The view holds device pointers owned by the filter and is
  * valid until the next insert, remove, clear or import on it; a GQF update
  * switches table buffers, so take the view again after one. Host only, does
- * not touch the device. Group members are not covered.
+ * not touch the device. Group members are not covered. A point-mode TCF can
+ * also be updated from a caller's kernel (gf_device_tcf_insert / _remove);
+ * those updates and the library's own calls on the filter must not overlap.
  */
 typedef struct filter_device_view {
     uint32_t kind;       /* FILTER_TCF or FILTER_GQF */
     uint32_t tag_bits;   /* TCF: tag bits f; GQF: remainder bits r */
     uint32_t q;          /* GQF: quotient bits; TCF: 0 */
-    uint32_t reserved;
+    uint32_t mode;       /* TCF: FILTER_MODE_BULK or FILTER_MODE_POINT; GQF: 0 */
     uint64_t seed;       /* the filter's hash seed (filter_config.hash_seed) */
-    const void *table;   /* TCF: nb blocks of 32 bytes; GQF: the 32-byte metadata records */
-    const void *aux;     /* TCF: the backing buckets (8 uint64 each); GQF: the remainders */
+    void *table;         /* TCF: nb blocks of 32 bytes; GQF: the 32-byte metadata records */
+    void *aux;           /* TCF: the backing buckets (8 uint64 each); GQF: the remainders */
     uint64_t n_blocks;   /* TCF: nb (a power of two); GQF: metadata records */
     uint64_t n_aux;      /* TCF: backing buckets; GQF: slots */
-    const unsigned long long *backing_used;  /* TCF: device count of backing entries; GQF: NULL */
+    unsigned long long *counters;  /* the filter's device counters: [0] status word,
+                                      [1] failed keys, [2] TCF backing entries */
 } filter_device_view;
 
 int filter_get_device_view(filter_t *f, filter_device_view *out);

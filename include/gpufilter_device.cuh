@@ -1,23 +1,28 @@
 /*
- * gpufilter_device.cuh - device-side point queries for filters built by the
+ * gpufilter_device.cuh - device-side point operations on filters built by the
  * library, callable from the caller's own CUDA kernels (header only).
  *
  * The paper's filters are also used from inside GPU applications, one key
  * per thread, next to the bulk API (Sec. 4: point operations; Sec. 6). This
  * header lets a kernel written elsewhere query a TCF or count a key in a GQF
- * that the C ABI built and filled:
+ * that the C ABI built and filled, and insert into or remove from a point-mode
+ * TCF:
  *
  *   host:    filter_device_view v;  filter_get_device_view(f, &v);
  *            pass v by value to the kernel
  *   device:  bool hit  = gf_device_tcf_contains(v, key);
  *            uint64_t c = gf_device_gqf_count(v, key);
+ *            int st = gf_device_tcf_insert(v, key);   (point-mode TCF only)
+ *            int st = gf_device_tcf_remove(v, key);   (point-mode TCF only)
  *
- * Both functions read only. A view describes the table as it is when
- * filter_get_device_view returns; it must be taken again after any insert,
- * remove, clear or import on the filter (a GQF update switches between two
- * table buffers), and the filter must not be updated while kernels use it.
- * The functions restate the library's hashing and table layouts; a GPU test
- * checks them against filter_query / filter_count on the same keys.
+ * A view describes the table as it is when filter_get_device_view returns;
+ * it must be taken again after any insert, remove, clear or import through
+ * the C ABI (a GQF update switches between two table buffers). Queries and
+ * counts read only. Point-mode TCF inserts and removes may run concurrently
+ * with each other and with queries from any number of threads (one atomic
+ * compare-and-swap per slot, Alg. 1), but not with the library's own calls on
+ * the filter. The functions restate the library's hashing, table layouts and
+ * point-mode algorithm; GPU tests check them against the C ABI.
  */
 #pragma once
 
@@ -64,8 +69,9 @@ __device__ __forceinline__ uint64_t gqf_fingerprint(uint64_t key, uint32_t p, ui
 // does the 32-byte block hold tag t (f = 8 or 16 bits per tag)?
 __device__ __forceinline__ bool tcf_block_has(const uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f)
 {
+    // L2 loads: coherent with device-side updates made by other threads
     const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
-    const uint4 lo = __ldg(p), hi = __ldg(p + 1);
+    const uint4 lo = __ldcg(p), hi = __ldcg(p + 1);
     const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
     uint32_t m = 0;
     if (f == 16) {
@@ -177,16 +183,155 @@ __device__ __forceinline__ bool gf_device_tcf_contains(const filter_device_view 
     const uint64_t b2 = b1 ^ g;
     const uint8_t *blocks = static_cast<const uint8_t *>(v.table);
     if (tcf_block_has(blocks, b1, t, v.tag_bits) || tcf_block_has(blocks, b2, t, v.tag_bits)) return true;
-    if (!v.backing_used || *v.backing_used == 0) return false;
+    if (!v.counters || *(volatile unsigned long long *)(v.counters + 2) == 0) return false;
     const uint64_t e = ((b1 < b2 ? b1 : b2) << v.tag_bits) | t;
     const uint64_t bucket = ((mix64(e) >> 32) * v.n_aux) >> 32;
     const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(static_cast<const uint64_t *>(v.aux) + bucket * 8);
 #pragma unroll
     for (int s = 0; s < 4; s++) {
-        const ulonglong2 w = __ldg(p + s);
+        const ulonglong2 w = __ldcg(p + s);
         if (w.x == e || w.y == e) return true;
     }
     return false;
+}
+
+namespace gf_device {
+
+__device__ __forceinline__ uint32_t tcf_tag_at(const uint8_t *blocks, uint64_t b, int s, uint32_t f)
+{
+    const volatile uint8_t *p = blocks + b * 32;
+    if (f == 16) return (uint32_t)p[2 * s] | ((uint32_t)p[2 * s + 1] << 8);
+    return p[s];
+}
+
+// tags of block b that are neither EMPTY (0) nor TOMBSTONE (1)
+__device__ __forceinline__ int tcf_live(const uint8_t *blocks, uint64_t b, uint32_t f)
+{
+    int c = 0;
+    for (int s = 0; s < (int)(256 / f); s++) c += tcf_tag_at(blocks, b, s, f) >= 2;
+    return c;
+}
+
+// put tag t into the first EMPTY or TOMBSTONE slot of block b (a bounded
+// number of compare-and-swap attempts; false when the block is full)
+__device__ __forceinline__ bool tcf_put(uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f,
+                                        unsigned long long *counters)
+{
+    const int B = (int)(256 / f);
+    for (int attempt = 0; attempt < 4 * B; attempt++) {
+        int s = -1;
+        uint32_t seen = 0;
+        for (int p = 0; p < B && s < 0; p++) {
+            const uint32_t x = tcf_tag_at(blocks, b, p, f);
+            if (x < 2) {
+                s = p;
+                seen = x;
+            }
+        }
+        if (s < 0) return false;
+        unsigned int *word = reinterpret_cast<unsigned int *>(blocks + b * 32) + ((s * f) >> 5);
+        const unsigned sh = (unsigned)((s * f) & 31);
+        const unsigned int lane = (f == 16 ? 0xffffu : 0xffu) << sh;
+        const unsigned int cur = *(volatile unsigned int *)word;
+        if (((cur & lane) >> sh) != seen) continue;  // changed since it was read
+        if (atomicCAS(word, cur, (cur & ~lane) | (t << sh)) == cur) return true;
+    }
+    atomicOr(counters, 1ull << FILTER_ERR_TIMEOUT);
+    return false;
+}
+
+// replace one copy of tag t in block b by TOMBSTONE
+__device__ __forceinline__ bool tcf_take(uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f,
+                                         unsigned long long *counters)
+{
+    const int B = (int)(256 / f);
+    for (int attempt = 0; attempt < 4 * B; attempt++) {
+        int s = -1;
+        for (int p = 0; p < B && s < 0; p++)
+            if (tcf_tag_at(blocks, b, p, f) == t) s = p;
+        if (s < 0) return false;
+        unsigned int *word = reinterpret_cast<unsigned int *>(blocks + b * 32) + ((s * f) >> 5);
+        const unsigned sh = (unsigned)((s * f) & 31);
+        const unsigned int lane = (f == 16 ? 0xffffu : 0xffu) << sh;
+        const unsigned int cur = *(volatile unsigned int *)word;
+        if (((cur & lane) >> sh) != t) continue;
+        if (atomicCAS(word, cur, (cur & ~lane) | (1u << sh)) == cur) return true;
+    }
+    atomicOr(counters, 1ull << FILTER_ERR_TIMEOUT);
+    return false;
+}
+
+__device__ __forceinline__ void tcf_key(const filter_device_view &v, uint64_t key, uint64_t &b1, uint64_t &b2,
+                                        uint32_t &t)
+{
+    const uint64_t nb = v.n_blocks;
+    const uint64_t h = mix64(key ^ v.seed);
+    t = (uint32_t)((h >> 44) & ((1u << v.tag_bits) - 1u));
+    if (t < 2) t += 2;
+    b1 = h & (nb - 1);
+    uint64_t g = mix64((uint64_t)t) & (nb - 1);
+    if (!g) g = 1;
+    b2 = b1 ^ g;
+}
+
+}  // namespace gf_device
+
+// Point-mode TCF insert (Alg. 1): into b1 while it holds fewer than 3B/4
+// live tags (the shortcut), else into the block with fewer live tags, then
+// the other, then an empty entry of the backing bucket. FILTER_KEY_OK, or
+// FILTER_KEY_FULL (also counted in the filter's counters); FILTER_KEY_FULL
+// without counting for a view that is not a point-mode TCF.
+__device__ __forceinline__ int gf_device_tcf_insert(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    if (v.kind != FILTER_TCF || v.mode != FILTER_MODE_POINT) return FILTER_KEY_FULL;
+    uint64_t b1, b2;
+    uint32_t t;
+    tcf_key(v, key, b1, b2, t);
+    const uint32_t f = v.tag_bits;
+    uint8_t *blocks = static_cast<uint8_t *>(v.table);
+    bool done = false;
+    if (tcf_live(blocks, b1, f) < (int)(3 * (256 / f) / 4)) done = tcf_put(blocks, b1, t, f, v.counters);
+    if (!done) {
+        const uint64_t first = tcf_live(blocks, b1, f) <= tcf_live(blocks, b2, f) ? b1 : b2;
+        done = tcf_put(blocks, first, t, f, v.counters) || tcf_put(blocks, first == b1 ? b2 : b1, t, f, v.counters);
+    }
+    if (!done) {
+        const uint64_t e = ((b1 < b2 ? b1 : b2) << f) | t;
+        unsigned long long *p =
+            static_cast<unsigned long long *>(v.aux) + (((mix64(e) >> 32) * v.n_aux) >> 32) * 8;
+        for (int s = 0; s < 8 && !done; s++)
+            if (atomicCAS(p + s, 0ull, (unsigned long long)e) == 0ull) done = true;
+        if (done) atomicAdd(v.counters + 2, 1ull);
+    }
+    if (done) return FILTER_KEY_OK;
+    atomicAdd(v.counters + 1, 1ull);
+    atomicOr(v.counters, 1ull << FILTER_ERR_FULL);
+    return FILTER_KEY_FULL;
+}
+
+// Point-mode TCF remove: one copy of the key's tag in b1, else b2, becomes
+// TOMBSTONE, else its entry leaves the backing bucket. FILTER_KEY_OK or
+// FILTER_KEY_NOT_FOUND (also for a view that is not a point-mode TCF).
+__device__ __forceinline__ int gf_device_tcf_remove(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    if (v.kind != FILTER_TCF || v.mode != FILTER_MODE_POINT) return FILTER_KEY_NOT_FOUND;
+    uint64_t b1, b2;
+    uint32_t t;
+    tcf_key(v, key, b1, b2, t);
+    const uint32_t f = v.tag_bits;
+    uint8_t *blocks = static_cast<uint8_t *>(v.table);
+    bool done = tcf_take(blocks, b1, t, f, v.counters) || tcf_take(blocks, b2, t, f, v.counters);
+    if (!done) {
+        const uint64_t e = ((b1 < b2 ? b1 : b2) << f) | t;
+        unsigned long long *p =
+            static_cast<unsigned long long *>(v.aux) + (((mix64(e) >> 32) * v.n_aux) >> 32) * 8;
+        for (int s = 0; s < 8 && !done; s++)
+            if (atomicCAS(p + s, (unsigned long long)e, 0ull) == (unsigned long long)e) done = true;
+        if (done) atomicAdd(v.counters + 2, ~0ull);
+    }
+    return done ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;
 }
 
 // How many copies of key the GQF counts (0 if absent; at least the true

@@ -60,9 +60,9 @@ class FilterStats(C.Structure):
 class FilterDeviceView(C.Structure):
     """The filter_device_view of include/gpufilter.h (pass it by value to a
     kernel that includes include/gpufilter_device.cuh)."""
-    _fields_ = [("kind", C.c_uint32), ("tag_bits", C.c_uint32), ("q", C.c_uint32), ("reserved", C.c_uint32),
+    _fields_ = [("kind", C.c_uint32), ("tag_bits", C.c_uint32), ("q", C.c_uint32), ("mode", C.c_uint32),
                 ("seed", C.c_uint64), ("table", C.c_void_p), ("aux", C.c_void_p), ("n_blocks", C.c_uint64),
-                ("n_aux", C.c_uint64), ("backing_used", C.c_void_p)]
+                ("n_aux", C.c_uint64), ("counters", C.c_void_p)]
 
 
 class FilterRequest(C.Structure):

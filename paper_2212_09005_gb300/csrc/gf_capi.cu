@@ -141,16 +141,20 @@ int filter_get_device_view(filter_t *f, filter_device_view *out)
 {
     if (!valid(f) || !out) return FILTER_ERR_ARG;
     std::memset(out, 0, sizeof(*out));
+    static_assert(offsetof(gf::DevCounters, status) == 0 && offsetof(gf::DevCounters, failed) == 8 &&
+                      offsetof(gf::DevCounters, backing) == 16,
+                  "the device view exposes the first three counters");
     out->kind = f->cfg.kind;
     out->tag_bits = f->cfg.tag_bits;
     out->seed = f->cfg.hash_seed;
+    out->counters = &f->ctr->status;
     if (f->cfg.kind == FILTER_TCF) {
         const TcfState &T = f->tcf;
+        out->mode = T.mode;
         out->table = T.blocks;
         out->aux = T.bk;
         out->n_blocks = T.G.nb;
         out->n_aux = T.G.nbk;
-        out->backing_used = &f->ctr->backing;
     } else {
         const GqfState &Q = f->gqf;
         out->q = Q.q;

@@ -1,4 +1,4 @@
-// A caller's own kernel using the device-side point queries of
+// A caller's own kernels using the device-side point operations of
 // include/gpufilter_device.cuh on filters built through the C ABI: one key
 // per thread, the view passed by value.
 #include <cuda_runtime.h>
@@ -25,5 +25,23 @@ extern "C" int device_query_example(const filter_device_view *v, const uint64_t 
     if (!v || n == 0) return 0;
     const unsigned grid = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
     device_query_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, found, counts);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}
+
+__global__ void device_update_kernel(filter_device_view v, const uint64_t *keys, uint64_t n, int remove,
+                                     uint8_t *status)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const int st = remove ? gf_device_tcf_remove(v, keys[i]) : gf_device_tcf_insert(v, keys[i]);
+        if (status) status[i] = (uint8_t)st;
+    }
+}
+
+extern "C" int device_update_example(const filter_device_view *v, const uint64_t *keys, uint64_t n, int remove,
+                                     uint8_t *status, void *stream)
+{
+    if (!v || n == 0) return 0;
+    const unsigned grid = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    device_update_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, remove, status);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
