@@ -169,6 +169,25 @@ typedef struct filter_device_view {
 
 int filter_get_device_view(filter_t *f, filter_device_view *out);
 
+/*
+ * filter_gqf_enumerate: the GQF's distinct fingerprints and their counts, in
+ * ascending fingerprint order (the table is walked run by run, as counts read
+ * it). *n_groups (host) receives the number of groups; the first min(cap,
+ * *n_groups) are written to d_fingerprints / d_counts (device, cap entries
+ * each). cap = 0 only counts. Synchronises `stream` once; takes (and returns)
+ * (64-slot blocks + 1) x 4 bytes plus scan scratch of stream-ordered device
+ * memory for the call. FILTER_ERR_ARG for a TCF.
+ *
+ * filter_gqf_keys_of: the keys whose fingerprints these are, by inverting the
+ * fingerprint hash (Sec. 5.1: it is a bijection on p = q + r bits). Exact for
+ * keys below 2^p; larger keys were folded to p bits first and come back as
+ * that fold. With filter_gqf_enumerate this lists a GQF's contents, e.g. to
+ * re-insert them into a larger filter (resize).
+ */
+int filter_gqf_enumerate(filter_t *f, uint64_t *d_fingerprints, uint64_t *d_counts, uint64_t cap,
+                         uint64_t *n_groups, void *stream);
+int filter_gqf_keys_of(filter_t *f, const uint64_t *d_fingerprints, uint64_t n, uint64_t *d_keys, void *stream);
+
 /* filter_export_size: bytes of the table image (see the layout above). */
 int filter_export_size(filter_t *f, uint64_t *nbytes);
 

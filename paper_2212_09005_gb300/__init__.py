@@ -33,6 +33,7 @@ STATUS_FULL, STATUS_TIMEOUT, STATUS_INTERNAL = 1 << ERR_FULL, 1 << ERR_TIMEOUT, 
 EXPORTS = [
     "filter_create", "filter_destroy", "filter_clear", "filter_insert", "filter_query",
     "filter_remove", "filter_count", "filter_get_stats", "filter_get_device_view", "filter_export_size",
+    "filter_gqf_enumerate", "filter_gqf_keys_of",
     "filter_export", "filter_import", "filter_error_string",
     "filter_trace_enable", "filter_trace_reset", "filter_trace_summary",
     "filter_gqf_insert_noalloc",
@@ -204,6 +205,24 @@ class Filter:
 
     def clear(self, stream=None):
         _check(lib().filter_clear(self._h, _stream(stream)), "filter_clear")
+
+    def enumerate(self, stream=None):
+        """GQF: (fingerprints, counts) of every group, ascending, as int64 CUDA tensors."""
+        import torch
+
+        n = C.c_uint64()
+        _check(lib().filter_gqf_enumerate(self._h, None, None, 0, C.byref(n), _stream(stream)), "filter_gqf_enumerate")
+        fps = torch.empty(n.value, dtype=torch.int64, device="cuda")
+        cnt = torch.empty(n.value, dtype=torch.int64, device="cuda")
+        m = C.c_uint64()
+        _check(lib().filter_gqf_enumerate(self._h, _dptr(fps, 8), _dptr(cnt, 8), n.value, C.byref(m),
+                                          _stream(stream)), "filter_gqf_enumerate")
+        return fps, cnt
+
+    def keys_of(self, fingerprints, keys, stream=None):
+        """GQF: the keys (below 2^(q + r)) whose fingerprints these are."""
+        _check(lib().filter_gqf_keys_of(self._h, _dptr(fingerprints, 8), fingerprints.numel(), _dptr(keys, 8),
+                                        _stream(stream)), "filter_gqf_keys_of")
 
     def device_view(self) -> "FilterDeviceView":
         """Table pointers and geometry for device-side point queries; take it

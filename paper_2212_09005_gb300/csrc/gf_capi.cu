@@ -166,6 +166,20 @@ int filter_get_device_view(filter_t *f, filter_device_view *out)
     return FILTER_OK;
 }
 
+int filter_gqf_enumerate(filter_t *f, uint64_t *d_fingerprints, uint64_t *d_counts, uint64_t cap,
+                         uint64_t *n_groups, void *stream)
+{
+    if (!valid(f) || !n_groups || f->cfg.kind != FILTER_GQF || (cap && (!d_fingerprints || !d_counts)))
+        return FILTER_ERR_ARG;
+    return gf::gqf_enumerate(f, d_fingerprints, d_counts, cap, n_groups, as_stream(stream));
+}
+
+int filter_gqf_keys_of(filter_t *f, const uint64_t *d_fingerprints, uint64_t n, uint64_t *d_keys, void *stream)
+{
+    if (!valid(f) || f->cfg.kind != FILTER_GQF || (n && (!d_fingerprints || !d_keys))) return FILTER_ERR_ARG;
+    return gf::gqf_unhash(f, d_fingerprints, n, d_keys, as_stream(stream));
+}
+
 int filter_export_size(filter_t *f, uint64_t *nbytes)
 {
     if (!valid(f) || !nbytes) return FILTER_ERR_ARG;

@@ -1393,80 +1393,125 @@ __global__ void gqf_account_full(DevCounters *ctr, const uint32_t *ustart, uint6
 // count / query
 // ---------------------------------------------------------------------------
 // stored count of fingerprint fp (0 if absent)
+// The run of occupied quotient x: it ends at the d-th run end from the
+// offset of x's block, d counting the block's occupied quotients up to x
+// (bit 0 excluded, which the offset itself covers); it starts one past the
+// previous run end, or at x. False if the run ends could not be found.
+__device__ __forceinline__ bool locate_run(uint64_t x, const Meta *__restrict__ meta, uint64_t nblk, long long &start,
+                                           long long &end)
+{
+    const uint64_t j = x >> 6;
+    const unsigned long long occ = __ldg(&meta[j].occ);
+    const long long base = (long long)(64 * j) + (long long)__ldg(&meta[j].off);
+    const unsigned sh = (unsigned)(x & 63);
+    const unsigned long long upto = (sh == 63) ? ~0ull : ((1ull << (sh + 1)) - 1ull);
+    int d = __popcll(occ & upto & ~1ull);
+    end = base;
+    if (d > 0) {
+        long long w = base >> 6;
+        unsigned bsh = (unsigned)(base & 63);
+        unsigned long long bits = (bsh == 63) ? 0ull : (__ldg(&meta[w].rend) & (~0ull << (bsh + 1)));
+        while (true) {
+            int pc = __popcll(bits);
+            if (pc >= d) {
+                for (int k = 1; k < d; k++) bits &= bits - 1;
+                end = 64 * w + __ffsll((long long)bits) - 1;
+                break;
+            }
+            d -= pc;
+            if (++w >= (long long)nblk) return false;
+            bits = __ldg(&meta[w].rend);
+        }
+    }
+    // start: one past the last runend in [x, end - 1], else x
+    start = (long long)x;
+    long long p = end - 1;
+    while (p >= (long long)x) {
+        long long w = p >> 6;
+        unsigned long long bits = __ldg(&meta[w].rend);
+        unsigned pb = (unsigned)(p & 63);
+        bits &= (pb == 63) ? ~0ull : ((1ull << (pb + 1)) - 1ull);
+        if (64 * w < (long long)x) bits &= ~0ull << (x & 63);
+        if (bits) {
+            start = 64 * w + 63 - __clzll((long long)bits) + 1;
+            break;
+        }
+        p = 64 * w - 1;
+    }
+    return true;
+}
+
+// the group at slot q of a run ending at `end`: remainder, count, slots used
+template <int R>
+__device__ __forceinline__ uint32_t group_at(const uint8_t *__restrict__ rem, long long q, long long end,
+                                             uint64_t &cnt, uint32_t &len)
+{
+    const uint32_t s = rd_slot<R>(rem, (uint64_t)q);
+    cnt = 1;
+    len = 1;
+    if (q + 2 <= end && rd_slot<R>(rem, (uint64_t)(q + 1)) == s) {
+        uint32_t nd = rd_slot<R>(rem, (uint64_t)(q + 2));
+        if (q + 2 + (long long)nd > end) nd = (uint32_t)(end - q - 2);
+        uint64_t acc = 0;
+        for (uint32_t dd = 0; dd < nd; dd++) acc = (acc << R) | rd_slot<R>(rem, (uint64_t)(q + 3 + dd));
+        cnt = acc + 2;
+        len = 3 + nd;
+    }
+    return s;
+}
+
 template <int R>
 __device__ __forceinline__ uint64_t count_fp(const uint64_t fp, const Meta *__restrict__ meta,
                                              const uint8_t *__restrict__ rem, const uint64_t nblk)
 {
     const uint64_t x = fp >> R;
     const uint32_t v = (uint32_t)(fp & ((1ull << R) - 1ull));
-    const uint64_t j = x >> 6;
-    const ulonglong2 or_ = __ldg(reinterpret_cast<const ulonglong2 *>(meta + j));
-    const unsigned long long occ = or_.x;
-    uint64_t c = 0;
-    if ((occ >> (x & 63)) & 1ull) {
-        const long long base = (long long)(64 * j) + (long long)__ldg(&meta[j].off);
-        const unsigned sh = (unsigned)(x & 63);
-        const unsigned long long upto = (sh == 63) ? ~0ull : ((1ull << (sh + 1)) - 1ull);
-        int d = __popcll(occ & upto & ~1ull);
-        long long end = base;
-        if (d > 0) {
-            long long w = base >> 6;
-            unsigned bsh = (unsigned)(base & 63);
-            unsigned long long bits = (bsh == 63) ? 0ull : (__ldg(&meta[w].rend) & (~0ull << (bsh + 1)));
-            while (true) {
-                int pc = __popcll(bits);
-                if (pc >= d) {
-                    for (int k = 1; k < d; k++) bits &= bits - 1;
-                    end = 64 * w + __ffsll((long long)bits) - 1;
-                    break;
-                }
-                d -= pc;
-                if (++w >= (long long)nblk) {
-                    end = -1;
-                    break;
-                }
-                bits = __ldg(&meta[w].rend);
-            }
-        }
-        if (end >= 0) {
-            // start: one past the last runend in [x, end - 1], else x
-            long long start = (long long)x;
-            long long p = end - 1;
-            while (p >= (long long)x) {
-                long long w = p >> 6;
-                unsigned long long bits = __ldg(&meta[w].rend);
-                unsigned pb = (unsigned)(p & 63);
-                bits &= (pb == 63) ? ~0ull : ((1ull << (pb + 1)) - 1ull);
-                if (64 * w < (long long)x) bits &= ~0ull << (x & 63);
-                if (bits) {
-                    start = 64 * w + 63 - __clzll((long long)bits) + 1;
-                    break;
-                }
-                p = 64 * w - 1;
-            }
-            long long q = start;
-            while (q <= end) {
-                uint32_t s = rd_slot<R>(rem, (uint64_t)q);
-                uint64_t cc = 1;
-                long long step = 1;
-                if (q + 2 <= end && rd_slot<R>(rem, (uint64_t)(q + 1)) == s) {
-                    uint32_t nd = rd_slot<R>(rem, (uint64_t)(q + 2));
-                    if (q + 2 + (long long)nd > end) nd = (uint32_t)(end - q - 2);
-                    uint64_t acc = 0;
-                    for (uint32_t dd = 0; dd < nd; dd++) acc = (acc << R) | rd_slot<R>(rem, (uint64_t)(q + 3 + dd));
-                    cc = acc + 2;
-                    step = 3 + nd;
-                }
-                if (s == v) {
-                    c = cc;
-                    break;
-                }
-                if (s > v) break;
-                q += step;
-            }
-        }
+    const unsigned long long occ = __ldg(&meta[x >> 6].occ);
+    if (!((occ >> (x & 63)) & 1ull)) return 0;
+    long long start, end;
+    if (!locate_run(x, meta, nblk, start, end)) return 0;
+    for (long long q = start; q <= end;) {
+        uint64_t cc;
+        uint32_t len;
+        const uint32_t s = group_at<R>(rem, q, end, cc, len);
+        if (s == v) return cc;
+        if (s > v) return 0;
+        q += len;
     }
-    return c;
+    return 0;
+}
+
+// Enumeration: one thread per 64-slot block walks the runs of its occupied
+// quotients in order and their groups in remainder order, so the groups come
+// out in fingerprint order. COUNT pass: groups per block; WRITE pass: the
+// groups at their scanned positions (those below cap).
+template <int R, bool WRITE>
+__global__ void gqf_enum_kernel(const Meta *__restrict__ meta, const uint8_t *__restrict__ rem, uint64_t nblk,
+                                uint64_t N, uint32_t *per_block, uint64_t *fps, uint64_t *counts, uint64_t cap)
+{
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < nblk; j += (uint64_t)gridDim.x * blockDim.x) {
+        unsigned long long occ = __ldg(&meta[j].occ);
+        uint64_t k = WRITE ? per_block[j] : 0;
+        while (occ) {
+            const uint64_t x = 64 * j + (uint64_t)(__ffsll((long long)occ) - 1);
+            occ &= occ - 1;
+            if (x >= N) break;
+            long long start, end;
+            if (!locate_run(x, meta, nblk, start, end)) break;
+            for (long long q = start; q <= end;) {
+                uint64_t cc;
+                uint32_t len;
+                const uint32_t s = group_at<R>(rem, q, end, cc, len);
+                if (WRITE && k < cap) {
+                    fps[k] = (x << R) | s;
+                    counts[k] = cc;
+                }
+                k++;
+                q += len;
+            }
+        }
+        if (!WRITE) per_block[j] = (uint32_t)k;
+    }
 }
 
 template <int R>
@@ -1820,6 +1865,82 @@ int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uin
         else gqf_count_kernel<16><<<g, 256, 0, st>>>(keys, n, Q.H, meta, Q.rem[Q.cur], Q.nblk, counts, found);
     }
     GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+// The fingerprint is invertible on p bits (Sec. 5.1): every xor-shift by
+// s >= p/2 is its own inverse and every product by an odd constant is undone
+// by the constant's inverse mod 2^p. A key below 2^p folds to itself, so it
+// is recovered exactly from its fingerprint.
+__global__ void gqf_unhash_kernel(const uint64_t *__restrict__ fps, uint64_t n, PHash H, uint64_t inv1, uint64_t inv2,
+                                  uint64_t *keys)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t x = fps[i] & H.mask;
+        x ^= x >> H.s;
+        x = (x * inv2) & H.mask;
+        x ^= x >> H.s;
+        x = (x * inv1) & H.mask;
+        x ^= x >> H.s;
+        keys[i] = x ^ H.seed;
+    }
+}
+
+static uint64_t inverse_odd(uint64_t c)
+{
+    uint64_t v = c;  // Newton: each step doubles the correct low bits
+    for (int k = 0; k < 6; k++) v *= 2 - c * v;
+    return v;
+}
+
+int gqf_unhash(filter *F, const uint64_t *fps, uint64_t n, uint64_t *keys, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = F->gqf;
+    {
+        gf::TraceScope ts_("gqf_unhash_kernel", n, st);
+        gqf_unhash_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(fps, n, Q.H, inverse_odd(0xff51afd7ed558ccdull),
+                                                                 inverse_odd(0xc4ceb9fe1a85ec53ull), keys);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+int gqf_enumerate(filter *F, uint64_t *fps, uint64_t *counts, uint64_t cap, uint64_t *n_out, cudaStream_t st)
+{
+    GqfState &Q = F->gqf;
+    const Meta *meta = reinterpret_cast<const Meta *>(Q.meta[Q.cur]);
+    // per-block group counts and their scan: stream-ordered scratch for the call
+    uint32_t *per = nullptr;
+    uint64_t *stmp = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&per), (Q.nblk + 1) * sizeof(uint32_t), st) != cudaSuccess ||
+        cudaMallocAsync(reinterpret_cast<void **>(&stmp), scan_tmp_words(Q.nblk + 1) * sizeof(uint64_t), st) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        if (per) cudaFreeAsync(per, st);
+        return FILTER_ERR_OOM;
+    }
+    const int g = grid_for(Q.nblk, 256, 8);
+    {
+        gf::TraceScope ts_("gqf_enum_kernel", Q.nblk, st);
+        if (Q.r == 8) gqf_enum_kernel<8, false><<<g, 256, 0, st>>>(meta, Q.rem[Q.cur], Q.nblk, Q.N, per, nullptr, nullptr, 0);
+        else gqf_enum_kernel<16, false><<<g, 256, 0, st>>>(meta, Q.rem[Q.cur], Q.nblk, Q.N, per, nullptr, nullptr, 0);
+    }
+    cudaMemsetAsync(per + Q.nblk, 0, 4, st);
+    exclusive_scan_u32(per, per, Q.nblk + 1, stmp, F->ctr, st);
+    uint32_t total = 0;
+    cudaMemcpyAsync(&total, per + Q.nblk, 4, cudaMemcpyDeviceToHost, st);
+    const cudaError_t e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && cap && fps && counts) {
+        gf::TraceScope ts_("gqf_enum_kernel", Q.nblk, st);
+        if (Q.r == 8) gqf_enum_kernel<8, true><<<g, 256, 0, st>>>(meta, Q.rem[Q.cur], Q.nblk, Q.N, per, fps, counts, cap);
+        else gqf_enum_kernel<16, true><<<g, 256, 0, st>>>(meta, Q.rem[Q.cur], Q.nblk, Q.N, per, fps, counts, cap);
+    }
+    cudaFreeAsync(stmp, st);
+    cudaFreeAsync(per, st);
+    GF_CUDA(e);
+    GF_CUDA(cudaGetLastError());
+    *n_out = total;
     return FILTER_OK;
 }
 

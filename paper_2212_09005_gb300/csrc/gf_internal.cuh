@@ -378,4 +378,6 @@ int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uin
               cudaStream_t st);
 uint64_t gqf_image_bytes(const filter *F);
 int gqf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st);
+int gqf_enumerate(filter *F, uint64_t *fps, uint64_t *counts, uint64_t cap, uint64_t *n_out, cudaStream_t st);
+int gqf_unhash(filter *F, const uint64_t *fps, uint64_t n, uint64_t *keys, cudaStream_t st);
 }  // namespace gf

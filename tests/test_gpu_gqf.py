@@ -355,3 +355,55 @@ def test_inplace_insert_and_delete_alternating(gf, oracle):
             getattr(G, op)(dev_u64(b), st)
             assert np.array_equal(host(st), st_o), (j, op)
             assert first_diff(G.export(), O.export()) is None, (j, op)
+
+
+def test_enumerate_equals_oracle_groups(gf, oracle):
+    """The groups of the table in fingerprint order, with their counts, equal
+    the oracle's, for 8- and 16-bit remainders, after inserts and deletes;
+    an empty filter has none; a smaller cap writes a prefix."""
+    import torch
+
+    for q, r in ((16, 8), (15, 16)):
+        keys = W.zipf_keys(91 + r, int(0.5 * (1 << q)), 1.0, 1 << 22)
+        O = oracle.GQF(q, r, seed=31)
+        G = gf.GQF(q, r, seed=31, max_batch=len(keys))
+        f0, c0 = G.enumerate()
+        assert f0.numel() == 0 and c0.numel() == 0
+        for op, b in (("ins", keys), ("rem", keys[::4])):
+            (O.insert if op == "ins" else O.remove)(b)
+            (G.insert if op == "ins" else G.remove)(dev_u64(b))
+            f, c = G.enumerate()
+            of, oc = O.groups()
+            assert np.array_equal(host(f), of) and np.array_equal(host(c), oc)
+        part = torch.empty(100, dtype=torch.int64, device="cuda")
+        partc = torch.empty(100, dtype=torch.int64, device="cuda")
+        import ctypes
+        m = ctypes.c_uint64()
+        assert gf.lib().filter_gqf_enumerate(G._h, ctypes.c_void_p(part.data_ptr()), ctypes.c_void_p(partc.data_ptr()),
+                                             100, ctypes.byref(m), None) == 0
+        assert m.value == len(of)
+        assert np.array_equal(host(part), of[:100]) and np.array_equal(host(partc), oc[:100])
+
+
+def test_keys_of_recovers_keys_and_resizes(gf, oracle):
+    """Keys below 2^p come back exactly from the enumerated fingerprints;
+    re-inserting them with their counts into a filter twice as large gives
+    the same counts there (a resize)."""
+    import torch
+
+    q, r = 14, 8
+    keys = W.zipf_keys(93, 6000, 1.0, 1 << 20)  # keys < 2^20 <= 2^(q + r)
+    G = gf.GQF(q, r, seed=37, max_batch=len(keys))
+    G.insert(dev_u64(keys))
+    f, c = G.enumerate()
+    back = torch.empty_like(f)
+    G.keys_of(f, back)
+    u, uc = np.unique(keys, return_counts=True)
+    got_keys, got_counts = host(back), host(c)
+    order = np.argsort(got_keys)
+    assert np.array_equal(got_keys[order], u) and np.array_equal(got_counts[order], uc.astype(np.uint64))
+    big = gf.GQF(q + 1, r, seed=41, max_batch=len(keys))
+    big.insert(dev_u64(np.repeat(got_keys, got_counts.astype(np.int64))))
+    cnt = zeros_u64(len(u))
+    big.count(dev_u64(u), cnt)
+    assert np.array_equal(host(cnt), uc.astype(np.uint64))
