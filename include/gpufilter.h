@@ -6,7 +6,8 @@
  * C ABI. Every pointer argument named d_* is a device pointer; host_* is host
  * memory. Streams are cudaStream_t values passed as void* (NULL = the legacy
  * default stream). All calls except filter_create, filter_destroy,
- * filter_get_stats, filter_export and filter_import are asynchronous: they
+ * filter_get_stats, filter_export, filter_import and filter_gqf_enumerate
+ * are asynchronous (filter_get_device_view does not touch the device): they
  * enqueue kernels on the stream and return; the caller's buffers must stay
  * valid until the stream reaches the call. Exceptions: GQF inserts and
  * removes synchronise the stream to read the number of distinct fingerprints
