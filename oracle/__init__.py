@@ -44,10 +44,14 @@ def _declare(L):
 
     L.or_tcf_new.restype = C.c_void_p
     L.or_tcf_new.argtypes = [C.c_uint, C.c_uint, C.c_uint64]
+    L.or_tcf_new_values.restype = C.c_void_p
+    L.or_tcf_new_values.argtypes = [C.c_uint, C.c_uint, C.c_uint, C.c_uint64]
     L.or_tcf_free.argtypes = [C.c_void_p]
     L.or_tcf_keyinfo.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u64p, _u64p, _u32p]
     L.or_tcf_insert.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p, _u8p, _u64p]
     L.or_tcf_query.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p]
+    L.or_tcf_insert_values.argtypes = [C.c_void_p, _u64p, _u8p, C.c_uint64, _u8p, _u8p, _u64p]
+    L.or_tcf_query_values.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p]
     L.or_tcf_remove.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p]
     L.or_tcf_export_size.restype = C.c_uint64
     L.or_tcf_export_size.argtypes = [C.c_void_p]
@@ -126,15 +130,16 @@ def mix_p_many(a, p: int):
 
 
 class TCF:
-    """Deterministic bulk two-choice filter (see tcf.c for the specification)."""
+    """Deterministic bulk two-choice filter (see tcf.c for the specification).
+    value_bits > 0 gives each slot a value of that many bits below the tag."""
 
-    def __init__(self, log2_slots: int, tag_bits: int = 16, seed: int = 0):
-        self._h = lib().or_tcf_new(log2_slots, tag_bits, seed)
+    def __init__(self, log2_slots: int, tag_bits: int = 16, seed: int = 0, value_bits: int = 0):
+        self._h = lib().or_tcf_new_values(log2_slots, tag_bits, value_bits, seed)
         if not self._h:
             raise ValueError("bad TCF geometry")
-        g = np.zeros(6, dtype=np.uint64)
+        g = np.zeros(7, dtype=np.uint64)
         lib().or_tcf_geometry(self._h, _p(g, _u64p))
-        self.nb, self.B, self.f, self.tsc, self.nbk, self.W = (int(v) for v in g)
+        self.nb, self.B, self.f, self.tsc, self.nbk, self.W, self.v = (int(v) for v in g)
         self.log2_slots, self.seed = log2_slots, seed
 
     def __del__(self):
@@ -156,17 +161,29 @@ class TCF:
         b1, b2, t = self.keyinfo(keys)
         return (np.minimum(b1, b2) << np.uint64(self.f)) | t.astype(np.uint64)
 
-    def insert(self, keys, trace: bool = False):
+    def insert(self, keys, trace: bool = False, values=None):
         keys = _u64(keys)
         st = np.zeros(keys.size, np.uint8)
+        vp = None
+        if values is not None:
+            values = np.ascontiguousarray(values, dtype=np.uint8)
+            assert values.size == keys.size
+            vp = _p(values, _u8p)
         if trace:
             ph = np.zeros(keys.size, np.uint8)
             wh = np.zeros(keys.size, np.uint64)
-            lib().or_tcf_insert(self._h, _p(keys, _u64p), keys.size, _p(st, _u8p), _p(ph, _u8p),
-                                _p(wh, _u64p))
+            lib().or_tcf_insert_values(self._h, _p(keys, _u64p), vp, keys.size, _p(st, _u8p), _p(ph, _u8p),
+                                       _p(wh, _u64p))
             return st, ph, wh
-        lib().or_tcf_insert(self._h, _p(keys, _u64p), keys.size, _p(st, _u8p), None, None)
+        lib().or_tcf_insert_values(self._h, _p(keys, _u64p), vp, keys.size, _p(st, _u8p), None, None)
         return st
+
+    def query_values(self, keys):
+        """Smallest value stored with each key's fingerprint, 0xFF if none."""
+        keys = _u64(keys)
+        out = np.zeros(keys.size, np.uint8)
+        lib().or_tcf_query_values(self._h, _p(keys, _u64p), keys.size, _p(out, _u8p))
+        return out
 
     def query(self, keys):
         keys = _u64(keys)

@@ -29,6 +29,7 @@ void or_mix_p_many(const uint64_t *in, uint64_t *out, uint64_t n, unsigned p);
 /* ---- TCF (tcf.c) ---- */
 typedef struct or_tcf or_tcf;
 or_tcf *or_tcf_new(unsigned log2_slots, unsigned tag_bits, uint64_t seed);
+or_tcf *or_tcf_new_values(unsigned log2_slots, unsigned tag_bits, unsigned value_bits, uint64_t seed);
 void or_tcf_free(or_tcf *T);
 void or_tcf_keyinfo(const or_tcf *T, const uint64_t *keys, uint64_t n,
                     uint64_t *b1, uint64_t *b2, uint32_t *tag);
@@ -36,13 +37,16 @@ void or_tcf_keyinfo(const or_tcf *T, const uint64_t *keys, uint64_t n,
    3 backing, 4 rejected (full). where: block or backing bucket index. */
 void or_tcf_insert(or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *status,
                    uint8_t *phase, uint64_t *where);
+void or_tcf_insert_values(or_tcf *T, const uint64_t *keys, const uint8_t *values, uint64_t n,
+                          uint8_t *status, uint8_t *phase, uint64_t *where);
 void or_tcf_query(const or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *found);
+void or_tcf_query_values(const or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *values);
 void or_tcf_remove(or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *status);
 uint64_t or_tcf_export_size(const or_tcf *T);
 void or_tcf_export(const or_tcf *T, uint8_t *buf);
 uint64_t or_tcf_backing_count(const or_tcf *T);
 uint64_t or_tcf_stored_count(const or_tcf *T);
-void or_tcf_geometry(const or_tcf *T, uint64_t *out6); /* nb, B, f, tsc, nbk, W */
+void or_tcf_geometry(const or_tcf *T, uint64_t *out7); /* nb, B, f, tsc, nbk, W, v */
 
 /* ---- GQF (gqf.c) ---- */
 typedef struct or_gqf or_gqf;

@@ -37,6 +37,22 @@
  *
  *  Query: tag in block b1, or in block b2, or e in its bucket.
  *
+ *  Values (Sec. 1 and Sec. 4 list associating small values with items as a
+ *  TCF feature; R: the layout below). With v value bits (v <= f / 2, and
+ *  v <= 7 so that 0xFF stays free to answer "absent"), a slot of f bits
+ *  holds the (f - v)-bit tag in its high bits and the value in its low bits,
+ *  so that tag 0 and 1 still never occur and a slot is EMPTY or TOMBSTONE only
+ *  when it is 0 or 1. The tag is bits 44.. of h, f - v bits wide; g and the
+ *  bucket of an entry depend on the tag and the blocks only (the value bits
+ *  are cleared before the bucket hash), so a key's placement never depends on
+ *  its value. Candidates of a block are taken in (slot, batch index) order,
+ *  slot = tag << v | value, and blocks and buckets stay sorted by slot.
+ *  Matching (query, delete) compares the tag part only. A value query answers
+ *  the smallest value among all stored copies of the key's fingerprint
+ *  (blocks b1, b2 and its backing bucket), or 0xFF when there is none; a
+ *  delete removes the first copy in b1, else in b2, else in the bucket, which
+ *  in a sorted block or bucket is the one with the smallest value.
+ *
  *  Deterministic bulk delete (Sec. 6.4 deletes one copy; R: phases as insert):
  *   1  block b1 removes one copy of the tag for each of its candidates, in
  *      (tag, batch index) order, while a copy is left;
@@ -53,6 +69,8 @@
 
 struct or_tcf {
     unsigned f, B, tsc;
+    unsigned vb;     /* value bits in each slot */
+    uint64_t vmask;  /* the value part of a slot or entry */
     uint64_t nb, nbk, seed;
     uint16_t *tags; /* nb * B */
     uint64_t *bk;   /* nbk * BK_W */
@@ -85,12 +103,20 @@ static int u64_cmp(const void *a, const void *b)
 
 or_tcf *or_tcf_new(unsigned log2_slots, unsigned tag_bits, uint64_t seed)
 {
+    return or_tcf_new_values(log2_slots, tag_bits, 0, seed);
+}
+
+or_tcf *or_tcf_new_values(unsigned log2_slots, unsigned tag_bits, unsigned value_bits, uint64_t seed)
+{
     if (tag_bits != 8 && tag_bits != 16) return NULL;
+    if (value_bits > tag_bits / 2 || value_bits > 7) return NULL; /* 0xFF answers "absent" */
     unsigned B = 256u / tag_bits;
     unsigned lb = (B == 16) ? 4 : 5;
     if (log2_slots < lb + 1 || log2_slots > 40) return NULL;
     or_tcf *T = (or_tcf *)calloc(1, sizeof(or_tcf));
     T->f = tag_bits;
+    T->vb = value_bits;
+    T->vmask = (1ULL << value_bits) - 1ULL;
     T->B = B;
     T->tsc = 3 * B / 4;
     T->nb = 1ULL << (log2_slots - lb);
@@ -124,18 +150,19 @@ void or_tcf_geometry(const or_tcf *T, uint64_t *o)
     o[3] = T->tsc;
     o[4] = T->nbk;
     o[5] = BK_W;
+    o[6] = T->vb;
 }
 
 static void keyinfo1(const or_tcf *T, uint64_t key, uint64_t *b1, uint64_t *b2, uint32_t *t)
 {
     uint64_t h = or_mix64(key ^ T->seed);
-    uint64_t tag = (h >> 44) & ((1ULL << T->f) - 1ULL);
+    uint64_t tag = (h >> 44) & ((1ULL << (T->f - T->vb)) - 1ULL);
     if (tag < 2) tag += 2;
     uint64_t g = or_mix64(tag) & (T->nb - 1);
     if (g == 0) g = 1;
     *b1 = h & (T->nb - 1);
     *b2 = *b1 ^ g;
-    *t = (uint32_t)tag;
+    *t = (uint32_t)(tag << T->vb); /* the slot with value 0 */
 }
 
 void or_tcf_keyinfo(const or_tcf *T, const uint64_t *keys, uint64_t n, uint64_t *b1,
@@ -152,7 +179,14 @@ static uint64_t entry_of(const or_tcf *T, uint64_t b1, uint64_t b2, uint32_t t)
 
 static uint64_t bucket_of(const or_tcf *T, uint64_t e)
 {
+    e &= ~T->vmask;
     return ((or_mix64(e) >> 32) * T->nbk) >> 32;
+}
+
+/* slot or entry x holds tag (or entry) t, whatever its value */
+static int same_tag(const or_tcf *T, uint64_t x, uint64_t t)
+{
+    return x != 0 && (x & ~T->vmask) == t;
 }
 
 static unsigned block_fill(const or_tcf *T, uint64_t b)
@@ -176,14 +210,23 @@ static void block_put(or_tcf *T, uint64_t b, uint32_t t)
 static int block_has(const or_tcf *T, uint64_t b, uint32_t t)
 {
     for (unsigned s = 0; s < T->B; s++)
-        if (T->tags[b * T->B + s] == t) return 1;
+        if (same_tag(T, T->tags[b * T->B + s], t)) return 1;
     return 0;
+}
+
+/* smallest value stored with tag t in block b, folded into *best */
+static void block_min_value(const or_tcf *T, uint64_t b, uint32_t t, unsigned *best)
+{
+    for (unsigned s = 0; s < T->B; s++) {
+        uint64_t x = T->tags[b * T->B + s];
+        if (same_tag(T, x, t) && (x & T->vmask) < *best) *best = (unsigned)(x & T->vmask);
+    }
 }
 
 static int block_take(or_tcf *T, uint64_t b, uint32_t t)
 {
     for (unsigned s = 0; s < T->B; s++) {
-        if (T->tags[b * T->B + s] == t) {
+        if (same_tag(T, T->tags[b * T->B + s], t)) {
             T->tags[b * T->B + s] = 0;
             return 1;
         }
@@ -222,6 +265,12 @@ static void bucket_canon(or_tcf *T, uint64_t k)
 void or_tcf_insert(or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *status, uint8_t *phase,
                    uint64_t *where)
 {
+    or_tcf_insert_values(T, keys, NULL, n, status, phase, where);
+}
+
+void or_tcf_insert_values(or_tcf *T, const uint64_t *keys, const uint8_t *values, uint64_t n, uint8_t *status,
+                          uint8_t *phase, uint64_t *where)
+{
     if (n == 0) return;
     uint64_t *b1 = malloc(n * 8), *b2 = malloc(n * 8);
     uint32_t *t = malloc(n * 4);
@@ -229,6 +278,8 @@ void or_tcf_insert(or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *status,
     rec_t *R = malloc(n * sizeof(rec_t));
     uint64_t *pend = malloc(n * 8);
     or_tcf_keyinfo(T, keys, n, b1, b2, t);
+    if (values)
+        for (uint64_t i = 0; i < n; i++) t[i] |= (uint32_t)(values[i] & T->vmask);
     if (status) memset(status, 0, n);
 
     /* Phase A: shortcut into b1 while fill(b1) + j < 3B/4 */
@@ -351,9 +402,27 @@ void or_tcf_query(const or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *fo
         if (!hit) {
             uint64_t e = entry_of(T, b1, b2, t), k = bucket_of(T, e);
             for (unsigned s = 0; s < BK_W; s++)
-                if (T->bk[k * BK_W + s] == e) hit = 1;
+                if (same_tag(T, T->bk[k * BK_W + s], e)) hit = 1;
         }
         found[i] = (uint8_t)hit;
+    }
+}
+
+void or_tcf_query_values(const or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *values)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        uint64_t b1, b2;
+        uint32_t t;
+        keyinfo1(T, keys[i], &b1, &b2, &t);
+        unsigned best = 0x100;
+        block_min_value(T, b1, t, &best);
+        block_min_value(T, b2, t, &best);
+        uint64_t e = entry_of(T, b1, b2, t), k = bucket_of(T, e);
+        for (unsigned s = 0; s < BK_W; s++) {
+            uint64_t x = T->bk[k * BK_W + s];
+            if (same_tag(T, x, e) && (x & T->vmask) < best) best = (unsigned)(x & T->vmask);
+        }
+        values[i] = best == 0x100 ? 0xFF : (uint8_t)best;
     }
 }
 
@@ -392,7 +461,7 @@ void or_tcf_remove(or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *status)
         uint64_t g = R[k].g;
         int done = 0;
         for (unsigned s = 0; s < BK_W && !done; s++) {
-            if (T->bk[g * BK_W + s] == R[k].k) {
+            if (same_tag(T, T->bk[g * BK_W + s], R[k].k)) {
                 T->bk[g * BK_W + s] = 0;
                 done = 1;
             }
