@@ -73,6 +73,9 @@ typedef struct filter_config {
     uint32_t mode;        /* TCF: FILTER_MODE_BULK or FILTER_MODE_POINT; GQF: 0 */
     uint64_t hash_seed;   /* xor-ed into keys before hashing */
     uint64_t max_batch;   /* largest n of one call; sizes the scratch memory (GQF: < 2^30) */
+    uint32_t value_bits;  /* TCF: v bits of each slot hold a value below an (f - v)-bit tag,
+                             0 <= v <= min(f / 2, 7); 0 = no values. GQF, groups: 0 */
+    uint32_t reserved;    /* 0 */
 } filter_config;
 
 typedef struct filter_stats {
@@ -89,7 +92,8 @@ typedef struct filter_stats {
  * batches of up to cfg->max_batch keys on the current device, and clear the
  * table on `stream`. The filter owns this memory until filter_destroy.
  * Returns FILTER_ERR_ARG for a bad geometry (TCF: f in {8,16}, 2^log2_slots
- * >= 2 blocks, nb <= 2^32; GQF: r in {8,16}, 6 <= q <= 36, q + r <= 64),
+ * >= 2 blocks, nb <= 2^32, value_bits <= min(f / 2, 7); GQF: r in {8,16},
+ * 6 <= q <= 36, q + r <= 64, value_bits 0),
  * FILTER_ERR_OOM if an allocation fails (nothing is leaked).
  */
 int filter_create(const filter_config *cfg, void *stream, filter_t **out);
@@ -115,6 +119,19 @@ int filter_insert(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_st
                   void *stream);
 
 /*
+ * filter_insert_values: as filter_insert, with a small value per key (the
+ * paper's TCF associates small values with items, Sec. 1 and Sec. 4). TCF
+ * with value_bits v > 0 only: a slot holds the key's (f - v)-bit tag and the
+ * low v bits of d_values[i] below it. The value never changes where a key
+ * goes: blocks, buckets and statuses are those filter_insert gives, and
+ * copies of one tag are kept sorted by value. filter_insert on such a filter
+ * stores value 0. d_values: n uint8. Returns FILTER_ERR_UNSUPPORTED for a
+ * GQF or a TCF without values.
+ */
+int filter_insert_values(filter_t *f, const uint64_t *d_keys, const uint8_t *d_values, uint64_t n,
+                         uint8_t *d_status, void *stream);
+
+/*
  * filter_query: d_found[i] = 1 if key i may be in the set (no false
  * negatives; false positives at the filter's rate), else 0.
  * TCF: tag in block b1 or b2 or the backing bucket. GQF: count > 0.
@@ -122,6 +139,18 @@ int filter_insert(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_st
  */
 int filter_query(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_found,
                  void *stream);
+
+/*
+ * filter_query_values: TCF with values only. d_values[i] = the smallest value
+ * stored with key i's fingerprint (its tag in block b1 or b2, or its entry in
+ * the backing bucket), or 0xFF when the fingerprint is absent; so
+ * d_values[i] != 0xFF exactly when filter_query answers 1. Matching ignores
+ * the value bits, and filter_remove deletes, per key, the copy with the
+ * smallest value in the first of b1, b2 and the bucket that holds one.
+ * Any n. Returns FILTER_ERR_UNSUPPORTED for a GQF or a TCF without values.
+ */
+int filter_query_values(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_values,
+                        void *stream);
 
 /*
  * filter_remove: delete one copy per key (Sec. 6.4 of the paper). Keys without a
@@ -166,6 +195,8 @@ typedef struct filter_device_view {
     uint64_t n_aux;      /* TCF: backing buckets; GQF: slots */
     unsigned long long *counters;  /* the filter's device counters: [0] status word,
                                       [1] failed keys, [2] TCF backing entries */
+    uint32_t value_bits; /* TCF: value bits below the tag in each slot; GQF: 0 */
+    uint32_t reserved;
 } filter_device_view;
 
 int filter_get_device_view(filter_t *f, filter_device_view *out);

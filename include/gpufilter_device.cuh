@@ -11,9 +11,10 @@
  *   host:    filter_device_view v;  filter_get_device_view(f, &v);
  *            pass v by value to the kernel
  *   device:  bool hit  = gf_device_tcf_contains(v, key);
+ *            uint32_t x = gf_device_tcf_value(v, key);     (TCF with values)
  *            uint64_t c = gf_device_gqf_count(v, key);
- *            int st = gf_device_tcf_insert(v, key);   (point-mode TCF only)
- *            int st = gf_device_tcf_remove(v, key);   (point-mode TCF only)
+ *            int st = gf_device_tcf_insert(v, key[, value]); (point-mode TCF only)
+ *            int st = gf_device_tcf_remove(v, key);          (point-mode TCF only)
  *
  * A view describes the table as it is when filter_get_device_view returns;
  * it must be taken again after any insert, remove, clear or import through
@@ -66,8 +67,18 @@ __device__ __forceinline__ uint64_t gqf_fingerprint(uint64_t key, uint32_t p, ui
     return x;
 }
 
-// does the 32-byte block hold tag t (f = 8 or 16 bits per tag)?
-__device__ __forceinline__ bool tcf_block_has(const uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f)
+// the tag part of every f-bit lane of a word (a TCF with v value bits keeps
+// the value in the low v bits of each slot)
+__device__ __forceinline__ uint32_t tcf_lane_mask(uint32_t f, uint32_t vbits)
+{
+    const uint32_t vm = (1u << vbits) - 1u;
+    return f == 16 ? (0xffffu & ~vm) * 0x00010001u : (0xffu & ~vm) * 0x01010101u;
+}
+
+// does the 32-byte block hold tag t (f = 8 or 16 bits per slot; t is the
+// slot with value 0, lm from tcf_lane_mask)?
+__device__ __forceinline__ bool tcf_block_has(const uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f,
+                                              uint32_t lm)
 {
     // L2 loads: coherent with device-side updates made by other threads
     const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
@@ -77,13 +88,35 @@ __device__ __forceinline__ bool tcf_block_has(const uint8_t *blocks, uint64_t b,
     if (f == 16) {
         const uint32_t tt = t | (t << 16);
 #pragma unroll
-        for (int k = 0; k < 8; k++) m |= __vcmpeq2(w[k], tt);
+        for (int k = 0; k < 8; k++) m |= __vcmpeq2(w[k] & lm, tt);
     } else {
         const uint32_t tt = t * 0x01010101u;
 #pragma unroll
-        for (int k = 0; k < 8; k++) m |= __vcmpeq4(w[k], tt);
+        for (int k = 0; k < 8; k++) m |= __vcmpeq4(w[k] & lm, tt);
     }
     return m != 0;
+}
+
+// smallest value part among the slots of block b that hold tag t, or 0xff /
+// 0xffff (more than any value) when none does
+__device__ __forceinline__ uint32_t tcf_block_min_value(const uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f,
+                                                        uint32_t lm)
+{
+    const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * 32);
+    const uint4 lo = __ldcg(p), hi = __ldcg(p + 1);
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+    uint32_t m = 0xffffffffu;
+    if (f == 16) {
+        const uint32_t tt = t | (t << 16);
+#pragma unroll
+        for (int k = 0; k < 8; k++) m = __vminu2(m, (w[k] & ~lm) | ~__vcmpeq2(w[k] & lm, tt));
+        return min(m & 0xffffu, m >> 16);
+    }
+    const uint32_t tt = t * 0x01010101u;
+#pragma unroll
+    for (int k = 0; k < 8; k++) m = __vminu4(m, (w[k] & ~lm) | ~__vcmpeq4(w[k] & lm, tt));
+    m = __vminu4(m, m >> 16);
+    return min(m & 0xffu, (m >> 8) & 0xffu);
 }
 
 template <int R>
@@ -170,29 +203,82 @@ __device__ uint64_t gqf_count_fp(uint64_t fp, const uint8_t *meta, const uint8_t
 // negative for an inserted key)? Tag t and block pair (b1, b2 = b1 xor g(t))
 // from one 64-bit hash; the backing bucket is read only when some key was
 // stored there.
+namespace gf_device {
+
+// the key's block pair and its slot with value 0: the (f - v)-bit tag from
+// bits 44.. of the hash, shifted above the v value bits; g uses the tag alone
+__device__ __forceinline__ void tcf_key(const filter_device_view &v, uint64_t key, uint64_t &b1, uint64_t &b2,
+                                        uint32_t &t)
+{
+    const uint64_t nb = v.n_blocks;
+    const uint64_t h = mix64(key ^ v.seed);
+    uint32_t tag = (uint32_t)((h >> 44) & ((1u << (v.tag_bits - v.value_bits)) - 1u));
+    if (tag < 2) tag += 2;
+    b1 = h & (nb - 1);
+    uint64_t g = mix64((uint64_t)tag) & (nb - 1);
+    if (!g) g = 1;
+    b2 = b1 ^ g;
+    t = tag << v.value_bits;
+}
+
+// the key's backing bucket (chosen by the entry without its value bits)
+__device__ __forceinline__ uint64_t *tcf_bucket_ptr(const filter_device_view &v, uint64_t e)
+{
+    return static_cast<uint64_t *>(v.aux) + (((mix64(e) >> 32) * v.n_aux) >> 32) * 8;
+}
+
+}  // namespace gf_device
+
+// Is key in the TCF (a false positive with the filter's rate, never a false
+// negative for an inserted key)? Tag t and block pair (b1, b2 = b1 xor g(t))
+// from one 64-bit hash; the backing bucket is read only when some key was
+// stored there.
 __device__ __forceinline__ bool gf_device_tcf_contains(const filter_device_view &v, uint64_t key)
 {
     using namespace gf_device;
-    const uint64_t nb = v.n_blocks;
-    const uint64_t h = mix64(key ^ v.seed);
-    uint32_t t = (uint32_t)((h >> 44) & ((1u << v.tag_bits) - 1u));
-    if (t < 2) t += 2;
-    const uint64_t b1 = h & (nb - 1);
-    uint64_t g = mix64((uint64_t)t) & (nb - 1);
-    if (!g) g = 1;
-    const uint64_t b2 = b1 ^ g;
+    uint64_t b1, b2;
+    uint32_t t;
+    tcf_key(v, key, b1, b2, t);
+    const uint32_t lm = tcf_lane_mask(v.tag_bits, v.value_bits);
     const uint8_t *blocks = static_cast<const uint8_t *>(v.table);
-    if (tcf_block_has(blocks, b1, t, v.tag_bits) || tcf_block_has(blocks, b2, t, v.tag_bits)) return true;
+    if (tcf_block_has(blocks, b1, t, v.tag_bits, lm) || tcf_block_has(blocks, b2, t, v.tag_bits, lm)) return true;
     if (!v.counters || *(volatile unsigned long long *)(v.counters + 2) == 0) return false;
     const uint64_t e = ((b1 < b2 ? b1 : b2) << v.tag_bits) | t;
-    const uint64_t bucket = ((mix64(e) >> 32) * v.n_aux) >> 32;
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(static_cast<const uint64_t *>(v.aux) + bucket * 8);
+    const uint64_t em = ~((1ull << v.value_bits) - 1ull);
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(tcf_bucket_ptr(v, e));
 #pragma unroll
     for (int s = 0; s < 4; s++) {
         const ulonglong2 w = __ldcg(p + s);
-        if (w.x == e || w.y == e) return true;
+        if ((w.x & em) == e || (w.y & em) == e) return true;
     }
     return false;
+}
+
+// TCF with values: the smallest value stored with the key's fingerprint (in
+// b1, b2 or its backing bucket), 0xFF when there is none. The same answer as
+// filter_query_values.
+__device__ __forceinline__ uint32_t gf_device_tcf_value(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    uint64_t b1, b2;
+    uint32_t t;
+    tcf_key(v, key, b1, b2, t);
+    const uint32_t lm = tcf_lane_mask(v.tag_bits, v.value_bits), vm = (1u << v.value_bits) - 1u;
+    const uint8_t *blocks = static_cast<const uint8_t *>(v.table);
+    uint32_t best = min(tcf_block_min_value(blocks, b1, t, v.tag_bits, lm),
+                        tcf_block_min_value(blocks, b2, t, v.tag_bits, lm));
+    if (v.counters && *(volatile unsigned long long *)(v.counters + 2) != 0) {
+        const uint64_t e = ((b1 < b2 ? b1 : b2) << v.tag_bits) | t;
+        const uint64_t em = ~(uint64_t)vm;
+        const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(tcf_bucket_ptr(v, e));
+#pragma unroll
+        for (int s = 0; s < 4; s++) {
+            const ulonglong2 w = __ldcg(p + s);
+            if ((w.x & em) == e) best = min(best, (uint32_t)w.x & vm);
+            if ((w.y & em) == e) best = min(best, (uint32_t)w.y & vm);
+        }
+    }
+    return best <= vm ? best : 0xffu;
 }
 
 namespace gf_device {
@@ -212,7 +298,7 @@ __device__ __forceinline__ int tcf_live(const uint8_t *blocks, uint64_t b, uint3
     return c;
 }
 
-// put tag t into the first EMPTY or TOMBSTONE slot of block b (a bounded
+// put slot t into the first EMPTY or TOMBSTONE slot of block b (a bounded
 // number of compare-and-swap attempts; false when the block is full)
 __device__ __forceinline__ bool tcf_put(uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f,
                                         unsigned long long *counters)
@@ -240,38 +326,32 @@ __device__ __forceinline__ bool tcf_put(uint8_t *blocks, uint64_t b, uint32_t t,
     return false;
 }
 
-// replace one copy of tag t in block b by TOMBSTONE
-__device__ __forceinline__ bool tcf_take(uint8_t *blocks, uint64_t b, uint32_t t, uint32_t f,
+// replace one copy of tag t (whatever its value: vm is the value part) in
+// block b by TOMBSTONE
+__device__ __forceinline__ bool tcf_take(uint8_t *blocks, uint64_t b, uint32_t t, uint32_t vm, uint32_t f,
                                          unsigned long long *counters)
 {
     const int B = (int)(256 / f);
     for (int attempt = 0; attempt < 4 * B; attempt++) {
         int s = -1;
-        for (int p = 0; p < B && s < 0; p++)
-            if (tcf_tag_at(blocks, b, p, f) == t) s = p;
+        uint32_t seen = 0;
+        for (int p = 0; p < B && s < 0; p++) {
+            const uint32_t x = tcf_tag_at(blocks, b, p, f);
+            if ((x & ~vm) == t) {
+                s = p;
+                seen = x;
+            }
+        }
         if (s < 0) return false;
         unsigned int *word = reinterpret_cast<unsigned int *>(blocks + b * 32) + ((s * f) >> 5);
         const unsigned sh = (unsigned)((s * f) & 31);
         const unsigned int lane = (f == 16 ? 0xffffu : 0xffu) << sh;
         const unsigned int cur = *(volatile unsigned int *)word;
-        if (((cur & lane) >> sh) != t) continue;
+        if (((cur & lane) >> sh) != seen) continue;  // changed since it was read
         if (atomicCAS(word, cur, (cur & ~lane) | (1u << sh)) == cur) return true;
     }
     atomicOr(counters, 1ull << FILTER_ERR_TIMEOUT);
     return false;
-}
-
-__device__ __forceinline__ void tcf_key(const filter_device_view &v, uint64_t key, uint64_t &b1, uint64_t &b2,
-                                        uint32_t &t)
-{
-    const uint64_t nb = v.n_blocks;
-    const uint64_t h = mix64(key ^ v.seed);
-    t = (uint32_t)((h >> 44) & ((1u << v.tag_bits) - 1u));
-    if (t < 2) t += 2;
-    b1 = h & (nb - 1);
-    uint64_t g = mix64((uint64_t)t) & (nb - 1);
-    if (!g) g = 1;
-    b2 = b1 ^ g;
 }
 
 }  // namespace gf_device
@@ -280,14 +360,16 @@ __device__ __forceinline__ void tcf_key(const filter_device_view &v, uint64_t ke
 // live tags (the shortcut), else into the block with fewer live tags, then
 // the other, then an empty entry of the backing bucket. FILTER_KEY_OK, or
 // FILTER_KEY_FULL (also counted in the filter's counters); FILTER_KEY_FULL
-// without counting for a view that is not a point-mode TCF.
-__device__ __forceinline__ int gf_device_tcf_insert(const filter_device_view &v, uint64_t key)
+// without counting for a view that is not a point-mode TCF. A TCF with
+// values stores the low value_bits of `value` with the tag.
+__device__ __forceinline__ int gf_device_tcf_insert(const filter_device_view &v, uint64_t key, uint32_t value = 0)
 {
     using namespace gf_device;
     if (v.kind != FILTER_TCF || v.mode != FILTER_MODE_POINT) return FILTER_KEY_FULL;
     uint64_t b1, b2;
     uint32_t t;
     tcf_key(v, key, b1, b2, t);
+    t |= value & ((1u << v.value_bits) - 1u);
     const uint32_t f = v.tag_bits;
     uint8_t *blocks = static_cast<uint8_t *>(v.table);
     bool done = false;
@@ -298,8 +380,8 @@ __device__ __forceinline__ int gf_device_tcf_insert(const filter_device_view &v,
     }
     if (!done) {
         const uint64_t e = ((b1 < b2 ? b1 : b2) << f) | t;
-        unsigned long long *p =
-            static_cast<unsigned long long *>(v.aux) + (((mix64(e) >> 32) * v.n_aux) >> 32) * 8;
+        unsigned long long *p = reinterpret_cast<unsigned long long *>(
+            tcf_bucket_ptr(v, e & ~((1ull << v.value_bits) - 1ull)));
         for (int s = 0; s < 8 && !done; s++)
             if (atomicCAS(p + s, 0ull, (unsigned long long)e) == 0ull) done = true;
         if (done) atomicAdd(v.counters + 2, 1ull);
@@ -311,8 +393,9 @@ __device__ __forceinline__ int gf_device_tcf_insert(const filter_device_view &v,
 }
 
 // Point-mode TCF remove: one copy of the key's tag in b1, else b2, becomes
-// TOMBSTONE, else its entry leaves the backing bucket. FILTER_KEY_OK or
-// FILTER_KEY_NOT_FOUND (also for a view that is not a point-mode TCF).
+// TOMBSTONE (the first slot holding the tag, whatever its value), else its
+// entry leaves the backing bucket. FILTER_KEY_OK or FILTER_KEY_NOT_FOUND
+// (also for a view that is not a point-mode TCF).
 __device__ __forceinline__ int gf_device_tcf_remove(const filter_device_view &v, uint64_t key)
 {
     using namespace gf_device;
@@ -320,15 +403,16 @@ __device__ __forceinline__ int gf_device_tcf_remove(const filter_device_view &v,
     uint64_t b1, b2;
     uint32_t t;
     tcf_key(v, key, b1, b2, t);
-    const uint32_t f = v.tag_bits;
+    const uint32_t f = v.tag_bits, vm = (1u << v.value_bits) - 1u;
     uint8_t *blocks = static_cast<uint8_t *>(v.table);
-    bool done = tcf_take(blocks, b1, t, f, v.counters) || tcf_take(blocks, b2, t, f, v.counters);
+    bool done = tcf_take(blocks, b1, t, vm, f, v.counters) || tcf_take(blocks, b2, t, vm, f, v.counters);
     if (!done) {
         const uint64_t e = ((b1 < b2 ? b1 : b2) << f) | t;
-        unsigned long long *p =
-            static_cast<unsigned long long *>(v.aux) + (((mix64(e) >> 32) * v.n_aux) >> 32) * 8;
-        for (int s = 0; s < 8 && !done; s++)
-            if (atomicCAS(p + s, (unsigned long long)e, 0ull) == (unsigned long long)e) done = true;
+        unsigned long long *p = reinterpret_cast<unsigned long long *>(tcf_bucket_ptr(v, e));
+        for (int s = 0; s < 8 && !done; s++) {
+            const unsigned long long x = __ldcg(p + s);
+            if ((x & ~(unsigned long long)vm) == e && atomicCAS(p + s, x, 0ull) == x) done = true;
+        }
         if (done) atomicAdd(v.counters + 2, ~0ull);
     }
     return done ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;

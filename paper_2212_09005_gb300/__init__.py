@@ -32,6 +32,7 @@ STATUS_FULL, STATUS_TIMEOUT, STATUS_INTERNAL = 1 << ERR_FULL, 1 << ERR_TIMEOUT, 
 # entry points declared in include/gpufilter.h
 EXPORTS = [
     "filter_create", "filter_destroy", "filter_clear", "filter_insert", "filter_query",
+    "filter_insert_values", "filter_query_values",
     "filter_remove", "filter_count", "filter_get_stats", "filter_get_device_view", "filter_export_size",
     "filter_gqf_enumerate", "filter_gqf_keys_of",
     "filter_export", "filter_import", "filter_error_string",
@@ -49,7 +50,8 @@ OP_INSERT, OP_QUERY, OP_REMOVE, OP_COUNT = 0, 1, 2, 3
 
 class FilterConfig(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("log2_slots", C.c_uint32), ("tag_bits", C.c_uint32),
-                ("mode", C.c_uint32), ("hash_seed", C.c_uint64), ("max_batch", C.c_uint64)]
+                ("mode", C.c_uint32), ("hash_seed", C.c_uint64), ("max_batch", C.c_uint64),
+                ("value_bits", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class FilterStats(C.Structure):
@@ -63,7 +65,8 @@ class FilterDeviceView(C.Structure):
     kernel that includes include/gpufilter_device.cuh)."""
     _fields_ = [("kind", C.c_uint32), ("tag_bits", C.c_uint32), ("q", C.c_uint32), ("mode", C.c_uint32),
                 ("seed", C.c_uint64), ("table", C.c_void_p), ("aux", C.c_void_p), ("n_blocks", C.c_uint64),
-                ("n_aux", C.c_uint64), ("counters", C.c_void_p)]
+                ("n_aux", C.c_uint64), ("counters", C.c_void_p), ("value_bits", C.c_uint32),
+                ("reserved", C.c_uint32)]
 
 
 class FilterRequest(C.Structure):
@@ -101,8 +104,9 @@ def lib():
         L.filter_create.argtypes = [C.POINTER(FilterConfig), vp, C.POINTER(vp)]
         L.filter_destroy.argtypes = [vp]
         L.filter_clear.argtypes = [vp, vp]
-        for name in ("filter_insert", "filter_query", "filter_remove", "filter_count"):
+        for name in ("filter_insert", "filter_query", "filter_remove", "filter_count", "filter_query_values"):
             getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
+        L.filter_insert_values.argtypes = [vp, vp, vp, u64, vp, vp]
         L.filter_get_stats.argtypes = [vp, vp, C.POINTER(FilterStats)]
         L.filter_export_size.argtypes = [vp, C.POINTER(u64)]
         L.filter_export.argtypes = [vp, vp, u64, vp]
@@ -166,14 +170,14 @@ class Filter:
     """One filter on the current CUDA device."""
 
     def __init__(self, kind: int, log2_slots: int, tag_bits: int, mode: int = MODE_BULK,
-                 seed: int = 0, max_batch: int = 1 << 22, stream=None):
+                 seed: int = 0, max_batch: int = 1 << 22, stream=None, value_bits: int = 0):
         self.cfg = FilterConfig(kind, log2_slots, tag_bits, mode, seed & 0xFFFFFFFFFFFFFFFF,
-                                max(1, int(max_batch)))
+                                max(1, int(max_batch)), value_bits, 0)
         h = C.c_void_p()
         _check(lib().filter_create(C.byref(self.cfg), _stream(stream), C.byref(h)), "filter_create")
         self._h = h
         self.kind, self.log2_slots, self.tag_bits, self.mode = kind, log2_slots, tag_bits, mode
-        self.seed, self.max_batch = seed, max(1, int(max_batch))
+        self.seed, self.max_batch, self.value_bits = seed, max(1, int(max_batch)), value_bits
 
     def close(self):
         if getattr(self, "_h", None):
@@ -187,13 +191,25 @@ class Filter:
             pass
 
     # ---- batched operations (asynchronous on the stream) ----
-    def insert(self, keys, status=None, stream=None):
+    def insert(self, keys, status=None, stream=None, values=None):
+        """values (TCF with value_bits > 0): one uint8 per key."""
+        if values is not None:
+            if values.numel() != keys.numel():
+                raise FilterError("one value per key")
+            _check(lib().filter_insert_values(self._h, _dptr(keys, 8), _dptr(values, 1), keys.numel(),
+                                              _dptr(status, 1), _stream(stream)), "filter_insert_values")
+            return
         _check(lib().filter_insert(self._h, _dptr(keys, 8), keys.numel(), _dptr(status, 1),
                                    _stream(stream)), "filter_insert")
 
     def query(self, keys, found, stream=None):
         _check(lib().filter_query(self._h, _dptr(keys, 8), keys.numel(), _dptr(found, 1),
                                   _stream(stream)), "filter_query")
+
+    def query_values(self, keys, values, stream=None):
+        """TCF with values: smallest stored value per key, 0xFF when absent."""
+        _check(lib().filter_query_values(self._h, _dptr(keys, 8), keys.numel(), _dptr(values, 1),
+                                         _stream(stream)), "filter_query_values")
 
     def remove(self, keys, status=None, stream=None):
         _check(lib().filter_remove(self._h, _dptr(keys, 8), keys.numel(), _dptr(status, 1),
@@ -252,8 +268,8 @@ class Filter:
 
 
 def TCF(log2_slots: int, tag_bits: int = 16, mode: int = MODE_BULK, seed: int = 0,
-        max_batch: int = 1 << 22, stream=None) -> Filter:
-    return Filter(FILTER_TCF, log2_slots, tag_bits, mode, seed, max_batch, stream)
+        max_batch: int = 1 << 22, stream=None, value_bits: int = 0) -> Filter:
+    return Filter(FILTER_TCF, log2_slots, tag_bits, mode, seed, max_batch, stream, value_bits)
 
 
 def GQF(q: int, r: int = 8, seed: int = 0, max_batch: int = 1 << 22, stream=None) -> Filter:

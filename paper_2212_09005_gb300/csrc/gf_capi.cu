@@ -95,15 +95,30 @@ int filter_clear(filter_t *f, void *stream)
 int filter_insert(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_status, void *stream)
 {
     if (!valid(f) || n > f->cfg.max_batch || (n && !d_keys)) return FILTER_ERR_ARG;
-    return f->cfg.kind == FILTER_TCF ? gf::tcf_insert(f, d_keys, n, d_status, as_stream(stream))
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_insert(f, d_keys, nullptr, n, d_status, as_stream(stream))
                                      : gf::gqf_insert(f, d_keys, n, d_status, as_stream(stream));
+}
+
+int filter_insert_values(filter_t *f, const uint64_t *d_keys, const uint8_t *d_values, uint64_t n,
+                         uint8_t *d_status, void *stream)
+{
+    if (!valid(f) || n > f->cfg.max_batch || (n && (!d_keys || !d_values))) return FILTER_ERR_ARG;
+    if (f->cfg.kind != FILTER_TCF || f->cfg.value_bits == 0) return FILTER_ERR_UNSUPPORTED;
+    return gf::tcf_insert(f, d_keys, d_values, n, d_status, as_stream(stream));
 }
 
 int filter_query(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_found, void *stream)
 {
     if (!valid(f) || (n && (!d_keys || !d_found))) return FILTER_ERR_ARG;
-    return f->cfg.kind == FILTER_TCF ? gf::tcf_query(f, d_keys, n, d_found, as_stream(stream))
+    return f->cfg.kind == FILTER_TCF ? gf::tcf_query(f, d_keys, n, d_found, false, as_stream(stream))
                                      : gf::gqf_count(f, d_keys, n, nullptr, d_found, as_stream(stream));
+}
+
+int filter_query_values(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_values, void *stream)
+{
+    if (!valid(f) || (n && (!d_keys || !d_values))) return FILTER_ERR_ARG;
+    if (f->cfg.kind != FILTER_TCF || f->cfg.value_bits == 0) return FILTER_ERR_UNSUPPORTED;
+    return gf::tcf_query(f, d_keys, n, d_values, true, as_stream(stream));
 }
 
 int filter_remove(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_status, void *stream)
@@ -151,6 +166,7 @@ int filter_get_device_view(filter_t *f, filter_device_view *out)
     if (f->cfg.kind == FILTER_TCF) {
         const TcfState &T = f->tcf;
         out->mode = T.mode;
+        out->value_bits = T.G.vbits;
         out->table = T.blocks;
         out->aux = T.bk;
         out->n_blocks = T.G.nb;

@@ -1551,6 +1551,7 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
 {
     const filter_config &c = F->cfg;
     if (c.tag_bits != 8 && c.tag_bits != 16) return FILTER_ERR_ARG;
+    if (c.value_bits != 0) return FILTER_ERR_ARG;  // values ride on the counters
     if (c.log2_slots < 6 || c.log2_slots > 36 || c.log2_slots + c.tag_bits > 64) return FILTER_ERR_ARG;
     GqfState &Q = F->gqf;
     Q.q = c.log2_slots;

@@ -95,11 +95,14 @@ struct TcfGeom {
     uint64_t nb;      // blocks (power of two)
     uint64_t nbk;     // backing buckets
     uint64_t seed;
-    uint32_t f, B;    // tag bits, tags per 32-byte block
+    uint32_t f, B;    // slot bits, slots per 32-byte block
     uint32_t tsc;     // shortcut threshold 3B/4
-    uint32_t tmask;
+    uint32_t tmask;   // the tag: f - vbits bits
+    uint32_t vbits = 0;  // value bits below the tag in each slot
+    uint32_t vmask = 0;  // (1 << vbits) - 1
 };
 
+// t is the key's slot with value 0: the tag shifted above the value bits
 struct KeyInfo {
     uint64_t b1, b2;
     uint32_t t;
@@ -117,7 +120,7 @@ __host__ __device__ __forceinline__ KeyInfo tcf_keyinfo(uint64_t key, const TcfG
     uint64_t h = mix64(key ^ G.seed);
     uint32_t t = (uint32_t)((h >> 44) & G.tmask);
     if (t < 2) t += 2;
-    k.t = t;
+    k.t = t << G.vbits;
     k.b1 = h & (G.nb - 1);
     k.b2 = k.b1 ^ tcf_g(t, G.nb);
     return k;
@@ -132,6 +135,12 @@ __host__ __device__ __forceinline__ uint64_t tcf_entry(const KeyInfo &k, uint32_
 __host__ __device__ __forceinline__ uint64_t tcf_bucket(uint64_t e, uint64_t nbk)
 {
     return ((mix64(e) >> 32) * nbk) >> 32;
+}
+
+// the bucket of an entry that may carry a value: chosen by the tag part only
+__host__ __device__ __forceinline__ uint64_t tcf_bucket_of(uint64_t e, const TcfGeom &G)
+{
+    return tcf_bucket(e & ~(uint64_t)G.vmask, G.nbk);
 }
 
 // ---------------------------------------------------------------------------
@@ -186,6 +195,7 @@ struct TcfPrep {
     uint32_t *b2;       // group-wide
     uint32_t *bucket;   // group-wide backing bucket
     uint64_t *e;        // backing entry (member-local block index << f | tag)
+    const uint8_t *vals = nullptr;  // single filters with values: the batch's values
 };
 
 // ---------------------------------------------------------------------------
@@ -307,7 +317,7 @@ struct GqfState {
 };
 
 struct filter {
-    filter_config cfg;
+    filter_config cfg{};
     gf::Arena arena;
     void *table_mem = nullptr;
     size_t table_bytes_alloc = 0;
@@ -363,8 +373,8 @@ enum GroupOp : int { GROUP_INSERT = 0, GROUP_REMOVE = 1, GROUP_QUERY = 2 };
 
 int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);
 int tcf_clear(filter *F, cudaStream_t st);
-int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
-int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, cudaStream_t st);
+int tcf_insert(filter *F, const uint64_t *keys, const uint8_t *vals, uint64_t n, uint8_t *status, cudaStream_t st);
+int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, bool values, cudaStream_t st);
 int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
 uint64_t tcf_image_bytes(const filter *F);
 int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st);

@@ -53,6 +53,7 @@ extern "C" int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_s
     if (q > NOALLOC_MAX_Q || n > NOALLOC_MAX_KEYS || !d_table_in || !d_table_out || (n && !d_keys))
         return FILTER_ERR_ARG;
     filter F;  // host-side description only; nothing is allocated
+    F.cfg = filter_config{};
     F.cfg.kind = FILTER_GQF;
     F.cfg.log2_slots = q;
     F.cfg.tag_bits = r;

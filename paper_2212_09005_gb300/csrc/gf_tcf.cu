@@ -72,19 +72,42 @@ struct Blk {
         if (F == 16) return (w[s >> 1] >> ((s & 1) * 16)) & 0xffffu;
         return (w[s >> 2] >> ((s & 3) * 8)) & 0xffu;
     }
-    __device__ __forceinline__ bool has(uint32_t t) const
+    // the tag part of every lane of a word (all ones without values)
+    static __device__ __forceinline__ uint32_t lane_mask(uint32_t vmask)
+    {
+        return F == 16 ? (0xffffu & ~vmask) * 0x00010001u : (0xffu & ~vmask) * 0x01010101u;
+    }
+    // some slot holds tag t (t: the slot with value 0; lm from lane_mask)
+    __device__ __forceinline__ bool has(uint32_t t, uint32_t lm) const
     {
         uint32_t m = 0;
         if (F == 16) {
             uint32_t tt = t | (t << 16);
 #pragma unroll
-            for (int k = 0; k < 8; k++) m |= __vcmpeq2(w[k], tt);
+            for (int k = 0; k < 8; k++) m |= __vcmpeq2(w[k] & lm, tt);
         } else {
             uint32_t tt = t * 0x01010101u;
 #pragma unroll
-            for (int k = 0; k < 8; k++) m |= __vcmpeq4(w[k], tt);
+            for (int k = 0; k < 8; k++) m |= __vcmpeq4(w[k] & lm, tt);
         }
         return m != 0;
+    }
+    // smallest value stored with tag t, or the lane maximum when none is
+    __device__ __forceinline__ uint32_t min_value(uint32_t t, uint32_t lm) const
+    {
+        uint32_t b = 0xffffffffu;
+        if (F == 16) {
+            const uint32_t tt = t | (t << 16);
+#pragma unroll
+            for (int k = 0; k < 8; k++) b = __vminu2(b, (w[k] & ~lm) | ~__vcmpeq2(w[k] & lm, tt));
+            return min(b & 0xffffu, b >> 16);
+        } else {
+            const uint32_t tt = t * 0x01010101u;
+#pragma unroll
+            for (int k = 0; k < 8; k++) b = __vminu4(b, (w[k] & ~lm) | ~__vcmpeq4(w[k] & lm, tt));
+            b = __vminu4(b, b >> 16);
+            return min(b & 0xffu, (b >> 8) & 0xffu);
+        }
     }
     // tags >= 2 (neither EMPTY nor TOMBSTONE)
     __device__ __forceinline__ int live() const
@@ -114,21 +137,21 @@ struct Blk {
         }
     }
     // bit s set where slot s holds tag t
-    __device__ __forceinline__ uint32_t eq_slots(uint32_t t) const
+    __device__ __forceinline__ uint32_t eq_slots(uint32_t t, uint32_t lm) const
     {
         uint32_t sm = 0;
         if (F == 16) {
             const uint32_t tt = t | (t << 16);
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                const uint32_t m = __vcmpeq2(w[k], tt);
+                const uint32_t m = __vcmpeq2(w[k] & lm, tt);
                 sm |= ((m & 1u) | ((m >> 15) & 2u)) << (2 * k);
             }
         } else {
             const uint32_t tt = t * 0x01010101u;
 #pragma unroll
             for (int k = 0; k < 8; k++) {
-                const uint32_t m = __vcmpeq4(w[k], tt);
+                const uint32_t m = __vcmpeq4(w[k] & lm, tt);
                 sm |= ((m & 1u) | ((m >> 7) & 2u) | ((m >> 14) & 4u) | ((m >> 21) & 8u)) << (4 * k);
             }
         }
@@ -269,7 +292,9 @@ __device__ __forceinline__ int topk_push(uint64_t *a, int have, int k, uint64_t 
 // ---------------------------------------------------------------------------
 // Query (both modes)
 // ---------------------------------------------------------------------------
-template <int F>
+// VAL: answer the smallest value stored with the key's fingerprint in its two
+// blocks and its backing bucket, 0xFF when there is none; else 1 / 0.
+template <int F, bool VAL>
 __global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restrict__ keys, uint64_t n,
                                                         TcfGeom G, const uint8_t *__restrict__ blocks,
                                                         const uint64_t *__restrict__ bk,
@@ -277,19 +302,36 @@ __global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restri
                                                         uint8_t *__restrict__ out)
 {
     const bool backing = ctr->backing != 0;
+    const uint32_t lm = Blk<F>::lane_mask(G.vmask);
+    const uint64_t em = ~(uint64_t)G.vmask;
     for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
         KeyInfo k = tcf_keyinfo(__ldcs(keys + i), G);  // keys and answers stream past the L2
         Blk<F> x, y;
         x.load_ro(blocks, k.b1);
         y.load_ro(blocks, k.b2);
-        bool hit = x.has(k.t) || y.has(k.t);
+        if (VAL) {
+            uint32_t best = min(x.min_value(k.t, lm), y.min_value(k.t, lm));
+            if (backing) {
+                const uint64_t e = tcf_entry(k, G.f);
+                const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bk + tcf_bucket_of(e, G) * BK_W);
+#pragma unroll
+                for (int s = 0; s < 4; s++) {
+                    const ulonglong2 v = __ldg(p + s);
+                    if ((v.x & em) == e) best = min(best, (uint32_t)v.x & G.vmask);
+                    if ((v.y & em) == e) best = min(best, (uint32_t)v.y & G.vmask);
+                }
+            }
+            __stcs(out + i, (uint8_t)(best <= G.vmask ? best : 0xffu));
+            continue;
+        }
+        bool hit = x.has(k.t, lm) || y.has(k.t, lm);
         if (!hit && backing) {
             uint64_t e = tcf_entry(k, G.f);
-            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bk + tcf_bucket(e, G.nbk) * BK_W);
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bk + tcf_bucket_of(e, G) * BK_W);
 #pragma unroll
             for (int s = 0; s < 4; s++) {
                 ulonglong2 v = __ldg(p + s);
-                hit |= (v.x == e) | (v.y == e);
+                hit |= ((v.x & em) == e) | ((v.y & em) == e);
             }
         }
         __stcs(out + i, (uint8_t)(hit ? 1 : 0));
@@ -318,7 +360,9 @@ __device__ __forceinline__ KeyInfo key_at(const uint64_t *keys, const TcfPrep &P
         k.b2 = (DST == DST_TARGET || DST == DST_B2) ? P.b2[i] : 0;
         return k;
     }
-    return tcf_keyinfo(keys[i], G);
+    KeyInfo k = tcf_keyinfo(keys[i], G);
+    if (P.vals) k.t |= P.vals[i] & G.vmask;
+    return k;
 }
 
 __device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t pend_word, const TcfGeom &G,
@@ -329,7 +373,7 @@ __device__ __forceinline__ uint64_t dest_of(int dst, const KeyInfo &k, uint64_t 
     case DST_B2: return k.b2;
     case DST_TARGET: return fill[k.b1] <= fill[k.b2] ? k.b1 : k.b2;
     case DST_ALT: return pend_word >> 32;
-    default: return P.bt ? (uint64_t)P.bucket[i] : tcf_bucket(tcf_entry(k, G.f), G.nbk);
+    default: return P.bt ? (uint64_t)P.bucket[i] : tcf_bucket_of(tcf_entry(k, G.f), G);
     }
 }
 
@@ -603,7 +647,8 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
             const uint32_t i = (uint32_t)r;
             if (phase == 1) {
                 // the other block of the pair: b1 + b2 - b
-                uint64_t alt = prep.bt ? (prep.bt[i] >> 32) + prep.b2[i] - b : b ^ tcf_g((uint32_t)(r >> 32), G.nb);
+                uint64_t alt = prep.bt ? (prep.bt[i] >> 32) + prep.b2[i] - b
+                                       : b ^ tcf_g((uint32_t)(r >> 32) >> G.vbits, G.nb);
                 pend64[slot++] = (alt << 32) | i;
             } else {
                 pend32[slot++] = i;
@@ -696,15 +741,16 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
     constexpr int B = Blk<F>::B;
     const uint64_t nd = phase_count(P, G.nb);
     if (P.dlist) note_units(units, nd);  // units: blocks with candidates
+    const uint32_t lm = Blk<F>::lane_mask(G.vmask);
     const uint64_t stride = (uint64_t)gridDim.x * TPB;
     for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
         const uint64_t j = j0 + (threadIdx.x & 31);
         uint32_t s = 0, e = 0, nunm = 0, unm = 0;
         bool fast = false;
         uint64_t r8[8];  // fast path: the candidates, sorted
-        // general path: per distinct stored tag, the copies, the candidates
-        // that matched and the largest matched record
-        uint32_t dt[B], dc[B], used[B];
+        // general path: per distinct stored tag, its first slot, the copies,
+        // the candidates that matched and the largest matched record
+        uint32_t dt[B], dp[B], dc[B], used[B];
         uint64_t thr[B];
         int ndt = 0;
         uint64_t b = 0;
@@ -730,7 +776,7 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
 #pragma unroll
                     for (int q = 0; q < 8; q++) {
                         if ((uint32_t)q < c) {
-                            const uint32_t sm = blk.eq_slots((uint32_t)(r8[q] >> 32));
+                            const uint32_t sm = blk.eq_slots((uint32_t)(r8[q] >> 32), lm);
                             if (sm) {
                                 blk.delete_at(__ffs(sm) - 1);
                                 removed++;
@@ -748,11 +794,14 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
                     uint32_t tags[B];
 #pragma unroll
                     for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
+                    // copies of a tag are adjacent (sorted by tag, then value)
                     for (int p = 0; p < (int)f0; p++) {
-                        if (ndt > 0 && dt[ndt - 1] == tags[p]) {
+                        const uint32_t mt = tags[p] & ~G.vmask;
+                        if (ndt > 0 && dt[ndt - 1] == mt) {
                             dc[ndt - 1]++;
                         } else {
-                            dt[ndt] = tags[p];
+                            dt[ndt] = mt;
+                            dp[ndt] = (uint32_t)p;
                             dc[ndt] = 1;
                             ndt++;
                         }
@@ -768,11 +817,12 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
                         used[d] = (uint32_t)have;
                         thr[d] = have ? a[have - 1] : 0;
                     }
-                    // rebuild the block without the removed copies
+                    // rebuild the block without the removed copies (the
+                    // smallest values of each tag)
                     uint32_t t_out[B];
                     int o = 0;
                     for (int d = 0; d < ndt; d++) {
-                        for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = dt[d];
+                        for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = tags[dp[d] + c];
                         removed += (int)used[d];
                     }
                     for (int p = o; p < B; p++) t_out[p] = 0;
@@ -816,17 +866,21 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk
         uint32_t s, e;
         const uint64_t q = phase_dst(P, j, s, e);
         if (s == e) continue;
-        // distinct stored entries (the bucket is sorted) with their copy counts
-        uint64_t dv[BK_W];
-        uint32_t dc[BK_W], used[BK_W], thr[BK_W];
+        // distinct stored entries without their values (the bucket is sorted,
+        // so copies are adjacent) with their first position and copy counts
+        uint64_t cur[BK_W], dv[BK_W];
+        uint32_t dp[BK_W], dc[BK_W], used[BK_W], thr[BK_W];
         int nd = 0;
         for (int j = 0; j < (int)BK_W; j++) {
-            uint64_t v = bk[q * BK_W + j];
+            const uint64_t v = bk[q * BK_W + j];
+            cur[j] = v;
             if (!v) continue;
-            if (nd > 0 && dv[nd - 1] == v) {
+            const uint64_t mv = v & ~(uint64_t)G.vmask;
+            if (nd > 0 && dv[nd - 1] == mv) {
                 dc[nd - 1]++;
             } else {
-                dv[nd] = v;
+                dv[nd] = mv;
+                dp[nd] = (uint32_t)j;
                 dc[nd] = 1;
                 nd++;
             }
@@ -845,7 +899,7 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk
         int o = 0;
         for (int d = 0; d < nd; d++) {
             removed += (int)used[d];
-            for (uint32_t c = used[d]; c < dc[d]; c++) outv[o++] = dv[d];
+            for (uint32_t c = used[d]; c < dc[d]; c++) outv[o++] = cur[dp[d] + c];
         }
         for (int j = o; j < (int)BK_W; j++) outv[j] = 0;
         if (removed) {
@@ -895,7 +949,7 @@ __device__ bool point_put(uint8_t *blocks, uint64_t b, uint32_t t, DevCounters *
 }
 
 template <int F>
-__device__ bool point_take(uint8_t *blocks, uint64_t b, uint32_t t, DevCounters *ctr)
+__device__ bool point_take(uint8_t *blocks, uint64_t b, uint32_t t, uint32_t vmask, DevCounters *ctr)
 {
     constexpr int B = Blk<F>::B;
     for (int attempt = 0; attempt < 4 * B; attempt++) {
@@ -904,11 +958,12 @@ __device__ bool point_take(uint8_t *blocks, uint64_t b, uint32_t t, DevCounters 
         int s = -1;
 #pragma unroll
         for (int p = 0; p < B; p++)
-            if (s < 0 && blk.tag(p) == t) s = p;
+            if (s < 0 && (blk.tag(p) & ~vmask) == t) s = p;
         if (s < 0) return false;
         if (F == 16) {
             unsigned short *slot = reinterpret_cast<unsigned short *>(blocks + b * 32) + s;
-            if (atomicCAS(slot, (unsigned short)t, (unsigned short)1) == (unsigned short)t) return true;
+            const unsigned short seen = (unsigned short)blk.tag(s);
+            if (atomicCAS(slot, seen, (unsigned short)1) == seen) return true;
         } else {
             unsigned int *word = reinterpret_cast<unsigned int *>(blocks + b * 32) + (s >> 2);
             unsigned sh = (s & 3) * 8;
@@ -922,12 +977,14 @@ __device__ bool point_take(uint8_t *blocks, uint64_t b, uint32_t t, DevCounters 
 }
 
 template <int F>
-__global__ void __launch_bounds__(TPB) tcf_point_insert(const uint64_t *__restrict__ keys, uint64_t n, TcfGeom G,
+__global__ void __launch_bounds__(TPB) tcf_point_insert(const uint64_t *__restrict__ keys,
+                                                        const uint8_t *__restrict__ vals, uint64_t n, TcfGeom G,
                                                         uint8_t *blocks, uint64_t *bk, uint8_t *status,
                                                         DevCounters *ctr)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
         KeyInfo k = tcf_keyinfo(keys[i], G);
+        if (vals) k.t |= vals[i] & G.vmask;
         Blk<F> x;
         x.load_l2(blocks, k.b1);
         int f1 = x.live();
@@ -944,7 +1001,7 @@ __global__ void __launch_bounds__(TPB) tcf_point_insert(const uint64_t *__restri
         if (!done) {
             uint64_t e = tcf_entry(k, G.f);
             unsigned long long *p =
-                reinterpret_cast<unsigned long long *>(bk + tcf_bucket(e, G.nbk) * BK_W);
+                reinterpret_cast<unsigned long long *>(bk + tcf_bucket_of(e, G) * BK_W);
             for (int s = 0; s < (int)BK_W && !done; s++)
                 if (atomicCAS(p + s, 0ull, (unsigned long long)e) == 0ull) done = true;
             if (done) atomicAdd(&ctr->backing, 1ull);
@@ -966,13 +1023,15 @@ __global__ void __launch_bounds__(TPB) tcf_point_remove(const uint64_t *__restri
 {
     for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
         KeyInfo k = tcf_keyinfo(keys[i], G);
-        bool done = point_take<F>(blocks, k.b1, k.t, ctr) || point_take<F>(blocks, k.b2, k.t, ctr);
+        bool done = point_take<F>(blocks, k.b1, k.t, G.vmask, ctr) || point_take<F>(blocks, k.b2, k.t, G.vmask, ctr);
         if (!done) {
-            uint64_t e = tcf_entry(k, G.f);
+            const uint64_t e = tcf_entry(k, G.f), em = ~(uint64_t)G.vmask;
             unsigned long long *p =
-                reinterpret_cast<unsigned long long *>(bk + tcf_bucket(e, G.nbk) * BK_W);
-            for (int s = 0; s < (int)BK_W && !done; s++)
-                if (atomicCAS(p + s, (unsigned long long)e, 0ull) == (unsigned long long)e) done = true;
+                reinterpret_cast<unsigned long long *>(bk + tcf_bucket_of(e, G) * BK_W);
+            for (int s = 0; s < (int)BK_W && !done; s++) {
+                const unsigned long long v = __ldcg(p + s);
+                if ((v & em) == e && atomicCAS(p + s, v, 0ull) == v) done = true;
+            }
             if (done) atomicAdd(&ctr->backing, (unsigned long long)-1ll);
         }
         if (status) status[i] = done ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;
@@ -1005,6 +1064,7 @@ int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
 {
     const filter_config &c = F->cfg;
     if (c.tag_bits != 8 && c.tag_bits != 16) return FILTER_ERR_ARG;
+    if (c.value_bits > c.tag_bits / 2 || c.value_bits > 7) return FILTER_ERR_ARG;
     if (c.mode != FILTER_MODE_BULK && c.mode != FILTER_MODE_POINT) return FILTER_ERR_ARG;
     const uint32_t B = 256 / c.tag_bits, lb = (B == 16) ? 4 : 5;
     if (c.log2_slots < lb + 1 || c.log2_slots > lb + 32) return FILTER_ERR_ARG;
@@ -1013,7 +1073,9 @@ int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     T.G.f = c.tag_bits;
     T.G.B = B;
     T.G.tsc = 3 * B / 4;
-    T.G.tmask = (1u << c.tag_bits) - 1u;
+    T.G.tmask = (1u << (c.tag_bits - c.value_bits)) - 1u;
+    T.G.vbits = c.value_bits;
+    T.G.vmask = (1u << c.value_bits) - 1u;
     T.G.nb = 1ull << (c.log2_slots - lb);
     T.G.seed = c.hash_seed;
     const uint64_t N = 1ull << c.log2_slots;
@@ -1222,7 +1284,7 @@ static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     }
 }
 
-int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+int tcf_insert(filter *F, const uint64_t *keys, const uint8_t *vals, uint64_t n, uint8_t *status, cudaStream_t st)
 {
     if (n == 0) return FILTER_OK;
     if (status) GF_CUDA(cudaMemsetAsync(status, 0, n, st));
@@ -1231,11 +1293,11 @@ int tcf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
         const int g = grid_for(n, TPB, 16);
         {
             gf::TraceScope ts_("tcf_point_insert", n, st);
-            if (T.G.f == 16) tcf_point_insert<16><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
-            else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
+            if (T.G.f == 16) tcf_point_insert<16><<<g, TPB, 0, st>>>(keys, vals, n, T.G, T.blocks, T.bk, status, F->ctr);
+            else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, vals, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr});
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr, vals});
         if (T.G.f == 16) tcf_bulk_insert<16>(W, keys, n, status, st);
         else tcf_bulk_insert<8>(W, keys, n, status, st);
     }
@@ -1264,15 +1326,19 @@ int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
     return FILTER_OK;
 }
 
-int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, cudaStream_t st)
+int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, bool values, cudaStream_t st)
 {
     if (n == 0) return FILTER_OK;
     TcfState &T = F->tcf;
     const int g = grid_for(n, TPB, 16);
-    {
+    if (values) {
+        gf::TraceScope ts_("tcf_query_values_kernel", n, st);
+        if (T.G.f == 16) tcf_query_kernel<16, true><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+        else tcf_query_kernel<8, true><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+    } else {
         gf::TraceScope ts_("tcf_query_kernel", n, st);
-        if (T.G.f == 16) tcf_query_kernel<16><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
-        else tcf_query_kernel<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+        if (T.G.f == 16) tcf_query_kernel<16, false><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+        else tcf_query_kernel<8, false><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -1373,7 +1439,7 @@ __global__ void __launch_bounds__(TPB) tcf_group_query_kernel(const uint64_t *__
         Blk<F> x, y;
         x.load_ro(blocks, M.block0 + k.b1);
         y.load_ro(blocks, M.block0 + k.b2);
-        bool hit = x.has(k.t) || y.has(k.t);
+        bool hit = x.has(k.t, 0xffffffffu) || y.has(k.t, 0xffffffffu);  // group members carry no values
         if (!hit && backing) {
             const uint64_t e = tcf_entry(k, F);
             const ulonglong2 *p =
@@ -1398,7 +1464,7 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     uint64_t nb_tot = 0, nbk_tot = 0;
     for (uint32_t m = 0; m < n; m++) {
         const filter_config &c = cfgs[m];
-        if (c.kind != FILTER_TCF || c.tag_bits != f || c.mode != FILTER_MODE_BULK) return FILTER_ERR_ARG;
+        if (c.kind != FILTER_TCF || c.tag_bits != f || c.mode != FILTER_MODE_BULK || c.value_bits) return FILTER_ERR_ARG;
         filter V;
         V.cfg = c;
         V.cfg.max_batch = M;

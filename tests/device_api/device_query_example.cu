@@ -45,3 +45,23 @@ extern "C" int device_update_example(const filter_device_view *v, const uint64_t
     device_update_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, remove, status);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
+
+// TCF with values: read the smallest stored value per key, or insert keys
+// with their values (point mode).
+__global__ void device_value_kernel(filter_device_view v, const uint64_t *keys, uint64_t n, const uint8_t *in,
+                                    uint8_t *out)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        if (in) out[i] = (uint8_t)gf_device_tcf_insert(v, keys[i], in[i]);
+        else out[i] = (uint8_t)gf_device_tcf_value(v, keys[i]);
+    }
+}
+
+extern "C" int device_value_example(const filter_device_view *v, const uint64_t *keys, uint64_t n,
+                                    const uint8_t *values_in, uint8_t *out, void *stream)
+{
+    if (!v || n == 0) return 0;
+    const unsigned grid = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+    device_value_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, values_in, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}

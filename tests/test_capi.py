@@ -53,6 +53,8 @@ def test_null_arguments_rejected_without_gpu(libpath):
     lib = ctypes.CDLL(libpath)
     assert lib.filter_create(None, None, None) == 1
     assert lib.filter_insert(None, None, 0, None, None) == 1
+    assert lib.filter_insert_values(None, None, None, 0, None, None) == 1
+    assert lib.filter_query_values(None, None, 0, None, None) == 1
     assert lib.filter_destroy(None) == 0
 
 
@@ -82,6 +84,8 @@ def test_group_configurations_rejected_without_gpu(libpath):
     assert create([tcf, gf.FilterConfig(gf.FILTER_TCF, 12, 8, 0, 1, 1)]) == 1    # mixed tag widths
     assert create([gf.FilterConfig(gf.FILTER_TCF, 12, 16, gf.MODE_POINT, 1, 1)]) == 1  # point mode
     assert create([gf.FilterConfig(gf.FILTER_GQF, 40, 16, 0, 1, 1)]) == 1        # q + r beyond limits
+    assert create([gf.FilterConfig(gf.FILTER_TCF, 12, 16, gf.MODE_BULK, 1, 1, 4)]) == 1  # members with values
+    assert create([gf.FilterConfig(gf.FILTER_GQF, 12, 8, 0, 1, 1, 4)]) == 1      # GQF values: counters
     assert lib.filter_group_create(None, 0, 1, None, ctypes.byref(h)) == 1
     assert lib.filter_group_insert(None, None, None, 0, None, None) == 1
     assert lib.filter_group_destroy(None) == 0

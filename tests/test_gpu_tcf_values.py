@@ -1,0 +1,221 @@
+"""GPU parity for the TCF with values (Sec. 1 and Sec. 4: small values stored
+with the items). Bulk mode: the table image equals the oracle's byte for byte
+after every batch of keys with values and after deletes; value answers and
+statuses equal the oracle's. Point mode (Alg. 1) places keys its own way, so
+there the stored (fingerprint, value) multiset read back from the image must
+equal the inserted one, and each value answer the smallest stored value of
+the key's fingerprint. Device-side inserts with values and value reads from a
+caller's kernel give the same answers as the C ABI."""
+import collections
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2212_09005_gb300 import workloads as W
+from gpu_util import dev_u64, zeros_u8, host, first_diff
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def gf():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2212_09005_gb300 as gf
+
+    gf.lib()
+    return gf
+
+
+def dev_u8(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint8)).cuda()
+
+
+def values_for(seed, n, v):
+    return np.random.default_rng(seed).integers(0, 1 << v, n).astype(np.uint8)
+
+
+def stored_pairs(image, O, gmap):
+    """(fingerprint, value) multiset of a table image (blocks, then buckets)."""
+    vm = (1 << O.v) - 1
+    nbB = O.nb * 32
+    blocks = image[:nbB].view(np.uint16 if O.f == 16 else np.uint8).reshape(O.nb, O.B)
+    out = collections.Counter()
+    for b, s in zip(*np.nonzero(blocks > 1)):  # neither EMPTY nor TOMBSTONE
+        x = int(blocks[b, s])
+        t = x & ~vm
+        b2 = int(b) ^ gmap[t]
+        out[((min(int(b), b2) << O.f) | t, x & vm)] += 1
+    for e in image[nbB:].view(np.uint64).tolist():
+        if e:
+            out[(e & ~vm, e & vm)] += 1
+    return out
+
+
+@pytest.mark.parametrize("log2_slots,f,v", [(12, 16, 4), (16, 16, 4), (15, 16, 7), (14, 8, 2), (11, 8, 4)])
+def test_bulk_values_image_and_answers(gf, oracle, log2_slots, f, v):
+    n = int(0.78 * (1 << log2_slots))
+    keys = W.uniform_keys(900 + log2_slots + v, n)
+    cuts = [0, 1, 7, n // 6, n // 3, n // 2, n]
+    batches = [np.concatenate([keys[a:b], keys[a:a + (b - a) // 5]]) for a, b in zip(cuts, cuts[1:]) if b > a]
+    vals = [values_for(k + v, len(b), v) for k, b in enumerate(batches)]
+    O = oracle.TCF(log2_slots, f, seed=log2_slots, value_bits=v)
+    mb = max(len(b) for b in batches)
+    G = gf.TCF(log2_slots, f, gf.MODE_BULK, seed=log2_slots, max_batch=mb, value_bits=v)
+    for k, (b, x) in enumerate(zip(batches, vals)):
+        st_o = O.insert(b, values=x)
+        st = zeros_u8(len(b))
+        G.insert(dev_u64(b), st, values=dev_u8(x))
+        assert np.array_equal(host(st), st_o), k
+        d = first_diff(G.export(), O.export())
+        assert d is None, (k, d)
+    assert G.stats()["backing_used"] == O.backing_count()
+    probe = np.concatenate([keys, W.uniform_keys(950 + log2_slots, 30000)])
+    got = zeros_u8(len(probe))
+    G.query_values(dev_u64(probe), got)
+    want = O.query_values(probe)
+    assert np.array_equal(host(got), want)
+    found = zeros_u8(len(probe))
+    G.query(dev_u64(probe), found)
+    assert np.array_equal(host(found), O.query(probe))
+    assert np.array_equal(host(found), (want != 0xFF).astype(np.uint8))
+    # deletes: each removes the smallest value of the first block holding a copy
+    for gone in (keys[::3], np.concatenate([keys[:50], keys[:50], W.uniform_keys(960, 500)])):
+        st_o = O.remove(gone)
+        st = zeros_u8(len(gone))
+        G.remove(dev_u64(gone), st)
+        assert np.array_equal(host(st), st_o)
+        d = first_diff(G.export(), O.export())
+        assert d is None, d
+    G.query_values(dev_u64(probe), got)
+    assert np.array_equal(host(got), O.query_values(probe))
+
+
+def test_plain_insert_stores_value_zero(gf, oracle):
+    keys = W.uniform_keys(970, 3000)
+    O = oracle.TCF(12, 16, seed=5, value_bits=4)
+    G = gf.TCF(12, 16, gf.MODE_BULK, seed=5, max_batch=len(keys), value_bits=4)
+    O.insert(keys)
+    G.insert(dev_u64(keys))
+    assert first_diff(G.export(), O.export()) is None
+    got = zeros_u8(len(keys))
+    G.query_values(dev_u64(keys), got)
+    assert (host(got) == 0).all()
+
+
+def test_value_calls_rejected_where_unsupported(gf):
+    keys = dev_u64(W.uniform_keys(971, 10))
+    out = zeros_u8(10)
+    plain = gf.TCF(10, 16, gf.MODE_BULK, max_batch=16)
+    with pytest.raises(gf.FilterError):
+        plain.query_values(keys, out)
+    with pytest.raises(gf.FilterError):
+        plain.insert(keys, values=out)
+    gq = gf.GQF(10, 8, max_batch=16)
+    with pytest.raises(gf.FilterError):
+        gq.query_values(keys, out)
+    for f, v in ((16, 8), (8, 5)):
+        with pytest.raises(gf.FilterError):
+            gf.TCF(10, f, gf.MODE_BULK, max_batch=16, value_bits=v)
+    with pytest.raises(gf.FilterError):
+        gf.Filter(gf.FILTER_GQF, 10, 8, 0, max_batch=16, value_bits=2)
+
+
+@pytest.mark.parametrize("f,v", [(16, 4), (8, 2)])
+def test_point_values_match_the_stored_multiset(gf, oracle, f, v):
+    log2 = 14
+    O = oracle.TCF(log2, f, seed=8, value_bits=v)  # geometry and fingerprints only
+    keys = W.uniform_keys(972 + f, int(0.85 * (1 << log2)))
+    keys = np.concatenate([keys, keys[:500]])
+    vals = values_for(973, len(keys), v)
+    G = gf.TCF(log2, f, gf.MODE_POINT, seed=8, max_batch=len(keys), value_bits=v)
+    st = zeros_u8(len(keys))
+    G.insert(dev_u64(keys), st, values=dev_u8(vals))
+    st = host(st)
+    b1, b2, t = O.keyinfo(keys)
+    gmap = {int(a): int(x ^ y) for a, x, y in zip(t, b1, b2)}
+    fps = O.fingerprints(keys).tolist()
+    want = collections.Counter((fps[i], int(vals[i])) for i in np.nonzero(st == 0)[0])
+    assert stored_pairs(G.export(), O, gmap) == want
+    assert (st == 0).mean() > 0.97  # near 88% load a point-mode key can find no room
+    best = {}
+    for (fp, x), _ in want.items():
+        best[fp] = min(best.get(fp, 0xFF), x)
+    probe = np.concatenate([keys[:5000], W.uniform_keys(974, 20000)])
+    exp = np.array([best.get(fp, 0xFF) for fp in O.fingerprints(probe).tolist()], np.uint8)
+    got = zeros_u8(len(probe))
+    G.query_values(dev_u64(probe), got)
+    assert np.array_equal(host(got), exp)
+    # removes take one copy of the fingerprint each, whatever its value
+    gone = keys[1::3]
+    rs = zeros_u8(len(gone))
+    G.remove(dev_u64(gone), rs)
+    rs = host(rs)
+    after = stored_pairs(G.export(), O, gmap)
+    assert not (after - want)
+    lost = collections.Counter()
+    for (fp, _), c in (want - after).items():
+        lost[fp] += c
+    assert lost == collections.Counter(np.asarray(O.fingerprints(gone))[rs == 0].tolist())
+
+
+@pytest.fixture(scope="module")
+def example(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("device_api_values") / "libdevice_query_example.so")
+    src = os.path.join(ROOT, "tests", "device_api", "device_query_example.cu")
+    cmd = ["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-shared", "-Xcompiler",
+           "-fPIC", "-I", os.path.join(ROOT, "include"), "-o", out, src]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lib = C.CDLL(out)
+    lib.device_value_example.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.device_value_example.restype = C.c_int
+    lib.device_query_example.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.device_query_example.restype = C.c_int
+    return lib
+
+
+def test_device_side_values_equal_the_c_abi(gf, oracle, example):
+    import torch
+
+    v = 4
+    keys = W.uniform_keys(975, 12000)
+    keys = np.concatenate([keys, keys[:2000]])
+    vals = values_for(976, len(keys), v)
+    G = gf.TCF(14, 16, gf.MODE_POINT, seed=12, max_batch=len(keys), value_bits=v)
+    view = G.device_view()
+    assert view.value_bits == v
+    dk, dv, st = dev_u64(keys), dev_u8(vals), zeros_u8(len(keys))
+    assert example.device_value_example(C.byref(view), C.c_void_p(dk.data_ptr()), len(keys),
+                                        C.c_void_p(dv.data_ptr()), C.c_void_p(st.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert (host(st) == 0).mean() > 0.99
+    probe = dev_u64(np.concatenate([keys, W.uniform_keys(977, 20000)]))
+    view = G.device_view()
+    mine, theirs = zeros_u8(probe.numel()), zeros_u8(probe.numel())
+    assert example.device_value_example(C.byref(view), C.c_void_p(probe.data_ptr()), probe.numel(), None,
+                                        C.c_void_p(mine.data_ptr()), None) == 0
+    G.query_values(probe, theirs)
+    a, b = host(mine), host(theirs)
+    assert np.array_equal(a, b)
+    assert (a[:len(keys)] != 0xFF).mean() > 0.99
+    found = zeros_u8(probe.numel())
+    assert example.device_query_example(C.byref(view), C.c_void_p(probe.data_ptr()), probe.numel(),
+                                        C.c_void_p(found.data_ptr()), None, None) == 0
+    assert np.array_equal(host(found), (b != 0xFF).astype(np.uint8))
+    # a bulk filter filled through the C ABI reads the same from a caller's kernel
+    B = gf.TCF(13, 8, gf.MODE_BULK, seed=3, max_batch=len(keys), value_bits=2)
+    B.insert(dk[:6000], values=dev_u8(vals[:6000] & 3))
+    view = B.device_view()
+    assert example.device_value_example(C.byref(view), C.c_void_p(probe.data_ptr()), probe.numel(), None,
+                                        C.c_void_p(mine.data_ptr()), None) == 0
+    B.query_values(probe, theirs)
+    assert np.array_equal(host(mine), host(theirs))
