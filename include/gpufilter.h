@@ -25,7 +25,10 @@
  *   bits 44.. of h (f bits, 0 and 1 moved to 2 and 3), b2 = b1 xor g(tag).
  *   nb = 2^log2_slots / B blocks of 32 bytes (B = 256 / f tags). Backing
  *   table: nbk buckets of 8 uint64 entries (min(b1,b2) << f | tag), nbk =
- *   max(8, ceil(ceil(N/100) / 8)) (Sec. 4.1, "backing table").
+ *   max(8, ceil(ceil(N/100) / 8)) (Sec. 4.1, "backing table"). With
+ *   value_bits v > 0 the tag is f - v bits wide and each slot holds
+ *   tag << v | value; g and the bucket (hashed with the value bits cleared)
+ *   depend on the tag alone.
  *   GQF (paper Sec. 5): p = q + r, fp = mix_p(fold_p(key) ^ seed mod 2^p),
  *   quotient = fp >> r, remainder = fp mod 2^r. N = 2^q home slots plus a
  *   tail of S = max(64, min(N, roundup64(1072 q))) slots. Per 64-slot block a
