@@ -67,6 +67,7 @@ def _declare(L):
     L.or_gqf_free.argtypes = [C.c_void_p]
     L.or_gqf_fingerprints.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u64p]
     L.or_gqf_insert.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p]
+    L.or_gqf_insert_counts.argtypes = [C.c_void_p, _u64p, _u32p, C.c_uint64, _u8p]
     L.or_gqf_remove.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p]
     L.or_gqf_count.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u64p]
     L.or_gqf_insert_groups.restype = C.c_uint64
@@ -249,6 +250,15 @@ class GQF:
         keys = _u64(keys)
         st = np.zeros(keys.size, np.uint8)
         lib().or_gqf_insert(self._h, _p(keys, _u64p), keys.size, _p(st, _u8p))
+        return st
+
+    def insert_counts(self, keys, counts):
+        """Key i counts as counts[i] >= 1 copies."""
+        keys = _u64(keys)
+        counts = np.ascontiguousarray(counts, dtype=np.uint32)
+        assert counts.size == keys.size
+        st = np.zeros(keys.size, np.uint8)
+        lib().or_gqf_insert_counts(self._h, _p(keys, _u64p), _p(counts, _u32p), keys.size, _p(st, _u8p))
         return st
 
     def remove(self, keys):

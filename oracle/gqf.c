@@ -39,6 +39,11 @@
  *  it and every later group of the batch are rejected (status 1), which keeps
  *  the longest prefix of the sorted batch that fits (R).
  *
+ *  Counted insert (values through the counters: Sec. 2 notes that the CQF
+ *  associates values with items by using its counters): key i comes with
+ *  c_i >= 1 and counts as c_i copies, so a group's count is the sum of the
+ *  c_i of its keys. Everything else is the bulk insert above.
+ *
  *  Bulk delete (Sec. 6.4): groups are removed in descending order ("larger
  *  items first"), shifting the following runs left but never before their
  *  home slot. A group of d deletes of a fingerprint with count c removes
@@ -443,6 +448,11 @@ static int pair_cmp(const void *a, const void *b)
 
 void or_gqf_insert(or_gqf *G, const uint64_t *keys, uint64_t n, uint8_t *status)
 {
+    or_gqf_insert_counts(G, keys, NULL, n, status);
+}
+
+void or_gqf_insert_counts(or_gqf *G, const uint64_t *keys, const uint32_t *counts, uint64_t n, uint8_t *status)
+{
     if (n == 0) return;
     pair_t *P = malloc(n * sizeof(pair_t));
     for (uint64_t i = 0; i < n; i++) P[i] = (pair_t){fp_of(G, keys[i]), i};
@@ -451,7 +461,12 @@ void or_gqf_insert(or_gqf *G, const uint64_t *keys, uint64_t n, uint8_t *status)
     for (uint64_t s = 0; s < n;) {
         uint64_t e = s;
         while (e < n && P[e].fp == P[s].fp) e++;
-        if (!overflowed && insert_group(G, P[s].fp, e - s)) overflowed = 1;
+        uint64_t c = e - s;
+        if (counts) {
+            c = 0;
+            for (uint64_t k = s; k < e; k++) c += counts[P[k].i];
+        }
+        if (!overflowed && insert_group(G, P[s].fp, c)) overflowed = 1;
         if (status)
             for (uint64_t k = s; k < e; k++) status[P[k].i] = overflowed ? 1 : 0;
         s = e;

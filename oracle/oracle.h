@@ -54,6 +54,8 @@ or_gqf *or_gqf_new(unsigned q, unsigned r, uint64_t seed);
 void or_gqf_free(or_gqf *G);
 void or_gqf_fingerprints(const or_gqf *G, const uint64_t *keys, uint64_t n, uint64_t *fp);
 void or_gqf_insert(or_gqf *G, const uint64_t *keys, uint64_t n, uint8_t *status);
+void or_gqf_insert_counts(or_gqf *G, const uint64_t *keys, const uint32_t *counts, uint64_t n,
+                          uint8_t *status);
 void or_gqf_remove(or_gqf *G, const uint64_t *keys, uint64_t n, uint8_t *status);
 void or_gqf_count(const or_gqf *G, const uint64_t *keys, uint64_t n, uint64_t *counts);
 /* raw fingerprint groups (ascending, distinct); returns index of the first

@@ -262,3 +262,33 @@ def test_uniform_config_shape_small(oracle):
     assert (G.count(keys) >= 1).all()
     _, f, n = brute(G.fingerprints(keys))
     assert np.array_equal(G.export(), oracle.gqf_build(q, 8, f, n))
+
+
+@pytest.mark.parametrize("q,r,load", [(10, 8, 0.6), (9, 16, 0.45), (8, 8, 1.3)])
+def test_counted_insert_equals_repeated_keys(oracle, q, r, load):
+    """Values through the counters: a key with count c is c copies. The table
+    equals the one built from the keys repeated c times (at load 1.3 the batch
+    overflows and the kept prefix must agree too), each key's status equals
+    its copies', and counts are the summed weights for injective keys."""
+    n = int(load * (1 << q))
+    keys = uniform_keys(1200 + q, n) & np.uint64((1 << (q + r)) - 1)
+    keys = np.concatenate([keys, keys[:n // 5]])
+    rng = np.random.default_rng(q)
+    counts = rng.integers(1, 5, keys.size).astype(np.uint32)
+    counts[::37] = rng.integers(250, 70000, counts[::37].size)  # counters of several digits
+    A, B = oracle.GQF(q, r, seed=3), oracle.GQF(q, r, seed=3)
+    st_a = A.insert_counts(keys, counts)
+    rep = np.repeat(keys, counts)
+    first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    st_b = B.insert(rep)
+    assert np.array_equal(A.export(), B.export())
+    assert np.array_equal(st_a, st_b[first])
+    if load > 1:
+        assert (st_a == 1).any() and (st_a == 0).any()
+    else:
+        assert (st_a == 0).all()
+        want = collections.Counter()
+        for k, c in zip(keys.tolist(), counts.tolist()):
+            want[k] += c
+        u = np.array(sorted(want), np.uint64)
+        assert np.array_equal(A.count(u), np.array([want[int(k)] for k in u], np.uint64))
