@@ -135,6 +135,21 @@ int filter_insert_values(filter_t *f, const uint64_t *d_keys, const uint8_t *d_v
                          uint8_t *d_status, void *stream);
 
 /*
+ * filter_insert_counts: GQF only. Key i counts as d_counts[i] copies: its
+ * fingerprint's count grows by that much, in the same single pass (sort,
+ * reduce with the counts summed per fingerprint, merge). This is how the GQF
+ * associates values with items: through its counters, as the counting
+ * quotient filter it follows does (Sec. 2 of the paper); filter_count reads
+ * them back. Statuses and the kept prefix on overflow are those of
+ * filter_insert. Every count must be >= 1 and their sum below 2^32, else
+ * FILTER_ERR_ARG and the table is unchanged (checked on the device; the call
+ * synchronises `stream`). d_counts: n uint32. n <= max_batch. Returns
+ * FILTER_ERR_UNSUPPORTED for a TCF.
+ */
+int filter_insert_counts(filter_t *f, const uint64_t *d_keys, const uint32_t *d_counts, uint64_t n,
+                         uint8_t *d_status, void *stream);
+
+/*
  * filter_query: d_found[i] = 1 if key i may be in the set (no false
  * negatives; false positives at the filter's rate), else 0.
  * TCF: tag in block b1 or b2 or the backing bucket. GQF: count > 0.

@@ -32,7 +32,7 @@ STATUS_FULL, STATUS_TIMEOUT, STATUS_INTERNAL = 1 << ERR_FULL, 1 << ERR_TIMEOUT, 
 # entry points declared in include/gpufilter.h
 EXPORTS = [
     "filter_create", "filter_destroy", "filter_clear", "filter_insert", "filter_query",
-    "filter_insert_values", "filter_query_values",
+    "filter_insert_values", "filter_query_values", "filter_insert_counts",
     "filter_remove", "filter_count", "filter_get_stats", "filter_get_device_view", "filter_export_size",
     "filter_gqf_enumerate", "filter_gqf_keys_of",
     "filter_export", "filter_import", "filter_error_string",
@@ -107,6 +107,7 @@ def lib():
         for name in ("filter_insert", "filter_query", "filter_remove", "filter_count", "filter_query_values"):
             getattr(L, name).argtypes = [vp, vp, u64, vp, vp]
         L.filter_insert_values.argtypes = [vp, vp, vp, u64, vp, vp]
+        L.filter_insert_counts.argtypes = [vp, vp, vp, u64, vp, vp]
         L.filter_get_stats.argtypes = [vp, vp, C.POINTER(FilterStats)]
         L.filter_export_size.argtypes = [vp, C.POINTER(u64)]
         L.filter_export.argtypes = [vp, vp, u64, vp]
@@ -205,6 +206,13 @@ class Filter:
     def query(self, keys, found, stream=None):
         _check(lib().filter_query(self._h, _dptr(keys, 8), keys.numel(), _dptr(found, 1),
                                   _stream(stream)), "filter_query")
+
+    def insert_counts(self, keys, counts, status=None, stream=None):
+        """GQF: key i counts as counts[i] >= 1 copies (int32 tensor, read as uint32)."""
+        if counts.numel() != keys.numel():
+            raise FilterError("one count per key")
+        _check(lib().filter_insert_counts(self._h, _dptr(keys, 8), _dptr(counts, 4), keys.numel(),
+                                          _dptr(status, 1), _stream(stream)), "filter_insert_counts")
 
     def query_values(self, keys, values, stream=None):
         """TCF with values: smallest stored value per key, 0xFF when absent."""

@@ -96,7 +96,15 @@ int filter_insert(filter_t *f, const uint64_t *d_keys, uint64_t n, uint8_t *d_st
 {
     if (!valid(f) || n > f->cfg.max_batch || (n && !d_keys)) return FILTER_ERR_ARG;
     return f->cfg.kind == FILTER_TCF ? gf::tcf_insert(f, d_keys, nullptr, n, d_status, as_stream(stream))
-                                     : gf::gqf_insert(f, d_keys, n, d_status, as_stream(stream));
+                                     : gf::gqf_insert(f, d_keys, nullptr, n, d_status, as_stream(stream));
+}
+
+int filter_insert_counts(filter_t *f, const uint64_t *d_keys, const uint32_t *d_counts, uint64_t n,
+                         uint8_t *d_status, void *stream)
+{
+    if (!valid(f) || n > f->cfg.max_batch || (n && (!d_keys || !d_counts))) return FILTER_ERR_ARG;
+    if (f->cfg.kind != FILTER_GQF) return FILTER_ERR_UNSUPPORTED;
+    return gf::gqf_insert(f, d_keys, d_counts, n, d_status, as_stream(stream));
 }
 
 int filter_insert_values(filter_t *f, const uint64_t *d_keys, const uint8_t *d_values, uint64_t n,

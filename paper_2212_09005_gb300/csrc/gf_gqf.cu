@@ -1363,6 +1363,45 @@ __global__ void gqf_delete_phase(GView g, const uint64_t *__restrict__ ufp, cons
 }
 
 // ---------------------------------------------------------------------------
+// Counted insert: each key stands for its count of copies
+// ---------------------------------------------------------------------------
+// ws[j] = count of sorted element j, ws[n] = 0; the 64-bit total and whether
+// some count was 0 go to *total and *zero
+__global__ void __launch_bounds__(256) gqf_counts_sorted(const uint32_t *__restrict__ counts,
+                                                         const uint32_t *__restrict__ sidx, uint64_t n,
+                                                         uint32_t *__restrict__ ws, unsigned long long *total,
+                                                         unsigned long long *zero)
+{
+    unsigned long long sum = 0;
+    bool z = false;
+    for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t c = counts[sidx[j]];
+        ws[j] = c;
+        sum += c;
+        z |= c == 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) ws[n] = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    const bool anyz = __any_sync(0xffffffffu, z);
+    if ((threadIdx.x & 31) == 0) {
+        if (sum) atomicAdd(total, sum);
+        if (anyz) atomicOr(zero, 1ull);
+    }
+}
+
+// cstart[g] = copies in the groups before g (g = 0 .. m), from the scanned
+// per-element counts: the group counts the merge and the in-place insert read
+__global__ void __launch_bounds__(256) gqf_group_counts(const uint32_t *__restrict__ scanned,
+                                                        const uint32_t *__restrict__ ustart, const uint32_t *pm,
+                                                        uint32_t *__restrict__ cstart)
+{
+    const uint64_t m = *pm;
+    for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g <= m; g += (uint64_t)gridDim.x * blockDim.x)
+        cstart[g] = scanned[ustart[g]];
+}
+
+// ---------------------------------------------------------------------------
 // per-key status after a batch
 // ---------------------------------------------------------------------------
 // run_of[i] = group of sorted element i
@@ -1632,7 +1671,9 @@ static void gqf_prepare(filter *F, const uint64_t *keys, uint64_t n, bool need_i
     *sorted_idx = Q.idx_b;
 }
 
-static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, cudaStream_t st)
+// cstart: group g adds (or removes) cstart[g + 1] - cstart[g] copies
+static int gqf_merge(filter *F, const uint32_t *cstart, uint64_t n, uint64_t m_limit, int del, int dry,
+                     cudaStream_t st)
 {
     GqfState &Q = F->gqf;
     const int nb = Q.cur ^ 1;
@@ -1642,7 +1683,7 @@ static int gqf_merge(filter *F, uint64_t n, uint64_t m_limit, int del, int dry, 
     a.meta_new = reinterpret_cast<Meta *>(Q.meta[nb]);
     a.rem_new = Q.rem[nb];
     a.ufp = Q.ufp;
-    a.ustart = Q.ustart;
+    a.ustart = cstart;
     a.pm = Q.flags + n;
     a.tlo = Q.tile_lo;
     a.m_limit = m_limit;
@@ -1687,7 +1728,8 @@ static int read_dev(const T *d, T *h, cudaStream_t st)
 // Small batches go in place over even-odd regions; `done` is false when the
 // pre-check found, at every region size tried, a region whose inserts could
 // reach the region after next (or the table's end).
-static int gqf_insert_in_place(filter *F, uint64_t n, uint32_t m, cudaStream_t st, bool &done)
+static int gqf_insert_in_place(filter *F, const uint32_t *cstart, uint64_t n, uint32_t m, cudaStream_t st,
+                               bool &done)
 {
     GqfState &Q = F->gqf;
     done = false;
@@ -1706,10 +1748,10 @@ static int gqf_insert_in_place(filter *F, uint64_t n, uint32_t m, cudaStream_t s
         {
             gf::TraceScope ts_("gqf_insert_precheck", nreg, st);
             if (Q.r == 8)
-                gqf_insert_precheck<8><<<grid_for(nreg, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq,
+                gqf_insert_precheck<8><<<grid_for(nreg, 128, 8), 128, 0, st>>>(g, Q.ufp, cstart, Q.tile_lo, nreg, rq,
                                                                                &F->ctr->overflow);
             else
-                gqf_insert_precheck<16><<<grid_for(nreg, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq,
+                gqf_insert_precheck<16><<<grid_for(nreg, 128, 8), 128, 0, st>>>(g, Q.ufp, cstart, Q.tile_lo, nreg, rq,
                                                                                 &F->ctr->overflow);
         }
         unsigned long long bad = 0;
@@ -1719,10 +1761,10 @@ static int gqf_insert_in_place(filter *F, uint64_t n, uint32_t m, cudaStream_t s
         for (int ph = 0; ph < 2; ph++) {
             gf::TraceScope ts_("gqf_insert_phase", half, st);
             if (Q.r == 8)
-                gqf_insert_phase<8><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq, ph,
+                gqf_insert_phase<8><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, cstart, Q.tile_lo, nreg, rq, ph,
                                                                             &F->ctr->status);
             else
-                gqf_insert_phase<16><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, Q.ustart, Q.tile_lo, nreg, rq,
+                gqf_insert_phase<16><<<grid_for(half, 128, 8), 128, 0, st>>>(g, Q.ufp, cstart, Q.tile_lo, nreg, rq,
                                                                              ph, &F->ctr->status);
         }
         GF_CUDA(cudaGetLastError());
@@ -1732,20 +1774,45 @@ static int gqf_insert_in_place(filter *F, uint64_t n, uint32_t m, cudaStream_t s
     return FILTER_OK;
 }
 
-int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t n, uint8_t *status,
+               cudaStream_t st)
 {
     if (n == 0) return FILTER_OK;
     GqfState &Q = F->gqf;
     uint32_t *sidx = nullptr;
-    gqf_prepare(F, keys, n, status != nullptr, st, &sidx);
+    gqf_prepare(F, keys, n, status != nullptr || counts != nullptr, st, &sidx);
     int rc;
+    // the copies each group adds: its keys, or the sum of their counts
+    const uint32_t *cstart = Q.ustart;
+    if (counts) {
+        // fp_a and fp_c (2 words per key each) are free once the sort is done
+        uint32_t *ws = reinterpret_cast<uint32_t *>(Q.fp_c), *cs = reinterpret_cast<uint32_t *>(Q.fp_a);
+        GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
+        GF_CUDA(cudaMemsetAsync(&F->ctr->wflag, 0, 8, st));
+        {
+            gf::TraceScope ts_("gqf_counts_sorted", n, st);
+            gqf_counts_sorted<<<grid_for(n, 256, 8), 256, 0, st>>>(counts, sidx, n, ws, &F->ctr->overflow,
+                                                                   &F->ctr->wflag);
+        }
+        unsigned long long total = 0, zero = 0;
+        if ((rc = read_dev(&F->ctr->overflow, &total, st))) return rc;
+        if ((rc = read_dev(&F->ctr->wflag, &zero, st))) return rc;
+        if (zero || total >= (1ull << 32)) return FILTER_ERR_ARG;  // nothing was written
+        exclusive_scan_u32(ws, ws, n + 1, F->scan_tmp, F->ctr, st);
+        {
+            gf::TraceScope ts_("gqf_group_counts", n, st);
+            gqf_group_counts<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(ws, Q.ustart, Q.flags + n, cs);
+        }
+        GF_CUDA(cudaGetLastError());
+        cstart = cs;
+    }
     // small batches: in place, region by region; larger ones: the merge
     {
         uint32_t m = 0;
         if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
         if ((uint64_t)m * RQ_MIN <= GROUPS_PER_REGION * Q.N && !Q.merge_only) {
             bool done = false;
-            if ((rc = gqf_insert_in_place(F, n, m, st, done))) return rc;
+            if ((rc = gqf_insert_in_place(F, cstart, n, m, st, done))) return rc;
             if (done) {
                 if (status) {
                     gf::TraceScope ts_("gqf_status_kernel", n, st);
@@ -1757,7 +1824,7 @@ int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             }
         }
     }
-    rc = gqf_merge(F, n, ~0ull, 0, 0, st);
+    rc = gqf_merge(F, cstart, n, ~0ull, 0, 0, st);
     if (rc) return rc;
     unsigned long long ovf = 0;
     if ((rc = read_dev(&F->ctr->overflow, &ovf, st))) return rc;
@@ -1769,14 +1836,14 @@ int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
         uint64_t lo = 0, hi = m;  // lo fits, hi does not
         while (hi - lo > 1) {
             uint64_t mid = (lo + hi) / 2;
-            if ((rc = gqf_merge(F, n, mid, 0, 1, st))) return rc;
+            if ((rc = gqf_merge(F, cstart, n, mid, 0, 1, st))) return rc;
             unsigned long long o2 = 0;
             if ((rc = read_dev(&F->ctr->overflow, &o2, st))) return rc;
             if (o2) hi = mid;
             else lo = mid;
         }
         m_keep = lo;
-        if ((rc = gqf_merge(F, n, m_keep, 0, 0, st))) return rc;
+        if ((rc = gqf_merge(F, cstart, n, m_keep, 0, 0, st))) return rc;
         {
             gf::TraceScope ts_("gqf_account_full", 1, st);
             gqf_account_full<<<1, 1, 0, st>>>(F->ctr, Q.ustart, m_keep, n);
@@ -1841,7 +1908,7 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
         }
     }
     if (!done) {
-        if ((rc = gqf_merge(F, n, ~0ull, 1, 0, st))) return rc;
+        if ((rc = gqf_merge(F, Q.ustart, n, ~0ull, 1, 0, st))) return rc;
         Q.cur ^= 1;
     }
     if (status) {
@@ -2319,7 +2386,7 @@ int gqf_group_insert(filter_group *GR, const uint64_t *off, const uint64_t *keys
             GF_CUDA(cudaStreamSynchronize(st));
             filter &F = GR->members[m];
             F.gqf.cur = GR->cur;
-            if ((rc = gqf_insert(&F, keys + o[0], o[1] - o[0], status ? status + o[0] : nullptr, st))) return rc;
+            if ((rc = gqf_insert(&F, keys + o[0], nullptr, o[1] - o[0], status ? status + o[0] : nullptr, st))) return rc;
         }
     }
     group_set_cur(GR, GR->cur ^ 1);

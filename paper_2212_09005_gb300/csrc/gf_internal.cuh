@@ -44,7 +44,7 @@ struct DevCounters {
     long long gqf_end;            // GQF merge: end of the last run (dry runs)
     unsigned int touched[4];      // TCF sparse phases: touched destinations (cursor must follow)
     unsigned int cursor[4];       // TCF sparse phases: records placed so far
-    unsigned long long pad[1];
+    unsigned long long wflag;     // GQF counted insert: 1 if some count was 0
 };
 static_assert(offsetof(DevCounters, cursor) == offsetof(DevCounters, touched) + sizeof(DevCounters::touched),
               "touched and cursor are cleared together");
@@ -382,7 +382,8 @@ int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st);
 int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);
 uint64_t gqf_tile_lo_words(const GqfState &Q);
 int gqf_clear(filter *F, cudaStream_t st);
-int gqf_insert(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
+int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t n, uint8_t *status,
+               cudaStream_t st);
 int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
 int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uint8_t *found,
               cudaStream_t st);

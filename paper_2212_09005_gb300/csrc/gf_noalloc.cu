@@ -109,7 +109,7 @@ extern "C" int filter_gqf_insert_noalloc(uint32_t q, uint32_t r, uint64_t hash_s
         GF_CUDA(cudaMemcpyAsync(tout, tin, imageB, cudaMemcpyDeviceToDevice, st));
         rc = FILTER_OK;
     } else {
-        rc = gqf_insert(&F, d_keys, n, d_status, st);
+        rc = gqf_insert(&F, d_keys, nullptr, n, d_status, st);
     }
     F.arena.base = nullptr;  // the host description goes out of scope; nothing to free
     return rc;
