@@ -53,6 +53,8 @@ BYTES_PER_UNIT = {
     "gqf_count_kernel": 80.0,    # key + metadata sector + remainder sector + count
     "gqf_status_kernel": 13.0,
     "tcf_query_kernel": 73.0,    # key + two 32-byte blocks + found byte
+    "tcf_query_values_kernel": 73.0,  # key + two 32-byte blocks + value byte (bucket reads not counted)
+    "gqf_counts_sorted": 12.0,   # sorted index read + count gather + sorted count write
     "tcf_group_hist": 8.0,       # key read
     "tcf_group_scatter": 16.0,   # key read + record write
     "tcf_group_hist_sparse": 12.0,     # per candidate (counted on the device): pending entry + key read
@@ -90,7 +92,7 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
-    ap.add_argument("--case", default="full", choices=["full", "profile", "batched", "serving", "kmer"],
+    ap.add_argument("--case", default="full", choices=["full", "profile", "batched", "serving", "kmer", "values"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
     return ap.parse_args()
@@ -600,6 +602,92 @@ def run_kmer(args, device):
     return out
 
 
+VALUES_WORKLOAD = ("values: TCF 2^26 slots f=16 bulk with 4-bit values (12-bit tags): 15 x 2^22-key insert "
+                   "batches with values to 90% load, then 2^25 value queries (half inserted keys, half fresh); "
+                   "counting GQF 2^28 slots r=8: one counted insert of 2^25 + 2^24 uniform keys below 2^32 "
+                   "with counts 1..8 (about 66% of the slots: a count of 2 or more takes 3 or 4), then 2^24 "
+                   "counts of inserted keys")
+
+
+def run_values(args, device):
+    """Value association in both filters: TCF slots carrying 4-bit values, and
+    the GQF's counted insert (values through the counters)."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    nt = 15 * (1 << 22)
+    tk = W.uniform_keys(7001, nt)
+    tv = (W.uniform_keys(7002, nt) & np.uint64(15)).astype(np.uint8)
+    tq = np.concatenate([tk[W.sample_with_replacement(7003, nt, 1 << 24)], W.uniform_keys(7004, 1 << 24)])
+    ng = (1 << 25) + (1 << 24)
+    gk = W.uniform_keys(7005, ng) & np.uint64(0xFFFFFFFF)
+    gc = (1 + (W.uniform_keys(7006, ng) & np.uint64(7))).astype(np.uint32)
+    gpos = W.sample_with_replacement(7007, ng, 1 << 24)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    tkd, tvd, tqd = to_dev(tk.view(np.int64)), to_dev(tv), to_dev(tq.view(np.int64))
+    gkd, gcd, gqd = to_dev(gk.view(np.int64)), to_dev(gc.view(np.int32)), to_dev(gk[gpos].view(np.int64))
+    tout = torch.zeros(len(tq), dtype=torch.uint8, device=device)
+    gout = torch.zeros(len(gpos), dtype=torch.int64, device=device)
+    T = gf.TCF(26, 16, gf.MODE_BULK, seed=21, max_batch=1 << 22, value_bits=4)
+    G = gf.GQF(28, 8, seed=22, max_batch=ng)
+    B = 1 << 22
+
+    def step():
+        T.clear()
+        for o in range(0, nt, B):
+            T.insert(tkd[o:o + B], values=tvd[o:o + B])
+        T.query_values(tqd, tout)
+        G.clear()
+        G.insert_counts(gkd, gcd)
+        G.count(gqd, gout)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    gf.trace_reset()
+    gf.trace_enable(True)
+    clocks = ClockSampler(device.index or 0)
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    gf.trace_enable(False)
+    trace = gf.trace_summary()
+    ms = e0.elapsed_time(e1)
+    kern, roof = roofline_from_trace(trace)
+    ops = nt + len(tq) + ng + len(gpos)
+    tv_got = tout.cpu().numpy()
+    # the true counts of the probed keys (keys below 2^32 < 2^36: the fingerprint
+    # is injective), reduced with torch outside the timed region
+    sk, order = torch.sort(gkd)
+    uk, inv = torch.unique_consecutive(sk, return_inverse=True)
+    tot = torch.zeros(len(uk), dtype=torch.int64, device=device).index_add_(0, inv, gcd[order].to(torch.int64))
+    exact = bool(torch.equal(tot[torch.searchsorted(uk, gqd)], gout))
+    del sk, order, uk, inv, tot
+    st_t, st_g = T.stats(), G.stats()
+    per_kind = {k["kernel"]: k for k in kern}
+    out = {"workload": VALUES_WORKLOAD, "value": round(aggregate_rate(ops, args.steps, 1, ms), 4), "unit": UNIT,
+           "ms_per_step": round(ms / args.steps, 3), "ops_per_step": ops,
+           "tcf_query_values_gops": round(len(tq) / (per_kind["tcf_query_values_kernel"]["ms"] / args.steps) / 1e6, 2),
+           "clocks": clk, "gpu_launches": sum(v["launches"] for v in trace.values()), "roofline": roof,
+           "kernels": kern,
+           "checks": {"tcf_inserted_found": float((tv_got[:1 << 24] != 0xFF).mean()),
+                      "tcf_value_equal": float((tv_got[:1 << 24] == tv[W.sample_with_replacement(7003, nt, 1 << 24)]).mean()),
+                      "gqf_counts_exact": exact,
+                      "tcf_failed_keys": st_t["failed_keys"], "gqf_failed_keys": st_g["failed_keys"],
+                      "status_word": st_t["status_word"] | st_g["status_word"]}}
+    del T, G
+    torch.cuda.empty_cache()
+    return out
+
+
 SERVING_WORKLOAD = ("serving loop: 64 filters of 2^24 slots (32 TCF f=16 bulk + 32 counting GQF r=8, "
                     "2^30 slots in all) pre-filled to 50%; batches of 2^10..2^24 keys (log-uniform) for a "
                     "uniformly chosen filter, 50/45/5 insert/query/delete, until 90% aggregate load; host "
@@ -855,6 +943,16 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": KMER_WORKLOAD}, "clocks": km["clocks"], "gpu_launches": km["gpu_launches"],
                 "roofline": km["roofline"], "kmer": km}
+    elif args.case == "values":
+        import torch
+
+        torch.cuda.set_device(local)
+        vl = run_values(args, torch.device("cuda", local))
+        line = {"metric": METRIC, "value": vl["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": vl["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": VALUES_WORKLOAD}, "clocks": vl["clocks"], "gpu_launches": vl["gpu_launches"],
+                "roofline": vl["roofline"], "values": vl}
     elif args.case == "batched":
         import torch
 

@@ -1365,8 +1365,9 @@ __global__ void gqf_delete_phase(GView g, const uint64_t *__restrict__ ufp, cons
 // ---------------------------------------------------------------------------
 // Counted insert: each key stands for its count of copies
 // ---------------------------------------------------------------------------
-// ws[j] = count of sorted element j, ws[n] = 0; the 64-bit total and whether
-// some count was 0 go to *total and *zero
+// ws[j] = count of sorted element j: counts[sidx[j]], or counts[j] when the
+// sort carried the counts (sidx null); the 64-bit total and whether some
+// count was 0 go to *total and *zero
 __global__ void __launch_bounds__(256) gqf_counts_sorted(const uint32_t *__restrict__ counts,
                                                          const uint32_t *__restrict__ sidx, uint64_t n,
                                                          uint32_t *__restrict__ ws, unsigned long long *total,
@@ -1375,12 +1376,11 @@ __global__ void __launch_bounds__(256) gqf_counts_sorted(const uint32_t *__restr
     unsigned long long sum = 0;
     bool z = false;
     for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < n; j += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t c = counts[sidx[j]];
+        const uint32_t c = sidx ? counts[sidx[j]] : counts[j];
         ws[j] = c;
         sum += c;
         z |= c == 0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) ws[n] = 0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
     const bool anyz = __any_sync(0xffffffffu, z);
@@ -1390,15 +1390,17 @@ __global__ void __launch_bounds__(256) gqf_counts_sorted(const uint32_t *__restr
     }
 }
 
-// cstart[g] = copies in the groups before g (g = 0 .. m), from the scanned
-// per-element counts: the group counts the merge and the in-place insert read
+// cstart[g] = copies in the groups before g (g = 0 .. m), from the exclusive
+// scan of the per-element counts and their total (below 2^32, checked on the
+// host): the group counts the merge and the in-place insert read
 __global__ void __launch_bounds__(256) gqf_group_counts(const uint32_t *__restrict__ scanned,
                                                         const uint32_t *__restrict__ ustart, const uint32_t *pm,
+                                                        const unsigned long long *total,
                                                         uint32_t *__restrict__ cstart)
 {
     const uint64_t m = *pm;
     for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g <= m; g += (uint64_t)gridDim.x * blockDim.x)
-        cstart[g] = scanned[ustart[g]];
+        cstart[g] = g < m ? scanned[ustart[g]] : (uint32_t)*total;
 }
 
 // ---------------------------------------------------------------------------
@@ -1658,13 +1660,15 @@ int gqf_clear(filter *F, cudaStream_t st)
     return FILTER_OK;
 }
 
-// sort + reduce: leaves groups in ufp / ustart, group count in flags[n]
+// sort + reduce: leaves groups in ufp / ustart, group count in flags[n]. The
+// sort carries the batch indices (need_idx: statuses) or a caller's per-key
+// values (vals, without statuses); either ends in idx_b in sorted order.
 static void gqf_prepare(filter *F, const uint64_t *keys, uint64_t n, bool need_idx, cudaStream_t st,
-                        uint32_t **sorted_idx)
+                        uint32_t **sorted_idx, const uint32_t *vals = nullptr)
 {
     GqfState &Q = F->gqf;
     fingerprint_for_sort(keys, n, Q.H, Q.fp_a, need_idx ? Q.idx_a : nullptr, Q.p, Q.radix_tmp, st);
-    radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : nullptr, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp,
+    radix_sort_u64(Q.fp_a, Q.fp_b, Q.fp_c, need_idx ? Q.idx_a : vals, Q.idx_b, Q.idx_c, n, Q.p, Q.radix_tmp,
                    F->scan_tmp, F->ctr, st, true);
     // groups: flags[n] = their number; flags[i] = the group of sorted element i (statuses only)
     rle_sorted_u64(Q.fp_b, n, Q.ufp, Q.ustart, need_idx ? Q.flags : nullptr, Q.flags + n, F->scan_tmp, F->ctr, st);
@@ -1780,7 +1784,9 @@ int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t
     if (n == 0) return FILTER_OK;
     GqfState &Q = F->gqf;
     uint32_t *sidx = nullptr;
-    gqf_prepare(F, keys, n, status != nullptr || counts != nullptr, st, &sidx);
+    // counts without statuses ride through the sort in place of the indices
+    const bool carry = counts != nullptr && status == nullptr;
+    gqf_prepare(F, keys, n, status != nullptr, st, &sidx, carry ? counts : nullptr);
     int rc;
     // the copies each group adds: its keys, or the sum of their counts
     const uint32_t *cstart = Q.ustart;
@@ -1791,17 +1797,18 @@ int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t
         GF_CUDA(cudaMemsetAsync(&F->ctr->wflag, 0, 8, st));
         {
             gf::TraceScope ts_("gqf_counts_sorted", n, st);
-            gqf_counts_sorted<<<grid_for(n, 256, 8), 256, 0, st>>>(counts, sidx, n, ws, &F->ctr->overflow,
-                                                                   &F->ctr->wflag);
+            gqf_counts_sorted<<<grid_for(n, 256, 8), 256, 0, st>>>(carry ? Q.idx_b : counts, carry ? nullptr : sidx,
+                                                                   n, ws, &F->ctr->overflow, &F->ctr->wflag);
         }
         unsigned long long total = 0, zero = 0;
         if ((rc = read_dev(&F->ctr->overflow, &total, st))) return rc;
         if ((rc = read_dev(&F->ctr->wflag, &zero, st))) return rc;
         if (zero || total >= (1ull << 32)) return FILTER_ERR_ARG;  // nothing was written
-        exclusive_scan_u32(ws, ws, n + 1, F->scan_tmp, F->ctr, st);
+        exclusive_scan_u32(ws, ws, n, F->scan_tmp, F->ctr, st);
         {
             gf::TraceScope ts_("gqf_group_counts", n, st);
-            gqf_group_counts<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(ws, Q.ustart, Q.flags + n, cs);
+            gqf_group_counts<<<grid_for(n + 1, 256, 8), 256, 0, st>>>(ws, Q.ustart, Q.flags + n, &F->ctr->overflow,
+                                                                      cs);
         }
         GF_CUDA(cudaGetLastError());
         cstart = cs;
