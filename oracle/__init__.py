@@ -46,6 +46,8 @@ def _declare(L):
     L.or_tcf_new.argtypes = [C.c_uint, C.c_uint, C.c_uint64]
     L.or_tcf_new_values.restype = C.c_void_p
     L.or_tcf_new_values.argtypes = [C.c_uint, C.c_uint, C.c_uint, C.c_uint64]
+    L.or_tcf_new_geom.restype = C.c_void_p
+    L.or_tcf_new_geom.argtypes = [C.c_uint, C.c_uint, C.c_uint, C.c_uint, C.c_uint64]
     L.or_tcf_free.argtypes = [C.c_void_p]
     L.or_tcf_keyinfo.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u64p, _u64p, _u32p]
     L.or_tcf_insert.argtypes = [C.c_void_p, _u64p, C.c_uint64, _u8p, _u8p, _u64p]
@@ -134,13 +136,19 @@ class TCF:
     """Deterministic bulk two-choice filter (see tcf.c for the specification).
     value_bits > 0 gives each slot a value of that many bits below the tag."""
 
-    def __init__(self, log2_slots: int, tag_bits: int = 16, seed: int = 0, value_bits: int = 0):
-        self._h = lib().or_tcf_new_values(log2_slots, tag_bits, value_bits, seed)
+    def __init__(self, log2_slots: int, tag_bits: int = 16, seed: int = 0, value_bits: int = 0,
+                 block_slots: int = 0, log2_blocks: int = 0):
+        """Either log2_slots (32-byte blocks of 256 / tag_bits slots) or
+        log2_blocks and block_slots (any geometry tcf.c allows)."""
+        if block_slots:
+            self._h = lib().or_tcf_new_geom(log2_blocks, tag_bits, block_slots, value_bits, seed)
+        else:
+            self._h = lib().or_tcf_new_values(log2_slots, tag_bits, value_bits, seed)
         if not self._h:
             raise ValueError("bad TCF geometry")
-        g = np.zeros(7, dtype=np.uint64)
+        g = np.zeros(8, dtype=np.uint64)
         lib().or_tcf_geometry(self._h, _p(g, _u64p))
-        self.nb, self.B, self.f, self.tsc, self.nbk, self.W, self.v = (int(v) for v in g)
+        self.nb, self.B, self.f, self.tsc, self.nbk, self.W, self.v, self.block_bytes = (int(v) for v in g)
         self.log2_slots, self.seed = log2_slots, seed
 
     def __del__(self):
@@ -205,12 +213,14 @@ class TCF:
         return buf
 
     def blocks(self) -> np.ndarray:
-        raw = self.export()[: self.nb * 32]
-        dt = np.uint16 if self.f == 16 else np.uint8
-        return raw.view(dt).reshape(self.nb, self.B)
+        """Slots per block, unpacked from the image (nb x B, uint16)."""
+        raw = self.export()[: self.nb * self.block_bytes].reshape(self.nb, self.block_bytes)
+        bits = np.unpackbits(raw, axis=1, bitorder="little")[:, : self.B * self.f]
+        w = (1 << np.arange(self.f)).astype(np.uint32)
+        return (bits.reshape(self.nb, self.B, self.f).astype(np.uint32) @ w).astype(np.uint16)
 
     def buckets(self) -> np.ndarray:
-        return self.export()[self.nb * 32:].view(np.uint64).reshape(self.nbk, self.W)
+        return self.export()[self.nb * self.block_bytes:].view(np.uint64).reshape(self.nbk, self.W)
 
     def backing_count(self) -> int:
         return lib().or_tcf_backing_count(self._h)

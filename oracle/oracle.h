@@ -30,6 +30,9 @@ void or_mix_p_many(const uint64_t *in, uint64_t *out, uint64_t n, unsigned p);
 typedef struct or_tcf or_tcf;
 or_tcf *or_tcf_new(unsigned log2_slots, unsigned tag_bits, uint64_t seed);
 or_tcf *or_tcf_new_values(unsigned log2_slots, unsigned tag_bits, unsigned value_bits, uint64_t seed);
+/* nb = 2^log2_blocks blocks of block_slots slots of tag_bits in {8, 12, 16} */
+or_tcf *or_tcf_new_geom(unsigned log2_blocks, unsigned tag_bits, unsigned block_slots, unsigned value_bits,
+                        uint64_t seed);
 void or_tcf_free(or_tcf *T);
 void or_tcf_keyinfo(const or_tcf *T, const uint64_t *keys, uint64_t n,
                     uint64_t *b1, uint64_t *b2, uint32_t *tag);
@@ -46,7 +49,7 @@ uint64_t or_tcf_export_size(const or_tcf *T);
 void or_tcf_export(const or_tcf *T, uint8_t *buf);
 uint64_t or_tcf_backing_count(const or_tcf *T);
 uint64_t or_tcf_stored_count(const or_tcf *T);
-void or_tcf_geometry(const or_tcf *T, uint64_t *out7); /* nb, B, f, tsc, nbk, W, v */
+void or_tcf_geometry(const or_tcf *T, uint64_t *out8); /* nb, B, f, tsc, nbk, W, v, block bytes */
 
 /* ---- GQF (gqf.c) ---- */
 typedef struct or_gqf or_gqf;

@@ -37,6 +37,16 @@
  *
  *  Query: tag in block b1, or in block b2, or e in its bucket.
  *
+ *  Other geometries (Sec. 4.1 bounds the point TCF's block by a 128-byte
+ *  cache line; Sec. 4.2 gives the bulk TCF 128-slot blocks of 16 bits; the
+ *  design study varies the block size and stores 12-bit tags, which then
+ *  straddle word boundaries). nb = 2^k blocks of B slots of f bits, f in
+ *  {8, 12, 16}, 4 <= B and f B <= 2048 bits. A block occupies the smallest
+ *  multiple of 32 bytes that holds its slots; slot s sits at bit f s of the
+ *  block, little-endian, and the bits past the last slot are 0. N = nb B,
+ *  the backing table is sized from N as above, and everything else is the
+ *  same, with the shortcut at fill + j < floor(3B/4).
+ *
  *  Values (Sec. 1 and Sec. 4 list associating small values with items as a
  *  TCF feature; R: the layout below). With v value bits (v <= f / 2, and
  *  v <= 7 so that 0xFF stays free to answer "absent"), a slot of f bits
@@ -69,6 +79,7 @@
 
 struct or_tcf {
     unsigned f, B, tsc;
+    unsigned bbytes; /* bytes per block in the image */
     unsigned vb;     /* value bits in each slot */
     uint64_t vmask;  /* the value part of a slot or entry */
     uint64_t nb, nbk, seed;
@@ -109,19 +120,29 @@ or_tcf *or_tcf_new(unsigned log2_slots, unsigned tag_bits, uint64_t seed)
 or_tcf *or_tcf_new_values(unsigned log2_slots, unsigned tag_bits, unsigned value_bits, uint64_t seed)
 {
     if (tag_bits != 8 && tag_bits != 16) return NULL;
-    if (value_bits > tag_bits / 2 || value_bits > 7) return NULL; /* 0xFF answers "absent" */
     unsigned B = 256u / tag_bits;
     unsigned lb = (B == 16) ? 4 : 5;
     if (log2_slots < lb + 1 || log2_slots > 40) return NULL;
+    return or_tcf_new_geom(log2_slots - lb, tag_bits, B, value_bits, seed);
+}
+
+or_tcf *or_tcf_new_geom(unsigned log2_blocks, unsigned tag_bits, unsigned block_slots, unsigned value_bits,
+                        uint64_t seed)
+{
+    if (tag_bits != 8 && tag_bits != 12 && tag_bits != 16) return NULL;
+    if (value_bits > tag_bits / 2 || value_bits > 7) return NULL; /* 0xFF answers "absent" */
+    unsigned B = block_slots;
+    if (B < 4 || tag_bits * B > 2048 || log2_blocks < 1 || log2_blocks > 34) return NULL;
     or_tcf *T = (or_tcf *)calloc(1, sizeof(or_tcf));
     T->f = tag_bits;
     T->vb = value_bits;
     T->vmask = (1ULL << value_bits) - 1ULL;
     T->B = B;
     T->tsc = 3 * B / 4;
-    T->nb = 1ULL << (log2_slots - lb);
+    T->bbytes = (tag_bits * B + 255) / 256 * 32;
+    T->nb = 1ULL << log2_blocks;
     T->seed = seed;
-    uint64_t N = 1ULL << log2_slots;
+    uint64_t N = T->nb * B;
     uint64_t cap = (N + 99) / 100;
     T->nbk = (cap + BK_W - 1) / BK_W;
     if (T->nbk < 8) T->nbk = 8;
@@ -151,6 +172,7 @@ void or_tcf_geometry(const or_tcf *T, uint64_t *o)
     o[4] = T->nbk;
     o[5] = BK_W;
     o[6] = T->vb;
+    o[7] = T->bbytes;
 }
 
 static void keyinfo1(const or_tcf *T, uint64_t key, uint64_t *b1, uint64_t *b2, uint32_t *t)
@@ -237,7 +259,7 @@ static int block_take(or_tcf *T, uint64_t b, uint32_t t)
 /* ascending tags, EMPTY padding */
 static void block_canon(or_tcf *T, uint64_t b)
 {
-    uint16_t v[32];
+    uint16_t v[256];
     unsigned c = 0;
     for (unsigned s = 0; s < T->B; s++)
         if (T->tags[b * T->B + s]) v[c++] = T->tags[b * T->B + s];
@@ -482,22 +504,24 @@ void or_tcf_remove(or_tcf *T, const uint64_t *keys, uint64_t n, uint8_t *status)
 
 uint64_t or_tcf_export_size(const or_tcf *T)
 {
-    return T->nb * 32ULL + T->nbk * BK_W * 8ULL;
+    return T->nb * (uint64_t)T->bbytes + T->nbk * BK_W * 8ULL;
 }
 
-/* Byte image of the device table: the blocks (tags little-endian, f bits
-   each, 32 bytes per block) followed by the backing buckets (8 little-endian
-   uint64 entries each). */
+/* Byte image of the device table: the blocks (slot s at bit f s of its
+   block, little-endian, bbytes per block, unused bits 0) followed by the
+   backing buckets (8 little-endian uint64 entries each). */
 void or_tcf_export(const or_tcf *T, uint8_t *buf)
 {
-    uint64_t o = 0;
-    for (uint64_t i = 0; i < T->nb * T->B; i++) {
-        uint16_t v = T->tags[i];
-        if (T->f == 8) {
-            buf[o++] = (uint8_t)v;
-        } else {
-            buf[o++] = (uint8_t)(v & 0xff);
-            buf[o++] = (uint8_t)(v >> 8);
+    uint64_t o = T->nb * (uint64_t)T->bbytes;
+    memset(buf, 0, o);
+    for (uint64_t b = 0; b < T->nb; b++) {
+        uint8_t *blk = buf + b * T->bbytes;
+        for (unsigned s = 0; s < T->B; s++) {
+            uint32_t v = T->tags[b * T->B + s];
+            for (unsigned k = 0; k < T->f; k++) {
+                unsigned bit = s * T->f + k;
+                if ((v >> k) & 1u) blk[bit >> 3] |= (uint8_t)(1u << (bit & 7));
+            }
         }
     }
     for (uint64_t i = 0; i < T->nbk * BK_W; i++) {

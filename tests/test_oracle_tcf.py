@@ -60,12 +60,17 @@ def test_membership_equals_fingerprint_multiset(oracle, log2_slots, f):
     assert np.array_equal(T.query(probe), exp)
 
 
-def test_placement_rules_via_trace(oracle):
-    T = oracle.TCF(12, 16, seed=5)  # 256 blocks of 16
+@pytest.mark.parametrize("log2_blocks,f,B", [(8, 16, 16), (9, 16, 8), (6, 16, 64), (5, 16, 128), (8, 12, 21),
+                                              (7, 12, 42), (7, 8, 32)])
+def test_placement_rules_via_trace(oracle, log2_blocks, f, B):
+    """Every geometry (16 slots of 16 bits is the 32-byte default)."""
+    T = oracle.TCF(0, f, seed=5, block_slots=B, log2_blocks=log2_blocks)
     B, tsc = T.B, T.tsc
-    keys = uniform_keys(61, int(0.92 * (1 << 12)))
-    for s in range(0, len(keys), 700):
-        batch = keys[s:s + 700]
+    assert tsc == 3 * B // 4
+    N = T.nb * B
+    keys = uniform_keys(61, int(0.92 * N))
+    for s in range(0, len(keys), N // 6):
+        batch = keys[s:s + N // 6]
         fill0 = (T.blocks() != 0).sum(1)
         bfill0 = (T.buckets() != 0).sum(1)
         st, ph, wh = T.insert(batch, trace=True)
