@@ -72,7 +72,7 @@ typedef struct filter filter_t;
 typedef struct filter_config {
     uint32_t kind;        /* FILTER_TCF or FILTER_GQF */
     uint32_t log2_slots;  /* TCF: log2 of total tag slots; GQF: q */
-    uint32_t tag_bits;    /* TCF: f in {8, 16}; GQF: r in {8, 16} */
+    uint32_t tag_bits;    /* TCF: slot bits f in {8, 16} (tag + value); GQF: r in {8, 16} */
     uint32_t mode;        /* TCF: FILTER_MODE_BULK or FILTER_MODE_POINT; GQF: 0 */
     uint64_t hash_seed;   /* xor-ed into keys before hashing */
     uint64_t max_batch;   /* largest n of one call; sizes the scratch memory (GQF: < 2^30) */
@@ -203,7 +203,7 @@ int filter_get_stats(filter_t *f, void *stream, filter_stats *out);
  */
 typedef struct filter_device_view {
     uint32_t kind;       /* FILTER_TCF or FILTER_GQF */
-    uint32_t tag_bits;   /* TCF: tag bits f; GQF: remainder bits r */
+    uint32_t tag_bits;   /* TCF: slot bits f (tag + value); GQF: remainder bits r */
     uint32_t q;          /* GQF: quotient bits; TCF: 0 */
     uint32_t mode;       /* TCF: FILTER_MODE_BULK or FILTER_MODE_POINT; GQF: 0 */
     uint64_t seed;       /* the filter's hash seed (filter_config.hash_seed) */
