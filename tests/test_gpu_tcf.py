@@ -182,3 +182,37 @@ def test_bulk_config_2_26(gf, oracle):
     found = zeros_u8(len(probe))
     G.query(dev_u64(probe), found)
     assert np.array_equal(host(found), O.query(probe))
+
+
+def test_worked_example_from_keys(gf, oracle):
+    """The hand-derived worked example of the placement rules (tests/golden/
+    tcf_q6_f16_worked.txt) through the C ABI: 4 blocks of 16, the shortcut
+    limit, the tie to b1, the other block, the backing table, and deletes
+    from b1, b2 and the backing table; bytes and statuses as derived."""
+    from test_oracle_tcf_golden import expect_rows, load
+
+    spec = load("tcf_q6_f16_worked.txt")
+    G = gf.TCF(6, 16, gf.MODE_BULK, seed=0, max_batch=64)
+    nb, nbk = 4, 8
+
+    def image():
+        img = G.export()
+        return img[:nb * 32].view(np.uint16).reshape(nb, 16), img[nb * 32:].view(np.uint64).reshape(nbk, 8)
+
+    st = zeros_u8(len(spec["batch1"]))
+    G.insert(dev_u64(np.array(spec["batch1"], np.uint64)), st)
+    assert (host(st) == 0).all()
+    blocks, buckets = image()
+    assert np.array_equal(blocks, expect_rows(spec["block1"], nb, 16, np.uint16)) and not buckets.any()
+    st = zeros_u8(3)
+    G.insert(dev_u64(np.array(spec["batch2"], np.uint64)), st)
+    assert (host(st) == 0).all()
+    blocks, buckets = image()
+    assert np.array_equal(buckets, expect_rows(spec["bucket2"], nbk, 8, np.uint64))
+    assert G.stats()["backing_used"] == 3
+    st = zeros_u8(len(spec["delete"]))
+    G.remove(dev_u64(np.array(spec["delete"], np.uint64)), st)
+    assert host(st).tolist() == spec["delete_status"]
+    blocks, buckets = image()
+    assert np.array_equal(blocks, expect_rows(spec["block3"], nb, 16, np.uint16))
+    assert np.array_equal(buckets, expect_rows(spec["bucket3"], nbk, 8, np.uint64))
