@@ -17,6 +17,15 @@
 // offsets into the other buffer. Every slot of the new buffer is written by
 // exactly one tile.
 //
+// Small batches (at most one group per 32 slots) are inserted in place over
+// even-odd regions instead (Sec. 5.3), and small deletes likewise (Sec. 6.4).
+//
+// Counted insert (values through the counters, as in the CQF the paper
+// follows): each key brings a count; the counts ride through the sort (or are
+// gathered through its index array when statuses are wanted), are scanned,
+// and the merge and the in-place inserts read each group's count from that
+// prefix instead of from the group's number of keys.
+//
 // Count / query (Sec. 5.1 via the cited CQF): offset of the home block,
 // rank over occupieds, select over runends, then a scan of the run.
 #include <type_traits>

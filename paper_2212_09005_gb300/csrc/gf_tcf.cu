@@ -21,6 +21,12 @@
 // Point mode (Alg. 1): one thread per key; the tag goes into the first EMPTY
 // or TOMBSTONE slot by an atomic compare-and-swap, retried a bounded number of
 // times; deletes swap the tag for TOMBSTONE.
+//
+// Values (Sec. 1 and Sec. 4: small values stored with the items): with v
+// value bits a slot holds the (f - v)-bit tag above the value. The phases
+// carry whole slots; g and the bucket use the tag alone; matching masks the
+// value bits; a value query answers the smallest value stored with the key's
+// fingerprint in its blocks and backing bucket.
 #include <type_traits>
 #include <vector>
 
