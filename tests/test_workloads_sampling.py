@@ -45,3 +45,19 @@ def test_batched_workload_shape():
     ch = W.round_chunks(off, w["tcf_rounds"])
     assert np.array_equal(ch[0, :, 0], off[:-1]) and np.array_equal(ch[-1, :, 1], off[1:])
     assert np.array_equal(ch[1:, :, 0], ch[:-1, :, 1])
+
+
+def test_tcf_and_gqf_workload_shapes():
+    t = W.tcf_workload(log2_slots=14, batch=1 << 11, n_query=1 << 12)
+    n = int(0.9 * (1 << 14))
+    ins = t["insert"]
+    assert ins.size == n and len(set(ins.tolist())) == n
+    assert len(set(t["pos_idx"].tolist())) == 1 << 12 and t["pos_idx"].max() < n
+    assert len(set(t["del_idx"].tolist())) == n // 2 and t["del_idx"].max() < n
+    assert not (set(t["negatives"].tolist()) & set(ins.tolist()))
+    g = W.gqf_zipf_workload(q=16, n=200_000, n_query=5000)
+    keys = g["insert"]
+    assert keys.size == 200_000 and int(keys.max()) < (1 << 32)
+    assert set(g["query"].tolist()) <= set(keys.tolist())
+    u, c = np.unique(keys, return_counts=True)
+    assert u[np.argmax(c)] == 0  # rank 1 (key 0) is the hottest
