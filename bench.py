@@ -54,7 +54,8 @@ BYTES_PER_UNIT = {
     "gqf_status_kernel": 13.0,
     "tcf_query_kernel": 73.0,    # key + two 32-byte blocks + found byte
     "tcf_query_values_kernel": 73.0,  # key + two 32-byte blocks + value byte (bucket reads not counted)
-    "gqf_counts_sorted": 12.0,   # sorted index read + count gather + sorted count write
+    "gqf_counts_sorted": 8.0,    # counts carried by the sort: sorted count read + write
+    "gqf_counts_gather": 12.0,   # with statuses: sorted index read + count gather + sorted count write
     "tcf_group_hist": 8.0,       # key read
     "tcf_group_scatter": 16.0,   # key read + record write
     "tcf_group_hist_sparse": 12.0,     # per candidate (counted on the device): pending entry + key read

@@ -1805,7 +1805,7 @@ int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t
         GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
         GF_CUDA(cudaMemsetAsync(&F->ctr->wflag, 0, 8, st));
         {
-            gf::TraceScope ts_("gqf_counts_sorted", n, st);
+            gf::TraceScope ts_(carry ? "gqf_counts_sorted" : "gqf_counts_gather", n, st);
             gqf_counts_sorted<<<grid_for(n, 256, 8), 256, 0, st>>>(carry ? Q.idx_b : counts, carry ? nullptr : sidx,
                                                                    n, ws, &F->ctr->overflow, &F->ctr->wflag);
         }
