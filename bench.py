@@ -410,11 +410,13 @@ def query_vs_gather(kern, footprints, device):
     return out
 
 
-def roofline_from_trace(trace):
+def roofline_from_trace(trace, with_traffic: bool = True):
     """Per-kernel shares and the roofline of the dominant kernel, from the live
-    CUDA-event trace of the timed region."""
+    CUDA-event trace of the timed region. with_traffic: attach the ncu DRAM
+    traffic recorded for this workload (cases without their own capture pass
+    False and report null)."""
     peak, peak_src = peaks()
-    traffic = ncu_traffic()
+    traffic = ncu_traffic() if with_traffic else {}
     kern = []
     tot_ms = sum(v["ms"] for v in trace.values())
     for name, v in trace.items():
@@ -592,7 +594,7 @@ def run_kmer(args, device):
     gf.trace_enable(False)
     trace = gf.trace_summary()
     ms = e0.elapsed_time(e1)
-    kern, roof = roofline_from_trace(trace)
+    kern, roof = roofline_from_trace(trace, with_traffic=False)
     ins_ms = sum(a.elapsed_time(b) for a, b in ins_ev) / len(ins_ev)
     st = G.stats()
     c = cnt.cpu().numpy()
@@ -668,7 +670,7 @@ def run_values(args, device):
     gf.trace_enable(False)
     trace = gf.trace_summary()
     ms = e0.elapsed_time(e1)
-    kern, roof = roofline_from_trace(trace)
+    kern, roof = roofline_from_trace(trace, with_traffic=False)
     ops = nt + len(tq) + ng + len(gpos)
     tv_got = tout.cpu().numpy()
     # the true counts of the probed keys (keys below 2^32 < 2^36: the fingerprint
