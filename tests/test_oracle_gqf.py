@@ -250,6 +250,7 @@ def test_cluster_length_bound(oracle):
     mc = G.max_cluster()
     assert mc < 8192
     assert mc < math.log(2 ** q) / (a - math.log(a) - 1)
+    assert mc == _clusters_from_image(G.export(), G.nblk, G.nslots)
 
 
 def test_uniform_config_shape_small(oracle):
@@ -292,3 +293,43 @@ def test_counted_insert_equals_repeated_keys(oracle, q, r, load):
             want[k] += c
         u = np.array(sorted(want), np.uint64)
         assert np.array_equal(A.count(u), np.array([want[int(k)] for k in u], np.uint64))
+
+
+def _clusters_from_image(img, nblk, nslots):
+    """Longest stretch of slots in use, read from an image's metadata bits by
+    prefix counts, not by walking runs: slot s is in use exactly when more
+    occupied quotients lie at or below s than run ends lie below s (the runs
+    of quotients <= s that are still open at s cover it; a run never starts
+    before its quotient)."""
+    meta = img[:nblk * 32].reshape(nblk, 32)
+    occ = np.unpackbits(meta[:, 0:8], axis=1, bitorder="little").reshape(-1)[:nslots].astype(np.int64)
+    rend = np.unpackbits(meta[:, 8:16], axis=1, bitorder="little").reshape(-1)[:nslots].astype(np.int64)
+    used = np.cumsum(occ) > (np.cumsum(rend) - rend)
+    best = cur = 0
+    for u in used.tolist():
+        cur = cur + 1 if u else 0
+        best = max(best, cur)
+    return best
+
+
+def test_max_cluster_worked_example(oracle):
+    """The hand-derived example's clusters are slots 3..7, 10..14, 60..66 and
+    127..133 (the derivation in the fixture), so the longest is 7 slots."""
+    spec = load("gqf_q7_r8_worked.txt")
+    G = oracle.GQF(spec["q"], spec["r"])
+    fps, cnt = group_arrays(spec)
+    G.insert_groups(fps, cnt)
+    assert G.max_cluster() == 7
+    assert _clusters_from_image(G.export(), G.nblk, G.nslots) == 7
+
+
+@pytest.mark.parametrize("q,r,load", [(10, 8, 0.5), (12, 8, 0.9), (12, 16, 0.95), (14, 8, 0.97)])
+def test_max_cluster_equals_prefix_count_scan(oracle, q, r, load):
+    """Sec. 5.2 cluster lengths: the oracle's longest cluster equals the
+    longest stretch of in-use slots found by prefix counts over the image."""
+    G = oracle.GQF(q, r, seed=q + r)
+    keys = uniform_keys(4000 + q, int(load * (1 << q)))
+    G.insert(np.concatenate([keys, keys[: len(keys) // 7]]))  # some counters too
+    mc = G.max_cluster()
+    assert mc >= 2
+    assert mc == _clusters_from_image(G.export(), G.nblk, G.nslots)

@@ -79,3 +79,51 @@ def test_avalanche(oracle, which):
         n += len(rng_keys) * bits
     assert abs(tot / n - 0.5) < 0.01
     assert worst > 0.40
+
+
+def _murmur3_x64_128(data: bytes, seed: int, fmix) -> bytes:
+    """MurmurHash3_x64_128 (Appleby, SMHasher), written from the published
+    algorithm, with its 64-bit finaliser passed in as `fmix`."""
+    M = (1 << 64) - 1
+
+    def rotl(x, r):
+        return ((x << r) | (x >> (64 - r))) & M
+
+    c1, c2 = 0x87C37B91114253D5, 0x4CF5AD432745937F
+    n = len(data)
+    h1 = h2 = seed & 0xFFFFFFFF
+    nb = n // 16
+    for i in range(nb):
+        k1 = int.from_bytes(data[16 * i:16 * i + 8], "little")
+        k2 = int.from_bytes(data[16 * i + 8:16 * i + 16], "little")
+        h1 ^= (rotl((k1 * c1) & M, 31) * c2) & M
+        h1 = (((rotl(h1, 27) + h2) & M) * 5 + 0x52DCE729) & M
+        h2 ^= (rotl((k2 * c2) & M, 33) * c1) & M
+        h2 = (((rotl(h2, 31) + h1) & M) * 5 + 0x38495AB5) & M
+    tail = data[16 * nb:]
+    if len(tail) > 8:
+        k2 = int.from_bytes(tail[8:], "little")
+        h2 ^= (rotl((k2 * c2) & M, 33) * c1) & M
+    if tail:
+        k1 = int.from_bytes(tail[:8], "little")
+        h1 ^= (rotl((k1 * c1) & M, 31) * c2) & M
+    h1 ^= n
+    h2 ^= n
+    h1 = (h1 + h2) & M
+    h2 = (h2 + h1) & M
+    h1, h2 = fmix(h1), fmix(h2)
+    h1 = (h1 + h2) & M
+    h2 = (h2 + h1) & M
+    return h1.to_bytes(8, "little") + h2.to_bytes(8, "little")
+
+
+def test_mix64_is_the_murmur3_finaliser_smhasher_verification(oracle):
+    """mix64 is MurmurHash3's fmix64. Pinned by SMHasher's published
+    verification code of MurmurHash3_x64_128, 0x6384BA69: hash the keys
+    {}, {0}, {0,1}, .. {0..254} with seeds 256, 255, .. 1, hash the 256
+    concatenated 16-byte results with seed 0, and read the first 4 bytes
+    little-endian. A wrong constant, shift or round in mix64 changes it."""
+    hashes = b"".join(_murmur3_x64_128(bytes(range(i)), 256 - i, oracle.mix64) for i in range(256))
+    final = _murmur3_x64_128(hashes, 0, oracle.mix64)
+    assert int.from_bytes(final[:4], "little") == 0x6384BA69
+    assert oracle.mix64(0) == 0  # fmix64 fixes 0: the x64_128 hash of no bytes with seed 0 is all zero
