@@ -78,6 +78,67 @@ BYTES_PER_UNIT = {
     "gqf_group_count_kernel": 73.0,    # key + metadata sector + remainder sector + found byte
 }
 
+# Algorithmic bytes of one operation (the sectors it must touch, plus its key
+# and result; sort traffic excluded): 32-byte sectors as the filters lay them
+# out, and the same count with every 32-byte sector taken as a 64-byte DRAM
+# access (a random 32-byte read can cost a whole 64-byte burst).
+OP_BYTES = {
+    "tcf_insert": (104, 200),   # key + two 32 B blocks read + one written
+    "tcf_query": (73, 137),     # key + two 32 B blocks + found byte
+    "tcf_delete": (104, 200),
+    "gqf_insert": (136, 264),   # key + metadata and remainder sectors read and written
+    "gqf_query": (73, 137),     # key + metadata sector + remainder sector + found byte
+    "gqf_count": (80, 144),     # key + metadata sector + remainder sector + 8-byte count
+    "gqf_delete": (136, 264),
+}
+
+
+class OpTimer:
+    """CUDA events around every operation call of the timed steps, on the
+    stream the library launches on (torch's current stream). Per operation:
+    the keys it processed and its summed device time, which includes any
+    host round trip inside the call (the GQF insert and delete read their
+    group count back)."""
+
+    def __init__(self, torch):
+        self.torch = torch
+        self.rec = []
+        self.on = False
+
+    def op(self, name, n):
+        timer = self
+
+        class _Scope:
+            def __enter__(self_):
+                if timer.on:
+                    self_.e = (timer.torch.cuda.Event(enable_timing=True), timer.torch.cuda.Event(enable_timing=True))
+                    self_.e[0].record()
+
+            def __exit__(self_, *a):
+                if timer.on:
+                    self_.e[1].record()
+                    timer.rec.append((name, int(n), self_.e))
+
+        return _Scope()
+
+    def summary(self, peak_gbs):
+        self.torch.cuda.synchronize()
+        agg = {}
+        for name, n, (a, b) in self.rec:
+            x = agg.setdefault(name, [0, 0.0])
+            x[0] += n
+            x[1] += a.elapsed_time(b)
+        out = {}
+        for name, (n, ms) in agg.items():
+            b32, b64 = OP_BYTES[name]
+            rate = n / (ms / 1e3)
+            out[name] = {"keys": n, "ms": round(ms, 3), "gops": round(rate / 1e9, 3),
+                         "bytes_per_op": b32, "achieved_gbs": round(rate * b32 / 1e9, 1),
+                         "frac": round(rate * b32 / 1e9 / peak_gbs, 4),
+                         "bytes_per_op_64b": b64, "frac_64b": round(rate * b64 / 1e9 / peak_gbs, 4)}
+        return out
+
+
 BATCHED_WORKLOAD = ("4096 filters: 2048 TCF f=16 bulk + 2048 counting GQF r=8, 2^e slots with e uniform in "
                     "10..20, 85-95% load (7.2e8 keys in total); TCF keys inserted in 8 rounds, GQF keys in "
                     "one batch; then every filter's own keys and as many fresh keys are queried; one group "
@@ -93,7 +154,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
-    ap.add_argument("--case", default="full", choices=["full", "profile", "batched", "serving", "kmer", "values"],
+    ap.add_argument("--no-target", action="store_true", help="skip the 2^28-slot, 90%%-load measurement")
+    ap.add_argument("--case", default="full", choices=["full", "profile", "target", "batched", "serving", "kmer", "values"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
     return ap.parse_args()
@@ -135,6 +197,17 @@ PROFILE_WORKLOAD = ("reduced copy for ncu captures: TCF 2^24 slots f=16 bulk, 2^
 def make_inputs(case: str = "full"):
     from paper_2212_09005_gb300 import workloads as W
 
+    if case == "target":
+        t = W.tcf_workload(log2_slots=28, seed=8, batch=1 << 24, n_query=1 << 24)
+        g = W.gqf_target_workload(q=28, seed=9, n_query=1 << 24)
+        ins = t["insert"]
+        gi = g["insert"]
+        return {
+            "tcf_ins": ins, "tcf_batch": t["batch"], "tcf_probe": np.concatenate([ins[t["pos_idx"]], t["negatives"]]),
+            "tcf_del": ins[t["del_idx"]], "tcf_log2": 28, "tcf_seed": 8, "gqf_qbits": 28, "gqf_seed": 9,
+            "gqf_ins": gi, "gqf_q": np.concatenate([gi[g["pos_idx"]], g["negatives"]]), "gqf_del": gi[g["del_idx"]],
+            "n_pos": len(t["pos_idx"]), "n_gpos": len(g["pos_idx"]),
+        }
     if case == "profile":
         t = W.tcf_workload(log2_slots=24, batch=1 << 20, n_query=1 << 22)
         g = W.gqf_zipf_workload(q=25, n=30_000_000, n_query=1 << 22)
@@ -152,8 +225,10 @@ def make_inputs(case: str = "full"):
 
 
 def ops_per_step(inp):
-    return (len(inp["tcf_ins"]) + 2 * len(inp["tcf_probe"]) + len(inp["tcf_del"])
-            + len(inp["gqf_ins"]) + 3 * len(inp["gqf_q"]))
+    n = len(inp["tcf_ins"]) + 2 * len(inp["tcf_probe"]) + len(inp["tcf_del"]) + len(inp["gqf_ins"])
+    if "gqf_del" in inp:  # count, query, delete, count
+        return n + 3 * len(inp["gqf_q"]) + len(inp["gqf_del"])
+    return n + 3 * len(inp["gqf_q"])
 
 
 def peaks():
@@ -242,14 +317,18 @@ class Runner:
         self.gf, self.torch, self.inp = gf, torch, inp
         self.dev = device
         to = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
-        self.d = {k: to(inp[k]) for k in ("tcf_ins", "tcf_probe", "tcf_del", "gqf_ins", "gqf_q")}
+        self.target = "gqf_del" in inp
+        names = ("tcf_ins", "tcf_probe", "tcf_del", "gqf_ins", "gqf_q") + (("gqf_del",) if self.target else ())
+        self.d = {k: to(inp[k]) for k in names}
         self.found = torch.zeros(len(inp["tcf_probe"]), dtype=torch.uint8, device=device)
         self.found2 = torch.zeros_like(self.found)
         self.cnt = torch.zeros(len(inp["gqf_q"]), dtype=torch.int64, device=device)
         self.cnt2 = torch.zeros_like(self.cnt)
+        self.gfound = torch.zeros(len(inp["gqf_q"]), dtype=torch.uint8, device=device)
+        self.timer = OpTimer(torch)
         self.B = inp["tcf_batch"]
-        self.tcf = gf.TCF(inp["tcf_log2"], 16, gf.MODE_BULK, seed=2, max_batch=self.B)
-        self.gqf = gf.GQF(inp["gqf_qbits"], 8, seed=3, max_batch=len(inp["gqf_ins"]))
+        self.tcf = gf.TCF(inp["tcf_log2"], 16, gf.MODE_BULK, seed=inp.get("tcf_seed", 2), max_batch=self.B)
+        self.gqf = gf.GQF(inp["gqf_qbits"], 8, seed=inp.get("gqf_seed", 3), max_batch=len(inp["gqf_ins"]))
 
     def step(self, src=None, wait=None):
         """One pass of the hot path. `src` maps input names to device tensors;
@@ -257,28 +336,52 @@ class Runner:
         first used, so that its host->device copy can still be in flight."""
         d = src or self.d
         w = wait or (lambda name, k=0: None)
+        op = self.timer.op
         tcf, gqf, B = self.tcf, self.gqf, self.B
         tcf.clear()
         ins = d["tcf_ins"]
         for k, s in enumerate(range(0, ins.numel(), B)):
             w("tcf_ins", k)
-            tcf.insert(ins[s:s + B])
+            b = ins[s:s + B]
+            with op("tcf_insert", b.numel()):
+                tcf.insert(b)
         w("tcf_probe")
-        tcf.query(d["tcf_probe"], self.found)
+        with op("tcf_query", d["tcf_probe"].numel()):
+            tcf.query(d["tcf_probe"], self.found)
         dl = d["tcf_del"]
         for k, s in enumerate(range(0, dl.numel(), B)):
             w("tcf_del", k)
-            tcf.remove(dl[s:s + B])
-        tcf.query(d["tcf_probe"], self.found2)
+            b = dl[s:s + B]
+            with op("tcf_delete", b.numel()):
+                tcf.remove(b)
+        with op("tcf_query", d["tcf_probe"].numel()):
+            tcf.query(d["tcf_probe"], self.found2)
         gqf.clear()
         w("gqf_ins")
-        gqf.insert(d["gqf_ins"])
+        with op("gqf_insert", d["gqf_ins"].numel()):
+            gqf.insert(d["gqf_ins"])
         w("gqf_q")
-        gqf.count(d["gqf_q"], self.cnt)
-        gqf.remove(d["gqf_q"])
-        gqf.count(d["gqf_q"], self.cnt2)
+        q = d["gqf_q"]
+        with op("gqf_count", q.numel()):
+            gqf.count(q, self.cnt)
+        if self.target:
+            with op("gqf_query", q.numel()):
+                gqf.query(q, self.gfound)
+            dq = d["gqf_del"]
+        else:
+            dq = q
+        with op("gqf_delete", dq.numel()):
+            gqf.remove(dq)
+        with op("gqf_count", q.numel()):
+            gqf.count(q, self.cnt2)
 
     def _recount_ok(self):
+        if self.target:
+            # distinct inserted keys were deleted: counts only fall, and the
+            # query answers are count > 0
+            c1, c2 = self.cnt.cpu().numpy(), self.cnt2.cpu().numpy()
+            f = self.gfound.cpu().numpy()
+            return bool((c2 <= c1).all() and np.array_equal(f != 0, c1 > 0))
         # each sampled key was deleted once per occurrence in the sample
         q = self.inp["gqf_q"]
         u, inv, occ = np.unique(q, return_inverse=True, return_counts=True)
@@ -295,7 +398,7 @@ class Runner:
         ok = {
             "tcf_pos_found": bool(self.found[:npos].all().item()),
             "tcf_fpr": float(self.found[npos:].float().mean().item()),
-            "gqf_counts_pos": bool((self.cnt >= 1).all().item()),
+            "gqf_counts_pos": bool((self.cnt[:self.inp.get("n_gpos", len(self.cnt))] >= 1).all().item()),
             "gqf_recount_ok": self._recount_ok(),
             "tcf_status_word": st_t["status_word"], "gqf_status_word": st_g["status_word"],
             "tcf_backing_used": st_t["backing_used"],
@@ -325,15 +428,18 @@ def run_ours(args, rank, world, device_index):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    R.timer.on = True
     e0.record(stream)
     for _ in range(args.steps):
         R.step()
     e1.record(stream)
     torch.cuda.synchronize()
+    R.timer.on = False
     clk = clocks.stop()
     gf.trace_enable(False)
     trace = gf.trace_summary()
     ms = max_over_ranks(e0.elapsed_time(e1), world, device)
+    per_op = R.timer.summary(peaks()[0])
     if world > 1:
         dist.barrier()
     checks = R.checks()
@@ -349,9 +455,15 @@ def run_ours(args, rank, world, device_index):
     if not args.no_e2e:
         e2e = run_e2e(R, args, world, device)
 
+    target = None
+    if args.case == "full" and not args.no_target:
+        del R
+        torch.cuda.empty_cache()
+        target = run_target(args, device)
+
     batched = None
     if args.case == "full" and not args.no_batched:
-        del R
+        R = None
         torch.cuda.empty_cache()
         batched = run_batched(args, device)
 
@@ -364,12 +476,60 @@ def run_ours(args, rank, world, device_index):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic (seeded SplitMix64 uniform keys, Zipf rejection-inversion keys)",
-        "config": {"workload": WORKLOAD if args.case == "full" else PROFILE_WORKLOAD, "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
+        "config": {"workload": {"full": WORKLOAD, "profile": PROFILE_WORKLOAD, "target": TARGET_WORKLOAD}[args.case],
+                   "ops_per_step": ops, "tcf_mode": "bulk (deterministic)",
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-        "cpu_baseline": cpu, "random_gather": gather, "kernels": kern, "checks": checks, "batched": batched,
+        "cpu_baseline": cpu, "random_gather": gather, "per_op": per_op, "kernels": kern, "checks": checks,
+        "target_2_28": target, "batched": batched,
     }
     return line
+
+
+TARGET_WORKLOAD = ("target size, 2^28 slots at 90% load: TCF f=16 bulk, floor(0.9 * 2^28) uniform keys in 2^24-key "
+                   "batches, 2^24 pos + 2^24 neg queries, delete a random half in 2^24-key batches, re-query; GQF "
+                   "r=8, as many uniform keys in one batch, count and query 2^24 inserted + 2^24 fresh keys, delete "
+                   "2^24 distinct inserted keys, re-count")
+
+
+def run_target(args, device):
+    """Both filters at the target size, every operation timed on its own
+    (same step structure as the main workload)."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+
+    inp = make_inputs("target")
+    R = Runner(inp, device)
+    stream = torch.cuda.current_stream()
+    for _ in range(max(3, args.warmup)):
+        R.step()
+    torch.cuda.synchronize()
+    gf.trace_reset()
+    gf.trace_enable(True)
+    clocks = ClockSampler(device.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    R.timer.on = True
+    e0.record(stream)
+    for _ in range(args.steps):
+        R.step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    R.timer.on = False
+    clk = clocks.stop()
+    gf.trace_enable(False)
+    trace = gf.trace_summary()
+    ms = e0.elapsed_time(e1)
+    ops = ops_per_step(inp)
+    kern, roof = roofline_from_trace(trace, with_traffic=False)
+    out = {"workload": TARGET_WORKLOAD, "value": round(aggregate_rate(ops, args.steps, 1, ms), 4), "unit": UNIT,
+           "ms_per_step": round(ms / args.steps, 3), "ops_per_step": ops, "clocks": clk,
+           "per_op": R.timer.summary(peaks()[0]), "gpu_launches": sum(v["launches"] for v in trace.values()),
+           "roofline": roof, "kernels": kern[:12], "checks": R.checks()}
+    del R
+    torch.cuda.empty_cache()
+    return out
 
 
 def gather_peak(footprint_bytes: int, device, sectors_per_key: int = 2, n: int = 1 << 24) -> float:
@@ -798,8 +958,8 @@ def run_e2e(R, args, world, device):
 
     inp = R.inp
     B = R.B
-    names = ("tcf_ins", "tcf_probe", "tcf_del", "gqf_ins", "gqf_q")
-    onames = ("found", "found2", "cnt", "cnt2")
+    names = tuple(R.d.keys())
+    onames = ("found", "found2", "cnt", "cnt2") + (("gfound",) if R.target else ())
     hostb = {k: torch.from_numpy(np.ascontiguousarray(inp[k]).view(np.int64)).pin_memory() for k in names}
     sets = [{k: torch.empty(hostb[k].shape, dtype=torch.int64, device=device) for k in names} for _ in range(2)]
     osets = [{k: torch.empty_like(getattr(R, k)) for k in onames} for _ in range(2)]

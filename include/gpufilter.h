@@ -315,10 +315,14 @@ int filter_calibrate_gather(const void *d_table, uint64_t table_bytes, const uin
  *   cleared), so calls whose GPU work overlaps - on different streams, or from
  *   several host threads - race on it and must be serialised by the caller.
  *   The first call on each device looks the array's device address up with
- *   cudaGetSymbolAddress, with that device current; make that first call
- *   before any stream capture. The call is asynchronous on `stream` except
- *   when the table overflows, where it synchronises `stream`, as
- *   filter_insert does.
+ *   cudaGetSymbolAddress, with that device current, and keeps it for the
+ *   life of the process; a cudaDeviceReset invalidates it, so the call must
+ *   not be used after one.
+ * Synchronisation: like a GQF filter_insert, a call with n > 0 synchronises
+ *   `stream` to read the number of distinct fingerprints in the batch and,
+ *   after the merge, whether the table overflowed (an overflowing batch
+ *   synchronises a few times more while it finds the prefix that fits). The
+ *   GPU work is enqueued on `stream`; d_table_in is only read.
  */
 #define FILTER_NOALLOC_MAX_KEYS 65536u
 #define FILTER_NOALLOC_MAX_Q 20u

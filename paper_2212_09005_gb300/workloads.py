@@ -181,6 +181,21 @@ def gqf_zipf_workload(q: int = 28, n: int = 240_000_000, seed: int = 3, s: float
     return {"q": q, "r": 8, "insert": keys, "query": keys[qpos]}
 
 
+def gqf_target_workload(q: int = 28, seed: int = 9, n_query: int = 1 << 24, load: float = 0.9):
+    """GQF at the target size, 2^q home slots, 8-bit remainders, filled to
+    `load` with uniform keys in one batch (stream seed); positive count
+    queries take n_query inserted keys drawn with replacement
+    (seed*1000 + 2), negatives are n_query fresh keys (seed + 1000); then
+    n_query distinct inserted keys (seed*1000 + 3) are deleted."""
+    n_ins = int(load * (1 << q))
+    ins = uniform_keys(seed, n_ins)
+    nq = min(n_query, n_ins)
+    pos_idx = sample_with_replacement(seed * 1000 + 2, n_ins, nq)
+    neg = uniform_keys(seed + 1000, n_query)
+    del_idx = sample_without_replacement(seed * 1000 + 3, n_ins, nq)
+    return {"q": q, "r": 8, "insert": ins, "pos_idx": pos_idx, "negatives": neg, "del_idx": del_idx}
+
+
 def batched_workload(n_filters: int = 4096, seed: int = 4, emin: int = 10, emax: int = 20,
                      load_lo: float = 0.85, load_hi: float = 0.95, tcf_rounds: int = 8):
     """Many small filters: the first half TCF (16-bit tags, bulk mode), the

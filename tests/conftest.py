@@ -19,3 +19,21 @@ def oracle():
 
     O.lib()
     return O
+
+
+def pytest_collection_finish(session):
+    """Start the minutes-long oracle runs of the target-size tests in spawned
+    processes as soon as one of those tests is selected (and a GPU is
+    present), so that they overlap the GPU tests that run before them."""
+    if not any("test_gpu_target" in it.nodeid for it in session.items):
+        return
+    try:
+        import torch
+
+        if not torch.cuda.is_available():
+            return
+    except Exception:
+        return
+    import target_oracle
+
+    target_oracle.start()
