@@ -406,6 +406,25 @@ class Runner:
         return ok
 
 
+def traced_steps(step, steps):
+    """Per-kernel split: the same steps again with the library's kernel trace
+    on (CUDA events around every launch, on the launching stream). Kept out
+    of the timed region, whose step time the extra event records would
+    lengthen."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+
+    torch.cuda.synchronize()
+    gf.trace_reset()
+    gf.trace_enable(True)
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    gf.trace_enable(False)
+    return gf.trace_summary()
+
+
 def run_ours(args, rank, world, device_index):
     import torch
     import torch.distributed as dist
@@ -422,8 +441,6 @@ def run_ours(args, rank, world, device_index):
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    gf.trace_reset()
-    gf.trace_enable(True)
     clocks = ClockSampler(device_index)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -436,10 +453,9 @@ def run_ours(args, rank, world, device_index):
     torch.cuda.synchronize()
     R.timer.on = False
     clk = clocks.stop()
-    gf.trace_enable(False)
-    trace = gf.trace_summary()
     ms = max_over_ranks(e0.elapsed_time(e1), world, device)
     per_op = R.timer.summary(peaks()[0])
+    trace = traced_steps(R.step, args.steps)
     if world > 1:
         dist.barrier()
     checks = R.checks()
@@ -505,8 +521,6 @@ def run_target(args, device):
     for _ in range(max(3, args.warmup)):
         R.step()
     torch.cuda.synchronize()
-    gf.trace_reset()
-    gf.trace_enable(True)
     clocks = ClockSampler(device.index or 0)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -518,9 +532,8 @@ def run_target(args, device):
     torch.cuda.synchronize()
     R.timer.on = False
     clk = clocks.stop()
-    gf.trace_enable(False)
-    trace = gf.trace_summary()
     ms = e0.elapsed_time(e1)
+    trace = traced_steps(R.step, args.steps)
     ops = ops_per_step(inp)
     kern, roof = roofline_from_trace(trace, with_traffic=False)
     out = {"workload": TARGET_WORKLOAD, "value": round(aggregate_rate(ops, args.steps, 1, ms), 4), "unit": UNIT,
@@ -672,17 +685,14 @@ def run_batched(args, device):
     for _ in range(max(3, args.warmup)):
         R.step()
     torch.cuda.synchronize()
-    gf.trace_reset()
-    gf.trace_enable(True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         R.step()
     e1.record(stream)
     torch.cuda.synchronize()
-    gf.trace_enable(False)
-    trace = gf.trace_summary()
     ms = e0.elapsed_time(e1)
+    trace = traced_steps(R.step, args.steps)
     kern, roof = roofline_from_trace(trace)
     gather = query_vs_gather(kern, {"tcf_group_query_kernel": sum(R.T.export_size(m) for m in range(R.T.n)),
                                     "gqf_group_count_kernel": sum(R.G.export_size(m) for m in range(R.G.n))}, device)

@@ -292,6 +292,29 @@ int filter_calibrate_gather(const void *d_table, uint64_t table_bytes, const uin
                             uint32_t sectors_per_key, uint8_t *d_out, void *stream);
 
 /*
+ * ---- failure-detection self-tests ----
+ * These exist so that the failure paths can be exercised without a real
+ * device fault (the paper has no counterpart).
+ *
+ * filter_debug_fail_alloc: make the nth device allocation the library
+ *   attempts from now on (filter_create, filter_group_create,
+ *   filter_server_create, filter_trace_enable, filter_gqf_enumerate) fail as
+ *   if the device were full; nth = 0 cancels. The call then returns
+ *   FILTER_ERR_OOM and frees what it had allocated. Process-wide.
+ * filter_debug_live_allocations: *n = device allocations the library holds
+ *   now (to check that a failed call leaked nothing).
+ * filter_debug_wait_timeout: run, on `stream`, the library's bounded
+ *   look-back wait (the one its scans and run-length encoding use) against a
+ *   predecessor that never publishes, giving up after spin_limit loads. The
+ *   wait records FILTER_ERR_TIMEOUT in f's sticky status word, which
+ *   filter_get_stats then reports; the filter's table is not touched and the
+ *   filter stays usable. FILTER_ERR_ARG for spin_limit 0.
+ */
+int filter_debug_fail_alloc(uint32_t nth);
+int filter_debug_live_allocations(uint64_t *n);
+int filter_debug_wait_timeout(filter_t *f, uint32_t spin_limit, void *stream);
+
+/*
  * filter_gqf_insert_noalloc: a GQF bulk insert (the same work as
  * filter_insert on a GQF) that allocates no device memory at all. The paper
  * has no counterpart; this exists for callers that must not call cudaMalloc:
@@ -407,34 +430,49 @@ int filter_group_export(filter_group_t *g, uint32_t member, void *host_buf, uint
 /*
  * ---- serving loop ----
  * Batches of host keys for many filters, run concurrently on several CUDA
- * streams. The paper measures isolated bulk calls; this runtime serves a
- * stream of requests (each a batch for one filter) as they arrive.
+ * streams with continuous batching. The paper measures isolated bulk calls;
+ * this runtime serves a stream of requests (each a batch for one filter) as
+ * they arrive.
  *
  * filter_server_create: serve the given filters (created by filter_create on
  *   the current device; the caller keeps ownership and must not use them
- *   while the server runs) with n_workers workers (1..64). Each worker owns a
- *   CUDA stream, a host thread and staging for max_keys keys: 16 bytes per key
- *   on the device and as much pinned host memory. Requests are admitted by
- *   free device memory: if the staging of all workers does not fit in the
- *   free device memory, FILTER_ERR_OOM and nothing is created. Filter i is
- *   served by worker i mod n_workers, which takes its requests in submission
- *   order, so every filter applies its batches in submission order and each
- *   batch's results equal those of the same per-filter sequence run alone.
- *   Every filter's max_batch must be >= the batches submitted to it.
+ *   while the server runs) with n_workers workers (1..64). Each worker is a
+ *   host thread with its own CUDA stream and pinned bounce buffers of
+ *   max_keys keys (16 bytes per key). All workers share one device staging
+ *   pool sized for n_workers batches of max_keys keys (16 bytes per key),
+ *   or, when the free device memory is smaller, for as many such batches as
+ *   fit (FILTER_ERR_OOM when not even one fits; nothing is created).
+ * Scheduling: each filter has a FIFO of requests and at most one batch in
+ *   flight. Any idle worker takes the oldest waiting request among the
+ *   filters with nothing in flight, together with the requests queued right
+ *   behind it on the same filter that can run as one device batch without
+ *   changing any result: queries, counts, and removes from a GQF (a GQF's
+ *   table depends only on the stored multiset, and the earlier request's keys
+ *   come first). TCF inserts and removes and GQF inserts run alone. A batch
+ *   is admitted when its staging (8 bytes per key plus its results) fits in
+ *   the free part of the pool; until then it waits while batches of other
+ *   filters run and release theirs (a batch passed over 8 times blocks
+ *   later ones until it fits). So every filter applies its requests in
+ *   submission order, batches of different filters overlap on the device,
+ *   and each request's results equal those of the same per-filter sequence
+ *   run alone. Every filter's max_batch must be >= the requests submitted to
+ *   it; merged batches stay within max_batch and max_keys.
  * filter_server_submit: enqueue one request and return at once with a
  *   ticket. The key buffer (host memory, pageable or pinned) and the output
  *   buffer must stay valid until the ticket is collected. Page-locked buffers
  *   (cudaHostAlloc / cudaHostRegister) are copied to and from the device
- *   directly; pageable ones go through the worker's pinned staging. host_out receives
- *   n bytes of statuses (insert, remove) or found flags (query), or n uint64
- *   counts (count, GQF only); NULL discards the results. FILTER_ERR_ARG for
- *   a bad filter index or op, n > max_keys, or a server being destroyed.
+ *   directly; pageable ones go through the worker's pinned bounce buffers.
+ *   host_out receives n bytes of statuses (insert, remove) or found flags
+ *   (query), or n uint64 counts (count, GQF only); NULL discards the
+ *   results. FILTER_ERR_ARG for a bad filter index or op, n > max_keys, or a
+ *   server being destroyed.
  * filter_server_wait: block until the request is done, then return
  *   FILTER_OK with *op_rc = the operation's return code and *latency_s = the
  *   seconds from submit to results in host_out. Each ticket is collected
  *   once; an unknown or collected ticket gives FILTER_ERR_ARG.
+ * filter_server_get_stats: counters since creation (see the struct).
  * filter_server_destroy: finish every submitted request, stop the workers
- *   and free the staging. The filters are left to the caller.
+ *   and free the pool and the buffers. The filters are left to the caller.
  */
 #define FILTER_OP_INSERT 0
 #define FILTER_OP_QUERY 1
@@ -455,6 +493,17 @@ int filter_server_create(filter_t *const *filters, uint32_t n_filters, uint32_t 
                          filter_server_t **out);
 int filter_server_submit(filter_server_t *s, const filter_request *req, uint64_t *ticket);
 int filter_server_wait(filter_server_t *s, uint64_t ticket, int *op_rc, double *latency_s);
+
+typedef struct filter_server_stats {
+    uint64_t batches;          /* device batches run */
+    uint64_t requests;         /* requests run */
+    uint64_t merged_requests;  /* requests that ran in a batch with others */
+    uint64_t max_concurrent;   /* most batches in flight at once */
+    uint64_t pool_bytes;       /* size of the device staging pool */
+    uint64_t pool_peak_bytes;  /* most of the pool reserved at once */
+} filter_server_stats;
+
+int filter_server_get_stats(filter_server_t *s, filter_server_stats *out);
 int filter_server_destroy(filter_server_t *s);
 
 #ifdef __cplusplus

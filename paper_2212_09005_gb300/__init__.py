@@ -41,8 +41,10 @@ EXPORTS = [
     "filter_group_create", "filter_group_destroy", "filter_group_clear", "filter_group_insert",
     "filter_group_remove", "filter_group_query", "filter_group_count", "filter_group_get_stats",
     "filter_group_export_size", "filter_group_export",
-    "filter_server_create", "filter_server_submit", "filter_server_wait", "filter_server_destroy",
+    "filter_server_create", "filter_server_submit", "filter_server_wait", "filter_server_get_stats",
+    "filter_server_destroy",
     "filter_calibrate_gather",
+    "filter_debug_fail_alloc", "filter_debug_live_allocations", "filter_debug_wait_timeout",
 ]
 
 OP_INSERT, OP_QUERY, OP_REMOVE, OP_COUNT = 0, 1, 2, 3
@@ -72,6 +74,11 @@ class FilterDeviceView(C.Structure):
 class FilterRequest(C.Structure):
     _fields_ = [("filter", C.c_uint32), ("op", C.c_uint32), ("host_keys", C.c_void_p), ("n", C.c_uint64),
                 ("host_out", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("batches", C.c_uint64), ("requests", C.c_uint64), ("merged_requests", C.c_uint64),
+                ("max_concurrent", C.c_uint64), ("pool_bytes", C.c_uint64), ("pool_peak_bytes", C.c_uint64)]
 
 
 class TraceEntry(C.Structure):
@@ -127,6 +134,10 @@ def lib():
         L.filter_server_create.argtypes = [C.POINTER(vp), C.c_uint32, C.c_uint32, u64, C.POINTER(vp)]
         L.filter_server_submit.argtypes = [vp, C.POINTER(FilterRequest), C.POINTER(u64)]
         L.filter_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
+        L.filter_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.filter_debug_fail_alloc.argtypes = [C.c_uint32]
+        L.filter_debug_live_allocations.argtypes = [C.POINTER(u64)]
+        L.filter_debug_wait_timeout.argtypes = [vp, C.c_uint32, vp]
         L.filter_server_destroy.argtypes = [vp]
         L.filter_calibrate_gather.argtypes = [vp, u64, vp, u64, C.c_uint32, vp, vp]
         L.filter_error_string.argtypes = [i32]
@@ -359,8 +370,11 @@ class FilterGroup:
 
 
 class FilterServer:
-    """Serves batches of host keys for many filters on `workers` CUDA streams.
-    Filter i's batches run in submission order on worker i mod workers."""
+    """Serves batches of host keys for many filters on `workers` CUDA streams
+    with continuous batching: any idle worker takes the oldest waiting request
+    of a filter with nothing in flight (merged with the queries, counts or GQF
+    removes queued right behind it) once its staging fits in the device pool.
+    Each filter's requests run in submission order."""
 
     _OUT_DTYPE = {OP_INSERT: np.uint8, OP_QUERY: np.uint8, OP_REMOVE: np.uint8, OP_COUNT: np.uint64}
 
@@ -399,6 +413,11 @@ class FilterServer:
         keys, out = self._pending.pop(ticket)
         return out, lat.value
 
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().filter_server_get_stats(self._h, C.byref(st)), "filter_server_get_stats")
+        return {k: int(getattr(st, k)) for k, _ in ServerStats._fields_}
+
     def close(self):
         if getattr(self, "_h", None):
             lib().filter_server_destroy(self._h)
@@ -409,6 +428,23 @@ class FilterServer:
             self.close()
         except Exception:
             pass
+
+
+def debug_fail_alloc(nth: int):
+    """Make the nth device allocation of the library from now on fail (0: off)."""
+    _check(lib().filter_debug_fail_alloc(nth), "filter_debug_fail_alloc")
+
+
+def debug_live_allocations() -> int:
+    n = C.c_uint64()
+    _check(lib().filter_debug_live_allocations(C.byref(n)), "filter_debug_live_allocations")
+    return n.value
+
+
+def debug_wait_timeout(f, spin_limit: int, stream=None):
+    """Run the bounded look-back wait against a predecessor that never
+    publishes; f's status word then carries STATUS_TIMEOUT."""
+    _check(lib().filter_debug_wait_timeout(f._h, spin_limit, _stream(stream)), "filter_debug_wait_timeout")
 
 
 def trace_enable(on: bool = True):

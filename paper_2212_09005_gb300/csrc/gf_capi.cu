@@ -47,15 +47,15 @@ int filter_create(const filter_config *cfg, void *stream, filter_t **out)
     }
     const size_t total = tb + sb + (64u << 10);
     cudaGetDevice(&F->device);
-    if (cudaMalloc(&F->arena.base, total) != cudaSuccess) {
+    if (gf::dev_malloc(reinterpret_cast<void **>(&F->arena.base), total) != cudaSuccess) {
         cudaGetLastError();
         delete F;
         return FILTER_ERR_OOM;
     }
     F->arena.size = total;
-    if (cudaMalloc(&F->ctr, sizeof(gf::DevCounters)) != cudaSuccess) {
+    if (gf::dev_malloc(reinterpret_cast<void **>(&F->ctr), sizeof(gf::DevCounters)) != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(F->arena.base);
+        gf::dev_free(F->arena.base);
         delete F;
         return FILTER_ERR_OOM;
     }
@@ -65,8 +65,8 @@ int filter_create(const filter_config *cfg, void *stream, filter_t **out)
     if (rc == FILTER_OK && !pointers_set(F)) rc = FILTER_ERR_INTERNAL;
     if (rc == FILTER_OK) rc = (cfg->kind == FILTER_TCF) ? gf::tcf_clear(F, as_stream(stream)) : gf::gqf_clear(F, as_stream(stream));
     if (rc != FILTER_OK) {
-        cudaFree(F->ctr);
-        cudaFree(F->arena.base);
+        gf::dev_free(F->ctr);
+        gf::dev_free(F->arena.base);
         delete F;
         return rc;
     }
@@ -79,8 +79,8 @@ int filter_destroy(filter_t *f)
     if (!f) return FILTER_OK;
     int rc = FILTER_OK;
     if (cudaDeviceSynchronize() != cudaSuccess) rc = FILTER_ERR_CUDA;
-    if (f->ctr) cudaFree(f->ctr);
-    if (f->arena.base) cudaFree(f->arena.base);
+    gf::dev_free(f->ctr);
+    gf::dev_free(f->arena.base);
     f->arena.base = nullptr;
     delete f;
     return rc;
@@ -241,6 +241,28 @@ const char *filter_error_string(int code)
     case FILTER_ERR_INTERNAL: return "internal consistency check failed";
     default: return "unknown error";
     }
+}
+
+int filter_debug_fail_alloc(uint32_t nth)
+{
+    gf::fail_allocation(nth);
+    return FILTER_OK;
+}
+
+int filter_debug_live_allocations(uint64_t *n)
+{
+    if (!n) return FILTER_ERR_ARG;
+    const long long v = gf::live_allocations();
+    *n = v > 0 ? (uint64_t)v : 0;
+    return FILTER_OK;
+}
+
+int filter_debug_wait_timeout(filter_t *f, uint32_t spin_limit, void *stream)
+{
+    if (!valid(f) || spin_limit == 0) return FILTER_ERR_ARG;
+    gf::debug_wait_timeout(f->scan_tmp, f->ctr, spin_limit, as_stream(stream));
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
 }
 
 }  // extern "C"

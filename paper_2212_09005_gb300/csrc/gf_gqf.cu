@@ -1997,11 +1997,11 @@ int gqf_enumerate(filter *F, uint64_t *fps, uint64_t *counts, uint64_t cap, uint
     // per-block group counts and their scan: stream-ordered scratch for the call
     uint32_t *per = nullptr;
     uint64_t *stmp = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&per), (Q.nblk + 1) * sizeof(uint32_t), st) != cudaSuccess ||
-        cudaMallocAsync(reinterpret_cast<void **>(&stmp), scan_tmp_words(Q.nblk + 1) * sizeof(uint64_t), st) !=
+    if (dev_malloc_async(reinterpret_cast<void **>(&per), (Q.nblk + 1) * sizeof(uint32_t), st) != cudaSuccess ||
+        dev_malloc_async(reinterpret_cast<void **>(&stmp), scan_tmp_words(Q.nblk + 1) * sizeof(uint64_t), st) !=
             cudaSuccess) {
         cudaGetLastError();
-        if (per) cudaFreeAsync(per, st);
+        dev_free_async(per, st);
         return FILTER_ERR_OOM;
     }
     const int g = grid_for(Q.nblk, 256, 8);
@@ -2020,8 +2020,8 @@ int gqf_enumerate(filter *F, uint64_t *fps, uint64_t *counts, uint64_t cap, uint
         if (Q.r == 8) gqf_enum_kernel<8, true><<<g, 256, 0, st>>>(meta, Q.rem[Q.cur], Q.nblk, Q.N, per, fps, counts, cap);
         else gqf_enum_kernel<16, true><<<g, 256, 0, st>>>(meta, Q.rem[Q.cur], Q.nblk, Q.N, per, fps, counts, cap);
     }
-    cudaFreeAsync(stmp, st);
-    cudaFreeAsync(per, st);
+    dev_free_async(stmp, st);
+    dev_free_async(per, st);
     GF_CUDA(e);
     GF_CUDA(cudaGetLastError());
     *n_out = total;

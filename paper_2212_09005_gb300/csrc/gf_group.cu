@@ -14,7 +14,7 @@ static bool valid(const filter_group_t *g) { return g != nullptr && g->arena.bas
 static void group_free(filter_group *G)
 {
     if (!G) return;
-    if (G->arena.base) cudaFree(G->arena.base);
+    gf::dev_free(G->arena.base);
     delete[] G->members;
     delete G;
 }
@@ -47,7 +47,7 @@ int filter_group_create(const filter_config *cfgs, uint32_t n_filters, uint64_t 
     }
     const size_t total = bytes + 512 + (64u << 10);
     cudaGetDevice(&G->device);
-    if (cudaMalloc(&G->arena.base, total) != cudaSuccess) {
+    if (gf::dev_malloc(reinterpret_cast<void **>(&G->arena.base), total) != cudaSuccess) {
         cudaGetLastError();
         G->arena.base = nullptr;
         group_free(G);

@@ -266,6 +266,19 @@ struct TraceScope {
     }
 };
 
+// Device allocations of the library go through these, so that a test can
+// make the n-th one fail as if the device were full (filter_debug_fail_alloc)
+// and count the allocations still held (filter_debug_live_allocations).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st);
+void dev_free(void *p);
+void dev_free_async(void *p, cudaStream_t st);
+long long live_allocations();
+void fail_allocation(uint32_t nth);
+// runs the look-back wait against a predecessor that never publishes, with
+// `limit` loads at most; the timeout lands in ctr->status (tmp: 2 words)
+void debug_wait_timeout(uint64_t *tmp, DevCounters *ctr, uint32_t limit, cudaStream_t st);
+
 // grid size helper: a multiple of the SM count
 int grid_for(uint64_t work, int threads, int per_sm = 8);
 int sm_count();
@@ -294,6 +307,10 @@ struct TcfState {
     uint32_t *tcount;  // one per CTA of a phase launch
     uint32_t *dlist;   // max_batch
     uint64_t *seg;     // max_batch: start << 32 | count
+    // tiled phases: per-tile counts and cursors, and a second pending list
+    uint32_t *tcur;    // 2 * ceil(nb / 32) + 264
+    uint64_t *pb;      // max_batch
+    uint32_t *pbi;     // max_batch
 };
 
 struct GqfState {

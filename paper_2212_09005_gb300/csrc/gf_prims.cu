@@ -2,6 +2,7 @@
 // look-back) and LSD radix sort of 64-bit keys with optional 32-bit values.
 // The GQF sorts fingerprints before inserting them (paper Sec. 5.3, "Sorting
 // hashes"); the TCF groups batches by block with the scan.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -24,6 +25,56 @@ int sm_count()
     }
     return g_sm_count;
 }
+
+// 0: no injected failure; k > 0: the k-th allocation from now fails
+static std::atomic<uint32_t> g_fail_nth{0};
+static std::atomic<long long> g_live_allocs{0};
+
+static bool injected_failure()
+{
+    uint32_t k = g_fail_nth.load();
+    while (k != 0) {
+        if (g_fail_nth.compare_exchange_weak(k, k - 1)) return k == 1;
+    }
+    return false;
+}
+
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_allocs++;
+    else *p = nullptr;
+    return e;
+}
+
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t st)
+{
+    *p = nullptr;
+    if (injected_failure()) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaSuccess) g_live_allocs++;
+    else *p = nullptr;
+    return e;
+}
+
+void dev_free(void *p)
+{
+    if (!p) return;
+    cudaFree(p);
+    g_live_allocs--;
+}
+
+void dev_free_async(void *p, cudaStream_t st)
+{
+    if (!p) return;
+    cudaFreeAsync(p, st);
+    g_live_allocs--;
+}
+
+long long live_allocations() { return g_live_allocs.load(); }
+void fail_allocation(uint32_t nth) { g_fail_nth.store(nth); }
 
 int grid_for(uint64_t work, int threads, int per_sm)
 {
@@ -57,7 +108,7 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 // All 32 lanes call it and get the prefix. A wait that reaches SPIN_LIMIT
 // records ST_TIMEOUT and gives up (prefix then incomplete).
 __device__ uint32_t lookback_prefix(unsigned long long *st, uint64_t tile, uint32_t total,
-                                    unsigned long long *status)
+                                    unsigned long long *status, uint32_t limit = SPIN_LIMIT)
 {
     const int lane = threadIdx.x & 31;
     uint32_t prefix = 0;
@@ -73,7 +124,7 @@ __device__ uint32_t lookback_prefix(unsigned long long *st, uint64_t tile, uint3
         unsigned long long w2 = 2ull << 32;  // before tile 0: inclusive prefix 0
         if (j >= 0) {
             w2 = ld_volatile(&st[j]);
-            while ((w2 >> 32) == 0 && ++spins <= SPIN_LIMIT) w2 = ld_volatile(&st[j]);
+            while ((w2 >> 32) == 0 && ++spins <= limit) w2 = ld_volatile(&st[j]);
         }
         const uint32_t flag = (uint32_t)(w2 >> 32);
         if (__ballot_sync(0xffffffffu, flag == 0)) {
@@ -162,6 +213,20 @@ __global__ void __launch_bounds__(SCAN_T) scan_kernel(const uint32_t *in, uint32
         for (int k = 0; k < SCAN_I; k++)
             if (base + k < n) out[base + k] = v[k] + add;
     }
+}
+
+// A look-back whose predecessor never publishes: tile 1 of a two-tile state
+// array whose tile 0 stays empty. The wait gives up after `limit` loads and
+// records ST_TIMEOUT in `status` (the self-test of the bounded waits).
+__global__ void debug_lookback_kernel(unsigned long long *st, unsigned long long *status, uint32_t limit)
+{
+    lookback_prefix(st, 1, 1, status, limit);
+}
+
+void debug_wait_timeout(uint64_t *tmp, DevCounters *ctr, uint32_t limit, cudaStream_t st)
+{
+    cudaMemsetAsync(tmp, 0, 2 * sizeof(uint64_t), st);
+    debug_lookback_kernel<<<1, 32, 0, st>>>((unsigned long long *)tmp, &ctr->status, limit);
 }
 
 void exclusive_scan_u32(const uint32_t *in, uint32_t *out, uint64_t n, uint64_t *tmp,
@@ -715,12 +780,12 @@ int filter_trace_enable(int on)
         std::lock_guard<std::mutex> g(gf::g_trace_mu);
         if (!gf::g_units_dev) {
             void *p = nullptr;
-            if (cudaMalloc(&p, sizeof(unsigned long long) * gf::TRACE_DEV_SLOTS) != cudaSuccess) {
+            if (gf::dev_malloc(&p, sizeof(unsigned long long) * gf::TRACE_DEV_SLOTS) != cudaSuccess) {
                 cudaGetLastError();
                 return FILTER_ERR_OOM;
             }
             if (cudaMemset(p, 0, sizeof(unsigned long long) * gf::TRACE_DEV_SLOTS) != cudaSuccess) {
-                cudaFree(p);
+                gf::dev_free(p);
                 return FILTER_ERR_CUDA;
             }
             gf::g_units_dev = static_cast<unsigned long long *>(p);

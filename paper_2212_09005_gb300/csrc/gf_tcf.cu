@@ -8,13 +8,15 @@
 // if the tag was in neither block.
 //
 // Bulk insert, deterministic mode (Sec. 4.1 shortcut + Sec. 4 two choices +
-// Sec. 4.1 backing table + Sec. 4.2 sorted blocks). Each phase groups its
-// candidates by destination block with a counting sort (histogram in a
-// per-block counter array, exclusive scan, scatter), then one thread per
-// block takes the k smallest (tag, batch index) candidates that fit, merges
-// them into its sorted block, and emits the rest to the next phase:
+// Sec. 4.1 backing table + Sec. 4.2 sorted blocks). Each block phase groups
+// its candidates by tile of consecutive blocks (one or two coalesced counting
+// passes), then one CTA per tile sorts them by block in shared memory and one
+// thread per block takes the k smallest (tag, batch index) candidates that
+// fit, merges them into its sorted block, and emits the rest to the next
+// phase:
 //   A shortcut into b1 while fill + j < 3B/4, B the less-full block under the
-//   post-A fills, C the other block, D the backing bucket.
+//   post-A fills, C the other block, D the backing bucket (few candidates:
+//   a counting sort over the touched buckets only).
 // Blocks keep a fill byte array beside them so that the two-choice decision
 // reads 1 byte from L2 instead of a 32-byte sector from HBM.
 //
@@ -573,96 +575,6 @@ __device__ __forceinline__ uint32_t warp_reserve(unsigned *counter, uint32_t min
     return base + incl - mine;
 }
 
-// The grid-stride loops of the per-block kernels step whole warps, so that
-// every lane reaches warp_reserve in every iteration.
-template <int F>
-__global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
-                                                        const uint64_t *__restrict__ rec, int phase,
-                                                        uint32_t cap, uint32_t *pend32, uint64_t *pend64,
-                                                        unsigned *npend, const TcfPrep prep,
-                                                        unsigned long long *units)
-{
-    constexpr int B = Blk<F>::B;
-    const uint64_t nd = phase_count(P, G.nb);
-    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
-    const uint64_t stride = (uint64_t)gridDim.x * TPB;
-    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
-        const uint64_t j = j0 + (threadIdx.x & 31);
-        uint32_t s = 0, e = 0, k = 0;
-        uint64_t b = 0, thr = 0;  // records <= thr are accepted
-        if (j < nd) b = phase_dst(P, j, s, e);
-        if (units && !P.dlist) {
-            const unsigned t = __ballot_sync(0xffffffffu, s != e);
-            if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
-        }
-        if (j < nd) {
-            if (s != e) {
-                const uint32_t cnt = e - s;
-                const uint32_t f0 = fill[b];
-                k = cap > f0 ? min(cnt, cap - f0) : 0u;
-                if (k > 0 && cnt <= 8) {
-                    // few candidates: all loads in flight at once, a sorting
-                    // network in registers, a bitonic merge into the block
-                    Blk<F> blk;
-                    blk.load(blocks, b);
-                    uint64_t r8[8];
-#pragma unroll
-                    for (int q = 0; q < 8; q++) r8[q] = q < (int)cnt ? rec[s + q] : ~0ull;
-                    sort_small(r8, cnt);
-#pragma unroll
-                    for (int q = 0; q < 8; q++)
-                        if (q == (int)k - 1) thr = r8[q];
-                    blk.merge_new(f0, k, r8);
-                    blk.store(blocks, b);
-                    fill[b] = (uint8_t)(f0 + k);
-                } else if (k > 0) {
-                    Blk<F> blk;
-                    blk.load(blocks, b);
-                    uint64_t a[MAXSEL];
-                    int have = 0;
-                    for (uint32_t q = s; q < e; q++) have = topk_push(a, have, (int)k, rec[q]);
-                    thr = a[k - 1];
-                    uint32_t t_out[B];
-                    int ia = 0, ib = 0;
-#pragma unroll
-                    for (int p = 0; p < B; p++) {
-                        uint32_t ta = (ia < (int)f0) ? blk.tag(ia) : 0xffffffffu;
-                        uint32_t tb = (ib < (int)k) ? (uint32_t)(a[ib] >> 32) : 0xffffffffu;
-                        if (ta == 0xffffffffu && tb == 0xffffffffu) {
-                            t_out[p] = 0;
-                        } else if (ta <= tb) {
-                            t_out[p] = ta;
-                            ia++;
-                        } else {
-                            t_out[p] = tb;
-                            ib++;
-                        }
-                    }
-                    blk.pack(t_out);
-                    blk.store(blocks, b);
-                    fill[b] = (uint8_t)(f0 + k);
-                }
-            }
-        }
-        const uint32_t nrej = (e - s) - k;
-        uint32_t slot = warp_reserve(npend, nrej);
-        if (nrej == 0) continue;
-        for (uint32_t q = s; q < e; q++) {
-            const uint64_t r = rec[q];
-            if (k > 0 && r <= thr) continue;
-            const uint32_t i = (uint32_t)r;
-            if (phase == 1) {
-                // the other block of the pair: b1 + b2 - b
-                uint64_t alt = prep.bt ? (prep.bt[i] >> 32) + prep.b2[i] - b
-                                       : b ^ tcf_g((uint32_t)(r >> 32) >> G.vbits, G.nb);
-                pend64[slot++] = (alt << 32) | i;
-            } else {
-                pend32[slot++] = i;
-            }
-        }
-    }
-}
-
 // backing buckets: candidates (entry in rec, index in recI) taken in (entry,
 // index) order while there is room; the rest are FULL
 __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk, PhaseDst P,
@@ -736,131 +648,9 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk
 }
 
 // ---------------------------------------------------------------------------
-// Bulk delete: per-block matching. For each tag present c times in the block,
-// the c smallest (tag, index) candidates with that tag remove one copy each.
+// Bulk delete of the backing buckets: per stored entry, the smallest batch
+// indices among the candidates with that entry remove one copy each.
 // ---------------------------------------------------------------------------
-template <int F>
-__global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
-                                                        const uint64_t *__restrict__ rec, uint32_t *pend32,
-                                                        unsigned *npend, unsigned long long *units)
-{
-    constexpr int B = Blk<F>::B;
-    const uint64_t nd = phase_count(P, G.nb);
-    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
-    const uint32_t lm = Blk<F>::lane_mask(G.vmask);
-    const uint64_t stride = (uint64_t)gridDim.x * TPB;
-    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
-        const uint64_t j = j0 + (threadIdx.x & 31);
-        uint32_t s = 0, e = 0, nunm = 0, unm = 0;
-        bool fast = false;
-        uint64_t r8[8];  // fast path: the candidates, sorted
-        // general path: per distinct stored tag, its first slot, the copies,
-        // the candidates that matched and the largest matched record
-        uint32_t dt[B], dp[B], dc[B], used[B];
-        uint64_t thr[B];
-        int ndt = 0;
-        uint64_t b = 0;
-        if (j < nd) b = phase_dst(P, j, s, e);
-        if (units && !P.dlist) {
-            const unsigned t = __ballot_sync(0xffffffffu, s != e);
-            if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
-        }
-        if (j < nd) {
-            if (s != e) {
-                const uint32_t f0 = fill[b];
-                Blk<F> blk;
-                blk.load(blocks, b);
-                int removed = 0;
-                if (e - s <= 8) {
-                    // few candidates: sort them in registers; each takes the
-                    // first remaining copy of its tag, so the block stays sorted
-                    fast = true;
-                    const uint32_t c = e - s;
-#pragma unroll
-                    for (int q = 0; q < 8; q++) r8[q] = (uint32_t)q < c ? rec[s + q] : ~0ull;
-                    sort_small(r8, c);
-#pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        if ((uint32_t)q < c) {
-                            const uint32_t sm = blk.eq_slots((uint32_t)(r8[q] >> 32), lm);
-                            if (sm) {
-                                blk.delete_at(__ffs(sm) - 1);
-                                removed++;
-                            } else {
-                                unm |= 1u << q;
-                                nunm++;
-                            }
-                        }
-                    }
-                    if (removed) {
-                        blk.store(blocks, b);
-                        fill[b] = (uint8_t)(f0 - removed);
-                    }
-                } else {
-                    uint32_t tags[B];
-#pragma unroll
-                    for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
-                    // copies of a tag are adjacent (sorted by tag, then value)
-                    for (int p = 0; p < (int)f0; p++) {
-                        const uint32_t mt = tags[p] & ~G.vmask;
-                        if (ndt > 0 && dt[ndt - 1] == mt) {
-                            dc[ndt - 1]++;
-                        } else {
-                            dt[ndt] = mt;
-                            dp[ndt] = (uint32_t)p;
-                            dc[ndt] = 1;
-                            ndt++;
-                        }
-                    }
-                    for (int d = 0; d < ndt; d++) {
-                        uint64_t a[MAXSEL];
-                        int have = 0;
-                        uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
-                        for (uint32_t q = s; q < e; q++) {
-                            uint64_t r = rec[q];
-                            if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
-                        }
-                        used[d] = (uint32_t)have;
-                        thr[d] = have ? a[have - 1] : 0;
-                    }
-                    // rebuild the block without the removed copies (the
-                    // smallest values of each tag)
-                    uint32_t t_out[B];
-                    int o = 0;
-                    for (int d = 0; d < ndt; d++) {
-                        for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = tags[dp[d] + c];
-                        removed += (int)used[d];
-                    }
-                    for (int p = o; p < B; p++) t_out[p] = 0;
-                    if (removed) {
-                        blk.pack(t_out);
-                        blk.store(blocks, b);
-                        fill[b] = (uint8_t)(f0 - removed);
-                    }
-                    nunm = (e - s) - (uint32_t)removed;
-                }
-            }
-        }
-        // unmatched candidates go on
-        uint32_t slot = warp_reserve(npend, nunm);
-        if (nunm == 0) continue;
-        if (fast) {
-#pragma unroll
-            for (int q = 0; q < 8; q++)
-                if ((unm >> q) & 1u) pend32[slot++] = (uint32_t)r8[q];
-        } else {
-            for (uint32_t q = s; q < e; q++) {
-                const uint64_t r = rec[q];
-                const uint32_t t = (uint32_t)(r >> 32);
-                bool matched = false;
-                for (int d = 0; d < ndt; d++)
-                    if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
-                if (!matched) pend32[slot++] = (uint32_t)r;
-            }
-        }
-    }
-}
-
 __global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk, PhaseDst P,
                                                          const uint64_t *__restrict__ rec,
                                                          const uint32_t *__restrict__ recI, uint8_t *status,
@@ -920,6 +710,669 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_remove(TcfGeom G, uint64_t *bk
                 if (dv[d] == v && used[d] > 0 && ii <= thr[d]) matched = true;
             if (!matched && status) status[ii] = FILTER_KEY_NOT_FOUND;
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled bulk phases. A phase groups its candidates by destination block in
+// two steps that keep every global write coalesced: a partition by tile (TB
+// consecutive blocks) in one or two counting passes, each staging a chunk of
+// candidates in shared memory in bin order before writing it out, then one
+// CTA per tile that sorts the tile's candidates by block in shared memory and
+// runs the per-block step (accept into the sorted block, or remove) with the
+// block loaded and stored by consecutive threads. A candidate record is
+// (dest << 16 | slot, batch index); inside a tile it becomes the per-block
+// record (slot << 32 | index) that the per-block steps take in (slot, index)
+// order. The partition passes write to L2-sized runs instead of scattering 8
+// bytes per key over a batch-sized array, which is what keeps large batches
+// (2^24 keys into 2^24 blocks) off the DRAM read-modify-write path.
+// ---------------------------------------------------------------------------
+static constexpr int TT_TPB = 256;      // threads of the partition and tile kernels
+static constexpr int TT_CH = 2048;      // items per partition chunk (8 per thread)
+static constexpr int TT_BINS = 512;     // shared-memory bins of a partition chunk
+static constexpr uint32_t TT_CAP = 2048;  // candidates a tile stages in shared memory (8 per thread)
+static constexpr uint32_t TT_TB_MAX = 4096;
+static constexpr uint64_t TT_LEFT = 1ull << 63;  // stage entry: the candidate is left for the next phase
+
+// words of the tile counters a filter needs: counts (nt + 1), high-bin
+// cursors (nh) and tile cursors (nt), at the smallest tile size
+static uint64_t tt_counter_words(uint64_t nb) { return 2 * ((nb + 31) / 32) + 256 + 8; }
+
+// tile geometry of one call: tiles of 2^tb_log blocks; lo > 0: two passes,
+// the first by tile >> lo (nh bins), the second by tile
+struct TtGeom {
+    uint64_t nb, nt, nh;
+    uint32_t tb_log, lo;
+};
+
+// where a phase's candidates come from: the call's keys (hashed here, or the
+// prepared keys of a group call), or a pending list (rec, idx) of n_dev items
+struct TtSrc {
+    const uint64_t *keys;
+    const uint64_t *rec;
+    const uint32_t *idx;
+    const unsigned *n_dev;  // pending lists: their length on the device
+    uint64_t n;             // keys: their number; pending lists: an upper bound
+};
+
+enum TtSrcKind : int { TT_KEYS = 0, TT_PEND = 1 };
+enum TtRule : int { TT_SAME = 0, TT_TARGET = 1 };              // dest: the record's block, or the less full
+enum TtNext : int { TT_NX_SAME = 0, TT_NX_OTHER = 1, TT_NX_IDX = 2 };  // what a reject becomes
+
+__device__ __forceinline__ uint64_t tt_count(const TtSrc &s) { return s.n_dev ? (uint64_t)*s.n_dev : s.n; }
+
+// the other block of the pair of candidate (b, slot, idx): b1 ^ b2 = g(tag)
+// for a single filter; group calls read the prepared pair
+__device__ __forceinline__ uint64_t tt_other(uint64_t b, uint32_t slot, uint32_t i, const TcfGeom &G,
+                                            const TcfPrep &P)
+{
+    if (P.bt) return (P.bt[i] >> 32) + P.b2[i] - b;
+    return b ^ tcf_g(slot >> G.vbits, G.nb);
+}
+
+// candidate j of a phase as (dest << 16 | slot, index)
+template <int SRC, int RULE>
+__device__ __forceinline__ void tt_item(const TtSrc &s, uint64_t j, const TcfGeom &G, const TcfPrep &P,
+                                        const uint8_t *fill, uint64_t &rec, uint32_t &idx)
+{
+    if (SRC == TT_KEYS) {
+        idx = (uint32_t)j;
+        if (P.bt) {
+            const uint64_t v = P.bt[j];
+            rec = ((v >> 32) << 16) | (uint32_t)(v & 0xffffu);
+        } else {
+            KeyInfo k = tcf_keyinfo(s.keys[j], G);
+            if (P.vals) k.t |= P.vals[j] & G.vmask;
+            rec = (k.b1 << 16) | k.t;
+        }
+        return;
+    }
+    rec = s.rec[j];
+    idx = s.idx[j];
+    if (RULE == TT_TARGET) {
+        const uint64_t b1 = rec >> 16;
+        const uint32_t slot = (uint32_t)(rec & 0xffffu);
+        const uint64_t b2 = tt_other(b1, slot, idx, G, P);
+        const uint64_t d = fill[b1] <= fill[b2] ? b1 : b2;
+        rec = (d << 16) | slot;
+    }
+}
+
+// Counter words of a phase: cnt[nt + 1] | hcur[nh] | tcur[nt] | done.
+struct TtCtr {
+    uint32_t *cnt, *hcur, *tcur, *done;
+};
+
+__device__ __forceinline__ TtCtr tt_ctr(uint32_t *base, const TtGeom &tg)
+{
+    TtCtr c;
+    c.cnt = base;
+    c.hcur = base + tg.nt + 1;
+    c.tcur = c.hcur + tg.nh;
+    c.done = c.tcur + tg.nt;
+    return c;
+}
+
+// Per-tile candidate counts, from a shared histogram when the tiles fit in
+// it. The last CTA to finish turns them into the tiles' offsets toff[0 ..
+// nt] (toff[nt] = all candidates) and clears the counts and `done`; `reset`
+// (first phase of a call) also clears the call's pending-list lengths and
+// bucket-phase cursors. Every counter word is zero between phases (the tile
+// kernel clears the partition cursors), whatever tile geometry a call uses.
+template <int SRC, int RULE>
+__global__ void __launch_bounds__(TT_TPB) tt_hist(const TtSrc s, TcfGeom G, TcfPrep P, const uint8_t *fill,
+                                                  TtGeom tg, uint32_t *ctr_words, uint32_t *toff,
+                                                  DevCounters *reset, unsigned long long *units)
+{
+    extern __shared__ uint32_t s_h[];
+    __shared__ uint32_t s_wsum[TT_TPB / 32];
+    __shared__ bool s_last;
+    const TtCtr C = tt_ctr(ctr_words, tg);
+    const uint64_t n = tt_count(s);
+    note_units(units, n);
+    const bool shared = tg.nt <= 8192;
+    if (shared) {
+        for (uint32_t t = threadIdx.x; t < tg.nt; t += TT_TPB) s_h[t] = 0;
+        __syncthreads();
+    }
+    for (uint64_t j = blockIdx.x * (uint64_t)TT_TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TT_TPB) {
+        uint64_t rec;
+        uint32_t idx;
+        tt_item<SRC, RULE>(s, j, G, P, fill, rec, idx);
+        const uint32_t t = (uint32_t)((rec >> 16) >> tg.tb_log);
+        if (shared) atomicAdd(&s_h[t], 1u);
+        else atomicAdd(&C.cnt[t], 1u);
+    }
+    if (shared) {
+        __syncthreads();
+        for (uint32_t t = threadIdx.x; t < tg.nt; t += TT_TPB)
+            if (s_h[t]) atomicAdd(&C.cnt[t], s_h[t]);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(C.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the last CTA: exclusive scan of cnt[0 .. nt] into toff, in chunks of
+    // 16 counts per thread with a running carry
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint32_t PER = 16;
+    uint32_t carry = 0;
+    for (uint64_t c0 = 0; c0 <= tg.nt; c0 += (uint64_t)TT_TPB * PER) {
+        const uint64_t b0 = c0 + (uint64_t)threadIdx.x * PER;
+        uint32_t v[PER], sum = 0;
+#pragma unroll
+        for (uint32_t k = 0; k < PER; k++) {
+            v[k] = (b0 + k <= tg.nt) ? __ldcg(C.cnt + b0 + k) : 0u;
+            sum += v[k];
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        uint32_t run = carry + incl - sum, tot = 0;
+        for (int w = 0; w < TT_TPB / 32; w++) {
+            if (w < warp) run += s_wsum[w];
+            tot += s_wsum[w];
+        }
+#pragma unroll
+        for (uint32_t k = 0; k < PER; k++) {
+            if (b0 + k <= tg.nt) toff[b0 + k] = run;
+            run += v[k];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    // clear the counts for the next phase (the partition cursors are
+    // cleared by the tile kernel, after the passes that use them)
+    for (uint64_t k = threadIdx.x; k <= tg.nt; k += TT_TPB) ctr_words[k] = 0;
+    if (reset && threadIdx.x == 0) {
+        for (int k = 0; k < 8; k++) reset->pend[k] = 0;
+        for (int k = 0; k < 4; k++) reset->touched[k] = reset->cursor[k] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *C.done = 0;
+}
+
+// One partition pass. PASS 0: the only pass, bins are tiles; PASS 1: bins are
+// tile >> lo, each bin's region the span of its tiles; PASS 2: the pass-1
+// output, bins are tiles relative to the chunk's first high bin (a chunk that
+// reaches past TT_BINS of them places the rest by global atomics). toff: the
+// tiles' scanned offsets; hcur / tcur: the running cursors of the high bins
+// and of the tiles (zero at the start of the phase).
+template <int SRC, int RULE, int PASS>
+__global__ void __launch_bounds__(TT_TPB, 4) tt_part(const TtSrc s, TcfGeom G, TcfPrep P, const uint8_t *fill,
+                                                  TtGeom tg, const uint32_t *__restrict__ toff, uint32_t *ctr_words,
+                                                  uint64_t *__restrict__ orec, uint32_t *__restrict__ oidx,
+                                                  unsigned long long *units)
+{
+    const TtCtr C = tt_ctr(ctr_words, tg);
+    uint32_t *hcur = C.hcur, *tcur = C.tcur;
+    __shared__ uint32_t s_cnt[TT_BINS], s_start[TT_BINS], s_base[TT_BINS];
+    __shared__ uint64_t s_rec[TT_CH];
+    __shared__ uint32_t s_idx[TT_CH];
+    __shared__ uint16_t s_bin[TT_CH];
+    __shared__ uint32_t s_wsum[TT_TPB / 32];
+    __shared__ uint64_t s_tbase;
+    constexpr int IPT = TT_CH / TT_TPB;
+    const uint64_t n = tt_count(s);
+    note_units(units, n);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t c0 = (uint64_t)blockIdx.x * TT_CH; c0 < n; c0 += (uint64_t)gridDim.x * TT_CH) {
+        for (int b = threadIdx.x; b < TT_BINS; b += TT_TPB) s_cnt[b] = 0;
+        if (PASS == 2 && threadIdx.x == 0) s_tbase = ((s.rec[c0] >> 16) >> (tg.tb_log + tg.lo)) << tg.lo;
+        __syncthreads();
+        uint64_t rec[IPT];
+        uint32_t idx[IPT], rank[IPT];
+        uint32_t bin[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; q++) {
+            const uint64_t j = c0 + threadIdx.x + (uint64_t)q * TT_TPB;
+            bin[q] = 0xffffffffu;
+            if (j < n) {
+                tt_item<SRC, RULE>(s, j, G, P, fill, rec[q], idx[q]);
+                const uint64_t t = (rec[q] >> 16) >> tg.tb_log;
+                const uint64_t b = PASS == 1 ? (t >> tg.lo) : (PASS == 2 ? t - s_tbase : t);
+                if (b < TT_BINS && t < tg.nt) {
+                    bin[q] = (uint32_t)b;
+                    rank[q] = atomicAdd(&s_cnt[b], 1u);
+                } else if (PASS == 2 && t < tg.nt) {  // a tile far past the chunk's first high bin
+                    const uint32_t pos = toff[t] + atomicAdd(&tcur[t], 1u);
+                    if (pos < toff[tg.nt]) {
+                        orec[pos] = rec[q];
+                        oidx[pos] = idx[q];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // bin starts inside the chunk (exclusive scan, 2 bins per thread) and
+        // each bin's global base, one atomic per non-empty bin
+        {
+            const uint32_t a = s_cnt[2 * threadIdx.x], b = s_cnt[2 * threadIdx.x + 1];
+            uint32_t incl = a + b;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            uint32_t pre = 0;
+            for (int w = 0; w < warp; w++) pre += s_wsum[w];
+            const uint32_t ex = pre + incl - a - b;
+            s_start[2 * threadIdx.x] = ex;
+            s_start[2 * threadIdx.x + 1] = ex + a;
+#pragma unroll
+            for (int k = 0; k < 2; k++) {
+                const uint32_t bb = 2 * threadIdx.x + k, c = k ? b : a;
+                if (!c) continue;
+                if (PASS == 1) {
+                    s_base[bb] = toff[(uint64_t)bb << tg.lo] + atomicAdd(&hcur[bb], c);
+                } else {
+                    const uint64_t t = PASS == 2 ? s_tbase + bb : bb;
+                    s_base[bb] = toff[t] + atomicAdd(&tcur[t], c);
+                }
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < IPT; q++) {
+            if (bin[q] != 0xffffffffu) {
+                const uint32_t p = s_start[bin[q]] + rank[q];
+                s_rec[p] = rec[q];
+                s_idx[p] = idx[q];
+                s_bin[p] = (uint16_t)bin[q];
+            }
+        }
+        __syncthreads();
+        const uint32_t total = s_start[TT_BINS - 1] + s_cnt[TT_BINS - 1];
+        const uint32_t lim = toff[tg.nt];
+        for (uint32_t p = threadIdx.x; p < total; p += TT_TPB) {
+            const uint32_t b = s_bin[p];
+            const uint32_t pos = s_base[b] + (p - s_start[b]);
+            if (pos < lim) {  // positions past the counted total would mean counts that disagree
+                orec[pos] = s_rec[p];
+                oidx[pos] = s_idx[p];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// block-wide exclusive scan of v[0 .. m) in place, v[m] = the total; m <= TT_TB_MAX
+__device__ __forceinline__ void tt_block_scan(uint32_t *v, uint32_t m, uint32_t *s_wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // chunks of TT_TPB entries in order, one entry per thread, with a carry
+    uint32_t carry = 0;
+    for (uint32_t k0 = 0; k0 <= m; k0 += TT_TPB) {
+        const uint32_t i = k0 + threadIdx.x;
+        const uint32_t x = i < m ? v[i] : 0u;
+        uint32_t incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        uint32_t pre = carry, tot = 0;
+        for (int w = 0; w < TT_TPB / 32; w++) {
+            if (w < warp) pre += s_wsum[w];
+            tot += s_wsum[w];
+        }
+        if (i <= m) v[i] = pre + incl - x;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+// Per-block steps with more than 8 candidates (rare: hot blocks), kept out
+// of line so that the common path stays light on registers. Insert: the k
+// smallest candidates join the sorted block (f0 tags); remove: for each
+// stored tag present d times, the d smallest candidates with that tag take
+// one copy each. Left candidates get `mark` in place. Return the new fill.
+template <int F>
+__device__ __noinline__ uint32_t tt_insert_many(uint8_t *blocks, uint64_t b, uint32_t f0, uint32_t k, uint64_t *cand,
+                                                uint32_t c, uint64_t mark)
+{
+    constexpr int B = Blk<F>::B;
+    Blk<F> blk;
+    blk.load(blocks, b);
+    uint64_t a[MAXSEL];
+    int have = 0;
+    for (uint32_t q = 0; q < c; q++) have = topk_push(a, have, (int)k, cand[q]);
+    const uint64_t thr = a[k - 1];
+    uint32_t t_out[B];
+    int ia = 0, ib = 0;
+#pragma unroll
+    for (int p = 0; p < B; p++) {
+        const uint32_t ta = (ia < (int)f0) ? blk.tag(ia) : 0xffffffffu;
+        const uint32_t tb = (ib < (int)k) ? (uint32_t)(a[ib] >> 32) : 0xffffffffu;
+        if (ta == 0xffffffffu && tb == 0xffffffffu) {
+            t_out[p] = 0;
+        } else if (ta <= tb) {
+            t_out[p] = ta;
+            ia++;
+        } else {
+            t_out[p] = tb;
+            ib++;
+        }
+    }
+    blk.pack(t_out);
+    blk.store(blocks, b);
+    for (uint32_t q = 0; q < c; q++)
+        if (cand[q] > thr) cand[q] |= mark;
+    return f0 + k;
+}
+
+template <int F>
+__device__ __noinline__ uint32_t tt_remove_many(uint8_t *blocks, uint64_t b, uint32_t f0, uint64_t *cand, uint32_t c,
+                                                uint32_t vmask, uint64_t mark)
+{
+    constexpr int B = Blk<F>::B;
+    Blk<F> blk;
+    blk.load(blocks, b);
+    uint32_t tags[B], dt[B], dp[B], dc[B], used[B];
+    uint64_t dthr[B];
+    int ndt = 0, removed = 0;
+#pragma unroll
+    for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
+    for (int p = 0; p < (int)f0; p++) {
+        const uint32_t mt = tags[p] & ~vmask;
+        if (ndt > 0 && dt[ndt - 1] == mt) {
+            dc[ndt - 1]++;
+        } else {
+            dt[ndt] = mt;
+            dp[ndt] = (uint32_t)p;
+            dc[ndt] = 1;
+            ndt++;
+        }
+    }
+    for (int d = 0; d < ndt; d++) {
+        uint64_t a[MAXSEL];
+        int have = 0;
+        const uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
+        for (uint32_t q = 0; q < c; q++) {
+            const uint64_t r = cand[q];
+            if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
+        }
+        used[d] = (uint32_t)have;
+        dthr[d] = have ? a[have - 1] : 0;
+    }
+    uint32_t t_out[B];
+    int o = 0;
+    for (int d = 0; d < ndt; d++) {
+        for (uint32_t q = used[d]; q < dc[d]; q++) t_out[o++] = tags[dp[d] + q];
+        removed += (int)used[d];
+    }
+    for (int p = o; p < B; p++) t_out[p] = 0;
+    for (uint32_t q = 0; q < c; q++) {
+        const uint64_t r = cand[q];
+        const uint32_t t = (uint32_t)(r >> 32);
+        bool matched = false;
+        for (int d = 0; d < ndt; d++)
+            if (dt[d] == t && used[d] > 0 && r <= dthr[d]) matched = true;
+        if (!matched) cand[q] = r | mark;
+    }
+    if (removed) {
+        blk.pack(t_out);
+        blk.store(blocks, b);
+    }
+    return f0 - (uint32_t)removed;
+}
+
+// The per-block step of one block: candidates cand[0 .. c) (slot << 32 |
+// index, any order), the block's fill f0. Insert: the k smallest that fit
+// under `cap` join the sorted block. Remove: each candidate removes one copy
+// of its tag, smallest first. Candidates that are left get TT_LEFT | lb << 48
+// in place. Returns the new fill.
+template <int F, int OP>
+__device__ __forceinline__ uint32_t tt_block_step(uint8_t *blocks, uint64_t b, uint32_t lb, uint32_t f0, uint32_t cap,
+                                                  uint64_t *cand, uint32_t c, uint32_t lm, uint32_t vmask,
+                                                  uint64_t &bytes)
+{
+    const uint64_t mark = TT_LEFT | ((uint64_t)lb << 48);
+    if (OP == 0) {
+        const uint32_t k = cap > f0 ? min(c, cap - f0) : 0u;
+        if (k == 0) {
+            for (uint32_t q = 0; q < c; q++) cand[q] |= mark;
+            return f0;
+        }
+        bytes += 66;
+        if (c > 8) return tt_insert_many<F>(blocks, b, f0, k, cand, c, mark);
+        Blk<F> blk;
+        blk.load(blocks, b);
+        uint64_t r8[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) r8[q] = q < (int)c ? cand[q] : ~0ull;
+        sort_small(r8, c);
+        blk.merge_new(f0, k, r8);
+        blk.store(blocks, b);
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (q < (int)c) cand[q] = q < (int)k ? r8[q] : (r8[q] | mark);
+        return f0 + k;
+    }
+    bytes += 32;
+    if (c > 8) {
+        const uint32_t f1 = tt_remove_many<F>(blocks, b, f0, cand, c, vmask, mark);
+        if (f1 != f0) bytes += 34;
+        return f1;
+    }
+    Blk<F> blk;
+    blk.load(blocks, b);
+    int removed = 0;
+    uint64_t r8[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) r8[q] = (uint32_t)q < c ? cand[q] : ~0ull;
+    sort_small(r8, c);
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        if ((uint32_t)q < c) {
+            const uint32_t sm = blk.eq_slots((uint32_t)(r8[q] >> 32), lm);
+            if (sm) {
+                blk.delete_at(__ffs(sm) - 1);
+                removed++;
+                cand[q] = r8[q];
+            } else {
+                cand[q] = r8[q] | mark;
+            }
+        }
+    }
+    if (removed) {
+        blk.store(blocks, b);
+        bytes += 34;
+    }
+    return f0 - (uint32_t)removed;
+}
+
+// One CTA per tile (looping over tiles): the tile's candidates are counted
+// per block with their rank (shared atomics, the records held in registers),
+// placed in block order in shared memory (a tile with more than TT_CAP of
+// them is staged in the spare record buffer `gstage` at the same offsets and
+// read twice), each block with candidates takes its step, and the candidates
+// left are written out with one reservation per tile. What a candidate left
+// becomes (NEXT): the same block's record (phase A rejects: phase B finds
+// their target), the other block's record (phase B rejects, remove misses in
+// b1), or its batch index (for the backing-bucket phase). units: algorithmic
+// bytes (12 per candidate read and per candidate left, 32 per block read, 32
+// per block written, 2 per fill read and written).
+template <int F, int OP, int NEXT>
+__global__ void __launch_bounds__(TT_TPB, 3) tt_tile(TcfGeom G, TcfPrep P, uint8_t *blocks, uint8_t *fill, TtGeom tg,
+                                                  const uint32_t *__restrict__ toff, const uint64_t *__restrict__ rec,
+                                                  const uint32_t *__restrict__ ridx, uint64_t *gstage, uint32_t cap,
+                                                  uint64_t *orec, uint32_t *oidx, unsigned *nout, uint64_t out_cap,
+                                                  uint32_t *ctr_words, unsigned long long *status,
+                                                  unsigned long long *units)
+{
+    constexpr uint32_t RPT = TT_CAP / TT_TPB;
+    {
+        // the partition passes of this phase are done with their cursors
+        const TtCtr C = tt_ctr(ctr_words, tg);
+        const uint64_t w = tg.nh + tg.nt;
+        for (uint64_t k = blockIdx.x * (uint64_t)TT_TPB + threadIdx.x; k < w; k += (uint64_t)gridDim.x * TT_TPB)
+            C.hcur[k] = 0;
+    }
+    extern __shared__ uint64_t s_mem[];
+    const uint32_t TB = 1u << tg.tb_log;
+    uint64_t *s_stage = s_mem;                                       // TT_CAP entries
+    uint32_t *s_start = reinterpret_cast<uint32_t *>(s_mem + TT_CAP);  // TB + 1
+    __shared__ uint32_t s_wsum[TT_TPB / 32];
+    __shared__ uint32_t s_base;
+    __shared__ unsigned long long s_bytes;
+    const uint32_t lm = Blk<F>::lane_mask(G.vmask);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint64_t T = blockIdx.x; T < tg.nt; T += gridDim.x) {
+        const uint32_t s = toff[T], e = toff[T + 1];
+        if (s == e) continue;
+        const uint64_t b0 = T << tg.tb_log;
+        const uint32_t nblk = (uint32_t)min((uint64_t)TB, tg.nb - b0);
+        const uint32_t cnt = e - s;
+        const bool in_smem = cnt <= TT_CAP;
+        uint64_t *stage = in_smem ? s_stage : gstage + s;
+        for (uint32_t k = threadIdx.x; k <= nblk; k += TT_TPB) s_start[k] = 0;
+        if (threadIdx.x == 0) s_bytes = 0;
+        __syncthreads();
+        uint64_t rv[RPT];
+        uint32_t rank[RPT];
+        if (in_smem) {
+#pragma unroll
+            for (uint32_t q = 0; q < RPT; q++) {
+                const uint32_t r = s + threadIdx.x + q * TT_TPB;
+                rank[q] = 0xffffffffu;
+                if (r < e) {
+                    const uint64_t v = rec[r];
+                    const uint64_t lb = (v >> 16) - b0;
+                    if (lb >= nblk) {  // a record outside its tile: report, never index with it
+                        atomicOr(status, ST_INTERNAL);
+                        continue;
+                    }
+                    rank[q] = atomicAdd(&s_start[lb], 1u);
+                    rv[q] = (lb << 48) | ((v & 0xffffu) << 32) | ridx[r];
+                }
+            }
+        } else {
+            for (uint32_t r = s + threadIdx.x; r < e; r += TT_TPB) {
+                const uint64_t lb = (rec[r] >> 16) - b0;
+                if (lb < nblk) atomicAdd(&s_start[lb], 1u);
+                else atomicOr(status, ST_INTERNAL);
+            }
+        }
+        __syncthreads();
+        tt_block_scan(s_start, nblk, s_wsum);
+        if (in_smem) {
+#pragma unroll
+            for (uint32_t q = 0; q < RPT; q++) {
+                const uint32_t r = s + threadIdx.x + q * TT_TPB;
+                if (r < e && rank[q] != 0xffffffffu) {
+                    const uint32_t lb = (uint32_t)(rv[q] >> 48);
+                    const uint32_t p = s_start[lb] + rank[q];
+                    if (p < cnt) stage[p] = rv[q] & 0x0000ffffffffffffull;
+                    else atomicOr(status, ST_INTERNAL);
+                }
+            }
+        } else {
+            // ranks come from a second pass: the counts above turned into
+            // starts, then advanced per placed candidate and restored
+            for (uint32_t r = s + threadIdx.x; r < e; r += TT_TPB) {
+                const uint64_t v = rec[r];
+                const uint64_t lb = (v >> 16) - b0;
+                if (lb >= nblk) continue;
+                const uint32_t p = atomicAdd(&s_start[lb], 1u);
+                if (p < cnt) stage[p] = ((v & 0xffffu) << 32) | ridx[r];
+                else atomicOr(status, ST_INTERNAL);
+            }
+            __syncthreads();
+            // s_start[lb] now holds the end of block lb, the start of lb + 1
+            constexpr uint32_t PB = TT_TB_MAX / TT_TPB;
+            uint32_t prev[PB];
+#pragma unroll
+            for (uint32_t j = 0; j < PB; j++) {
+                const uint32_t k = threadIdx.x + j * TT_TPB;
+                prev[j] = (k < nblk && k > 0) ? s_start[k - 1] : 0u;
+            }
+            __syncthreads();
+#pragma unroll
+            for (uint32_t j = 0; j < PB; j++) {
+                const uint32_t k = threadIdx.x + j * TT_TPB;
+                if (k < nblk) s_start[k] = prev[j];
+            }
+        }
+        __syncthreads();
+        // each block with candidates takes its step
+        uint64_t bytes = 0;
+        for (uint32_t k = threadIdx.x; k < nblk; k += TT_TPB) {
+            const uint32_t c = s_start[k + 1] - s_start[k];
+            if (!c) continue;
+            const uint64_t b = b0 + k;
+            const uint32_t f0 = fill[b];
+            if (s_start[k + 1] > cnt || s_start[k + 1] < s_start[k] || f0 > (uint32_t)Blk<F>::B) {
+                atomicOr(status, ST_INTERNAL);
+                continue;
+            }
+            bytes += 12ull * c + 2;
+            const uint32_t f1 =
+                tt_block_step<F, OP>(blocks, b, k, f0, cap, stage + s_start[k], c, lm, G.vmask, bytes);
+            if (f1 != f0) fill[b] = (uint8_t)f1;
+        }
+        __syncthreads();
+        // the candidates left, written out in stage order with one reservation
+        for (uint32_t c0 = 0; c0 < cnt; c0 += TT_CAP) {
+            const uint32_t i0 = c0 + threadIdx.x * RPT;
+            uint32_t mine = 0;
+#pragma unroll
+            for (uint32_t q = 0; q < RPT; q++)
+                if (i0 + q < cnt && (stage[i0 + q] & TT_LEFT)) mine++;
+            uint32_t incl = mine;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            uint32_t pre = 0, tot = 0;
+            for (int w = 0; w < TT_TPB / 32; w++) {
+                if (w < warp) pre += s_wsum[w];
+                tot += s_wsum[w];
+            }
+            if (threadIdx.x == 0 && tot) s_base = atomicAdd(nout, tot);
+            __syncthreads();
+            uint32_t pos = s_base + pre + incl - mine;
+            if (mine) {
+#pragma unroll
+                for (uint32_t q = 0; q < RPT; q++) {
+                    if (i0 + q >= cnt) break;
+                    const uint64_t v = stage[i0 + q];
+                    if (!(v & TT_LEFT)) continue;
+                    const uint32_t sl = (uint32_t)(v >> 32) & 0xffffu, i = (uint32_t)v;
+                    if (pos >= out_cap) {  // more left than the pending list holds
+                        atomicOr(status, ST_INTERNAL);
+                        break;
+                    }
+                    if (NEXT == TT_NX_IDX) {
+                        oidx[pos++] = i;
+                    } else {
+                        const uint64_t b = b0 + ((v >> 48) & 0x7fffu);
+                        const uint64_t d = NEXT == TT_NX_OTHER ? tt_other(b, sl, i, G, P) : b;
+                        orec[pos] = (d << 16) | sl;
+                        oidx[pos++] = i;
+                    }
+                }
+            }
+            bytes += 12ull * mine;
+            __syncthreads();
+        }
+        if (units && bytes) atomicAdd(&s_bytes, bytes);
+        __syncthreads();
+        if (units && threadIdx.x == 0 && s_bytes) atomicAdd(units, s_bytes);
     }
 }
 
@@ -1115,6 +1568,9 @@ int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     piece(T.tcount, (uint64_t)sm_count() * 8);
     piece(T.dlist, M);
     piece(T.seg, M);
+    piece(T.tcur, tt_counter_words(T.G.nb));
+    piece(T.pb, M);
+    piece(T.pbi, M);
     piece(F->scan_tmp, scan_tmp_words(groups));
     scratch_bytes = bytes - table_bytes;
     return FILTER_OK;
@@ -1128,6 +1584,7 @@ int tcf_clear(filter *F, cudaStream_t st)
     GF_CUDA(cudaMemsetAsync(T.bk, 0, T.G.nbk * BK_W * 8, st));
     GF_CUDA(cudaMemsetAsync(T.fill, 0, T.G.nb, st));
     GF_CUDA(cudaMemsetAsync(T.cnt, 0, groups * 4, st));
+    GF_CUDA(cudaMemsetAsync(T.tcur, 0, tt_counter_words(T.G.nb) * 4, st));
     GF_CUDA(cudaMemsetAsync(F->ctr, 0, sizeof(DevCounters), st));
     return FILTER_OK;
 }
@@ -1147,14 +1604,19 @@ struct TcfBulk {
     uint32_t *pend2;
     uint32_t *tlist, *tcount, *dlist;
     uint64_t *seg;
+    uint64_t max_n;  // entries of every per-key scratch list (max_batch)
+    uint32_t *tcur;  // tiled phases: tile counts and cursors
+    uint64_t *pb;    // tiled phases: the second pending list
+    uint32_t *pbi;
     uint64_t *scan_tmp;
     DevCounters *ctr;
     TcfPrep prep;
 };
 
-static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep &prep)
+static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep &prep, uint64_t max_n)
 {
     TcfBulk W;
+    W.max_n = max_n;
     W.G = T.G;
     W.blocks = T.blocks;
     W.bk = T.bk;
@@ -1169,6 +1631,9 @@ static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, 
     W.tcount = T.tcount;
     W.dlist = T.dlist;
     W.seg = T.seg;
+    W.tcur = T.tcur;
+    W.pb = T.pb;
+    W.pbi = T.pbi;
     W.scan_tmp = scan_tmp;
     W.ctr = ctr;
     W.prep = prep;
@@ -1225,37 +1690,106 @@ static int dst_grid(const PhaseDst &P, uint64_t n, uint64_t ndst)
     return grid_for(P.dlist ? (n < ndst ? n : ndst) : ndst, TPB, 8);
 }
 
+// ---------------------------------------------------------------------------
+// Tiled phases: host side
+// ---------------------------------------------------------------------------
+// Tiles of TB blocks, TB the largest power of two in [32, TT_TB_MAX] that
+// keeps a tile's expected candidates (n keys spread over nb blocks) at or
+// below half of TT_CAP; partitioned in one pass up to 256 tiles and in two
+// above (at most 256 high bins).
+static TtGeom tt_geom(uint64_t nb, uint64_t n)
+{
+    TtGeom g;
+    g.nb = nb;
+    uint32_t tl = 5;
+    while (tl < 12 && (n << (tl + 1)) <= (uint64_t)(TT_CAP / 2) * nb) tl++;
+    g.tb_log = tl;
+    g.nt = (nb + (1ull << tl) - 1) >> tl;
+    uint32_t lg = 0;
+    while ((1ull << lg) < g.nt) lg++;
+    g.lo = g.nt <= 256 ? 0 : ((lg + 1) / 2 > lg - 8 ? (lg + 1) / 2 : lg - 8);
+    g.nh = g.lo ? (g.nt + (1ull << g.lo) - 1) >> g.lo : g.nt;
+    return g;
+}
+
+template <int F, int OP, int NEXT>
+static void tt_tile_launch(const TcfBulk &T, const TtGeom &tg, const uint64_t *rec, const uint32_t *ridx,
+                           uint64_t *gstage, uint32_t cap, uint64_t *orec, uint32_t *oidx, unsigned *nout,
+                           const char *name, cudaStream_t st)
+{
+    const size_t smem = TT_CAP * 8 + (((size_t)1 << tg.tb_log) + 1) * 4;
+    cudaFuncSetAttribute(tt_tile<F, OP, NEXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(TT_CAP * 8 + (TT_TB_MAX + 1) * 4));
+    const uint64_t grid = tg.nt < (uint64_t)sm_count() * 8 ? tg.nt : (uint64_t)sm_count() * 8;
+    gf::TraceScope ts_(name, 0, st, true);
+    tt_tile<F, OP, NEXT><<<(unsigned)grid, TT_TPB, smem, st>>>(T.G, T.prep, T.blocks, T.fill, tg, T.off, rec, ridx,
+                                                               gstage, cap, orec, oidx, nout, T.max_n, T.tcur,
+                                                               &T.ctr->status, ts_.units());
+}
+
+// group one phase's candidates by tile: counts (their last CTA scans them
+// into T.off and clears the counters), then one or two partition passes;
+// returns the buffers holding the grouped records (and the spare pair,
+// which the tile kernel may use for a hot tile)
+template <int SRC, int RULE>
+static void tt_group(const TcfBulk &T, const TtGeom &tg, const TtSrc &src, DevCounters *reset, const uint64_t **grec,
+                     const uint32_t **gidx, uint64_t **spare, cudaStream_t st)
+{
+    const bool keys = SRC == TT_KEYS;
+    const int ghist = grid_for(src.n, TT_TPB * 16, 4);
+    {
+        gf::TraceScope ts_(keys ? "tcf_tile_hist" : "tcf_tile_hist_pend", keys ? src.n : 0, st, !keys);
+        tt_hist<SRC, RULE><<<ghist, TT_TPB, tg.nt <= 8192 ? tg.nt * 4 : 0, st>>>(src, T.G, T.prep, T.fill, tg, T.tcur,
+                                                                                T.off, reset, ts_.units());
+    }
+    const int gpart = grid_for((src.n + TT_CH - 1) / TT_CH * TT_TPB, TT_TPB, 6);
+    if (tg.lo == 0) {
+        gf::TraceScope ts_(keys ? "tcf_tile_part" : "tcf_tile_part_pend", keys ? src.n : 0, st, !keys);
+        tt_part<SRC, RULE, 0><<<gpart, TT_TPB, 0, st>>>(src, T.G, T.prep, T.fill, tg, T.off, T.tcur, T.rec, T.tlist,
+                                                        ts_.units());
+        *grec = T.rec;
+        *gidx = T.tlist;
+        *spare = T.seg;
+        return;
+    }
+    {
+        gf::TraceScope ts_(keys ? "tcf_tile_part" : "tcf_tile_part_pend", keys ? src.n : 0, st, !keys);
+        tt_part<SRC, RULE, 1><<<gpart, TT_TPB, 0, st>>>(src, T.G, T.prep, T.fill, tg, T.off, T.tcur, T.rec, T.tlist,
+                                                        ts_.units());
+    }
+    TtSrc s2{nullptr, T.rec, T.tlist, src.n_dev, src.n};
+    {
+        gf::TraceScope ts_("tcf_tile_part2", 0, st, true);
+        tt_part<TT_PEND, TT_SAME, 2><<<gpart, TT_TPB, 0, st>>>(s2, T.G, T.prep, T.fill, tg, T.off, T.tcur, T.seg,
+                                                               T.dlist, ts_.units());
+    }
+    *grec = T.seg;
+    *gidx = T.dlist;
+    *spare = T.rec;
+}
+
 template <int F>
-static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+static void tcf_tiled_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
 {
     const TcfGeom G = T.G;
     DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
-    cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
-    cudaMemsetAsync(ctr->touched, 0, sizeof(ctr->touched) + sizeof(ctr->cursor), st);  // adjacent fields
-    // A: shortcut into b1
-    PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
-    {
-        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
-        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc, T.pend0,
-                                                                   nullptr, &np[0], T.prep, ts_.units());
-    }
-    // B: the less full of b1, b2 under the post-A fills
-    P = group_phase<SRC_PEND_U32, DST_TARGET>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
-    {
-        gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
-        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
-                                                                   T.pend1, &np[1], T.prep, ts_.units());
-    }
-    // C: the other block
-    P = group_phase<SRC_PEND_U64, DST_ALT>(T, keys, n, T.pend1, &np[1], 2, nullptr, st);
-    {
-        gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
-        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
-                                                                   nullptr, &np[2], T.prep, ts_.units());
-    }
+    const TtGeom tg = tt_geom(G.nb, n);
+    const uint64_t *gr;
+    const uint32_t *gi;
+    uint64_t *sp;
+    // A: shortcut into b1 while fill < 3B/4; rejects keep b1 (the counts'
+    // last CTA also clears the call's pending-list lengths)
+    tt_group<TT_KEYS, TT_SAME>(T, tg, TtSrc{keys, nullptr, nullptr, nullptr, n}, ctr, &gr, &gi, &sp, st);
+    tt_tile_launch<F, 0, TT_NX_SAME>(T, tg, gr, gi, sp, G.tsc, T.pend1, T.pend0, &np[0], "tcf_tile_insert", st);
+    // B: the less full of b1, b2 under the post-A fills; rejects go to the other block
+    tt_group<TT_PEND, TT_TARGET>(T, tg, TtSrc{nullptr, T.pend1, T.pend0, &np[0], n}, nullptr, &gr, &gi, &sp, st);
+    tt_tile_launch<F, 0, TT_NX_OTHER>(T, tg, gr, gi, sp, G.B, T.pb, T.pbi, &np[1], "tcf_tile_insert", st);
+    // C: the other block; rejects go to the backing buckets by index
+    tt_group<TT_PEND, TT_SAME>(T, tg, TtSrc{nullptr, T.pb, T.pbi, &np[1], n}, nullptr, &gr, &gi, &sp, st);
+    tt_tile_launch<F, 0, TT_NX_IDX>(T, tg, gr, gi, sp, G.B, nullptr, T.pend2, &np[2], "tcf_tile_insert", st);
     // D: backing buckets
-    P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
+    PhaseDst P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
     {
         gf::TraceScope ts_("tcf_bucket_insert", 0, st, true);
         tcf_bucket_insert<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr, ts_.units());
@@ -1263,30 +1797,27 @@ static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
 }
 
 template <int F>
-static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+static void tcf_tiled_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
 {
     const TcfGeom G = T.G;
     DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
-    cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
-    cudaMemsetAsync(ctr->touched, 0, sizeof(ctr->touched) + sizeof(ctr->cursor), st);  // adjacent fields
-    // 1: primary block
-    PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
-    {
-        gf::TraceScope ts_("tcf_block_remove", 0, st, true);
-        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0], ts_.units());
-    }
-    // 2: secondary block
-    P = group_phase<SRC_PEND_U32, DST_B2>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
-    {
-        gf::TraceScope ts_("tcf_block_remove_sparse", 0, st, true);
-        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2], ts_.units());
-    }
+    const TtGeom tg = tt_geom(G.nb, n);
+    const uint64_t *gr;
+    const uint32_t *gi;
+    uint64_t *sp;
+    // 1: primary block; misses go on to the secondary block
+    tt_group<TT_KEYS, TT_SAME>(T, tg, TtSrc{keys, nullptr, nullptr, nullptr, n}, ctr, &gr, &gi, &sp, st);
+    tt_tile_launch<F, 1, TT_NX_OTHER>(T, tg, gr, gi, sp, 0, T.pend1, T.pend0, &np[0], "tcf_tile_remove", st);
+    // 2: secondary block; misses go to the backing buckets by index
+    tt_group<TT_PEND, TT_SAME>(T, tg, TtSrc{nullptr, T.pend1, T.pend0, &np[0], n}, nullptr, &gr, &gi, &sp, st);
+    tt_tile_launch<F, 1, TT_NX_IDX>(T, tg, gr, gi, sp, 0, nullptr, T.pend2, &np[2], "tcf_tile_remove", st);
     // 3: backing bucket; what is left is not found
-    P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
+    PhaseDst P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
     {
         gf::TraceScope ts_("tcf_bucket_remove", 0, st, true);
-        tcf_bucket_remove<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr, ts_.units());
+        tcf_bucket_remove<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr,
+                                                                 ts_.units());
     }
 }
 
@@ -1303,9 +1834,9 @@ int tcf_insert(filter *F, const uint64_t *keys, const uint8_t *vals, uint64_t n,
             else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, vals, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr, vals});
-        if (T.G.f == 16) tcf_bulk_insert<16>(W, keys, n, status, st);
-        else tcf_bulk_insert<8>(W, keys, n, status, st);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr, vals}, F->cfg.max_batch);
+        if (T.G.f == 16) tcf_tiled_insert<16>(W, keys, n, status, st);
+        else tcf_tiled_insert<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -1324,9 +1855,9 @@ int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             else tcf_point_remove<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr});
-        if (T.G.f == 16) tcf_bulk_remove<16>(W, keys, n, status, st);
-        else tcf_bulk_remove<8>(W, keys, n, status, st);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr}, F->cfg.max_batch);
+        if (T.G.f == 16) tcf_tiled_remove<16>(W, keys, n, status, st);
+        else tcf_tiled_remove<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -1516,6 +2047,9 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     piece(T.tcount, (uint64_t)sm_count() * 8);
     piece(T.dlist, M);
     piece(T.seg, M);
+    piece(T.tcur, tt_counter_words(nb_tot));
+    piece(T.pb, M);
+    piece(T.pbi, M);
     piece(GR->prep.bt, M);
     piece(GR->prep.b2, M);
     piece(GR->prep.bucket, M);
@@ -1525,7 +2059,7 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     bytes_out = bytes;
     if (plan_only) return FILTER_OK;
     if (!T.blocks || !T.bk || !T.fill || !T.cnt || !T.off || !T.rec || !T.pend0 || !T.pend1 || !T.pend2 ||
-        !T.tlist || !T.tcount || !T.dlist || !T.seg || !GR->prep.bt || !GR->prep.b2 || !GR->prep.bucket ||
+        !T.tlist || !T.tcount || !T.dlist || !T.seg || !T.tcur || !T.pb || !T.pbi || !GR->prep.bt || !GR->prep.b2 || !GR->prep.bucket ||
         !GR->prep.e || !GR->d_tmem || !GR->scan_tmp)
         return FILTER_ERR_INTERNAL;
     GF_CUDA(cudaMemcpy(GR->d_tmem, tm.data(), n * sizeof(TcfMember), cudaMemcpyHostToDevice));
@@ -1550,6 +2084,9 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
         S.tcount = T.tcount;
         S.dlist = T.dlist;
         S.seg = T.seg;
+        S.tcur = T.tcur;
+        S.pb = T.pb;
+        S.pbi = T.pbi;
         V.ctr = GR->ctr;
         V.scan_tmp = GR->scan_tmp;
         V.arena.base = GR->arena.base;  // marks the view valid; the group owns the memory
@@ -1566,6 +2103,7 @@ int tcf_group_clear(filter_group *GR, cudaStream_t st)
     GF_CUDA(cudaMemsetAsync(T.bk, 0, T.G.nbk * BK_W * 8, st));
     GF_CUDA(cudaMemsetAsync(T.fill, 0, T.G.nb, st));
     GF_CUDA(cudaMemsetAsync(T.cnt, 0, groups * 4, st));
+    GF_CUDA(cudaMemsetAsync(T.tcur, 0, tt_counter_words(T.G.nb) * 4, st));
     GF_CUDA(cudaMemsetAsync(GR->ctr, 0, sizeof(DevCounters), st));
     return FILTER_OK;
 }
@@ -1590,13 +2128,13 @@ int tcf_group_op(filter_group *GR, int op, const uint64_t *off, const uint64_t *
         gf::TraceScope ts_("tcf_group_prep", n, st);
         tcf_group_prep<<<grid_for(n, TPB, 8), TPB, 0, st>>>(keys, n, off, GR->n, GR->d_tmem, T.G.f, GR->prep);
     }
-    const TcfBulk W = bulk_of(T, GR->scan_tmp, GR->ctr, GR->prep);
+    const TcfBulk W = bulk_of(T, GR->scan_tmp, GR->ctr, GR->prep, GR->max_total);
     if (op == GROUP_INSERT) {
-        if (T.G.f == 16) tcf_bulk_insert<16>(W, nullptr, n, out, st);
-        else tcf_bulk_insert<8>(W, nullptr, n, out, st);
+        if (T.G.f == 16) tcf_tiled_insert<16>(W, nullptr, n, out, st);
+        else tcf_tiled_insert<8>(W, nullptr, n, out, st);
     } else {
-        if (T.G.f == 16) tcf_bulk_remove<16>(W, nullptr, n, out, st);
-        else tcf_bulk_remove<8>(W, nullptr, n, out, st);
+        if (T.G.f == 16) tcf_tiled_remove<16>(W, nullptr, n, out, st);
+        else tcf_tiled_remove<8>(W, nullptr, n, out, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;

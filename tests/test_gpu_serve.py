@@ -116,3 +116,60 @@ def test_server_rejects_oversized_batch(gf):
     with pytest.raises(gf.FilterError):
         S.submit(5, 0, np.arange(4, dtype=np.uint64))  # no such filter
     S.close()
+
+
+def test_merged_requests_equal_alone(gf):
+    """Continuous batching merges the queries, counts and GQF removes queued
+    behind each other on one filter into one device batch; every request's
+    results still equal the same per-filter sequence run alone, and the
+    filters end byte-identical."""
+    import torch
+
+    lg = 12
+    keys = W.uniform_keys(77, 6000)
+
+    def filters():
+        fs = [gf.TCF(lg, 16, gf.MODE_BULK, seed=300 + i, max_batch=4096) for i in range(2)] + \
+             [gf.GQF(lg, 8, seed=300 + i, max_batch=4096) for i in range(2, 4)]
+        for i, f in enumerate(fs):
+            f.insert(dev_u64(keys[i * 1000:(i + 1) * 1000]))
+            if i >= 2:  # some repeated copies in the GQFs, so that removes can leave counts behind
+                f.insert(dev_u64(keys[i * 1000:i * 1000 + 300]))
+        return fs
+
+    rng = np.random.default_rng(5)
+    reqs = []
+    for r in range(120):
+        f = int(rng.integers(4))
+        kind = rng.choice(["q", "q", "q", "r", "c", "i"])
+        pool = keys[f * 1000:(f + 1) * 1000]
+        k = np.concatenate([pool[rng.integers(0, 1000, 40)], W.uniform_keys(900 + r, 10)])
+        if kind == "i":
+            reqs.append((f, gf.OP_INSERT, W.uniform_keys(2000 + r, 30)))
+        elif kind == "r" and f >= 2:
+            reqs.append((f, gf.OP_REMOVE, pool[rng.integers(0, 1000, 25)]))
+        elif kind == "c" and f >= 2:
+            reqs.append((f, gf.OP_COUNT, k))
+        else:
+            reqs.append((f, gf.OP_QUERY, k))
+    fs = filters()
+    S = gf.FilterServer(fs, workers=1, max_keys=4096)
+    tickets = [S.submit(f, op, k) for f, op, k in reqs]
+    served = [S.wait(t)[0] for t in tickets]
+    st = S.stats()
+    S.close()
+    assert st["requests"] == len(reqs) and st["merged_requests"] > 0 and st["batches"] < len(reqs)
+    ref = filters()
+    for j, (f, op, k) in enumerate(reqs):
+        d = dev_u64(k)
+        if op == gf.OP_COUNT:
+            out = torch.zeros(len(k), dtype=torch.int64, device="cuda")
+            ref[f].count(d, out)
+            want = out.cpu().numpy().view(np.uint64)
+        else:
+            out = torch.zeros(len(k), dtype=torch.uint8, device="cuda")
+            {gf.OP_INSERT: ref[f].insert, gf.OP_QUERY: ref[f].query, gf.OP_REMOVE: ref[f].remove}[op](d, out)
+            want = out.cpu().numpy()
+        assert np.array_equal(served[j], want), (j, op)
+    for a, b in zip(fs, ref):
+        assert first_diff(a.export(), b.export()) is None
