@@ -155,6 +155,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
     ap.add_argument("--no-target", action="store_true", help="skip the 2^28-slot, 90%%-load measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving-loop measurement")
     ap.add_argument("--case", default="full", choices=["full", "profile", "target", "batched", "serving", "kmer", "values"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
@@ -483,6 +484,12 @@ def run_ours(args, rank, world, device_index):
         torch.cuda.empty_cache()
         batched = run_batched(args, device)
 
+    serving = None
+    if args.case == "full" and not args.no_serving:
+        R = None
+        torch.cuda.empty_cache()
+        serving = run_serving(args, device, log2_slots=20, bmax=20, workload=SERVING_SMALL)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.case == "full":
         cpu = cpu_sample(inp)
@@ -497,7 +504,7 @@ def run_ours(args, rank, world, device_index):
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
         "cpu_baseline": cpu, "random_gather": gather, "per_op": per_op, "kernels": kern, "checks": checks,
-        "target_2_28": target, "batched": batched,
+        "target_2_28": target, "batched": batched, "serving": serving,
     }
     return line
 
@@ -870,13 +877,19 @@ def run_values(args, device):
 SERVING_WORKLOAD = ("serving loop: 64 filters of 2^24 slots (32 TCF f=16 bulk + 32 counting GQF r=8, "
                     "2^30 slots in all) pre-filled to 50%; batches of 2^10..2^24 keys (log-uniform) for a "
                     "uniformly chosen filter, 50/45/5 insert/query/delete, until 90% aggregate load; host "
-                    "keys in, host results out (page-locked buffers); 8 worker streams; Poisson arrivals at 0.5x and 0.8x of the "
-                    "back-to-back capacity")
+                    "keys in, host results out (page-locked buffers); 8 worker streams; Poisson arrivals at 0.5x and "
+                    "0.8x of the back-to-back capacity")
+SERVING_SMALL = ("serving loop, reduced: 64 filters of 2^20 slots (32 TCF f=16 bulk + 32 counting GQF r=8, 2^26 "
+                 "slots in all) pre-filled to 50%; batches of 2^10..2^20 keys (log-uniform), 50/45/5 "
+                 "insert/query/delete, until 90% aggregate load; otherwise as the full serving case")
 
 
-def run_serving(args, device):
+def run_serving(args, device, log2_slots: int = 24, bmax: int = 24, workload: str = SERVING_WORKLOAD):
     """Capacity (every request submitted at once) and latency under Poisson
-    arrivals at 0.5x and 0.8x of that capacity, from the same pre-filled state."""
+    arrivals at 0.5x and 0.8x of that capacity, from the same pre-filled
+    state; then the same request sequence run back to back through the plain
+    single-filter calls (host keys in, host results out, one stream), whose
+    results must equal the served ones."""
     import time as _t
 
     import torch
@@ -884,7 +897,7 @@ def run_serving(args, device):
     import paper_2212_09005_gb300 as gf
     from paper_2212_09005_gb300 import workloads as W
 
-    w = W.serving_workload()
+    w = W.serving_workload(log2_slots=log2_slots, bmax=bmax)
     reqs, nt, lg = w["requests"], w["n_tcf"], w["log2_slots"]
     mb = max(max(len(b) for b in w["prefill"]), max(len(k) for _, _, k in reqs))
     fs = [gf.TCF(lg, 16, gf.MODE_BULK, seed=5000 + i, max_batch=mb) if i < nt else
@@ -925,7 +938,12 @@ def run_serving(args, device):
         return sec, np.array(lat)
 
     run(None)  # warm-up
+    clocks = ClockSampler(device.index or 0)
+    clocks.start()
+    st0 = S.stats()
     sec, lat = run(None)
+    st1 = S.stats()
+    served = ov.copy()
     cap = ops / sec
     # where the time goes: summed latency per filter kind and operation
     brk = {}
@@ -936,9 +954,10 @@ def run_serving(args, device):
         b[1] += len(keys)
         b[2] += float(l)
     breakdown = {k: {"requests": v[0], "keys": v[1], "latency_s_sum": round(v[2], 3)} for k, v in brk.items()}
-    out = {"workload": SERVING_WORKLOAD, "requests": len(reqs), "ops": ops, "capacity_gops": round(cap / 1e9, 4),
+    out = {"workload": workload, "requests": len(reqs), "ops": ops, "capacity_gops": round(cap / 1e9, 4),
            "capacity_p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
            "capacity_p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3), "capacity_breakdown": breakdown,
+           "server": {k: st1[k] - st0[k] if k in ("batches", "requests", "merged_requests") else st1[k] for k in st1},
            "loads": []}
     mean_ops = ops / len(reqs)
     for frac in (0.5, 0.8):
@@ -949,8 +968,29 @@ def run_serving(args, device):
                              "achieved_gops": round(ops / sec / 1e9, 4),
                              "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                              "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)})
+    out["clocks"] = clocks.stop()
     S.close()
-    del fs, pre, kbuf, obuf
+    # the plain path: the same requests back to back through the single-filter
+    # calls, host keys in and host results out on one stream
+    prefill()
+    dk = torch.empty(max(len(k) for _, _, k in reqs), dtype=torch.int64, device=device)
+    dr = torch.empty(dk.numel(), dtype=torch.uint8, device=device)
+    pout = torch.empty(ops, dtype=torch.uint8).pin_memory()
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    for j, (f, op, keys) in enumerate(reqs):
+        a, b = spans[j]
+        n = b - a
+        dk[:n].copy_(kbuf[a:b], non_blocking=True)
+        call = fs[f].insert if op == 0 else (fs[f].query if op == 1 else fs[f].remove)
+        call(dk[:n], dr[:n])
+        pout[a:b].copy_(dr[:n], non_blocking=True)
+    torch.cuda.synchronize()
+    psec = _t.perf_counter() - t0
+    out["plain_gops"] = round(ops / psec / 1e9, 4)
+    out["served_over_plain"] = round(cap / (ops / psec), 3)
+    out["results_equal_plain"] = bool(np.array_equal(pout.numpy(), served))
+    del fs, pre, kbuf, obuf, dk, dr, pout
     torch.cuda.empty_cache()
     return out
 

@@ -428,6 +428,59 @@ int filter_group_export_size(filter_group_t *g, uint32_t member, uint64_t *nbyte
 int filter_group_export(filter_group_t *g, uint32_t member, void *host_buf, uint64_t nbytes, void *stream);
 
 /*
+ * ---- batched work list ----
+ * One call applies a list of work items to a TCF group and a GQF group (the
+ * paper's batched bulk calls, Sec. 4.2 and Sec. 5.3, over thousands of
+ * filters at once). Each item is (group, member, operation, device keys,
+ * device results). The list itself is host memory, read during the call, so
+ * that every launch is sized when it is enqueued; the call never
+ * synchronises the host, so a sequence of calls on one stream can be captured
+ * in one CUDA graph and replayed (the data in the items' buffers may change
+ * between replays, the list may not).
+ *
+ * filter_batch_create: a batch context over `tcf` (a TCF group, or NULL) and
+ *   `gqf` (a GQF group, or NULL), for calls of at most max_items items and at
+ *   most max_keys keys per (group, operation) class. It allocates max_keys x
+ *   16 bytes of device scratch and a ring of descriptor slots (pinned host
+ *   and device memory, 16 slots). The groups stay owned by the caller and
+ *   must outlive the batch.
+ * filter_batch_run: per group, all inserts run first, then removes, then
+ *   queries, then counts (GQF only); within one class, member m's items are
+ *   concatenated in list order and applied as one batch (one group call for
+ *   all members). d_out receives n uint8 statuses (insert, remove) or found
+ *   flags (query), or n uint64 counts (count); NULL discards them. Inserts
+ *   into a GQF member that do not fit leave that member's table unchanged and
+ *   report FILTER_KEY_FULL for all of its keys in the call (unlike
+ *   filter_group_insert, which keeps the longest prefix that fits and needs
+ *   host round trips). Each call uses the next slot of the ring for its
+ *   descriptors: a captured graph may hold at most 16 calls of one batch, and
+ *   no further calls of that batch may be made while the graph is still to
+ *   be replayed. FILTER_ERR_ARG for a bad group, member or op, n_items >
+ *   max_items, or a class above max_keys (inserts and removes also above the
+ *   group's max_total); FILTER_ERR_UNSUPPORTED for a count on the TCF group.
+ *   Nothing is enqueued when an item is rejected.
+ */
+typedef struct filter_batch filter_batch_t;
+
+#define FILTER_BATCH_TCF 0
+#define FILTER_BATCH_GQF 1
+
+typedef struct filter_work {
+    uint32_t group;         /* FILTER_BATCH_TCF or FILTER_BATCH_GQF */
+    uint32_t member;        /* member index in that group */
+    uint32_t op;            /* FILTER_OP_* */
+    uint32_t reserved;      /* 0 */
+    const uint64_t *d_keys; /* n keys, device */
+    uint64_t n;
+    void *d_out;            /* device results, or NULL */
+} filter_work;
+
+int filter_batch_create(filter_group_t *tcf, filter_group_t *gqf, uint64_t max_keys, uint32_t max_items,
+                        filter_batch_t **out);
+int filter_batch_run(filter_batch_t *b, const filter_work *items, uint32_t n_items, void *stream);
+int filter_batch_destroy(filter_batch_t *b);
+
+/*
  * ---- serving loop ----
  * Batches of host keys for many filters, run concurrently on several CUDA
  * streams with continuous batching. The paper measures isolated bulk calls;

@@ -16,8 +16,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpufilter.so")
-SOURCES = ["gf_prims.cu", "gf_tcf.cu", "gf_gqf.cu", "gf_capi.cu", "gf_group.cu", "gf_serve.cu", "gf_noalloc.cu"]
-HEADERS = ["gf_internal.cuh"]
+SOURCES = ["gf_prims.cu", "gf_tcf.cu", "gf_gqf.cu", "gf_capi.cu", "gf_group.cu", "gf_serve.cu", "gf_noalloc.cu",
+           "gf_batch.cu"]
+HEADERS = ["gf_internal.cuh", "gf_sched.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -2119,6 +2119,47 @@ __global__ void gqf_group_overflow(const DevCounters *mctr, uint32_t n, DevCount
         if (mctr[m].overflow) list[atomicAdd(&gctr->pend[0], 1u)] = m;
 }
 
+// Asynchronous group updates: copy every block of a member whose merge fit
+// from the spare buffer back to the current one (a member that overflowed
+// keeps its current, old table).
+template <int R>
+__global__ void gqf_group_commit(const uint64_t *__restrict__ mblk0, uint32_t nmem, const DevCounters *mctr,
+                                 const uint8_t *__restrict__ meta_src, const uint8_t *__restrict__ rem_src,
+                                 uint8_t *meta_dst, uint8_t *rem_dst, uint64_t nblk)
+{
+    constexpr int RW = 64 * R / 8 / 16;  // 16-byte words of one block's remainders
+    for (uint64_t b = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; b < nblk; b += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = nmem;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (__ldg(mblk0 + mid) <= b) lo = mid;
+            else hi = mid;
+        }
+        if (mctr[lo].overflow) continue;
+        const uint4 *ms = reinterpret_cast<const uint4 *>(meta_src + b * 32);
+        uint4 *md = reinterpret_cast<uint4 *>(meta_dst + b * 32);
+        md[0] = ms[0];
+        md[1] = ms[1];
+        const uint4 *rs = reinterpret_cast<const uint4 *>(rem_src + b * 64 * (R / 8));
+        uint4 *rd = reinterpret_cast<uint4 *>(rem_dst + b * 64 * (R / 8));
+#pragma unroll
+        for (int w = 0; w < RW; w++) rd[w] = rs[w];
+    }
+}
+
+// the keys of members whose insert did not fit: FULL, counted per member
+__global__ void gqf_group_reject(const uint64_t *__restrict__ off, uint32_t nmem, uint64_t n, DevCounters *mctr,
+                                 uint8_t *status)
+{
+    MemberCursor c(off, nmem, n);
+    for (; c.valid(); c.next(off)) {
+        if (!mctr[c.m].overflow) continue;
+        if (status) status[c.i] = FILTER_KEY_FULL;
+        atomicAdd(&mctr[c.m].failed, 1ull);
+        atomicOr(&mctr[c.m].status, ST_FULL);
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(256) gqf_group_count_kernel(const uint64_t *__restrict__ keys, uint64_t n,
                                                               const uint64_t *__restrict__ off, uint32_t nmem,
@@ -2215,6 +2256,7 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     piece(GR->mctr, (uint64_t)n);
     piece(GR->d_tile_member, tiles);
     piece(GR->d_ovf, (uint64_t)n);
+    piece(GR->d_mblk0, (uint64_t)n + 1);
     {
         MergeArgs *ma = nullptr;
         GqfMemberDev *gd = nullptr;
@@ -2226,7 +2268,7 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     bytes_out = bytes;
     if (plan_only) return FILTER_OK;
     if (!Q.meta[1] || !Q.rem[1] || !Q.radix_tmp || !GR->scan_tmp || !GR->mctr || !GR->d_tile_member || !GR->d_ovf ||
-        !GR->d_margs || !GR->d_gmem)
+        !GR->d_margs || !GR->d_gmem || !GR->d_mblk0)
         return FILTER_ERR_INTERNAL;
     Q.cur = 0;
     GR->cur = 0;
@@ -2298,6 +2340,11 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
             }
     }
     GF_CUDA(cudaMemcpy(GR->d_margs, margs.data(), margs.size() * sizeof(MergeArgs), cudaMemcpyHostToDevice));
+    {
+        std::vector<uint64_t> mb(meta_off);
+        mb.push_back(nblk_tot);
+        GF_CUDA(cudaMemcpy(GR->d_mblk0, mb.data(), mb.size() * 8, cudaMemcpyHostToDevice));
+    }
     GF_CUDA(cudaMemcpy(GR->d_gmem, gmem.data(), gmem.size() * sizeof(GqfMemberDev), cudaMemcpyHostToDevice));
     if (tiles) GF_CUDA(cudaMemcpy(GR->d_tile_member, tmem.data(), tiles * 4, cudaMemcpyHostToDevice));
     return FILTER_OK;
@@ -2436,6 +2483,39 @@ int gqf_group_count(filter_group *GR, const uint64_t *off, const uint64_t *keys,
         gf::TraceScope ts_("gqf_group_count_kernel", n, st);
         if (GR->gqf.r == 8) gqf_group_count_kernel<8><<<g, 256, 0, st>>>(keys, n, off, GR->n, gm, GR->cur, counts, found);
         else gqf_group_count_kernel<16><<<g, 256, 0, st>>>(keys, n, off, GR->n, gm, GR->cur, counts, found);
+    }
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
+int gqf_group_update_async(filter_group *GR, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *status,
+                           int del, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = GR->gqf;
+    group_prepare(GR, off, keys, n, status != nullptr, st);
+    int rc = group_merge(GR, n, del, st);
+    if (rc) return rc;
+    if (status) {
+        gf::TraceScope ts_("gqf_status_kernel", n, st);
+        gqf_status_kernel<<<grid_for(n, 256, 8), 256, 0, st>>>(n, Q.flags, Q.ustart, Q.idx_b, Q.removed,
+                                                              del ? 0 : ~0ull, del, status);
+    }
+    const int nb = GR->cur ^ 1;
+    {
+        gf::TraceScope ts_("gqf_group_commit", Q.nblk, st);
+        if (Q.r == 8)
+            gqf_group_commit<8><<<grid_for(Q.nblk, 256, 8), 256, 0, st>>>(GR->d_mblk0, GR->n, GR->mctr, Q.meta[nb],
+                                                                         Q.rem[nb], Q.meta[GR->cur], Q.rem[GR->cur],
+                                                                         Q.nblk);
+        else
+            gqf_group_commit<16><<<grid_for(Q.nblk, 256, 8), 256, 0, st>>>(GR->d_mblk0, GR->n, GR->mctr, Q.meta[nb],
+                                                                          Q.rem[nb], Q.meta[GR->cur], Q.rem[GR->cur],
+                                                                          Q.nblk);
+    }
+    if (!del) {
+        gf::TraceScope ts_("gqf_group_reject", n, st);
+        gqf_group_reject<<<grid_for(n, 256, 8), 256, 0, st>>>(off, GR->n, n, GR->mctr, status);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;

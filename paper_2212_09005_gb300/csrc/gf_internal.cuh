@@ -144,6 +144,67 @@ __host__ __device__ __forceinline__ uint64_t tcf_bucket_of(uint64_t e, const Tcf
 }
 
 // ---------------------------------------------------------------------------
+// One-dimensional bulk copies between global and shared memory (the TMA's
+// cp.async.bulk, sm_90 and later), completed through an mbarrier. Addresses
+// 16-byte aligned, sizes a multiple of 16 bytes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// one arrival that also announces `bytes` of copies completing on the barrier
+__device__ __forceinline__ void mbar_arrive_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// the phase with this parity completed, or false after `limit` tries
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit)
+{
+    for (uint32_t i = 0; i < limit; i++)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst_smem)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *dst, const void *src_smem, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src_smem)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+// the shared-memory sources of this thread's bulk stores have been read
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// this thread's bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// this thread's shared-memory writes become visible to the bulk copies
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // Filter groups: member m of a group call owns keys [off[m], off[m + 1]).
 // ---------------------------------------------------------------------------
 // The member holding key i: the largest m with off[m] <= i (so empty members
@@ -370,6 +431,7 @@ struct filter_group {
     void *d_gmem = nullptr;           // per-member hash and table descriptors
     uint32_t *d_tile_member = nullptr;
     uint32_t *d_ovf = nullptr;        // members that overflowed in the last insert
+    uint64_t *d_mblk0 = nullptr;      // GQF: each member's first 64-slot block (n + 1 entries)
     int cur = 0;
 };
 
@@ -386,6 +448,12 @@ int gqf_group_remove(filter_group *G, const uint64_t *off, const uint64_t *keys,
                      cudaStream_t st);
 int gqf_group_count(filter_group *G, const uint64_t *off, const uint64_t *keys, uint64_t n, uint64_t *counts,
                     uint8_t *found, cudaStream_t st);
+// Insert (del = 0) or remove (del = 1) without any host synchronisation: the
+// merge goes to the spare buffer and every member whose merge fit is copied
+// back, so the current buffer never changes; a member whose insert does not
+// fit keeps its table and its keys get FILTER_KEY_FULL.
+int gqf_group_update_async(filter_group *G, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *status,
+                           int del, cudaStream_t st);
 enum GroupOp : int { GROUP_INSERT = 0, GROUP_REMOVE = 1, GROUP_QUERY = 2 };
 
 int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only);

@@ -731,7 +731,7 @@ static constexpr int TT_TPB = 256;      // threads of the partition and tile ker
 static constexpr int TT_CH = 2048;      // items per partition chunk (8 per thread)
 static constexpr int TT_BINS = 512;     // shared-memory bins of a partition chunk
 static constexpr uint32_t TT_CAP = 2048;  // candidates a tile stages in shared memory (8 per thread)
-static constexpr uint32_t TT_TB_MAX = 4096;
+static constexpr uint32_t TT_TB_MAX = 2048;
 static constexpr uint64_t TT_LEFT = 1ull << 63;  // stage entry: the candidate is left for the next phase
 
 // words of the tile counters a filter needs: counts (nt + 1), high-bin
@@ -830,7 +830,9 @@ __global__ void __launch_bounds__(TT_TPB) tt_hist(const TtSrc s, TcfGeom G, TcfP
     const TtCtr C = tt_ctr(ctr_words, tg);
     const uint64_t n = tt_count(s);
     note_units(units, n);
-    const bool shared = tg.nt <= 8192;
+    if (n == 0) return;  // an empty phase: the later kernels of the phase see n = 0 and do nothing
+    // a shared histogram pays off when each CTA has enough items for its bins
+    const bool shared = tg.nt <= 8192 && n * 8 >= (uint64_t)gridDim.x * tg.nt;
     if (shared) {
         for (uint32_t t = threadIdx.x; t < tg.nt; t += TT_TPB) s_h[t] = 0;
         __syncthreads();
@@ -1198,21 +1200,39 @@ __device__ __forceinline__ uint32_t tt_block_step(uint8_t *blocks, uint64_t b, u
 // placed in block order in shared memory (a tile with more than TT_CAP of
 // them is staged in the spare record buffer `gstage` at the same offsets and
 // read twice), each block with candidates takes its step, and the candidates
-// left are written out with one reservation per tile. What a candidate left
-// becomes (NEXT): the same block's record (phase A rejects: phase B finds
-// their target), the other block's record (phase B rejects, remove misses in
-// b1), or its batch index (for the backing-bucket phase). units: algorithmic
-// bytes (12 per candidate read and per candidate left, 32 per block read, 32
-// per block written, 2 per fill read and written).
+// left are written out with one reservation per tile. A dense tile (at least
+// one candidate per TT_DENSE blocks) moves its blocks into shared memory with
+// one bulk copy, issued before the staging so that the two overlap, and back
+// with one bulk store; a sparse one reads and writes only the blocks it
+// touches. What a candidate left becomes (NEXT): the same block's record
+// (phase A rejects: phase B finds their target), the other block's record
+// (phase B rejects, remove misses in b1), or its batch index (for the
+// backing-bucket phase). n_dev: the phase's candidate count when it comes from
+// a pending list (the kernel returns at once for an empty phase). units:
+// algorithmic bytes (12 per candidate read and per candidate left, 32 per
+// block read, 32 per block written, 2 per fill read and written).
+static constexpr uint32_t TT_DENSE = 4;
+
 template <int F, int OP, int NEXT>
-__global__ void __launch_bounds__(TT_TPB, 3) tt_tile(TcfGeom G, TcfPrep P, uint8_t *blocks, uint8_t *fill, TtGeom tg,
+__global__ void __launch_bounds__(TT_TPB, 4) tt_tile(TcfGeom G, TcfPrep P, uint8_t *blocks, uint8_t *fill, TtGeom tg,
                                                   const uint32_t *__restrict__ toff, const uint64_t *__restrict__ rec,
                                                   const uint32_t *__restrict__ ridx, uint64_t *gstage, uint32_t cap,
                                                   uint64_t *orec, uint32_t *oidx, unsigned *nout, uint64_t out_cap,
-                                                  uint32_t *ctr_words, unsigned long long *status,
-                                                  unsigned long long *units)
+                                                  const unsigned *n_dev, uint32_t *ctr_words,
+                                                  unsigned long long *status, unsigned long long *units)
 {
     constexpr uint32_t RPT = TT_CAP / TT_TPB;
+    if (n_dev && *n_dev == 0) return;  // an empty phase: nothing was counted or placed
+    extern __shared__ __align__(128) uint64_t s_mem[];
+    const uint32_t TB = 1u << tg.tb_log;
+    uint8_t *s_blocks = reinterpret_cast<uint8_t *>(s_mem);                     // TB x 32 bytes
+    uint64_t *s_stage = s_mem + TB * 4;                                         // TT_CAP entries
+    uint32_t *s_start = reinterpret_cast<uint32_t *>(s_stage + TT_CAP);         // TB + 1
+    uint8_t *s_fill = reinterpret_cast<uint8_t *>(s_start + TB + 1);            // TB
+    __shared__ uint32_t s_wsum[TT_TPB / 32];
+    __shared__ uint32_t s_base;
+    __shared__ unsigned long long s_bytes;
+    __shared__ __align__(8) uint64_t s_bar;
     {
         // the partition passes of this phase are done with their cursors
         const TtCtr C = tt_ctr(ctr_words, tg);
@@ -1220,13 +1240,10 @@ __global__ void __launch_bounds__(TT_TPB, 3) tt_tile(TcfGeom G, TcfPrep P, uint8
         for (uint64_t k = blockIdx.x * (uint64_t)TT_TPB + threadIdx.x; k < w; k += (uint64_t)gridDim.x * TT_TPB)
             C.hcur[k] = 0;
     }
-    extern __shared__ uint64_t s_mem[];
-    const uint32_t TB = 1u << tg.tb_log;
-    uint64_t *s_stage = s_mem;                                       // TT_CAP entries
-    uint32_t *s_start = reinterpret_cast<uint32_t *>(s_mem + TT_CAP);  // TB + 1
-    __shared__ uint32_t s_wsum[TT_TPB / 32];
-    __shared__ uint32_t s_base;
-    __shared__ unsigned long long s_bytes;
+    if (threadIdx.x == 0) mbar_init(&s_bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
+    bool stores_pending = false;  // thread 0: a bulk store may still read s_blocks
     const uint32_t lm = Blk<F>::lane_mask(G.vmask);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint64_t T = blockIdx.x; T < tg.nt; T += gridDim.x) {
@@ -1236,8 +1253,17 @@ __global__ void __launch_bounds__(TT_TPB, 3) tt_tile(TcfGeom G, TcfPrep P, uint8
         const uint32_t nblk = (uint32_t)min((uint64_t)TB, tg.nb - b0);
         const uint32_t cnt = e - s;
         const bool in_smem = cnt <= TT_CAP;
+        const bool dense = (uint64_t)cnt * TT_DENSE >= nblk;
         uint64_t *stage = in_smem ? s_stage : gstage + s;
+        if (dense && threadIdx.x == 0) {
+            if (stores_pending) bulk_wait_read();  // the previous tile's store has read s_blocks
+            stores_pending = false;
+            mbar_arrive_expect(&s_bar, nblk * 32);
+            bulk_load(s_blocks, blocks + b0 * 32, nblk * 32, &s_bar);
+        }
         for (uint32_t k = threadIdx.x; k <= nblk; k += TT_TPB) s_start[k] = 0;
+        if (dense)
+            for (uint32_t k = threadIdx.x; k < nblk; k += TT_TPB) s_fill[k] = fill[b0 + k];
         if (threadIdx.x == 0) s_bytes = 0;
         __syncthreads();
         uint64_t rv[RPT];
@@ -1305,24 +1331,45 @@ __global__ void __launch_bounds__(TT_TPB, 3) tt_tile(TcfGeom G, TcfPrep P, uint8
                 if (k < nblk) s_start[k] = prev[j];
             }
         }
-        __syncthreads();
+        if (dense) {
+            // the tile's blocks have arrived (a bounded wait: give up on the
+            // whole kernel, reporting a timeout, rather than spin for ever)
+            const bool ok = mbar_wait_bounded(&s_bar, parity, SPIN_LIMIT);
+            parity ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+                break;
+            }
+        } else {
+            __syncthreads();
+        }
         // each block with candidates takes its step
+        uint8_t *blk_base = dense ? s_blocks : blocks;
         uint64_t bytes = 0;
         for (uint32_t k = threadIdx.x; k < nblk; k += TT_TPB) {
             const uint32_t c = s_start[k + 1] - s_start[k];
             if (!c) continue;
             const uint64_t b = b0 + k;
-            const uint32_t f0 = fill[b];
+            const uint32_t f0 = dense ? s_fill[k] : fill[b];
             if (s_start[k + 1] > cnt || s_start[k + 1] < s_start[k] || f0 > (uint32_t)Blk<F>::B) {
                 atomicOr(status, ST_INTERNAL);
                 continue;
             }
             bytes += 12ull * c + 2;
-            const uint32_t f1 =
-                tt_block_step<F, OP>(blocks, b, k, f0, cap, stage + s_start[k], c, lm, G.vmask, bytes);
+            const uint32_t f1 = tt_block_step<F, OP>(blk_base, dense ? k : b, k, f0, cap, stage + s_start[k], c, lm,
+                                                     G.vmask, bytes);
             if (f1 != f0) fill[b] = (uint8_t)f1;
         }
-        __syncthreads();
+        if (dense) {
+            fence_async_shared();  // the block writes above, before the bulk store reads them
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                bulk_store(blocks + b0 * 32, s_blocks, nblk * 32);
+                stores_pending = true;
+            }
+        } else {
+            __syncthreads();
+        }
         // the candidates left, written out in stage order with one reservation
         for (uint32_t c0 = 0; c0 < cnt; c0 += TT_CAP) {
             const uint32_t i0 = c0 + threadIdx.x * RPT;
@@ -1374,6 +1421,7 @@ __global__ void __launch_bounds__(TT_TPB, 3) tt_tile(TcfGeom G, TcfPrep P, uint8
         __syncthreads();
         if (units && threadIdx.x == 0 && s_bytes) atomicAdd(units, s_bytes);
     }
+    if (threadIdx.x == 0 && stores_pending) bulk_wait_all();
 }
 
 // ---------------------------------------------------------------------------
@@ -1702,7 +1750,7 @@ static TtGeom tt_geom(uint64_t nb, uint64_t n)
     TtGeom g;
     g.nb = nb;
     uint32_t tl = 5;
-    while (tl < 12 && (n << (tl + 1)) <= (uint64_t)(TT_CAP / 2) * nb) tl++;
+    while ((1u << (tl + 1)) <= TT_TB_MAX && (n << (tl + 1)) <= (uint64_t)(TT_CAP / 2) * nb) tl++;
     g.tb_log = tl;
     g.nt = (nb + (1ull << tl) - 1) >> tl;
     uint32_t lg = 0;
@@ -1713,17 +1761,18 @@ static TtGeom tt_geom(uint64_t nb, uint64_t n)
 }
 
 template <int F, int OP, int NEXT>
-static void tt_tile_launch(const TcfBulk &T, const TtGeom &tg, const uint64_t *rec, const uint32_t *ridx,
-                           uint64_t *gstage, uint32_t cap, uint64_t *orec, uint32_t *oidx, unsigned *nout,
-                           const char *name, cudaStream_t st)
+static void tt_tile_launch(const TcfBulk &T, const TtGeom &tg, const unsigned *n_dev, const uint64_t *rec,
+                           const uint32_t *ridx, uint64_t *gstage, uint32_t cap, uint64_t *orec, uint32_t *oidx,
+                           unsigned *nout, const char *name, cudaStream_t st)
 {
-    const size_t smem = TT_CAP * 8 + (((size_t)1 << tg.tb_log) + 1) * 4;
+    const size_t TB = (size_t)1 << tg.tb_log;
+    const size_t smem = TB * 32 + TT_CAP * 8 + (TB + 1) * 4 + TB;
     cudaFuncSetAttribute(tt_tile<F, OP, NEXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(TT_CAP * 8 + (TT_TB_MAX + 1) * 4));
+                         (int)(TT_TB_MAX * 32 + TT_CAP * 8 + (TT_TB_MAX + 1) * 4 + TT_TB_MAX));
     const uint64_t grid = tg.nt < (uint64_t)sm_count() * 8 ? tg.nt : (uint64_t)sm_count() * 8;
     gf::TraceScope ts_(name, 0, st, true);
     tt_tile<F, OP, NEXT><<<(unsigned)grid, TT_TPB, smem, st>>>(T.G, T.prep, T.blocks, T.fill, tg, T.off, rec, ridx,
-                                                               gstage, cap, orec, oidx, nout, T.max_n, T.tcur,
+                                                               gstage, cap, orec, oidx, nout, T.max_n, n_dev, T.tcur,
                                                                &T.ctr->status, ts_.units());
 }
 
@@ -1781,13 +1830,13 @@ static void tcf_tiled_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n,
     // A: shortcut into b1 while fill < 3B/4; rejects keep b1 (the counts'
     // last CTA also clears the call's pending-list lengths)
     tt_group<TT_KEYS, TT_SAME>(T, tg, TtSrc{keys, nullptr, nullptr, nullptr, n}, ctr, &gr, &gi, &sp, st);
-    tt_tile_launch<F, 0, TT_NX_SAME>(T, tg, gr, gi, sp, G.tsc, T.pend1, T.pend0, &np[0], "tcf_tile_insert", st);
+    tt_tile_launch<F, 0, TT_NX_SAME>(T, tg, nullptr, gr, gi, sp, G.tsc, T.pend1, T.pend0, &np[0], "tcf_tile_insert", st);
     // B: the less full of b1, b2 under the post-A fills; rejects go to the other block
     tt_group<TT_PEND, TT_TARGET>(T, tg, TtSrc{nullptr, T.pend1, T.pend0, &np[0], n}, nullptr, &gr, &gi, &sp, st);
-    tt_tile_launch<F, 0, TT_NX_OTHER>(T, tg, gr, gi, sp, G.B, T.pb, T.pbi, &np[1], "tcf_tile_insert", st);
+    tt_tile_launch<F, 0, TT_NX_OTHER>(T, tg, &np[0], gr, gi, sp, G.B, T.pb, T.pbi, &np[1], "tcf_tile_insert", st);
     // C: the other block; rejects go to the backing buckets by index
     tt_group<TT_PEND, TT_SAME>(T, tg, TtSrc{nullptr, T.pb, T.pbi, &np[1], n}, nullptr, &gr, &gi, &sp, st);
-    tt_tile_launch<F, 0, TT_NX_IDX>(T, tg, gr, gi, sp, G.B, nullptr, T.pend2, &np[2], "tcf_tile_insert", st);
+    tt_tile_launch<F, 0, TT_NX_IDX>(T, tg, &np[1], gr, gi, sp, G.B, nullptr, T.pend2, &np[2], "tcf_tile_insert", st);
     // D: backing buckets
     PhaseDst P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
     {
@@ -1808,10 +1857,10 @@ static void tcf_tiled_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n,
     uint64_t *sp;
     // 1: primary block; misses go on to the secondary block
     tt_group<TT_KEYS, TT_SAME>(T, tg, TtSrc{keys, nullptr, nullptr, nullptr, n}, ctr, &gr, &gi, &sp, st);
-    tt_tile_launch<F, 1, TT_NX_OTHER>(T, tg, gr, gi, sp, 0, T.pend1, T.pend0, &np[0], "tcf_tile_remove", st);
+    tt_tile_launch<F, 1, TT_NX_OTHER>(T, tg, nullptr, gr, gi, sp, 0, T.pend1, T.pend0, &np[0], "tcf_tile_remove", st);
     // 2: secondary block; misses go to the backing buckets by index
     tt_group<TT_PEND, TT_SAME>(T, tg, TtSrc{nullptr, T.pend1, T.pend0, &np[0], n}, nullptr, &gr, &gi, &sp, st);
-    tt_tile_launch<F, 1, TT_NX_IDX>(T, tg, gr, gi, sp, 0, nullptr, T.pend2, &np[2], "tcf_tile_remove", st);
+    tt_tile_launch<F, 1, TT_NX_IDX>(T, tg, &np[0], gr, gi, sp, 0, nullptr, T.pend2, &np[2], "tcf_tile_remove", st);
     // 3: backing bucket; what is left is not found
     PhaseDst P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
     {
