@@ -68,6 +68,17 @@ BYTES_PER_UNIT = {
     "tcf_block_remove_sparse": 74.0,
     "tcf_bucket_insert": 136.0,  # per bucket with candidates: segment + 64-byte bucket read and write
     "tcf_bucket_remove": 136.0,
+    "tcf_tile_hist": 8.0,        # key read (tile histogram through shared memory)
+    "tcf_tile_hist_pend": 12.0,  # pending record read
+    "tcf_tile_part": 20.0,       # key read + 12-byte record write
+    "tcf_tile_part_pend": 24.0,  # record read + record write
+    "tcf_tile_part2": 24.0,      # record read + record write (second partition pass)
+    "tcf_tile_insert": 1.0,      # unit = algorithmic byte, counted on the device: 12 per candidate read and
+    "tcf_tile_remove": 1.0,      # per candidate left, 32 per block read, 32 per block written, 2 per fill
+    "batch_gather": 16.0,        # key read + key write
+    "batch_scatter": 9.0,        # result read + write (1 byte; counts: 16)
+    "gqf_group_commit": 192.0,   # per 64-slot block: 32 B metadata + 64 B remainders, read and written (r = 8)
+    "gqf_group_reject": 8.0,
     "tcf_point_insert": 104.0,
     "tcf_point_remove": 104.0,
     # filter groups
@@ -658,6 +669,53 @@ class BatchedRunner:
         self.tf, self.tfn = u8(self.tkeys.numel()), u8(self.tneg.numel())
         self.gf_, self.gfn = u8(self.gkeys.numel()), u8(self.gneg.numel())
         self.ops = int(off[-1]) * 3  # inserts, own-key queries, fresh-key queries
+        # the same step as work lists: one list per TCF round, then one with the
+        # TCF queries, the GQF insert and the GQF queries
+        # the last list queries each group's own keys and as many fresh keys in one class
+        self.B = gf.FilterBatch(self.T, self.G, max_keys=max(mt, 2 * int(self.tkeys.numel()), 2 * int(self.gkeys.numel())),
+                                max_items=4 * len(logs))
+        TB, GB = gf.BATCH_TCF, gf.BATCH_GQF
+        self.lists = []
+        for o, k in self.rounds:
+            oh = o.cpu().numpy()
+            self.lists.append([(TB, m, gf.OP_INSERT, k[oh[m]:oh[m + 1]], None) for m in range(nt)])
+        last = []
+        for m in range(nt):
+            a, b = int(toff[m]), int(toff[m + 1])
+            last.append((TB, m, gf.OP_QUERY, self.tkeys[a:b], self.tf[a:b]))
+            last.append((TB, m, gf.OP_QUERY, self.tneg[a:b], self.tfn[a:b]))
+        for m in range(len(logs) - nt):
+            a, b = int(goff[m]), int(goff[m + 1])
+            last.append((GB, m, gf.OP_INSERT, self.gkeys[a:b], None))
+            last.append((GB, m, gf.OP_QUERY, self.gkeys[a:b], self.gf_[a:b]))
+            last.append((GB, m, gf.OP_QUERY, self.gneg[a:b], self.gfn[a:b]))
+        self.lists.append(last)
+        self.graph = None
+
+    def step_batch(self):
+        self.T.clear()
+        self.G.clear()
+        for items in self.lists:
+            self.B.run(items)
+
+    def capture(self):
+        torch = self.torch
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step_batch()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.step_batch()
+
+    def step_graph(self):
+        self.graph.replay()
+
+    def outputs(self):
+        self.torch.cuda.synchronize()
+        return [t.clone() for t in (self.tf, self.tfn, self.gf_, self.gfn)]
 
     def step(self):
         T, G = self.T, self.G
@@ -679,6 +737,73 @@ class BatchedRunner:
                 "tcf_fpr": float(self.tfn.float().mean().item()),
                 "gqf_own_found": bool(self.gf_.all().item()),
                 "gqf_fpr": float(self.gfn.float().mean().item())}
+
+
+def run_single_filters(w, device, args):
+    """The batched workload through one standalone filter per member and one
+    call per filter and operation (the plain path the groups replace): one
+    timed step after one warm-up step; sampled members' images are compared
+    with a group's."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    off, keys, neg = w["offsets"], w["insert"], w["negatives"]
+    logs, seeds, nt, rounds = w["log2_slots"], w["hash_seeds"], w["n_tcf"], w["tcf_rounds"]
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
+    dk, dn = to_dev(keys), to_dev(neg)
+    found = torch.zeros(int(off[-1]), dtype=torch.uint8, device=device)
+    chunks = W.round_chunks(off[: nt + 1], rounds)
+    fs = []
+    for m in range(len(logs)):
+        n = int(off[m + 1] - off[m])
+        if m < nt:
+            mb = max(1, int((chunks[:, m, 1] - chunks[:, m, 0]).max()))
+            fs.append(gf.TCF(int(logs[m]), 16, gf.MODE_BULK, seed=int(seeds[m]), max_batch=mb))
+        else:
+            fs.append(gf.GQF(int(logs[m]), 8, seed=int(seeds[m]), max_batch=max(1, n)))
+
+    def step():
+        for f in fs:
+            f.clear()
+        for j in range(rounds):
+            for m in range(nt):
+                a, b = int(chunks[j, m, 0]), int(chunks[j, m, 1])
+                if b > a:
+                    fs[m].insert(dk[a:b])
+        for m in range(len(logs)):
+            a, b = int(off[m]), int(off[m + 1])
+            if b == a:
+                continue
+            if m >= nt:
+                fs[m].insert(dk[a:b])
+            fs[m].query(dk[a:b], found[a:b])
+            fs[m].query(dn[a:b], found[a:b])
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    step()
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    ops = int(off[-1]) * 3
+    # members sampled against a group built the same way
+    T = gf.FilterGroup(gf.FILTER_TCF, logs[:nt], 16, seeds[:nt], max_total=int(off[nt]))
+    G = gf.FilterGroup(gf.FILTER_GQF, logs[nt:], 8, seeds[nt:], max_total=int(off[-1] - off[nt]))
+    for j in range(rounds):
+        lens = chunks[j, :, 1] - chunks[j, :, 0]
+        o = np.zeros(nt + 1, np.int64)
+        np.cumsum(lens, out=o[1:])
+        idx = np.concatenate([np.arange(a, b) for a, b in chunks[j]])
+        T.insert(to_dev(o), to_dev(keys[idx]))
+    G.insert(to_dev(off[nt:] - off[nt]), dk[int(off[nt]):])
+    same = all(np.array_equal(fs[m].export(), T.export(m)) for m in range(0, nt, 97)) and \
+        all(np.array_equal(fs[m].export(), G.export(m - nt)) for m in range(nt, len(logs), 97))
+    del fs, T, G, dk, dn, found
+    torch.cuda.empty_cache()
+    return {"seconds_per_step": round(sec, 3), "value": round(ops / sec / 1e9, 4), "filters": len(logs),
+            "member_images_equal_group": bool(same), "sample": "every 97th member of each kind"}
 
 
 def run_batched(args, device):
@@ -707,9 +832,39 @@ def run_batched(args, device):
            "ms_per_step": round(ms / args.steps, 3), "ops_per_step": R.ops,
            "gpu_launches": sum(v["launches"] for v in trace.values()), "roofline": roof,
            "random_gather": gather, "kernels": kern, "checks": R.checks()}
+    ref = R.outputs()
+    img_t, img_g = R.T.export(0), R.G.export(0)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    # the work-list form of the same step, run directly and replayed from one CUDA graph
+    ms_b = timed(R.step_batch)
+    same_b = all(torch.equal(x, y) for x, y in zip(R.outputs(), ref))
+    R.capture()
+    ms_g = timed(R.step_graph)
+    same_g = all(torch.equal(x, y) for x, y in zip(R.outputs(), ref))
+    same_img = bool(np.array_equal(R.T.export(0), img_t) and np.array_equal(R.G.export(0), img_g))
+    out["work_list"] = {"ms_per_step": round(ms_b, 3), "value": round(R.ops / (ms_b / 1e3) / 1e9, 4),
+                        "answers_equal_group_calls": bool(same_b),
+                        "graph": {"ms_per_step": round(ms_g, 3), "value": round(R.ops / (ms_g / 1e3) / 1e9, 4),
+                                  "answers_equal_group_calls": bool(same_g), "member_images_equal": same_img},
+                        "calls_per_step": len(R.lists)}
     w = R.w
+    R.graph = None
+    R.B.close()
     del R
     torch.cuda.empty_cache()
+    out["single_filter_calls"] = run_single_filters(w, device, args)
     if not args.no_cpu:
         try:
             out["cpu_baseline"] = cpu_batched_sample(w)
@@ -1253,7 +1408,7 @@ def main():
                 "warmup": max(3, args.warmup), "ms_per_step": b["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": BATCHED_WORKLOAD}, "gpu_launches": b["gpu_launches"],
-                "roofline": b["roofline"], "kernels": b["kernels"], "checks": b["checks"]}
+                "roofline": b["roofline"], "kernels": b["kernels"], "checks": b["checks"], "batched": b}
     else:
         line = run_ours(args, rank, world, local)
     if rank == 0 and line is not None:

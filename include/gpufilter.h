@@ -104,8 +104,44 @@ int filter_create(const filter_config *cfg, void *stream, filter_t **out);
 /* filter_destroy: synchronise the device and free everything. NULL is a no-op. */
 int filter_destroy(filter_t *f);
 
+/*
+ * ---- tuning ----
+ * Knobs of the bulk paths that change only the time taken: tables, answers
+ * and statuses are the same under every setting (the GPU tests check both TCF
+ * paths and the GQF in-place and merge paths against the same oracle).
+ *   tcf_path: how a TCF bulk insert or remove groups its candidates by block.
+ *     FILTER_TCF_PATH_BLOCK: a counting sort by block (a counter and an offset
+ *     per block, an 8-byte record per key, scattered); fastest while that
+ *     scratch stays in the L2. FILTER_TCF_PATH_TILED: a partition by tile of
+ *     consecutive blocks in coalesced passes, then a shared-memory sort per
+ *     tile; fastest for large tables and batches. FILTER_TCF_PATH_AUTO takes
+ *     TILED when the table has at least tcf_tiled_min_blocks blocks and the
+ *     batch at least as many keys (0: 2^23).
+ *   tcf_tile_target: tiled path, the expected candidates per tile, 128 ..
+ *     1024 (0: 1024).
+ *   gqf_region_groups: GQF batches with at most this many distinct
+ *     fingerprints per 256 quotients on average are inserted or removed in
+ *     place (even-odd regions); denser ones take the merge (0: 8).
+ * filter_set_tuning / filter_group_set_tuning: FILTER_ERR_ARG for values out
+ * of range. filter_get_tuning: the current settings (0 fields = defaults).
+ */
+#define FILTER_TCF_PATH_AUTO 0
+#define FILTER_TCF_PATH_BLOCK 1
+#define FILTER_TCF_PATH_TILED 2
+
+typedef struct filter_tuning {
+    uint32_t tcf_path;
+    uint32_t tcf_tile_target;
+    uint32_t gqf_region_groups;
+    uint32_t reserved;
+    uint64_t tcf_tiled_min_blocks;
+} filter_tuning;
+
 /* filter_clear: empty the table (asynchronous) and reset the statistics. */
 int filter_clear(filter_t *f, void *stream);
+
+int filter_set_tuning(filter_t *f, const filter_tuning *t);
+int filter_get_tuning(filter_t *f, filter_tuning *out);
 
 /*
  * filter_insert: insert n keys (a multiset: duplicates are counted, Sec. 5 of
@@ -383,6 +419,9 @@ int filter_group_create(const filter_config *cfgs, uint32_t n_filters, uint64_t 
 /* filter_group_destroy: synchronise the device and free everything. NULL is a no-op. */
 int filter_group_destroy(filter_group_t *g);
 
+/* filter_group_set_tuning: the tuning of every member's calls (see filter_set_tuning). */
+int filter_group_set_tuning(filter_group_t *g, const filter_tuning *t);
+
 /* filter_group_clear: empty every member (asynchronous) and reset the statistics. */
 int filter_group_clear(filter_group_t *g, void *stream);
 
@@ -441,9 +480,9 @@ int filter_group_export(filter_group_t *g, uint32_t member, void *host_buf, uint
  * filter_batch_create: a batch context over `tcf` (a TCF group, or NULL) and
  *   `gqf` (a GQF group, or NULL), for calls of at most max_items items and at
  *   most max_keys keys per (group, operation) class. It allocates max_keys x
- *   16 bytes of device scratch and a ring of descriptor slots (pinned host
- *   and device memory, 16 slots). The groups stay owned by the caller and
- *   must outlive the batch.
+ *   16 bytes of device scratch and one device descriptor buffer (about
+ *   40 bytes per item plus 8 per member and class). The groups stay owned by
+ *   the caller and must outlive the batch.
  * filter_batch_run: per group, all inserts run first, then removes, then
  *   queries, then counts (GQF only); within one class, member m's items are
  *   concatenated in list order and applied as one batch (one group call for
@@ -452,10 +491,12 @@ int filter_group_export(filter_group_t *g, uint32_t member, void *host_buf, uint
  *   into a GQF member that do not fit leave that member's table unchanged and
  *   report FILTER_KEY_FULL for all of its keys in the call (unlike
  *   filter_group_insert, which keeps the longest prefix that fits and needs
- *   host round trips). Each call uses the next slot of the ring for its
- *   descriptors: a captured graph may hold at most 16 calls of one batch, and
- *   no further calls of that batch may be made while the graph is still to
- *   be replayed. FILTER_ERR_ARG for a bad group, member or op, n_items >
+ *   host round trips). A call's descriptors travel by value in the
+ *   parameters of its own upload launches, so the list may be reused or
+ *   freed as soon as the call returns, and direct calls and replays of
+ *   captured graphs may be mixed freely; they share the batch's scratch, so
+ *   they must run in order (one stream, or streams the caller orders).
+ *   FILTER_ERR_ARG for a bad group, member or op, n_items >
  *   max_items, or a class above max_keys (inserts and removes also above the
  *   group's max_total); FILTER_ERR_UNSUPPORTED for a count on the TCF group.
  *   Nothing is enqueued when an item is rejected.

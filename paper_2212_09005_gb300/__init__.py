@@ -17,7 +17,7 @@ import numpy as np
 __all__ = [
     "Filter", "TCF", "GQF", "FilterGroup", "FilterServer", "lib", "build", "FilterError",
     "FILTER_TCF", "FILTER_GQF", "MODE_BULK", "MODE_POINT",
-    "KEY_OK", "KEY_FULL", "KEY_NOT_FOUND", "STATUS_FULL", "STATUS_TIMEOUT",
+    "KEY_OK", "KEY_FULL", "KEY_NOT_FOUND", "STATUS_FULL", "STATUS_TIMEOUT", "FilterBatch", "BATCH_TCF", "BATCH_GQF",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -45,7 +45,13 @@ EXPORTS = [
     "filter_server_destroy",
     "filter_calibrate_gather",
     "filter_debug_fail_alloc", "filter_debug_live_allocations", "filter_debug_wait_timeout",
+    "filter_batch_create", "filter_batch_run", "filter_batch_destroy",
+    "filter_set_tuning", "filter_get_tuning", "filter_group_set_tuning",
 ]
+
+TCF_PATH_AUTO, TCF_PATH_BLOCK, TCF_PATH_TILED = 0, 1, 2
+
+BATCH_TCF, BATCH_GQF = 0, 1
 
 OP_INSERT, OP_QUERY, OP_REMOVE, OP_COUNT = 0, 1, 2, 3
 
@@ -74,6 +80,16 @@ class FilterDeviceView(C.Structure):
 class FilterRequest(C.Structure):
     _fields_ = [("filter", C.c_uint32), ("op", C.c_uint32), ("host_keys", C.c_void_p), ("n", C.c_uint64),
                 ("host_out", C.c_void_p)]
+
+
+class FilterWork(C.Structure):
+    _fields_ = [("group", C.c_uint32), ("member", C.c_uint32), ("op", C.c_uint32), ("reserved", C.c_uint32),
+                ("d_keys", C.c_void_p), ("n", C.c_uint64), ("d_out", C.c_void_p)]
+
+
+class FilterTuning(C.Structure):
+    _fields_ = [("tcf_path", C.c_uint32), ("tcf_tile_target", C.c_uint32), ("gqf_region_groups", C.c_uint32),
+                ("reserved", C.c_uint32), ("tcf_tiled_min_blocks", C.c_uint64)]
 
 
 class ServerStats(C.Structure):
@@ -135,10 +151,16 @@ def lib():
         L.filter_server_submit.argtypes = [vp, C.POINTER(FilterRequest), C.POINTER(u64)]
         L.filter_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
         L.filter_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.filter_batch_create.argtypes = [vp, vp, u64, C.c_uint32, C.POINTER(vp)]
+        L.filter_batch_run.argtypes = [vp, C.POINTER(FilterWork), C.c_uint32, vp]
+        L.filter_batch_destroy.argtypes = [vp]
         L.filter_debug_fail_alloc.argtypes = [C.c_uint32]
         L.filter_debug_live_allocations.argtypes = [C.POINTER(u64)]
         L.filter_debug_wait_timeout.argtypes = [vp, C.c_uint32, vp]
         L.filter_server_destroy.argtypes = [vp]
+        L.filter_set_tuning.argtypes = [vp, C.POINTER(FilterTuning)]
+        L.filter_get_tuning.argtypes = [vp, C.POINTER(FilterTuning)]
+        L.filter_group_set_tuning.argtypes = [vp, C.POINTER(FilterTuning)]
         L.filter_calibrate_gather.argtypes = [vp, u64, vp, u64, C.c_uint32, vp, vp]
         L.filter_error_string.argtypes = [i32]
         L.filter_error_string.restype = C.c_char_p
@@ -190,6 +212,19 @@ class Filter:
         self._h = h
         self.kind, self.log2_slots, self.tag_bits, self.mode = kind, log2_slots, tag_bits, mode
         self.seed, self.max_batch, self.value_bits = seed, max(1, int(max_batch)), value_bits
+        t = tuning.lookup(kind, log2_slots)
+        if t:
+            self.set_tuning(**t)
+
+    def set_tuning(self, **knobs):
+        """Kernel choices that never change results: tcf_path (TCF_PATH_*),
+        tcf_tile_target, tcf_tiled_min_blocks, gqf_region_groups; 0 = default."""
+        _check(lib().filter_set_tuning(self._h, C.byref(tuning.struct(knobs))), "filter_set_tuning")
+
+    def get_tuning(self) -> dict:
+        t = FilterTuning()
+        _check(lib().filter_get_tuning(self._h, C.byref(t)), "filter_get_tuning")
+        return {k: getattr(t, k) for k, _ in FilterTuning._fields_ if k != "reserved"}
 
     def close(self):
         if getattr(self, "_h", None):
@@ -316,6 +351,14 @@ class FilterGroup:
         self._h = h
         self.kind, self.tag_bits, self.log2_slots, self.seeds = kind, tag_bits, log2_slots, seeds
         self.max_total = max(1, int(max_total))
+        total = sum(1 << lg for lg in log2_slots)
+        t = tuning.lookup(kind, total.bit_length() - 1)
+        if t:
+            self.set_tuning(**t)
+
+    def set_tuning(self, **knobs):
+        """The same knobs as Filter.set_tuning, for the group and every member."""
+        _check(lib().filter_group_set_tuning(self._h, C.byref(tuning.struct(knobs))), "filter_group_set_tuning")
 
     def close(self):
         if getattr(self, "_h", None):
@@ -367,6 +410,44 @@ class FilterGroup:
         _check(lib().filter_group_export(self._h, member, buf.ctypes.data_as(C.c_void_p), n.value,
                                          _stream(stream)), "filter_group_export")
         return buf
+
+
+class FilterBatch:
+    """A work list over a TCF group and a GQF group (either may be None): each
+    run applies items (group, member, op, keys, out) with one group call per
+    (group, operation) class; per group inserts run first, then removes, then
+    queries, then counts. Keys and results are CUDA tensors; the list is host
+    data, so a run never synchronises and can be captured in a CUDA graph."""
+
+    def __init__(self, tcf_group=None, gqf_group=None, max_keys: int = 1 << 22, max_items: int = 8192):
+        self.groups = (tcf_group, gqf_group)  # keeps the groups alive
+        h = C.c_void_p()
+        _check(lib().filter_batch_create(tcf_group._h if tcf_group else None, gqf_group._h if gqf_group else None,
+                                         int(max_keys), int(max_items), C.byref(h)), "filter_batch_create")
+        self._h = h
+
+    def run(self, items, stream=None):
+        """items: iterable of (group, member, op, keys, out); group BATCH_TCF or
+        BATCH_GQF, op OP_*, keys an int64 CUDA tensor, out a uint8 (statuses,
+        found flags) or int64 (counts) CUDA tensor of the same length, or None."""
+        items = list(items)
+        arr = (FilterWork * max(1, len(items)))()
+        for k, (g, m, op, keys, out) in enumerate(items):
+            arr[k] = FilterWork(g, m, op, 0, _dptr(keys, 8) if keys.numel() else None, keys.numel(),
+                                _dptr(out) if out is not None else None)
+        self._keep = items
+        _check(lib().filter_batch_run(self._h, arr, len(items), _stream(stream)), "filter_batch_run")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().filter_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class FilterServer:
@@ -486,3 +567,6 @@ def gqf_insert_noalloc(q: int, r: int, seed: int, table_in, table_out, keys, sta
                                            _dptr(table_out, 1), _dptr(keys, 8), keys.numel(),
                                            _dptr(status, 1), _stream(stream)),
            "filter_gqf_insert_noalloc")
+
+
+from . import tuning  # noqa: E402  (uses the classes above)

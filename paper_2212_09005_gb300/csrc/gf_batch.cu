@@ -9,9 +9,12 @@
 // queries, counts. A class gathers its items' keys into one member-ordered
 // array (a member's items in list order), runs one group call over it, and
 // scatters the results back to the items. The descriptors of a call (member
-// offsets, item placements) are staged in a ring of pinned host slots and
-// copied to a device ring, one slot per call, so that the calls of a captured
-// graph read their own descriptors when it is replayed.
+// offsets, item placements) travel inside the parameters of small upload
+// kernels (up to 32 KB each), which write them to one device buffer ahead of
+// the call's other launches. A launch keeps its parameters by value, so the
+// host may build the next call's descriptors at once, and a captured graph
+// carries its own copy; calls and replays on one stream run in order and
+// can share that buffer.
 #include <cstring>
 #include <new>
 #include <vector>
@@ -20,7 +23,13 @@
 
 namespace {
 
-constexpr uint32_t RING = 16;  // calls whose descriptors stay live (a captured graph may hold this many)
+// 16-byte words of descriptors one upload kernel carries (the parameter
+// space of a launch holds 32,764 bytes; this leaves room for the others)
+constexpr uint32_t UPLOAD_WORDS = 2040;
+
+struct UploadChunk {
+    uint4 w[UPLOAD_WORDS];
+};
 
 struct ItemDesc {
     const uint64_t *src;  // the item's keys
@@ -38,13 +47,18 @@ struct filter_batch {
     uint32_t max_items = 0;
     uint64_t *d_keys = nullptr;  // gathered keys of one class
     uint8_t *d_out = nullptr;    // its results (8 bytes per key)
-    char *h_ring = nullptr, *d_ring = nullptr;
-    size_t slot_bytes = 0;
-    uint32_t slot = 0;
+    char *d_desc = nullptr;      // descriptors of the current call
+    std::vector<uint4> h_desc;   // their host image (built per call)
+    size_t desc_bytes = 0;
     int device = 0;
 };
 
 namespace {
+
+__global__ void batch_upload(const __grid_constant__ UploadChunk c, uint32_t words, uint4 *dst)
+{
+    for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) dst[i] = c.w[i];
+}
 
 // key j of a class (list order) goes to its member-ordered place
 __global__ void batch_gather(const ItemDesc *__restrict__ items, uint32_t ni, uint64_t total, uint64_t *keys)
@@ -86,8 +100,7 @@ static void batch_free(filter_batch *B)
     if (!B) return;
     gf::dev_free(B->d_keys);
     gf::dev_free(B->d_out);
-    gf::dev_free(B->d_ring);
-    if (B->h_ring) cudaFreeHost(B->h_ring);
+    gf::dev_free(B->d_desc);
     delete B;
 }
 
@@ -112,12 +125,17 @@ int filter_batch_create(filter_group_t *tcf, filter_group_t *gqf, uint64_t max_k
     for (int g = 0; g < 2; g++)
         if (B->g[g] && B->g[g]->n > nm) nm = B->g[g]->n;
     // one call: at most 8 classes of member offsets, and one descriptor per item
-    B->slot_bytes = (8 * (((nm + 1) * 8 + 255) & ~255ull) + (uint64_t)max_items * sizeof(ItemDesc) + 8 * 256 + 255) &
+    B->desc_bytes = (8 * (((nm + 1) * 8 + 255) & ~255ull) + (uint64_t)max_items * sizeof(ItemDesc) + 8 * 256 + 255) &
                     ~(size_t)255;
+    try {
+        B->h_desc.resize(B->desc_bytes / 16);
+    } catch (...) {
+        batch_free(B);
+        return FILTER_ERR_OOM;
+    }
     if (gf::dev_malloc(reinterpret_cast<void **>(&B->d_keys), max_keys * 8) != cudaSuccess ||
         gf::dev_malloc(reinterpret_cast<void **>(&B->d_out), max_keys * 8) != cudaSuccess ||
-        gf::dev_malloc(reinterpret_cast<void **>(&B->d_ring), B->slot_bytes * RING) != cudaSuccess ||
-        cudaMallocHost(&B->h_ring, B->slot_bytes * RING) != cudaSuccess) {
+        gf::dev_malloc(reinterpret_cast<void **>(&B->d_desc), B->desc_bytes) != cudaSuccess) {
         cudaGetLastError();
         batch_free(B);
         return FILTER_ERR_OOM;
@@ -149,77 +167,105 @@ int filter_batch_run(filter_batch_t *B, const filter_work *items, uint32_t n_ite
     }
     for (int g = 0; g < 2; g++)
         for (int op = 0; op < 4; op++) {
+            if (tot[g][op] == 0) continue;  // (only a configured group has items)
             if (tot[g][op] > B->max_keys) return FILTER_ERR_ARG;
             if ((op == FILTER_OP_INSERT || op == FILTER_OP_REMOVE) && tot[g][op] > B->g[g]->max_total)
                 return FILTER_ERR_ARG;
         }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    char *h = B->h_ring + (size_t)B->slot * B->slot_bytes;
-    char *d = B->d_ring + (size_t)B->slot * B->slot_bytes;
-    B->slot = (B->slot + 1) % RING;
+    // descriptors of every class, built on the host first
+    struct Class {
+        int g;
+        uint32_t op, ni;
+        uint64_t n;
+        size_t off_at, desc_at;  // byte offsets in the descriptor buffer
+        bool want_out;
+    };
+    Class cls[8];
+    int ncls = 0;
+    char *h = reinterpret_cast<char *>(B->h_desc.data());
     size_t used = 0;
     static const uint32_t order[4] = {FILTER_OP_INSERT, FILTER_OP_REMOVE, FILTER_OP_QUERY, FILTER_OP_COUNT};
+    std::vector<uint64_t> cursor;
     for (int g = 0; g < 2; g++) {
         filter_group *G = B->g[g];
         if (!G) continue;
         for (uint32_t op : order) {
             if (tot[g][op] == 0) continue;
-            std::vector<uint32_t> sel;
-            bool want_out = false;
-            for (uint32_t i = 0; i < n_items; i++)
-                if (items[i].group == (uint32_t)g && items[i].op == op && items[i].n) {
-                    sel.push_back(i);
-                    want_out |= items[i].d_out != nullptr;
-                }
+            Class &c = cls[ncls++];
+            c.g = g;
+            c.op = op;
+            c.want_out = false;
             const uint32_t nm = G->n;
+            c.off_at = used;
             uint64_t *h_off = reinterpret_cast<uint64_t *>(h + used);
-            uint64_t *d_off = reinterpret_cast<uint64_t *>(d + used);
-            const size_t off_bytes = (((size_t)nm + 1) * 8 + 255) & ~(size_t)255;
-            ItemDesc *h_desc = reinterpret_cast<ItemDesc *>(h + used + off_bytes);
-            ItemDesc *d_desc = reinterpret_cast<ItemDesc *>(d + used + off_bytes);
-            const size_t desc_bytes = (sel.size() * sizeof(ItemDesc) + 255) & ~(size_t)255;
+            used += (((size_t)nm + 1) * 8 + 255) & ~(size_t)255;
+            c.desc_at = used;
+            ItemDesc *h_item = reinterpret_cast<ItemDesc *>(h + used);
             // member offsets of the class, then each item's place
             std::memset(h_off, 0, ((size_t)nm + 1) * 8);
-            for (uint32_t i : sel) h_off[items[i].member + 1] += items[i].n;
+            for (uint32_t i = 0; i < n_items; i++)
+                if (items[i].group == (uint32_t)g && items[i].op == op && items[i].n) h_off[items[i].member + 1] += items[i].n;
             for (uint32_t m = 0; m < nm; m++) h_off[m + 1] += h_off[m];
-            std::vector<uint64_t> cursor(h_off, h_off + nm);
+            cursor.assign(h_off, h_off + nm);
             uint64_t at = 0;
-            for (size_t k = 0; k < sel.size(); k++) {
-                const filter_work &w = items[sel[k]];
-                h_desc[k] = ItemDesc{w.d_keys, w.d_out, w.n, cursor[w.member], at};
+            uint32_t k = 0;
+            for (uint32_t i = 0; i < n_items; i++) {
+                const filter_work &w = items[i];
+                if (w.group != (uint32_t)g || w.op != op || !w.n) continue;
+                h_item[k++] = ItemDesc{w.d_keys, w.d_out, w.n, cursor[w.member], at};
+                c.want_out |= w.d_out != nullptr;
                 cursor[w.member] += w.n;
                 at += w.n;
             }
-            GF_CUDA(cudaMemcpyAsync(d + used, h + used, off_bytes + sel.size() * sizeof(ItemDesc),
-                                    cudaMemcpyHostToDevice, st));
-            used += off_bytes + desc_bytes;
-            const uint64_t n = at;
-            {
-                gf::TraceScope ts_("batch_gather", n, st);
-                batch_gather<<<gf::grid_for(n, 256, 8), 256, 0, st>>>(d_desc, (uint32_t)sel.size(), n, B->d_keys);
-            }
-            uint8_t *res = want_out ? B->d_out : nullptr;
-            int rc;
-            if (g == 0) {
-                const int gop = op == FILTER_OP_INSERT ? gf::GROUP_INSERT
-                                                       : (op == FILTER_OP_REMOVE ? gf::GROUP_REMOVE : gf::GROUP_QUERY);
-                if (gop == gf::GROUP_QUERY && !res) res = B->d_out;  // a query always needs somewhere to answer
-                rc = gf::tcf_group_op(G, gop, d_off, B->d_keys, n, res, st);
-            } else if (op == FILTER_OP_INSERT || op == FILTER_OP_REMOVE) {
-                rc = gf::gqf_group_update_async(G, d_off, B->d_keys, n, res, op == FILTER_OP_REMOVE, st);
-            } else if (op == FILTER_OP_QUERY) {
-                rc = gf::gqf_group_count(G, d_off, B->d_keys, n, nullptr, B->d_out, st);
-            } else {
-                rc = gf::gqf_group_count(G, d_off, B->d_keys, n, reinterpret_cast<uint64_t *>(B->d_out), nullptr, st);
-            }
-            if (rc != FILTER_OK) return rc;
-            if (want_out) {
-                gf::TraceScope ts_("batch_scatter", n, st);
-                batch_scatter<<<gf::grid_for(n, 256, 8), 256, 0, st>>>(d_desc, (uint32_t)sel.size(), n, B->d_out,
-                                                                       op == FILTER_OP_COUNT ? 8u : 1u);
-            }
-            GF_CUDA(cudaGetLastError());
+            c.ni = k;
+            c.n = at;
+            used += ((size_t)k * sizeof(ItemDesc) + 255) & ~(size_t)255;
         }
+    }
+    // to the device, inside the parameters of the upload launches
+    {
+        const uint32_t words = (uint32_t)(used / 16);
+        gf::TraceScope ts_("batch_upload", words, st);
+        for (uint32_t w0 = 0; w0 < words; w0 += UPLOAD_WORDS) {
+            const uint32_t nw = words - w0 < UPLOAD_WORDS ? words - w0 : UPLOAD_WORDS;
+            UploadChunk chunk;
+            std::memcpy(chunk.w, B->h_desc.data() + w0, (size_t)nw * 16);
+            batch_upload<<<1, 256, 0, st>>>(chunk, nw, reinterpret_cast<uint4 *>(B->d_desc) + w0);
+        }
+        GF_CUDA(cudaGetLastError());
+    }
+    for (int ci = 0; ci < ncls; ci++) {
+        const Class &c = cls[ci];
+        filter_group *G = B->g[c.g];
+        const uint64_t *d_off = reinterpret_cast<const uint64_t *>(B->d_desc + c.off_at);
+        const ItemDesc *d_item = reinterpret_cast<const ItemDesc *>(B->d_desc + c.desc_at);
+        const uint64_t n = c.n;
+        {
+            gf::TraceScope ts_("batch_gather", n, st);
+            batch_gather<<<gf::grid_for(n, 256, 8), 256, 0, st>>>(d_item, c.ni, n, B->d_keys);
+        }
+        uint8_t *res = c.want_out ? B->d_out : nullptr;
+        int rc;
+        if (c.g == 0) {
+            const int gop = c.op == FILTER_OP_INSERT ? gf::GROUP_INSERT
+                                                     : (c.op == FILTER_OP_REMOVE ? gf::GROUP_REMOVE : gf::GROUP_QUERY);
+            if (gop == gf::GROUP_QUERY && !res) res = B->d_out;  // a query always needs somewhere to answer
+            rc = gf::tcf_group_op(G, gop, d_off, B->d_keys, n, res, st);
+        } else if (c.op == FILTER_OP_INSERT || c.op == FILTER_OP_REMOVE) {
+            rc = gf::gqf_group_update_async(G, d_off, B->d_keys, n, res, c.op == FILTER_OP_REMOVE, st);
+        } else if (c.op == FILTER_OP_QUERY) {
+            rc = gf::gqf_group_count(G, d_off, B->d_keys, n, nullptr, B->d_out, st);
+        } else {
+            rc = gf::gqf_group_count(G, d_off, B->d_keys, n, reinterpret_cast<uint64_t *>(B->d_out), nullptr, st);
+        }
+        if (rc != FILTER_OK) return rc;
+        if (c.want_out) {
+            gf::TraceScope ts_("batch_scatter", n, st);
+            batch_scatter<<<gf::grid_for(n, 256, 8), 256, 0, st>>>(d_item, c.ni, n, B->d_out,
+                                                                   c.op == FILTER_OP_COUNT ? 8u : 1u);
+        }
+        GF_CUDA(cudaGetLastError());
     }
     return FILTER_OK;
 }

@@ -26,7 +26,44 @@ static bool pointers_set(const filter *F)
            Q.idx_b && Q.idx_c && Q.ustart && Q.flags && Q.removed && Q.tile_state && Q.tile_lo && Q.radix_tmp;
 }
 
+namespace gf {
+
+bool tuning_valid(const filter_tuning &t)
+{
+    if (t.tcf_path > FILTER_TCF_PATH_TILED) return false;
+    if (t.tcf_tile_target && (t.tcf_tile_target < 128 || t.tcf_tile_target > 1024)) return false;
+    if (t.gqf_region_groups > 256) return false;
+    return true;
+}
+
+bool tcf_tiled(const filter_tuning &t, uint64_t nb, uint64_t n)
+{
+    if (t.tcf_path == FILTER_TCF_PATH_BLOCK) return false;
+    if (t.tcf_path == FILTER_TCF_PATH_TILED) return true;
+    const uint64_t m = t.tcf_tiled_min_blocks ? t.tcf_tiled_min_blocks : (1ull << 23);
+    return nb >= m && n >= m;
+}
+
+uint32_t tcf_tile_target(const filter_tuning &t) { return t.tcf_tile_target ? t.tcf_tile_target : 1024u; }
+uint64_t gqf_region_groups(const filter_tuning &t) { return t.gqf_region_groups ? t.gqf_region_groups : 8u; }
+
+}  // namespace gf
+
 extern "C" {
+
+int filter_set_tuning(filter_t *f, const filter_tuning *t)
+{
+    if (!valid(f) || !t || !gf::tuning_valid(*t)) return FILTER_ERR_ARG;
+    f->tune = *t;
+    return FILTER_OK;
+}
+
+int filter_get_tuning(filter_t *f, filter_tuning *out)
+{
+    if (!valid(f) || !out) return FILTER_ERR_ARG;
+    *out = f->tune;
+    return FILTER_OK;
+}
 
 int filter_create(const filter_config *cfg, void *stream, filter_t **out)
 {

@@ -1750,7 +1750,7 @@ static int gqf_insert_in_place(filter *F, const uint32_t *cstart, uint64_t n, ui
             (long long)Q.nblk};
     int rc = FILTER_OK;
     // a few region sizes, growing fourfold; dense batches go to the merge
-    for (uint64_t rq = RQ_MIN; rq <= (uint64_t)RQ_MAX / 4 && (uint64_t)m * rq <= GROUPS_PER_REGION * Q.N; rq <<= 2) {
+    for (uint64_t rq = RQ_MIN; rq <= (uint64_t)RQ_MAX / 4 && (uint64_t)m * rq <= gqf_region_groups(F->tune) * Q.N; rq <<= 2) {
         const uint64_t nreg = (Q.N + rq - 1) / rq;
         {
             gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);
@@ -1826,7 +1826,7 @@ int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t
     {
         uint32_t m = 0;
         if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
-        if ((uint64_t)m * RQ_MIN <= GROUPS_PER_REGION * Q.N && !Q.merge_only) {
+        if ((uint64_t)m * RQ_MIN <= gqf_region_groups(F->tune) * Q.N && !Q.merge_only) {
             bool done = false;
             if ((rc = gqf_insert_in_place(F, cstart, n, m, st, done))) return rc;
             if (done) {
@@ -1889,7 +1889,7 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
     uint32_t m = 0;
     if ((rc = read_dev(Q.flags + n, &m, st))) return rc;
     bool done = false;
-    if ((uint64_t)m * RQ_MIN <= GROUPS_PER_REGION * Q.N) {
+    if ((uint64_t)m * RQ_MIN <= gqf_region_groups(F->tune) * Q.N) {
         GView g{reinterpret_cast<Meta *>(Q.meta[Q.cur]), Q.rem[Q.cur], (long long)Q.N, (long long)Q.nslots,
                 (long long)Q.nblk};
         GF_CUDA(cudaMemsetAsync(&F->ctr->overflow, 0, 8, st));
@@ -1902,7 +1902,7 @@ int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
         if ((rc = read_dev(&F->ctr->overflow, &reach, st))) return rc;
         uint64_t rq = RQ_MIN;
         while ((unsigned long long)rq < reach) rq <<= 1;
-        if (rq <= (uint64_t)RQ_MAX && (uint64_t)m * rq <= GROUPS_PER_REGION * Q.N) {
+        if (rq <= (uint64_t)RQ_MAX && (uint64_t)m * rq <= gqf_region_groups(F->tune) * Q.N) {
             const uint64_t nreg = (Q.N + rq - 1) / rq;
             {
                 gf::TraceScope ts_("gqf_region_ranges", nreg + 1, st);

@@ -21,6 +21,14 @@ static void group_free(filter_group *G)
 
 extern "C" {
 
+int filter_group_set_tuning(filter_group_t *g, const filter_tuning *t)
+{
+    if (!valid(g) || !t || !gf::tuning_valid(*t)) return FILTER_ERR_ARG;
+    g->tune = *t;
+    for (uint32_t m = 0; m < g->n; m++) g->members[m].tune = *t;
+    return FILTER_OK;
+}
+
 int filter_group_create(const filter_config *cfgs, uint32_t n_filters, uint64_t max_total, void *stream,
                         filter_group_t **out)
 {

@@ -396,6 +396,7 @@ struct GqfState {
 
 struct filter {
     filter_config cfg{};
+    filter_tuning tune{};
     gf::Arena arena;
     void *table_mem = nullptr;
     size_t table_bytes_alloc = 0;
@@ -410,6 +411,7 @@ struct filter {
 // launches per call. members[m] is a host-side view of member m whose table
 // pointers point into the group's arrays and whose scratch is the group's.
 struct filter_group {
+    filter_tuning tune{};
     uint32_t kind = 0, n = 0;
     uint32_t bits = 0;          // TCF f / GQF r, shared by all members
     uint64_t max_total = 0;
@@ -436,6 +438,12 @@ struct filter_group {
 };
 
 namespace gf {
+// tuning values with the defaults filled in; false if one is out of range
+bool tuning_valid(const filter_tuning &t);
+// TCF bulk calls: the tiled path for this table and batch?
+bool tcf_tiled(const filter_tuning &t, uint64_t nb, uint64_t n);
+uint32_t tcf_tile_target(const filter_tuning &t);
+uint64_t gqf_region_groups(const filter_tuning &t);
 int tcf_group_setup(filter_group *G, const filter_config *cfgs, uint64_t &bytes, bool plan_only);
 int tcf_group_clear(filter_group *G, cudaStream_t st);
 int tcf_group_op(filter_group *G, int op, const uint64_t *off, const uint64_t *keys, uint64_t n, uint8_t *out,

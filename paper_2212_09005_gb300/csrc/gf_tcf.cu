@@ -575,6 +575,96 @@ __device__ __forceinline__ uint32_t warp_reserve(unsigned *counter, uint32_t min
     return base + incl - mine;
 }
 
+// The grid-stride loops of the per-block kernels step whole warps, so that
+// every lane reaches warp_reserve in every iteration.
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
+                                                        const uint64_t *__restrict__ rec, int phase,
+                                                        uint32_t cap, uint32_t *pend32, uint64_t *pend64,
+                                                        unsigned *npend, const TcfPrep prep,
+                                                        unsigned long long *units)
+{
+    constexpr int B = Blk<F>::B;
+    const uint64_t nd = phase_count(P, G.nb);
+    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
+    const uint64_t stride = (uint64_t)gridDim.x * TPB;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
+        const uint64_t j = j0 + (threadIdx.x & 31);
+        uint32_t s = 0, e = 0, k = 0;
+        uint64_t b = 0, thr = 0;  // records <= thr are accepted
+        if (j < nd) b = phase_dst(P, j, s, e);
+        if (units && !P.dlist) {
+            const unsigned t = __ballot_sync(0xffffffffu, s != e);
+            if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
+        }
+        if (j < nd) {
+            if (s != e) {
+                const uint32_t cnt = e - s;
+                const uint32_t f0 = fill[b];
+                k = cap > f0 ? min(cnt, cap - f0) : 0u;
+                if (k > 0 && cnt <= 8) {
+                    // few candidates: all loads in flight at once, a sorting
+                    // network in registers, a bitonic merge into the block
+                    Blk<F> blk;
+                    blk.load(blocks, b);
+                    uint64_t r8[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) r8[q] = q < (int)cnt ? rec[s + q] : ~0ull;
+                    sort_small(r8, cnt);
+#pragma unroll
+                    for (int q = 0; q < 8; q++)
+                        if (q == (int)k - 1) thr = r8[q];
+                    blk.merge_new(f0, k, r8);
+                    blk.store(blocks, b);
+                    fill[b] = (uint8_t)(f0 + k);
+                } else if (k > 0) {
+                    Blk<F> blk;
+                    blk.load(blocks, b);
+                    uint64_t a[MAXSEL];
+                    int have = 0;
+                    for (uint32_t q = s; q < e; q++) have = topk_push(a, have, (int)k, rec[q]);
+                    thr = a[k - 1];
+                    uint32_t t_out[B];
+                    int ia = 0, ib = 0;
+#pragma unroll
+                    for (int p = 0; p < B; p++) {
+                        uint32_t ta = (ia < (int)f0) ? blk.tag(ia) : 0xffffffffu;
+                        uint32_t tb = (ib < (int)k) ? (uint32_t)(a[ib] >> 32) : 0xffffffffu;
+                        if (ta == 0xffffffffu && tb == 0xffffffffu) {
+                            t_out[p] = 0;
+                        } else if (ta <= tb) {
+                            t_out[p] = ta;
+                            ia++;
+                        } else {
+                            t_out[p] = tb;
+                            ib++;
+                        }
+                    }
+                    blk.pack(t_out);
+                    blk.store(blocks, b);
+                    fill[b] = (uint8_t)(f0 + k);
+                }
+            }
+        }
+        const uint32_t nrej = (e - s) - k;
+        uint32_t slot = warp_reserve(npend, nrej);
+        if (nrej == 0) continue;
+        for (uint32_t q = s; q < e; q++) {
+            const uint64_t r = rec[q];
+            if (k > 0 && r <= thr) continue;
+            const uint32_t i = (uint32_t)r;
+            if (phase == 1) {
+                // the other block of the pair: b1 + b2 - b
+                uint64_t alt = prep.bt ? (prep.bt[i] >> 32) + prep.b2[i] - b
+                                       : b ^ tcf_g((uint32_t)(r >> 32) >> G.vbits, G.nb);
+                pend64[slot++] = (alt << 32) | i;
+            } else {
+                pend32[slot++] = i;
+            }
+        }
+    }
+}
+
 // backing buckets: candidates (entry in rec, index in recI) taken in (entry,
 // index) order while there is room; the rest are FULL
 __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk, PhaseDst P,
@@ -643,6 +733,132 @@ __global__ void __launch_bounds__(TPB) tcf_bucket_insert(TcfGeom G, uint64_t *bk
                 }
             }
             atomicOr(&ctr->status, ST_FULL);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk delete: per-block matching. For each tag present c times in the block,
+// the c smallest (tag, index) candidates with that tag remove one copy each.
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
+                                                        const uint64_t *__restrict__ rec, uint32_t *pend32,
+                                                        unsigned *npend, unsigned long long *units)
+{
+    constexpr int B = Blk<F>::B;
+    const uint64_t nd = phase_count(P, G.nb);
+    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
+    const uint32_t lm = Blk<F>::lane_mask(G.vmask);
+    const uint64_t stride = (uint64_t)gridDim.x * TPB;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
+        const uint64_t j = j0 + (threadIdx.x & 31);
+        uint32_t s = 0, e = 0, nunm = 0, unm = 0;
+        bool fast = false;
+        uint64_t r8[8];  // fast path: the candidates, sorted
+        // general path: per distinct stored tag, its first slot, the copies,
+        // the candidates that matched and the largest matched record
+        uint32_t dt[B], dp[B], dc[B], used[B];
+        uint64_t thr[B];
+        int ndt = 0;
+        uint64_t b = 0;
+        if (j < nd) b = phase_dst(P, j, s, e);
+        if (units && !P.dlist) {
+            const unsigned t = __ballot_sync(0xffffffffu, s != e);
+            if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
+        }
+        if (j < nd) {
+            if (s != e) {
+                const uint32_t f0 = fill[b];
+                Blk<F> blk;
+                blk.load(blocks, b);
+                int removed = 0;
+                if (e - s <= 8) {
+                    // few candidates: sort them in registers; each takes the
+                    // first remaining copy of its tag, so the block stays sorted
+                    fast = true;
+                    const uint32_t c = e - s;
+#pragma unroll
+                    for (int q = 0; q < 8; q++) r8[q] = (uint32_t)q < c ? rec[s + q] : ~0ull;
+                    sort_small(r8, c);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        if ((uint32_t)q < c) {
+                            const uint32_t sm = blk.eq_slots((uint32_t)(r8[q] >> 32), lm);
+                            if (sm) {
+                                blk.delete_at(__ffs(sm) - 1);
+                                removed++;
+                            } else {
+                                unm |= 1u << q;
+                                nunm++;
+                            }
+                        }
+                    }
+                    if (removed) {
+                        blk.store(blocks, b);
+                        fill[b] = (uint8_t)(f0 - removed);
+                    }
+                } else {
+                    uint32_t tags[B];
+#pragma unroll
+                    for (int p = 0; p < B; p++) tags[p] = blk.tag(p);
+                    // copies of a tag are adjacent (sorted by tag, then value)
+                    for (int p = 0; p < (int)f0; p++) {
+                        const uint32_t mt = tags[p] & ~G.vmask;
+                        if (ndt > 0 && dt[ndt - 1] == mt) {
+                            dc[ndt - 1]++;
+                        } else {
+                            dt[ndt] = mt;
+                            dp[ndt] = (uint32_t)p;
+                            dc[ndt] = 1;
+                            ndt++;
+                        }
+                    }
+                    for (int d = 0; d < ndt; d++) {
+                        uint64_t a[MAXSEL];
+                        int have = 0;
+                        uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
+                        for (uint32_t q = s; q < e; q++) {
+                            uint64_t r = rec[q];
+                            if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
+                        }
+                        used[d] = (uint32_t)have;
+                        thr[d] = have ? a[have - 1] : 0;
+                    }
+                    // rebuild the block without the removed copies (the
+                    // smallest values of each tag)
+                    uint32_t t_out[B];
+                    int o = 0;
+                    for (int d = 0; d < ndt; d++) {
+                        for (uint32_t c = used[d]; c < dc[d]; c++) t_out[o++] = tags[dp[d] + c];
+                        removed += (int)used[d];
+                    }
+                    for (int p = o; p < B; p++) t_out[p] = 0;
+                    if (removed) {
+                        blk.pack(t_out);
+                        blk.store(blocks, b);
+                        fill[b] = (uint8_t)(f0 - removed);
+                    }
+                    nunm = (e - s) - (uint32_t)removed;
+                }
+            }
+        }
+        // unmatched candidates go on
+        uint32_t slot = warp_reserve(npend, nunm);
+        if (nunm == 0) continue;
+        if (fast) {
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if ((unm >> q) & 1u) pend32[slot++] = (uint32_t)r8[q];
+        } else {
+            for (uint32_t q = s; q < e; q++) {
+                const uint64_t r = rec[q];
+                const uint32_t t = (uint32_t)(r >> 32);
+                bool matched = false;
+                for (int d = 0; d < ndt; d++)
+                    if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
+                if (!matched) pend32[slot++] = (uint32_t)r;
+            }
         }
     }
 }
@@ -1653,6 +1869,7 @@ struct TcfBulk {
     uint32_t *tlist, *tcount, *dlist;
     uint64_t *seg;
     uint64_t max_n;  // entries of every per-key scratch list (max_batch)
+    uint32_t tile_target;  // tiled path: expected candidates per tile
     uint32_t *tcur;  // tiled phases: tile counts and cursors
     uint64_t *pb;    // tiled phases: the second pending list
     uint32_t *pbi;
@@ -1661,10 +1878,12 @@ struct TcfBulk {
     TcfPrep prep;
 };
 
-static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep &prep, uint64_t max_n)
+static TcfBulk bulk_of(const TcfState &T, uint64_t *scan_tmp, DevCounters *ctr, const TcfPrep &prep, uint64_t max_n,
+                       const filter_tuning &tune)
 {
     TcfBulk W;
     W.max_n = max_n;
+    W.tile_target = tcf_tile_target(tune);
     W.G = T.G;
     W.blocks = T.blocks;
     W.bk = T.bk;
@@ -1738,19 +1957,90 @@ static int dst_grid(const PhaseDst &P, uint64_t n, uint64_t ndst)
     return grid_for(P.dlist ? (n < ndst ? n : ndst) : ndst, TPB, 8);
 }
 
+// The per-block counting-sort path: each phase groups its candidates by
+// destination block (counts, scan, scatter) and one thread per block takes
+// its step. Its scratch (a counter and an offset per block, a record per
+// candidate) stays in the L2 for moderate tables and batches.
+template <int F>
+static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    const TcfGeom G = T.G;
+    DevCounters *ctr = T.ctr;
+    unsigned *np = ctr->pend;
+    cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
+    cudaMemsetAsync(ctr->touched, 0, sizeof(ctr->touched) + sizeof(ctr->cursor), st);  // adjacent fields
+    // A: shortcut into b1
+    PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
+    {
+        gf::TraceScope ts_("tcf_block_insert", 0, st, true);
+        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc, T.pend0,
+                                                                   nullptr, &np[0], T.prep, ts_.units());
+    }
+    // B: the less full of b1, b2 under the post-A fills
+    P = group_phase<SRC_PEND_U32, DST_TARGET>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
+    {
+        gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
+        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
+                                                                   T.pend1, &np[1], T.prep, ts_.units());
+    }
+    // C: the other block
+    P = group_phase<SRC_PEND_U64, DST_ALT>(T, keys, n, T.pend1, &np[1], 2, nullptr, st);
+    {
+        gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
+        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
+                                                                   nullptr, &np[2], T.prep, ts_.units());
+    }
+    // D: backing buckets
+    P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
+    {
+        gf::TraceScope ts_("tcf_bucket_insert", 0, st, true);
+        tcf_bucket_insert<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr, ts_.units());
+    }
+}
+
+template <int F>
+static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
+{
+    const TcfGeom G = T.G;
+    DevCounters *ctr = T.ctr;
+    unsigned *np = ctr->pend;
+    cudaMemsetAsync(np, 0, sizeof(ctr->pend), st);
+    cudaMemsetAsync(ctr->touched, 0, sizeof(ctr->touched) + sizeof(ctr->cursor), st);  // adjacent fields
+    // 1: primary block
+    PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
+    {
+        gf::TraceScope ts_("tcf_block_remove", 0, st, true);
+        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0], ts_.units());
+    }
+    // 2: secondary block
+    P = group_phase<SRC_PEND_U32, DST_B2>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
+    {
+        gf::TraceScope ts_("tcf_block_remove_sparse", 0, st, true);
+        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2], ts_.units());
+    }
+    // 3: backing bucket; what is left is not found
+    P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
+    {
+        gf::TraceScope ts_("tcf_bucket_remove", 0, st, true);
+        tcf_bucket_remove<<<dst_grid(P, n, G.nbk), TPB, 0, st>>>(G, T.bk, P, T.rec, T.pend0, status, ctr, ts_.units());
+    }
+}
+
+
 // ---------------------------------------------------------------------------
 // Tiled phases: host side
 // ---------------------------------------------------------------------------
 // Tiles of TB blocks, TB the largest power of two in [32, TT_TB_MAX] that
 // keeps a tile's expected candidates (n keys spread over nb blocks) at or
-// below half of TT_CAP; partitioned in one pass up to 256 tiles and in two
-// above (at most 256 high bins).
-static TtGeom tt_geom(uint64_t nb, uint64_t n)
+// below `target` (at most half of TT_CAP, so that a tile's records fit its
+// shared-memory stage with room for the spread); partitioned in one pass up
+// to 256 tiles and in two above (at most 256 high bins).
+static TtGeom tt_geom(uint64_t nb, uint64_t n, uint32_t target)
 {
     TtGeom g;
     g.nb = nb;
     uint32_t tl = 5;
-    while ((1u << (tl + 1)) <= TT_TB_MAX && (n << (tl + 1)) <= (uint64_t)(TT_CAP / 2) * nb) tl++;
+    while ((1u << (tl + 1)) <= TT_TB_MAX && (n << (tl + 1)) <= (uint64_t)target * nb) tl++;
     g.tb_log = tl;
     g.nt = (nb + (1ull << tl) - 1) >> tl;
     uint32_t lg = 0;
@@ -1823,7 +2113,7 @@ static void tcf_tiled_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n,
     const TcfGeom G = T.G;
     DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
-    const TtGeom tg = tt_geom(G.nb, n);
+    const TtGeom tg = tt_geom(G.nb, n, T.tile_target);
     const uint64_t *gr;
     const uint32_t *gi;
     uint64_t *sp;
@@ -1851,7 +2141,7 @@ static void tcf_tiled_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n,
     const TcfGeom G = T.G;
     DevCounters *ctr = T.ctr;
     unsigned *np = ctr->pend;
-    const TtGeom tg = tt_geom(G.nb, n);
+    const TtGeom tg = tt_geom(G.nb, n, T.tile_target);
     const uint64_t *gr;
     const uint32_t *gi;
     uint64_t *sp;
@@ -1883,9 +2173,11 @@ int tcf_insert(filter *F, const uint64_t *keys, const uint8_t *vals, uint64_t n,
             else tcf_point_insert<8><<<g, TPB, 0, st>>>(keys, vals, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr, vals}, F->cfg.max_batch);
-        if (T.G.f == 16) tcf_tiled_insert<16>(W, keys, n, status, st);
-        else tcf_tiled_insert<8>(W, keys, n, status, st);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr, vals}, F->cfg.max_batch,
+                                   F->tune);
+        const bool tiled = tcf_tiled(F->tune, T.G.nb, n);
+        if (T.G.f == 16) tiled ? tcf_tiled_insert<16>(W, keys, n, status, st) : tcf_bulk_insert<16>(W, keys, n, status, st);
+        else tiled ? tcf_tiled_insert<8>(W, keys, n, status, st) : tcf_bulk_insert<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -1904,9 +2196,10 @@ int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
             else tcf_point_remove<8><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, status, F->ctr);
         }
     } else {
-        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr}, F->cfg.max_batch);
-        if (T.G.f == 16) tcf_tiled_remove<16>(W, keys, n, status, st);
-        else tcf_tiled_remove<8>(W, keys, n, status, st);
+        const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr}, F->cfg.max_batch, F->tune);
+        const bool tiled = tcf_tiled(F->tune, T.G.nb, n);
+        if (T.G.f == 16) tiled ? tcf_tiled_remove<16>(W, keys, n, status, st) : tcf_bulk_remove<16>(W, keys, n, status, st);
+        else tiled ? tcf_tiled_remove<8>(W, keys, n, status, st) : tcf_bulk_remove<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
@@ -2177,13 +2470,14 @@ int tcf_group_op(filter_group *GR, int op, const uint64_t *off, const uint64_t *
         gf::TraceScope ts_("tcf_group_prep", n, st);
         tcf_group_prep<<<grid_for(n, TPB, 8), TPB, 0, st>>>(keys, n, off, GR->n, GR->d_tmem, T.G.f, GR->prep);
     }
-    const TcfBulk W = bulk_of(T, GR->scan_tmp, GR->ctr, GR->prep, GR->max_total);
+    const TcfBulk W = bulk_of(T, GR->scan_tmp, GR->ctr, GR->prep, GR->max_total, GR->tune);
+    const bool tiled = tcf_tiled(GR->tune, T.G.nb, n);
     if (op == GROUP_INSERT) {
-        if (T.G.f == 16) tcf_tiled_insert<16>(W, nullptr, n, out, st);
-        else tcf_tiled_insert<8>(W, nullptr, n, out, st);
+        if (T.G.f == 16) tiled ? tcf_tiled_insert<16>(W, nullptr, n, out, st) : tcf_bulk_insert<16>(W, nullptr, n, out, st);
+        else tiled ? tcf_tiled_insert<8>(W, nullptr, n, out, st) : tcf_bulk_insert<8>(W, nullptr, n, out, st);
     } else {
-        if (T.G.f == 16) tcf_tiled_remove<16>(W, nullptr, n, out, st);
-        else tcf_tiled_remove<8>(W, nullptr, n, out, st);
+        if (T.G.f == 16) tiled ? tcf_tiled_remove<16>(W, nullptr, n, out, st) : tcf_bulk_remove<16>(W, nullptr, n, out, st);
+        else tiled ? tcf_tiled_remove<8>(W, nullptr, n, out, st) : tcf_bulk_remove<8>(W, nullptr, n, out, st);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
