@@ -40,6 +40,8 @@ static constexpr int QPT = 8;           // quotients per thread
 static constexpr int TQ = MT * QPT;     // quotients per tile
 static constexpr int TBLK = TQ / 64;    // blocks per tile
 static constexpr int OLDBUF = 3072;     // staged old slots
+static constexpr int GSMALL = 640;      // staged new groups of a tile that has old runs
+static constexpr int MIXCAP = 512;      // listed quotients whose run has old and new groups
 static constexpr int OUTBUF = 3072;     // staged new slots
 static constexpr int MERGE_CTAS = 5;    // resident merge CTAs per SM
 static constexpr int RWORDS = OUTBUF / 64 + 2;
@@ -116,19 +118,41 @@ template <int R>
 struct MergeSmem {
     unsigned long long occ[TBLK];
     unsigned int kpre[MT + 1];      // old runs before each thread's 8 quotients
-    int oend[TQ];                   // old run ends relative to Q0
     unsigned int Lq[TQ];            // new run length per quotient
     unsigned int qfirst[TQ];        // first new group of each quotient (or ~0)
     int qstart[TQ];                 // new run start relative to Q0
+    // oend, old and gsm are adjacent: a tile without old runs stages its new
+    // groups over all three
+    int oend[TQ];                   // old run ends relative to Q0
     typename SlotIO<R>::T old[OLDBUF];
+    unsigned int gsm[GSMALL];       // new groups, packed (qoff << 21 | rem << 5 | min(count, 31))
     typename SlotIO<R>::T out[OUTBUF];
     unsigned long long rend[RWORDS];
+    unsigned short mix[MIXCAP];     // quotients (from Q0) with mixed runs, merged by all threads
     unsigned char newocc[MT];
     long long wA[MT / 32], wB[MT / 32];
     long long prev_end_old, os0, ein, w0, w1, tileP;
     unsigned long long glo, ghi;
-    unsigned int tile, kold, oldlen, err;
+    unsigned int tile, kold, oldlen, err, gcap, nmix;
 };
+
+// staged groups: GSMALL of them, or (no old runs) as many as fill oend, old and gsm
+template <int R>
+__host__ __device__ constexpr unsigned gbig()
+{
+    return (unsigned)((sizeof(int) * TQ + sizeof(typename SlotIO<R>::T) * OLDBUF) / 4 + GSMALL);
+}
+static_assert(offsetof(MergeSmem<8>, old) == offsetof(MergeSmem<8>, oend) + 4 * TQ &&
+                  offsetof(MergeSmem<8>, gsm) == offsetof(MergeSmem<8>, old) + OLDBUF &&
+                  offsetof(MergeSmem<16>, old) == offsetof(MergeSmem<16>, oend) + 4 * TQ &&
+                  offsetof(MergeSmem<16>, gsm) == offsetof(MergeSmem<16>, old) + 2 * OLDBUF,
+              "the group stage spans oend, old and gsm without gaps");
+
+template <int R>
+__device__ __forceinline__ const unsigned *gstage(const MergeSmem<R> &S)
+{
+    return S.gcap > GSMALL ? reinterpret_cast<const unsigned *>(S.oend) : S.gsm;
+}
 
 static_assert(offsetof(MergeSmem<8>, out) % 4 == 0 && offsetof(MergeSmem<16>, out) % 4 == 0 &&
                   OUTBUF % 4 == 0,
@@ -148,11 +172,21 @@ __device__ __forceinline__ void decode_group(const MergeArgs &a, long long Q0, u
 
 static constexpr int GB = 4;  // groups a thread loads before using them
 
-// new group g: quotient offset from Q0, remainder and batch count
+// new group g: quotient offset from Q0, remainder and batch count (from the
+// tile's stage when it holds g)
 template <int R>
-__device__ __forceinline__ void new_group(const MergeSmem<R> &, const MergeArgs &a, long long Q0, uint32_t g,
+__device__ __forceinline__ void new_group(const MergeSmem<R> &S, const MergeArgs &a, long long Q0, uint32_t g,
                                           uint32_t &qoff, uint32_t &rem, uint64_t &cnt)
 {
+    const uint64_t i = (uint64_t)g - S.glo;
+    if (i < S.gcap) {
+        const unsigned e = gstage<R>(S)[i];
+        qoff = e >> 21;
+        rem = (e >> 5) & 0xffffu;
+        cnt = e & 31u;
+        if (cnt == 31u) cnt = a.ustart[g + 1] - a.ustart[g];
+        return;
+    }
     const uint64_t f = a.ufp[g] & a.fmask;
     qoff = (uint32_t)((long long)(f >> R) - Q0);
     rem = (uint32_t)(f & ((1ull << R) - 1ull));
@@ -268,6 +302,30 @@ __device__ __forceinline__ uint32_t merge_run(MergeSmem<R> &S, const MergeArgs &
     return len;
 }
 
+// The run of tile quotient y that has both old and new groups: its encoded
+// length (WRITE = false) or its slots written from `start` (WRITE = true).
+template <int R, bool WRITE>
+__device__ __forceinline__ uint32_t mixed_run(MergeSmem<R> &S, const MergeArgs &a, long long Q0, int y,
+                                              long long start)
+{
+    const unsigned byte = (unsigned)(S.occ[y >> 6] >> ((y & 56))) & 0xffu;
+    const unsigned k = S.kpre[y >> 3] + __popc(byte & ((1u << (y & 7)) - 1u));
+    const long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
+    OldRun o;
+    o.e = Q0 + S.oend[k];
+    o.p = (Q0 + y) > pe + 1 ? (Q0 + y) : pe + 1;
+    const uint32_t gf = S.qfirst[y];
+    uint32_t ge = gf;
+    while (ge < S.ghi) {
+        uint32_t qo, rm;
+        uint64_t cn;
+        new_group<R>(S, a, Q0, ge, qo, rm, cn);
+        if ((int)qo != y) break;
+        ge++;
+    }
+    return merge_run<R, WRITE>(S, a, o, true, gf, ge, start, Q0);
+}
+
 __device__ __forceinline__ unsigned long long ld_vol(const unsigned long long *p)
 {
     return *(const volatile unsigned long long *)p;
@@ -312,42 +370,56 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
     }
     __syncthreads();
     const uint32_t kold = S.kold;
+    // the group stage (read by later phases, after further barriers)
+    const uint32_t gcap = kold == 0 ? gbig<R>() : GSMALL;
+    if (tid == 0) S.gcap = gcap;
+    unsigned *gst = kold == 0 ? reinterpret_cast<unsigned *>(S.oend) : S.gsm;
 
-    // 3. old run ends (warp 0): select over runends after the offset of block j0
-    if (warp == 0 && kold > 0) {
-        const Meta &m0 = a.meta_old[j0];
-        const long long base = Q0 + (long long)m0.off;
+    // 3. old run ends: select over runends after the offset of block j0, the
+    // whole CTA at once (each thread takes 16 bits of one of 64 words a round)
+    __shared__ unsigned int selw[MT / 32];
+    if (kold > 0) {
+        const long long base = Q0 + (long long)a.meta_old[j0].off;
         const bool q0occ = (S.occ[0] & 1ull) != 0;
-        long long sp = q0occ ? base : base + 1;
+        const long long sp = q0occ ? base : base + 1;
+        const unsigned quarter = tid & 3;
         uint32_t found = 0;
-        long long w = sp >> 6;
-        bool first = true;
-        while (found < kold) {
-            long long ww = w + lane;
+        for (long long w0 = sp >> 6; found < kold; w0 += MT / 4) {
+            const long long ww = w0 + (tid >> 2);
             unsigned long long bits = (ww < (long long)a.nblk) ? a.meta_old[ww].rend : 0ull;
-            if (first && lane == 0) bits &= (~0ull) << (sp & 63);
-            uint32_t c = __popcll(bits), incl = c;
+            if (ww == (sp >> 6)) bits &= (~0ull) << (sp & 63);
+            uint32_t b16 = (uint32_t)(bits >> (16 * quarter)) & 0xffffu;
+            const uint32_t c = __popc(b16);
+            uint32_t incl = c;
             for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            uint32_t idx = found + incl - c;
-            while (bits && idx < kold) {
-                int b = __ffsll((long long)bits) - 1;
-                S.oend[idx] = (int)(ww * 64 + b - Q0);
-                bits &= bits - 1;
+            if (lane == 31) selw[warp] = incl;
+            __syncthreads();
+            uint32_t pre = 0, tot = 0;
+#pragma unroll
+            for (int v = 0; v < MT / 32; v++) {
+                const uint32_t x = selw[v];
+                pre += v < warp ? x : 0u;
+                tot += x;
+            }
+            uint32_t idx = found + pre + incl - c;
+            while (b16 && idx < kold) {
+                const int b = __ffs(b16) - 1;
+                S.oend[idx] = (int)(ww * 64 + 16 * quarter + b - Q0);
+                b16 &= b16 - 1;
                 idx++;
             }
-            found += __shfl_sync(0xffffffffu, incl, 31);
-            w += 32;
-            first = false;
-            if (w >= (long long)a.nblk + 32) {
-                if (lane == 0) S.err = 1;
+            found += tot;
+            __syncthreads();  // selw is rewritten by the next round
+            if (found < kold && w0 + MT / 4 >= (long long)a.nblk) {  // the same decision in every thread
+                if (tid == 0) S.err = 1;
                 break;
             }
         }
         // end of the run before the tile's first run
-        if (lane == 0) {
+        if (tid == 0) {
             long long pe;
             if (q0occ) {
                 // last runend in [Q0, base - 1]; Q0 is a multiple of 64
@@ -396,6 +468,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
                 uint32_t qo, rm;
                 uint64_t cn;
                 decode_group<R>(a, Q0, fv[u], s0[u], s1[u], qo, rm, cn);
+                if (g - S.glo < gcap) gst[g - S.glo] = (qo << 21) | (rm << 5) | (unsigned)(cn < 31 ? cn : 31);
                 atomicMin(&S.qfirst[qo], (unsigned)g);
                 if (!a.del) {
                     atomicAdd(&S.Lq[qo], enc_len(cn, R));
@@ -416,6 +489,7 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
     } else {
     if (tid == 0) {
         // 5. staged window of the old runs
+        S.nmix = 0;
         if (kold > 0 && S.err == 0) {
             long long yfirst = -1;
             for (int w = 0; w < TBLK && yfirst < 0; w++)
@@ -431,7 +505,22 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
         }
     }
     __syncthreads();
-    for (unsigned p = tid; p < S.oldlen; p += MT) S.old[p] = (typename SlotIO<R>::T)rd_slot<R>(a.rem_old, (uint64_t)(S.os0 + p));
+    {
+        constexpr int OPT = (OLDBUF + MT - 1) / MT;
+        const unsigned len = S.oldlen;
+        const long long os0 = S.os0;
+        uint32_t v[OPT];
+#pragma unroll
+        for (int u = 0; u < OPT; u++) {
+            const unsigned p = tid + u * MT;
+            if (p < len) v[u] = rd_slot<R>(a.rem_old, (uint64_t)(os0 + p));
+        }
+#pragma unroll
+        for (int u = 0; u < OPT; u++) {
+            const unsigned p = tid + u * MT;
+            if (p < len) S.old[p] = (typename SlotIO<R>::T)v[u];
+        }
+    }
     __syncthreads();
 
     // 6. run length of every quotient: copy length for old-only runs, the summed
@@ -454,15 +543,19 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
         if (!hn) {
             S.Lq[y] = (unsigned)(o.e - o.p + 1);
         } else {
-            uint32_t ge = gf;
-            while (ge < S.ghi) {
-                uint32_t qo, rm;
-                uint64_t cn;
-                new_group<R>(S, a, Q0, ge, qo, rm, cn);
-                if ((int)qo != y) break;
-                ge++;
-            }
-            S.Lq[y] = merge_run<R, false>(S, a, o, true, gf, ge, 0, Q0);
+            // mixed runs are few and long to merge: listed, so that whole
+            // warps take them together below (inline once the list is full)
+            const unsigned slot = atomicAdd(&S.nmix, 1u);
+            if (slot < MIXCAP) S.mix[slot] = (unsigned short)y;
+            else S.Lq[y] = mixed_run<R, false>(S, a, Q0, y, 0);
+        }
+    }
+    __syncthreads();
+    {
+        const unsigned nm = S.nmix < MIXCAP ? S.nmix : MIXCAP;
+        for (unsigned i = tid; i < nm; i += MT) {
+            const int y = S.mix[i];
+            S.Lq[y] = mixed_run<R, false>(S, a, Q0, y, 0);
         }
     }
     }  // kold > 0
@@ -669,64 +762,71 @@ __device__ __forceinline__ void merge_tile(const MergeArgs &a, MergeSmem<R> &S, 
 
     // 10. write the runs: old-only runs are copied, mixed runs merged, and the
     // groups of new-only runs encoded by one thread each
-    for (int y = tid; kold > 0 && y < TQ; y += MT) {
+    const bool listed = kold > 0 && S.nmix <= MIXCAP;  // every mixed run is in the list
+    // old-only runs are copied by whole warps: a warp's 32 quotients lay
+    // their runs end to end (a scan of their lengths) and every lane copies
+    // every 32nd slot of the concatenation
+    for (int y = tid; kold > 0 && y < TQ; y += MT) {  // (y - tid is the same for the whole CTA)
         const unsigned L = S.Lq[y];
-        if (!L) continue;
-        const bool ho = old_ok && ((S.occ[y >> 6] >> (y & 63)) & 1ull);
-        if (!ho) continue;
+        const bool ho = L && old_ok && ((S.occ[y >> 6] >> (y & 63)) & 1ull);
         const unsigned gf = S.qfirst[y];
-        const unsigned byte = (unsigned)(S.occ[y >> 6] >> ((y & 56))) & 0xffu;
-        const unsigned k = S.kpre[y >> 3] + __popc(byte & ((1u << (y & 7)) - 1u));
-        const long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
-        OldRun o;
-        o.e = Q0 + S.oend[k];
-        o.p = (Q0 + y) > pe + 1 ? (Q0 + y) : pe + 1;
         const long long start = Q0 + S.qstart[y];
-        if (gf == NONE) {
-            for (long long p = 0; p < (long long)L; p++) put_slot<R>(S, a, start + p, old_at<R>(S, a, o.p + p));
-        } else {
-            uint32_t ge = gf;
-            while (ge < S.ghi) {
-                uint32_t qo, rm;
-                uint64_t cn;
-                new_group<R>(S, a, Q0, ge, qo, rm, cn);
-                if ((int)qo != y) break;
-                ge++;
+        unsigned cl = 0;  // slots this lane's quotient copies
+        long long op = 0;
+        if (ho && gf == NONE) {
+            const unsigned byte = (unsigned)(S.occ[y >> 6] >> ((y & 56))) & 0xffu;
+            const unsigned k = S.kpre[y >> 3] + __popc(byte & ((1u << (y & 7)) - 1u));
+            const long long pe = (k == 0) ? S.prev_end_old : (Q0 + S.oend[k - 1]);
+            op = (Q0 + y) > pe + 1 ? (Q0 + y) : pe + 1;
+            cl = L;
+        } else if (ho && !listed) {
+            mixed_run<R, true>(S, a, Q0, y, start);
+        }
+        unsigned incl = cl;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const unsigned excl = incl - cl;
+        const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+        for (unsigned b0 = 0; b0 < total; b0 += 32) {
+            const unsigned i = b0 + lane;
+            // the last lane whose run starts at or before slot i of the concatenation
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step; step >>= 1) {
+                const unsigned e = __shfl_sync(0xffffffffu, excl, (j + step) & 31);
+                if (j + step < 32 && e <= i) j += step;
             }
-            merge_run<R, true>(S, a, o, true, gf, ge, start, Q0);
+            const unsigned ej = __shfl_sync(0xffffffffu, excl, j);
+            const long long sj = __shfl_sync(0xffffffffu, op, j);
+            const long long dj = __shfl_sync(0xffffffffu, start, j);
+            if (i < total) put_slot<R>(S, a, dj + (i - ej), old_at<R>(S, a, sj + (i - ej)));
+        }
+    }
+    if (listed) {
+        for (unsigned i = tid; i < S.nmix; i += MT) {
+            const int y = S.mix[i];
+            if (S.Lq[y]) mixed_run<R, true>(S, a, Q0, y, Q0 + S.qstart[y]);
         }
     }
     if (!a.del) {
-        for (uint64_t g0 = S.glo + tid; g0 < S.ghi; g0 += GB * MT) {
-            uint64_t fv[GB];
-            uint32_t s0[GB], s1[GB];
-#pragma unroll
-            for (int u = 0; u < GB; u++) {
-                const uint64_t g = g0 + (uint64_t)u * MT;
-                if (g < S.ghi) {
-                    fv[u] = a.ufp[g];
-                    s0[u] = a.ustart[g];
-                    s1[u] = a.ustart[g + 1];
-                }
+        // groups of new-only runs, one thread each, from the stage where it
+        // holds them
+        for (uint64_t g = S.glo + tid; g < S.ghi; g += MT) {
+            uint32_t qo, rm;
+            uint64_t cn;
+            new_group<R>(S, a, Q0, (uint32_t)g, qo, rm, cn);
+            const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
+            if (ho) continue;  // written by the merge above
+            long long pos = Q0 + S.qstart[qo];
+            for (uint32_t h = S.qfirst[qo]; h < (uint32_t)g; h++) {
+                uint32_t q2, r2;
+                uint64_t c2;
+                new_group<R>(S, a, Q0, h, q2, r2, c2);
+                pos += enc_len(c2, R);
             }
-#pragma unroll
-            for (int u = 0; u < GB; u++) {
-                const uint64_t g = g0 + (uint64_t)u * MT;
-                if (g >= S.ghi) continue;
-                uint32_t qo, rm;
-                uint64_t cn;
-                decode_group<R>(a, Q0, fv[u], s0[u], s1[u], qo, rm, cn);
-                const bool ho = old_ok && ((S.occ[qo >> 6] >> (qo & 63)) & 1ull);
-                if (ho) continue;  // written by the merge above
-                long long pos = Q0 + S.qstart[qo];
-                for (uint32_t h = S.qfirst[qo]; h < (uint32_t)g; h++) {
-                    uint32_t q2, r2;
-                    uint64_t c2;
-                    new_group<R>(S, a, Q0, h, q2, r2, c2);
-                    pos += enc_len(c2, R);
-                }
-                put_group<R>(S, a, pos, rm, cn);
-            }
+            put_group<R>(S, a, pos, rm, cn);
         }
     }
     __syncthreads();
@@ -832,8 +932,8 @@ static constexpr long long RQ_MIN = 256;     // quotients per delete region, sma
 static constexpr long long RQ_MAX = 1 << 16;
 // In-place batches are worth it only while each region thread has few groups
 // to apply one after another; past that the merge, whose cost does not grow
-// with the batch, is faster. Limit on the mean groups per region.
-static constexpr uint64_t GROUPS_PER_REGION = 8;
+// with the batch, is faster. The limit on the mean groups per region is a
+// tuning knob (gqf_region_groups, 8 by default).
 
 struct GView {
     Meta *meta;
