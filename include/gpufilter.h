@@ -72,13 +72,22 @@ typedef struct filter filter_t;
 typedef struct filter_config {
     uint32_t kind;        /* FILTER_TCF or FILTER_GQF */
     uint32_t log2_slots;  /* TCF: log2 of total tag slots; GQF: q */
-    uint32_t tag_bits;    /* TCF: slot bits f in {8, 16} (tag + value); GQF: r in {8, 16} */
+    uint32_t tag_bits;    /* TCF: slot bits f in {8, 12, 16} (tag + value; 12 only with
+                             block_slots geometry, see below); GQF: r in {8, 16} */
     uint32_t mode;        /* TCF: FILTER_MODE_BULK or FILTER_MODE_POINT; GQF: 0 */
     uint64_t hash_seed;   /* xor-ed into keys before hashing */
     uint64_t max_batch;   /* largest n of one call; sizes the scratch memory (GQF: < 2^30) */
     uint32_t value_bits;  /* TCF: v bits of each slot hold a value below an (f - v)-bit tag,
                              0 <= v <= min(f / 2, 7); 0 = no values. GQF, groups: 0 */
-    uint32_t reserved;    /* 0 */
+    uint32_t block_slots; /* TCF: slots per block B; 0 = 256 / f (one 32-byte sector, 21 for
+                             f = 12). Other block sizes (paper Sec. 4.1 blocks up to and past a
+                             cache line, Sec. 4.2 128-slot bulk blocks): (f, B) in (16, 8),
+                             (16, 32), (16, 64), (16, 128), (12, 21), (8, 64), bulk mode only,
+                             no values, not in groups or the device view. The B slots of a
+                             block are packed little-endian (slot s at bit f s) into the
+                             smallest whole number of 32-byte sectors; the filter has nb
+                             blocks, nb the largest power of two with nb B <= 2^log2_slots.
+                             GQF: 0 */
 } filter_config;
 
 typedef struct filter_stats {

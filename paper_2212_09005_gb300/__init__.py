@@ -59,7 +59,7 @@ OP_INSERT, OP_QUERY, OP_REMOVE, OP_COUNT = 0, 1, 2, 3
 class FilterConfig(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("log2_slots", C.c_uint32), ("tag_bits", C.c_uint32),
                 ("mode", C.c_uint32), ("hash_seed", C.c_uint64), ("max_batch", C.c_uint64),
-                ("value_bits", C.c_uint32), ("reserved", C.c_uint32)]
+                ("value_bits", C.c_uint32), ("block_slots", C.c_uint32)]
 
 
 class FilterStats(C.Structure):
@@ -204,9 +204,9 @@ class Filter:
     """One filter on the current CUDA device."""
 
     def __init__(self, kind: int, log2_slots: int, tag_bits: int, mode: int = MODE_BULK,
-                 seed: int = 0, max_batch: int = 1 << 22, stream=None, value_bits: int = 0):
+                 seed: int = 0, max_batch: int = 1 << 22, stream=None, value_bits: int = 0, block_slots: int = 0):
         self.cfg = FilterConfig(kind, log2_slots, tag_bits, mode, seed & 0xFFFFFFFFFFFFFFFF,
-                                max(1, int(max_batch)), value_bits, 0)
+                                max(1, int(max_batch)), value_bits, int(block_slots))
         h = C.c_void_p()
         _check(lib().filter_create(C.byref(self.cfg), _stream(stream), C.byref(h)), "filter_create")
         self._h = h
@@ -322,8 +322,11 @@ class Filter:
 
 
 def TCF(log2_slots: int, tag_bits: int = 16, mode: int = MODE_BULK, seed: int = 0,
-        max_batch: int = 1 << 22, stream=None, value_bits: int = 0) -> Filter:
-    return Filter(FILTER_TCF, log2_slots, tag_bits, mode, seed, max_batch, stream, value_bits)
+        max_batch: int = 1 << 22, stream=None, value_bits: int = 0, block_slots: int = 0) -> Filter:
+    """block_slots: slots per block (0: one 32-byte sector); other sizes are
+    packed bulk-mode geometries with nb the largest power of two such that
+    nb * block_slots <= 2^log2_slots."""
+    return Filter(FILTER_TCF, log2_slots, tag_bits, mode, seed, max_batch, stream, value_bits, block_slots)
 
 
 def GQF(q: int, r: int = 8, seed: int = 0, max_batch: int = 1 << 22, stream=None) -> Filter:

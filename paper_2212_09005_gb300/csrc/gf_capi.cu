@@ -204,6 +204,7 @@ int filter_get_device_view(filter_t *f, filter_device_view *out)
     static_assert(offsetof(gf::DevCounters, status) == 0 && offsetof(gf::DevCounters, failed) == 8 &&
                       offsetof(gf::DevCounters, backing) == 16,
                   "the device view exposes the first three counters");
+    if (f->cfg.kind == FILTER_TCF && gf::tcf_custom(f->tcf.G)) return FILTER_ERR_UNSUPPORTED;  // 32-byte blocks only
     out->kind = f->cfg.kind;
     out->tag_bits = f->cfg.tag_bits;
     out->seed = f->cfg.hash_seed;

@@ -1700,7 +1700,7 @@ uint64_t gqf_tile_lo_words(const GqfState &Q)
 int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only)
 {
     const filter_config &c = F->cfg;
-    if (c.tag_bits != 8 && c.tag_bits != 16) return FILTER_ERR_ARG;
+    if ((c.tag_bits != 8 && c.tag_bits != 16) || c.block_slots) return FILTER_ERR_ARG;
     if (c.value_bits != 0) return FILTER_ERR_ARG;  // values ride on the counters
     if (c.log2_slots < 6 || c.log2_slots > 36 || c.log2_slots + c.tag_bits > 64) return FILTER_ERR_ARG;
     GqfState &Q = F->gqf;
@@ -2296,7 +2296,7 @@ int gqf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     uint64_t nblk_tot = 0, nslots_tot = 0, tiles = 0, ts_words = 2, tlo_words = 1;
     uint32_t pbits = 0;
     for (uint32_t m = 0; m < n; m++) {
-        if (cfgs[m].kind != FILTER_GQF || cfgs[m].tag_bits != r) return FILTER_ERR_ARG;
+        if (cfgs[m].kind != FILTER_GQF || cfgs[m].tag_bits != r || cfgs[m].block_slots) return FILTER_ERR_ARG;
         V[m].cfg = cfgs[m];
         V[m].cfg.max_batch = M;
         uint64_t tb = 0, sb = 0;

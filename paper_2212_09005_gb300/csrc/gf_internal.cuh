@@ -95,12 +95,16 @@ struct TcfGeom {
     uint64_t nb;      // blocks (power of two)
     uint64_t nbk;     // backing buckets
     uint64_t seed;
-    uint32_t f, B;    // slot bits, slots per 32-byte block
+    uint32_t f, B;    // slot bits, slots per block
+    uint32_t bbytes = 32;  // bytes per block (whole 32-byte sectors)
     uint32_t tsc;     // shortcut threshold 3B/4
     uint32_t tmask;   // the tag: f - vbits bits
     uint32_t vbits = 0;  // value bits below the tag in each slot
     uint32_t vmask = 0;  // (1 << vbits) - 1
 };
+
+// a block geometry other than one 32-byte sector of 8- or 16-bit slots
+__host__ __device__ __forceinline__ bool tcf_custom(const TcfGeom &G) { return G.f == 12 || G.B * G.f != 256; }
 
 // t is the key's slot with value 0: the tag shifted above the value bits
 struct KeyInfo {
@@ -442,6 +446,7 @@ namespace gf {
 bool tuning_valid(const filter_tuning &t);
 // TCF bulk calls: the tiled path for this table and batch?
 bool tcf_tiled(const filter_tuning &t, uint64_t nb, uint64_t n);
+bool tcf_geom_supported(uint32_t f, uint32_t B);
 uint32_t tcf_tile_target(const filter_tuning &t);
 uint64_t gqf_region_groups(const filter_tuning &t);
 int tcf_group_setup(filter_group *G, const filter_config *cfgs, uint64_t &bytes, bool plan_only);

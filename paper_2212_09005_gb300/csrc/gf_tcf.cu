@@ -33,6 +33,7 @@
 #include <vector>
 
 #include "gf_internal.cuh"
+#include "gf_packed.cuh"
 
 namespace gf {
 
@@ -1786,22 +1787,28 @@ __global__ void tcf_count_backing(TcfGeom G, const uint64_t *bk, DevCounters *ct
 int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool plan_only)
 {
     const filter_config &c = F->cfg;
-    if (c.tag_bits != 8 && c.tag_bits != 16) return FILTER_ERR_ARG;
+    if (c.tag_bits != 8 && c.tag_bits != 12 && c.tag_bits != 16) return FILTER_ERR_ARG;
     if (c.value_bits > c.tag_bits / 2 || c.value_bits > 7) return FILTER_ERR_ARG;
     if (c.mode != FILTER_MODE_BULK && c.mode != FILTER_MODE_POINT) return FILTER_ERR_ARG;
-    const uint32_t B = 256 / c.tag_bits, lb = (B == 16) ? 4 : 5;
-    if (c.log2_slots < lb + 1 || c.log2_slots > lb + 32) return FILTER_ERR_ARG;
+    const uint32_t B = c.block_slots ? c.block_slots : 256 / c.tag_bits;
     TcfState &T = F->tcf;
-    T.mode = c.mode;
     T.G.f = c.tag_bits;
     T.G.B = B;
+    if (tcf_custom(T.G) && (!tcf_geom_supported(c.tag_bits, B) || c.mode != FILTER_MODE_BULK || c.value_bits))
+        return FILTER_ERR_ARG;
+    // nb: the largest power of two with nb B <= 2^log2_slots
+    uint32_t lb = 0;
+    while ((1ull << lb) < B) lb++;  // ceil(log2 B)
+    if (c.log2_slots < lb + 1 || c.log2_slots > lb + 32) return FILTER_ERR_ARG;
+    T.mode = c.mode;
+    T.G.bbytes = (c.tag_bits * B + 255) / 256 * 32;
     T.G.tsc = 3 * B / 4;
     T.G.tmask = (1u << (c.tag_bits - c.value_bits)) - 1u;
     T.G.vbits = c.value_bits;
     T.G.vmask = (1u << c.value_bits) - 1u;
     T.G.nb = 1ull << (c.log2_slots - lb);
     T.G.seed = c.hash_seed;
-    const uint64_t N = 1ull << c.log2_slots;
+    const uint64_t N = T.G.nb * B;
     uint64_t cap = (N + 99) / 100;
     T.G.nbk = (cap + BK_W - 1) / BK_W;
     if (T.G.nbk < 8) T.G.nbk = 8;
@@ -1818,7 +1825,7 @@ int tcf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
         bytes += b;
         if (!plan_only) ptr = A.take<T_>(count);
     };
-    piece(T.blocks, T.G.nb * 32);
+    piece(T.blocks, T.G.nb * T.G.bbytes);
     piece(T.bk, T.G.nbk * BK_W);
     piece(T.fill, T.G.nb);
     table_bytes = bytes;
@@ -1844,7 +1851,7 @@ int tcf_clear(filter *F, cudaStream_t st)
 {
     TcfState &T = F->tcf;
     const uint64_t groups = (T.G.nb > T.G.nbk ? T.G.nb : T.G.nbk) + 1;
-    GF_CUDA(cudaMemsetAsync(T.blocks, 0, T.G.nb * 32, st));
+    GF_CUDA(cudaMemsetAsync(T.blocks, 0, T.G.nb * T.G.bbytes, st));
     GF_CUDA(cudaMemsetAsync(T.bk, 0, T.G.nbk * BK_W * 8, st));
     GF_CUDA(cudaMemsetAsync(T.fill, 0, T.G.nb, st));
     GF_CUDA(cudaMemsetAsync(T.cnt, 0, groups * 4, st));
@@ -1957,11 +1964,206 @@ static int dst_grid(const PhaseDst &P, uint64_t n, uint64_t ndst)
     return grid_for(P.dlist ? (n < ndst ? n : ndst) : ndst, TPB, 8);
 }
 
+// ---------------------------------------------------------------------------
+// Other block geometries (Sec. 4.1: blocks sized up to a cache line and
+// beyond; Sec. 4.2: the bulk TCF's 128-slot blocks; Sec. 4: 12-bit tags that
+// straddle word boundaries). A block is B slots of F bits packed
+// little-endian into whole 32-byte sectors (gf_packed.cuh); the phases and
+// their grouping are the ones above, only the per-block steps and the query
+// read and write packed slots. One thread per block, as in the 32-byte path;
+// the per-block candidate and tag lists live in local memory.
+// ---------------------------------------------------------------------------
+template <int F, int B>
+struct GBlk : Packed<F, B> {
+    using Packed<F, B>::w;
+    static constexpr int WORDS = Packed<F, B>::WORDS;
+    static constexpr int BYTES = WORDS * 4;
+    static_assert(BYTES % 32 == 0, "whole sectors");
+
+    __device__ __forceinline__ void load(const uint8_t *blocks, uint64_t b, bool ro)
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(blocks + b * BYTES);
+#pragma unroll
+        for (int k = 0; k < WORDS / 4; k++) {
+            const uint4 v = ro ? __ldg(p + k) : p[k];
+            w[4 * k] = v.x;
+            w[4 * k + 1] = v.y;
+            w[4 * k + 2] = v.z;
+            w[4 * k + 3] = v.w;
+        }
+    }
+    __device__ __forceinline__ void store(uint8_t *blocks, uint64_t b) const
+    {
+        uint4 *p = reinterpret_cast<uint4 *>(blocks + b * BYTES);
+#pragma unroll
+        for (int k = 0; k < WORDS / 4; k++) p[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+    }
+    // some slot holds tag t (t >= 2; the bits past the last slot are 0)
+    __device__ __forceinline__ bool has(uint32_t t) const
+    {
+        if constexpr (F == 16 || F == 8) {
+            const uint32_t tt = F == 16 ? (t | (t << 16)) : t * 0x01010101u;
+            uint32_t m = 0;
+#pragma unroll
+            for (int k = 0; k < WORDS; k++) m |= F == 16 ? __vcmpeq2(w[k], tt) : __vcmpeq4(w[k], tt);
+            return m != 0;
+        } else {
+            for (int s = 0; s < B; s++)
+                if (this->get(s) == t) return true;
+            return false;
+        }
+    }
+};
+
+template <int F, int B>
+__global__ void __launch_bounds__(TPB) tcf_gblock_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
+                                                         const uint64_t *__restrict__ rec, int phase, uint32_t cap,
+                                                         uint32_t *pend32, uint64_t *pend64, unsigned *npend,
+                                                         unsigned long long *units)
+{
+    const uint64_t nd = phase_count(P, G.nb);
+    if (P.dlist) note_units(units, nd);  // units: blocks with candidates
+    const uint64_t stride = (uint64_t)gridDim.x * TPB;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
+        const uint64_t j = j0 + (threadIdx.x & 31);
+        uint32_t s = 0, e = 0, k = 0;
+        uint64_t b = 0, thr = 0;  // records <= thr are accepted
+        if (j < nd) {
+            b = phase_dst(P, j, s, e);
+            if (s != e) {
+                const uint32_t f0 = fill[b];
+                k = cap > f0 ? min(e - s, cap - f0) : 0u;
+                if (k > 0) {
+                    // the k smallest (tag, index) candidates, merged into the sorted block
+                    uint64_t a[B];
+                    int have = 0;
+                    for (uint32_t q = s; q < e; q++) have = topk_push(a, have, (int)k, rec[q]);
+                    thr = a[k - 1];
+                    uint32_t nv[B];
+                    for (uint32_t q = 0; q < k; q++) nv[q] = (uint32_t)(a[q] >> 32);
+                    GBlk<F, B> blk;
+                    blk.load(blocks, b, false);
+                    blk.merge_sorted((int)f0, nv, (int)k);
+                    blk.store(blocks, b);
+                    fill[b] = (uint8_t)(f0 + k);
+                }
+            }
+        }
+        const uint32_t nrej = (e - s) - k;
+        uint32_t slot = warp_reserve(npend, nrej);
+        if (nrej == 0) continue;
+        for (uint32_t q = s; q < e; q++) {
+            const uint64_t r = rec[q];
+            if (k > 0 && r <= thr) continue;
+            const uint32_t i = (uint32_t)r;
+            if (phase == 1) pend64[slot++] = ((b ^ tcf_g((uint32_t)(r >> 32), G.nb)) << 32) | i;  // the other block
+            else pend32[slot++] = i;
+        }
+    }
+}
+
+// per distinct stored tag, the smallest candidates with that tag remove one copy each
+template <int F, int B>
+__global__ void __launch_bounds__(TPB) tcf_gblock_remove(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
+                                                         const uint64_t *__restrict__ rec, uint32_t *pend32,
+                                                         unsigned *npend, unsigned long long *units)
+{
+    const uint64_t nd = phase_count(P, G.nb);
+    if (P.dlist) note_units(units, nd);
+    const uint64_t stride = (uint64_t)gridDim.x * TPB;
+    for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
+        const uint64_t j = j0 + (threadIdx.x & 31);
+        uint32_t s = 0, e = 0, removed = 0;
+        uint32_t dt[B], dc[B], used[B];
+        uint64_t thr[B];
+        int ndt = 0;
+        if (j < nd) {
+            const uint64_t b = phase_dst(P, j, s, e);
+            if (s != e) {
+                const uint32_t f0 = fill[b];
+                GBlk<F, B> blk;
+                blk.load(blocks, b, false);
+                for (int p = 0; p < (int)f0; p++) {  // copies of a tag are adjacent
+                    const uint32_t t = blk.get(p);
+                    if (ndt > 0 && dt[ndt - 1] == t) {
+                        dc[ndt - 1]++;
+                    } else {
+                        dt[ndt] = t;
+                        dc[ndt] = 1;
+                        ndt++;
+                    }
+                }
+                for (int d = 0; d < ndt; d++) {
+                    uint64_t a[B];
+                    int have = 0;
+                    const uint64_t lo = (uint64_t)dt[d] << 32, hi = lo | 0xffffffffull;
+                    for (uint32_t q = s; q < e; q++) {
+                        const uint64_t r = rec[q];
+                        if (r >= lo && r <= hi) have = topk_push(a, have, (int)dc[d], r);
+                    }
+                    used[d] = (uint32_t)have;
+                    thr[d] = have ? a[have - 1] : 0;
+                    removed += (uint32_t)have;
+                }
+                if (removed) {
+                    GBlk<F, B> out;
+                    out.clear();
+                    int o = 0;
+                    for (int d = 0; d < ndt; d++)
+                        for (uint32_t c = used[d]; c < dc[d]; c++) out.set(o++, dt[d]);
+                    out.store(blocks, b);
+                    fill[b] = (uint8_t)(f0 - removed);
+                }
+            }
+        }
+        const uint32_t nunm = (e - s) - removed;  // unmatched candidates go on
+        uint32_t slot = warp_reserve(npend, nunm);
+        if (nunm == 0) continue;
+        for (uint32_t q = s; q < e; q++) {
+            const uint64_t r = rec[q];
+            const uint32_t t = (uint32_t)(r >> 32);
+            bool matched = false;
+            for (int d = 0; d < ndt; d++)
+                if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
+            if (!matched) pend32[slot++] = (uint32_t)r;
+        }
+    }
+}
+
+template <int F, int B>
+__global__ void __launch_bounds__(TPB) tcf_gquery_kernel(const uint64_t *__restrict__ keys, uint64_t n, TcfGeom G,
+                                                         const uint8_t *__restrict__ blocks,
+                                                         const uint64_t *__restrict__ bk, const DevCounters *ctr,
+                                                         uint8_t *__restrict__ out)
+{
+    const bool backing = ctr->backing != 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)TPB + threadIdx.x; i < n; i += (uint64_t)gridDim.x * TPB) {
+        const KeyInfo k = tcf_keyinfo(__ldcs(keys + i), G);
+        GBlk<F, B> x;
+        x.load(blocks, k.b1, true);
+        bool hit = x.has(k.t);
+        if (!hit) {
+            x.load(blocks, k.b2, true);
+            hit = x.has(k.t);
+        }
+        if (!hit && backing) {
+            const uint64_t e = tcf_entry(k, G.f);
+            const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bk + tcf_bucket_of(e, G) * BK_W);
+#pragma unroll
+            for (int s = 0; s < 4; s++) {
+                const ulonglong2 v = __ldg(p + s);
+                hit |= (v.x == e) | (v.y == e);
+            }
+        }
+        __stcs(out + i, (uint8_t)(hit ? 1 : 0));
+    }
+}
+
 // The per-block counting-sort path: each phase groups its candidates by
 // destination block (counts, scan, scatter) and one thread per block takes
 // its step. Its scratch (a counter and an offset per block, a record per
 // candidate) stays in the L2 for moderate tables and batches.
-template <int F>
+template <int F, int GB = 0>  // GB: slots of a packed block of another geometry
 static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
 {
     const TcfGeom G = T.G;
@@ -1973,22 +2175,34 @@ static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_insert", 0, st, true);
-        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc, T.pend0,
-                                                                   nullptr, &np[0], T.prep, ts_.units());
+        if constexpr (GB == 0)
+            tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc, T.pend0,
+                                                                       nullptr, &np[0], T.prep, ts_.units());
+        else
+            tcf_gblock_insert<F, GB><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 0, G.tsc,
+                                                                           T.pend0, nullptr, &np[0], ts_.units());
     }
     // B: the less full of b1, b2 under the post-A fills
     P = group_phase<SRC_PEND_U32, DST_TARGET>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
-        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
-                                                                   T.pend1, &np[1], T.prep, ts_.units());
+        if constexpr (GB == 0)
+            tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B, nullptr,
+                                                                       T.pend1, &np[1], T.prep, ts_.units());
+        else
+            tcf_gblock_insert<F, GB><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 1, G.B,
+                                                                           nullptr, T.pend1, &np[1], ts_.units());
     }
     // C: the other block
     P = group_phase<SRC_PEND_U64, DST_ALT>(T, keys, n, T.pend1, &np[1], 2, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_insert_sparse", 0, st, true);
-        tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
-                                                                   nullptr, &np[2], T.prep, ts_.units());
+        if constexpr (GB == 0)
+            tcf_block_insert<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B, T.pend2,
+                                                                       nullptr, &np[2], T.prep, ts_.units());
+        else
+            tcf_gblock_insert<F, GB><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, 2, G.B,
+                                                                           T.pend2, nullptr, &np[2], ts_.units());
     }
     // D: backing buckets
     P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 3, T.pend0, st);
@@ -1998,7 +2212,7 @@ static void tcf_bulk_insert(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     }
 }
 
-template <int F>
+template <int F, int GB = 0>
 static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st)
 {
     const TcfGeom G = T.G;
@@ -2010,13 +2224,23 @@ static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     PhaseDst P = group_phase<SRC_KEYS, DST_B1>(T, keys, n, nullptr, nullptr, 0, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_remove", 0, st, true);
-        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0], ts_.units());
+        if constexpr (GB == 0)
+            tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0, &np[0],
+                                                                       ts_.units());
+        else
+            tcf_gblock_remove<F, GB><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend0,
+                                                                           &np[0], ts_.units());
     }
     // 2: secondary block
     P = group_phase<SRC_PEND_U32, DST_B2>(T, keys, n, T.pend0, &np[0], 1, nullptr, st);
     {
         gf::TraceScope ts_("tcf_block_remove_sparse", 0, st, true);
-        tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2], ts_.units());
+        if constexpr (GB == 0)
+            tcf_block_remove<F><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2, &np[2],
+                                                                       ts_.units());
+        else
+            tcf_gblock_remove<F, GB><<<dst_grid(P, n, G.nb), TPB, 0, st>>>(G, T.blocks, T.fill, P, T.rec, T.pend2,
+                                                                           &np[2], ts_.units());
     }
     // 3: backing bucket; what is left is not found
     P = group_phase<SRC_PEND_U32, DST_BUCKET>(T, keys, n, T.pend2, &np[2], 2, T.pend0, st);
@@ -2026,6 +2250,31 @@ static void tcf_bulk_remove(const TcfBulk &T, const uint64_t *keys, uint64_t n, 
     }
 }
 
+
+// the packed geometries (f, B) that have kernels
+#define GF_TCF_GEOMS(X) X(16, 8) X(16, 32) X(16, 64) X(16, 128) X(12, 21) X(8, 64)
+
+bool tcf_geom_supported(uint32_t f, uint32_t B)
+{
+#define GF_GEOM_IS(FF, BB) \
+    if (f == FF && B == BB) return true;
+    GF_TCF_GEOMS(GF_GEOM_IS)
+#undef GF_GEOM_IS
+    return false;
+}
+
+static void tcf_custom_bulk(const TcfBulk &W, const uint64_t *keys, uint64_t n, uint8_t *status, bool del,
+                            cudaStream_t st)
+{
+#define GF_GEOM_BULK(FF, BB)                                      \
+    if (W.G.f == FF && W.G.B == BB) {                             \
+        if (del) tcf_bulk_remove<FF, BB>(W, keys, n, status, st); \
+        else tcf_bulk_insert<FF, BB>(W, keys, n, status, st);     \
+        return;                                                   \
+    }
+    GF_TCF_GEOMS(GF_GEOM_BULK)
+#undef GF_GEOM_BULK
+}
 
 // ---------------------------------------------------------------------------
 // Tiled phases: host side
@@ -2175,8 +2424,9 @@ int tcf_insert(filter *F, const uint64_t *keys, const uint8_t *vals, uint64_t n,
     } else {
         const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr, vals}, F->cfg.max_batch,
                                    F->tune);
-        const bool tiled = tcf_tiled(F->tune, T.G.nb, n);
-        if (T.G.f == 16) tiled ? tcf_tiled_insert<16>(W, keys, n, status, st) : tcf_bulk_insert<16>(W, keys, n, status, st);
+        const bool tiled = !tcf_custom(T.G) && tcf_tiled(F->tune, T.G.nb, n);
+        if (tcf_custom(T.G)) tcf_custom_bulk(W, keys, n, status, false, st);
+        else if (T.G.f == 16) tiled ? tcf_tiled_insert<16>(W, keys, n, status, st) : tcf_bulk_insert<16>(W, keys, n, status, st);
         else tiled ? tcf_tiled_insert<8>(W, keys, n, status, st) : tcf_bulk_insert<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
@@ -2197,8 +2447,9 @@ int tcf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cud
         }
     } else {
         const TcfBulk W = bulk_of(T, F->scan_tmp, F->ctr, TcfPrep{nullptr, nullptr, nullptr, nullptr}, F->cfg.max_batch, F->tune);
-        const bool tiled = tcf_tiled(F->tune, T.G.nb, n);
-        if (T.G.f == 16) tiled ? tcf_tiled_remove<16>(W, keys, n, status, st) : tcf_bulk_remove<16>(W, keys, n, status, st);
+        const bool tiled = !tcf_custom(T.G) && tcf_tiled(F->tune, T.G.nb, n);
+        if (tcf_custom(T.G)) tcf_custom_bulk(W, keys, n, status, true, st);
+        else if (T.G.f == 16) tiled ? tcf_tiled_remove<16>(W, keys, n, status, st) : tcf_bulk_remove<16>(W, keys, n, status, st);
         else tiled ? tcf_tiled_remove<8>(W, keys, n, status, st) : tcf_bulk_remove<8>(W, keys, n, status, st);
     }
     GF_CUDA(cudaGetLastError());
@@ -2214,6 +2465,13 @@ int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, bool 
         gf::TraceScope ts_("tcf_query_values_kernel", n, st);
         if (T.G.f == 16) tcf_query_kernel<16, true><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
         else tcf_query_kernel<8, true><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+    } else if (tcf_custom(T.G)) {
+        gf::TraceScope ts_("tcf_gquery_kernel", n, st);
+#define GF_GEOM_QUERY(FF, BB)                                                                                   \
+    if (T.G.f == FF && T.G.B == BB) tcf_gquery_kernel<FF, BB><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, \
+                                                                                F->ctr, found);
+        GF_TCF_GEOMS(GF_GEOM_QUERY)
+#undef GF_GEOM_QUERY
     } else {
         gf::TraceScope ts_("tcf_query_kernel", n, st);
         if (T.G.f == 16) tcf_query_kernel<16, false><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
@@ -2223,13 +2481,13 @@ int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, bool 
     return FILTER_OK;
 }
 
-uint64_t tcf_image_bytes(const filter *F) { return F->tcf.G.nb * 32 + F->tcf.G.nbk * BK_W * 8; }
+uint64_t tcf_image_bytes(const filter *F) { return F->tcf.G.nb * F->tcf.G.bbytes + F->tcf.G.nbk * BK_W * 8; }
 
 int tcf_copy_image(filter *F, void *host, bool to_host, cudaStream_t st)
 {
     TcfState &T = F->tcf;
     char *h = static_cast<char *>(host);
-    const uint64_t nbB = T.G.nb * 32, bkB = T.G.nbk * BK_W * 8;
+    const uint64_t nbB = T.G.nb * T.G.bbytes, bkB = T.G.nbk * BK_W * 8;
     if (to_host) {
         GF_CUDA(cudaMemcpyAsync(h, T.blocks, nbB, cudaMemcpyDeviceToHost, st));
         GF_CUDA(cudaMemcpyAsync(h + nbB, T.bk, bkB, cudaMemcpyDeviceToHost, st));
@@ -2343,7 +2601,9 @@ int tcf_group_setup(filter_group *GR, const filter_config *cfgs, uint64_t &bytes
     uint64_t nb_tot = 0, nbk_tot = 0;
     for (uint32_t m = 0; m < n; m++) {
         const filter_config &c = cfgs[m];
-        if (c.kind != FILTER_TCF || c.tag_bits != f || c.mode != FILTER_MODE_BULK || c.value_bits) return FILTER_ERR_ARG;
+        if (c.kind != FILTER_TCF || c.tag_bits != f || c.mode != FILTER_MODE_BULK || c.value_bits || c.block_slots ||
+            (f != 8 && f != 16))
+            return FILTER_ERR_ARG;  // members: 32-byte blocks of 8- or 16-bit tags
         filter V;
         V.cfg = c;
         V.cfg.max_batch = M;
@@ -2441,7 +2701,7 @@ int tcf_group_clear(filter_group *GR, cudaStream_t st)
 {
     TcfState &T = GR->tcf;
     const uint64_t groups = (T.G.nb > T.G.nbk ? T.G.nb : T.G.nbk) + 1;
-    GF_CUDA(cudaMemsetAsync(T.blocks, 0, T.G.nb * 32, st));
+    GF_CUDA(cudaMemsetAsync(T.blocks, 0, T.G.nb * T.G.bbytes, st));
     GF_CUDA(cudaMemsetAsync(T.bk, 0, T.G.nbk * BK_W * 8, st));
     GF_CUDA(cudaMemsetAsync(T.fill, 0, T.G.nb, st));
     GF_CUDA(cudaMemsetAsync(T.cnt, 0, groups * 4, st));

@@ -67,6 +67,32 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
         gf.lib()
 
 
+def test_tcf_geometries_validated_without_gpu(libpath):
+    """Block geometries are checked before any device memory is taken: the
+    packed (f, B) pairs with kernels pass the check (and then fail only at the
+    allocation on a machine without a GPU), the others are refused."""
+    import paper_2212_09005_gb300 as gf
+
+    lib = gf.lib()
+    h = ctypes.c_void_p()
+
+    def create(lg, f, mode=gf.MODE_BULK, v=0, B=0):
+        return lib.filter_create(ctypes.byref(gf.FilterConfig(gf.FILTER_TCF, lg, f, mode, 1, 1, v, B)), None,
+                                 ctypes.byref(h))
+
+    ok_or_oom = (0, 2)
+    for f, B in ((16, 8), (16, 32), (16, 64), (16, 128), (12, 21), (12, 0), (8, 64), (16, 16), (8, 32), (16, 0)):
+        assert create(20, f, B=B) in ok_or_oom, (f, B)
+    for f, B in ((16, 48), (16, 256), (12, 32), (8, 8), (10, 0)):
+        assert create(20, f, B=B) == 1, (f, B)
+    assert create(20, 16, mode=gf.MODE_POINT, B=64) == 1  # packed blocks: bulk mode only
+    assert create(20, 12, mode=gf.MODE_POINT) == 1
+    assert create(20, 16, v=4, B=64) == 1                  # no values
+    assert create(7, 16, B=128) == 1                       # fewer than two blocks
+    assert lib.filter_create(ctypes.byref(gf.FilterConfig(gf.FILTER_GQF, 12, 8, 0, 1, 1, 0, 16)), None,
+                             ctypes.byref(h)) == 1
+
+
 def test_group_configurations_rejected_without_gpu(libpath):
     """Group creation validates the member list before touching the device."""
     import paper_2212_09005_gb300 as gf
@@ -86,6 +112,8 @@ def test_group_configurations_rejected_without_gpu(libpath):
     assert create([gf.FilterConfig(gf.FILTER_GQF, 40, 16, 0, 1, 1)]) == 1        # q + r beyond limits
     assert create([gf.FilterConfig(gf.FILTER_TCF, 12, 16, gf.MODE_BULK, 1, 1, 4)]) == 1  # members with values
     assert create([gf.FilterConfig(gf.FILTER_GQF, 12, 8, 0, 1, 1, 4)]) == 1      # GQF values: counters
+    assert create([gf.FilterConfig(gf.FILTER_TCF, 12, 16, gf.MODE_BULK, 1, 1, 0, 64)]) == 1  # packed geometry
+    assert create([gf.FilterConfig(gf.FILTER_TCF, 12, 12, gf.MODE_BULK, 1, 1)]) == 1  # 12-bit tags
     assert lib.filter_group_create(None, 0, 1, None, ctypes.byref(h)) == 1
     assert lib.filter_group_insert(None, None, None, 0, None, None) == 1
     assert lib.filter_group_destroy(None) == 0
