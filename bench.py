@@ -167,6 +167,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
     ap.add_argument("--no-target", action="store_true", help="skip the 2^28-slot, 90%%-load measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving-loop measurement")
+    ap.add_argument("--no-geometry", action="store_true", help="skip the TCF block-geometry sweep")
     ap.add_argument("--case", default="full", choices=["full", "profile", "target", "batched", "serving", "kmer", "values"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
@@ -501,6 +502,12 @@ def run_ours(args, rank, world, device_index):
         torch.cuda.empty_cache()
         serving = run_serving(args, device, log2_slots=20, bmax=20, workload=SERVING_SMALL)
 
+    geometry = None
+    if args.case == "full" and not args.no_geometry:
+        R = None
+        torch.cuda.empty_cache()
+        geometry = run_geometry(args, device)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.case == "full":
         cpu = cpu_sample(inp)
@@ -515,7 +522,7 @@ def run_ours(args, rank, world, device_index):
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
         "cpu_baseline": cpu, "random_gather": gather, "per_op": per_op, "kernels": kern, "checks": checks,
-        "target_2_28": target, "batched": batched, "serving": serving,
+        "target_2_28": target, "batched": batched, "serving": serving, "tcf_geometry": geometry,
     }
     return line
 
@@ -524,6 +531,59 @@ TARGET_WORKLOAD = ("target size, 2^28 slots at 90% load: TCF f=16 bulk, floor(0.
                    "batches, 2^24 pos + 2^24 neg queries, delete a random half in 2^24-key batches, re-query; GQF "
                    "r=8, as many uniform keys in one batch, count and query 2^24 inserted + 2^24 fresh keys, delete "
                    "2^24 distinct inserted keys, re-count")
+
+
+GEOMETRY_WORKLOAD = ("TCF block-geometry sweep (paper Sec. 4.1 block sizes, Sec. 4.2 128-slot blocks, 12-bit tags): "
+                     "per (tag bits, slots per block), a bulk TCF of 2^24 slots (nb the largest power of two with "
+                     "nb * B <= 2^24) filled to 90% with uniform keys in 2^21-key batches, 2^22 positive + 2^22 "
+                     "fresh queries, then a random half deleted in 2^21-key batches")
+GEOMETRIES = [(16, 16), (16, 8), (16, 32), (16, 64), (16, 128), (12, 21), (8, 32), (8, 64)]
+
+
+def run_geometry(args, device, log2_slots=24, batch=1 << 21, nq=1 << 22):
+    """Insert, query and delete rates per block geometry, with the measured
+    false-positive rate; one timed pass after one warm-up pass per geometry."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    keys = torch.from_numpy(W.uniform_keys(31, int(0.9 * (1 << log2_slots))).view(np.int64)).to(device)
+    neg = torch.from_numpy(W.uniform_keys(32, nq).view(np.int64)).to(device)
+    found = torch.zeros(nq, dtype=torch.uint8, device=device)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    rows = []
+    for f, B in GEOMETRIES:
+        F = gf.TCF(log2_slots, f, gf.MODE_BULK, seed=33, max_batch=batch, block_slots=0 if B * f == 256 and f != 12 else B)
+        n = min(int(0.9 * F.stats()["nslots"]), keys.numel())
+        ins = [keys[i:min(i + batch, n)] for i in range(0, n, batch)]
+        dels = [keys[i:min(i + batch, n // 2)] for i in range(0, n // 2, batch)]
+        pos = keys[: min(nq, n)]
+        for rep in range(2):  # warm-up, then the timed pass
+            F.clear()
+            t = [ev() for _ in range(5)]
+            t[0].record()
+            for k in ins:
+                F.insert(k)
+            t[1].record()
+            F.query(pos, found[: pos.numel()])
+            t[2].record()
+            F.query(neg, found)
+            t[3].record()
+            for k in dels:
+                F.remove(k)
+            t[4].record()
+            torch.cuda.synchronize()
+        fpr = float(found.float().mean().item())
+        ms = [t[i].elapsed_time(t[i + 1]) for i in range(4)]
+        st = F.stats()
+        rows.append({"tag_bits": f, "block_slots": B, "block_bytes": int((f * B + 255) // 256 * 32),
+                     "nslots": st["nslots"], "keys": n,
+                     "insert_gops": round(n / ms[0] / 1e6, 3), "query_gops": round((pos.numel() + nq) / (ms[1] + ms[2]) / 1e6, 3),
+                     "delete_gops": round((n // 2) / ms[3] / 1e6, 3), "fpr": round(fpr, 6),
+                     "backing_used": st["backing_used"], "failed_keys": st["failed_keys"]})
+        F.close()
+    return {"workload": GEOMETRY_WORKLOAD, "rows": rows}
 
 
 def run_target(args, device):
@@ -1332,7 +1392,7 @@ def cpu_batched_sample(w, target_keys: int = 1 << 25, wseed: int = 4):
             "sample": (f"every {k}-th filter of the batched workload ({len(tasks)} filters, {nk} keys), one oracle "
                        f"filter each, TCF keys in {w['tcf_rounds']} rounds, own + fresh queries; one process per "
                        f"core, rate over the slowest core's oracle time"),
-            "seconds": round(sec, 2), "ops": ops}
+            "seconds": round(sec, 4), "ops": ops}
 
 
 def run_reference(args, rank, world):

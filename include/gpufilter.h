@@ -243,8 +243,11 @@ int filter_get_stats(filter_t *f, void *stream, filter_stats *out);
  * valid until the next insert, remove, clear or import on it; a GQF update
  * switches table buffers, so take the view again after one. Host only, does
  * not touch the device. Group members are not covered. A point-mode TCF can
- * also be updated from a caller's kernel (gf_device_tcf_insert / _remove);
- * those updates and the library's own calls on the filter must not overlap.
+ * also be updated from a caller's kernel (gf_device_tcf_insert / _remove),
+ * and a GQF likewise (gf_device_gqf_insert / _remove, the locked point GQF
+ * of Sec. 5.2: they update the current buffer in place, so the view stays
+ * valid); those updates and the library's own calls on the filter must not
+ * overlap, and GQF point updates must not overlap GQF counts of the filter.
  */
 typedef struct filter_device_view {
     uint32_t kind;       /* FILTER_TCF or FILTER_GQF */
@@ -260,6 +263,8 @@ typedef struct filter_device_view {
                                       [1] failed keys, [2] TCF backing entries */
     uint32_t value_bits; /* TCF: value bits below the tag in each slot; GQF: 0 */
     uint32_t reserved;
+    uint32_t *locks;     /* GQF: the point-update locks, one 32-bit word per 8192 quotients,
+                            32 words apart (gf_device_gqf_insert / _remove); TCF: NULL */
 } filter_device_view;
 
 int filter_get_device_view(filter_t *f, filter_device_view *out);

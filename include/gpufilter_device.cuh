@@ -15,6 +15,8 @@
  *            uint64_t c = gf_device_gqf_count(v, key);
  *            int st = gf_device_tcf_insert(v, key[, value]); (point-mode TCF only)
  *            int st = gf_device_tcf_remove(v, key);          (point-mode TCF only)
+ *            int st = gf_device_gqf_insert(v, key);          (GQF, Sec. 5.2 locks)
+ *            int st = gf_device_gqf_remove(v, key);
  *
  * A view describes the table as it is when filter_get_device_view returns;
  * it must be taken again after any insert, remove, clear or import through
@@ -22,14 +24,20 @@
  * counts read only. Point-mode TCF inserts and removes may run concurrently
  * with each other and with queries from any number of threads (one atomic
  * compare-and-swap per slot, Alg. 1), but not with the library's own calls on
- * the filter. The functions restate the library's hashing, table layouts and
- * point-mode algorithm; GPU tests check them against the C ABI.
+ * the filter. GQF point inserts and removes may run concurrently with each
+ * other (region locks, gpufilter_gqf_ops.cuh, shared with the library's
+ * in-place bulk updates); they update the current table buffer in place, so
+ * the view stays valid, but they must not overlap counts or the library's
+ * own calls on the filter. The TCF functions restate the library's hashing,
+ * table layouts and point-mode algorithm; GPU tests check them against the
+ * C ABI.
  */
 #pragma once
 
 #include <stdint.h>
 
 #include "gpufilter.h"
+#include "gpufilter_gqf_ops.cuh"
 
 namespace gf_device {
 
@@ -428,4 +436,43 @@ __device__ __forceinline__ uint64_t gf_device_gqf_count(const filter_device_view
     const uint8_t *meta = static_cast<const uint8_t *>(v.table);
     const uint8_t *rem = static_cast<const uint8_t *>(v.aux);
     return r == 8 ? gqf_count_fp<8>(fp, meta, rem, v.n_blocks) : gqf_count_fp<16>(fp, meta, rem, v.n_blocks);
+}
+
+// GQF point insert of one copy of key (Sec. 5.2): FILTER_KEY_OK;
+// FILTER_KEY_FULL when the shift it needs would leave the two lock regions
+// or the table (counted in the filter's counters, nothing changed); or 3
+// when a lock wait gave up (the status word records FILTER_ERR_TIMEOUT,
+// nothing changed; the caller may retry).
+__device__ __forceinline__ int gf_device_gqf_insert(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    const uint32_t r = v.tag_bits;
+    const uint64_t fp = gqf_fingerprint(key, v.q + r, v.seed);
+    const gf::GView g{static_cast<gf::Meta *>(v.table), static_cast<uint8_t *>(v.aux), 1ll << v.q,
+                      (long long)v.n_aux, (long long)v.n_blocks};
+    const int rc = r == 8 ? gf::gqf_point_insert<8>(g, v.locks, fp, 1, v.counters)
+                          : gf::gqf_point_insert<16>(g, v.locks, fp, 1, v.counters);
+    if (rc == FILTER_KEY_FULL) {
+        atomicOr(v.counters, 1ull << FILTER_ERR_FULL);
+        atomicAdd(v.counters + 1, 1ull);
+    } else if (rc == gf::GQF_POINT_BUSY) {
+        atomicOr(v.counters, 1ull << FILTER_ERR_TIMEOUT);
+    }
+    return rc;
+}
+
+// GQF point remove of one copy of key: FILTER_KEY_OK, FILTER_KEY_NOT_FOUND,
+// or 3 as for the insert (a lock wait gave up, or the key's cluster runs past
+// the two lock regions; nothing changed).
+__device__ __forceinline__ int gf_device_gqf_remove(const filter_device_view &v, uint64_t key)
+{
+    using namespace gf_device;
+    const uint32_t r = v.tag_bits;
+    const uint64_t fp = gqf_fingerprint(key, v.q + r, v.seed);
+    const gf::GView g{static_cast<gf::Meta *>(v.table), static_cast<uint8_t *>(v.aux), 1ll << v.q,
+                      (long long)v.n_aux, (long long)v.n_blocks};
+    const int rc = r == 8 ? gf::gqf_point_remove<8>(g, v.locks, fp, v.counters)
+                          : gf::gqf_point_remove<16>(g, v.locks, fp, v.counters);
+    if (rc == gf::GQF_POINT_BUSY) atomicOr(v.counters, 1ull << FILTER_ERR_TIMEOUT);
+    return rc;
 }

@@ -74,7 +74,7 @@ class FilterDeviceView(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("tag_bits", C.c_uint32), ("q", C.c_uint32), ("mode", C.c_uint32),
                 ("seed", C.c_uint64), ("table", C.c_void_p), ("aux", C.c_void_p), ("n_blocks", C.c_uint64),
                 ("n_aux", C.c_uint64), ("counters", C.c_void_p), ("value_bits", C.c_uint32),
-                ("reserved", C.c_uint32)]
+                ("reserved", C.c_uint32), ("locks", C.c_void_p)]
 
 
 class FilterRequest(C.Structure):

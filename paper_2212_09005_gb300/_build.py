@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgpufilter.so")
 SOURCES = ["gf_prims.cu", "gf_tcf.cu", "gf_gqf.cu", "gf_capi.cu", "gf_group.cu", "gf_serve.cu", "gf_noalloc.cu",
            "gf_batch.cu"]
-HEADERS = ["gf_internal.cuh", "gf_sched.h"]
+HEADERS = ["gf_internal.cuh", "gf_sched.h", "gf_packed.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -42,6 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     hdrs = [os.path.join(CSRC, h) for h in HEADERS]
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "gpufilter.h"))
+    hdrs.append(os.path.join(os.path.dirname(HERE), "include", "gpufilter_gqf_ops.cuh"))
     jobs = []
     objs = []
     for src in SOURCES:

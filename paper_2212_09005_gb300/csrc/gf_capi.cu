@@ -224,6 +224,7 @@ int filter_get_device_view(filter_t *f, filter_device_view *out)
         out->aux = Q.rem[Q.cur];
         out->n_blocks = Q.nblk;
         out->n_aux = Q.nslots;
+        out->locks = Q.locks;
     }
     return FILTER_OK;
 }

@@ -385,6 +385,8 @@ struct GqfState {
     uint8_t *meta[2];  // nblk * 32
     uint8_t *rem[2];   // nslots * r/8
     int cur;           // which buffer holds the table
+    uint32_t *locks;   // point updates: a lock word per 8192 quotients, 128 bytes apart
+    uint64_t nlocks;
     bool merge_only;   // inserts always merge into the other buffer (no in-place path)
     // scratch
     uint64_t *fp_a, *fp_b, *fp_c;  // max_batch

@@ -32,7 +32,9 @@ __global__ void device_update_kernel(filter_device_view v, const uint64_t *keys,
                                      uint8_t *status)
 {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        const int st = remove ? gf_device_tcf_remove(v, keys[i]) : gf_device_tcf_insert(v, keys[i]);
+        int st;
+        if (v.kind == FILTER_GQF) st = remove ? gf_device_gqf_remove(v, keys[i]) : gf_device_gqf_insert(v, keys[i]);
+        else st = remove ? gf_device_tcf_remove(v, keys[i]) : gf_device_tcf_insert(v, keys[i]);
         if (status) status[i] = (uint8_t)st;
     }
 }

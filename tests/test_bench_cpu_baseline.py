@@ -16,7 +16,7 @@ def test_batched_oracle_baseline_on_all_cores():
     assert r["kind"] == "oracle" and r["unit"] == "Gops/s"
     assert r["ops"] == 3 * nk
     assert 1 <= r["cores"] <= len(picked)
-    assert r["value"] > 0 and r["seconds"] > 0
+    assert r["value"] > 0 and r["seconds"] >= 0  # (a small sample can round to 0 s)
     assert f"{len(picked)} filters" in r["sample"]
 
 

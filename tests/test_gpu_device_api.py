@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2212_09005_gb300 import workloads as W
-from gpu_util import dev_u64, zeros_u8, zeros_u64, host
+from gpu_util import dev_u64, zeros_u8, zeros_u64, host, first_diff
 
 pytestmark = pytest.mark.gpu
 
@@ -133,3 +133,67 @@ def test_point_tcf_updates_from_a_user_kernel(gf, oracle, example, f):
     st3 = zeros_u8(16)
     run_update(example, B.device_view(), dev_u64(keys[:16]), False, st3)
     assert (host(st3) == 1).all() and B.stats()["failed_keys"] == 0
+
+
+@pytest.mark.parametrize("q,r", [(14, 8), (16, 16)])
+def test_point_gqf_updates_from_a_user_kernel(gf, oracle, example, q, r):
+    """Locked point GQF (Sec. 5.2): one key per thread, many threads on the
+    same regions at once (repeated keys, neighbouring quotients). The table
+    of a GQF is a function of its fingerprint multiset, so after the point
+    inserts the image equals the oracle's after a bulk insert of the same
+    keys, and after point removes the oracle's after the same removes."""
+    import torch
+
+    G = gf.GQF(q, r, seed=q + r, max_batch=1 << 16)
+    n = int(0.85 * (1 << q))
+    base = W.uniform_keys(5100 + q, n * 3 // 4)
+    keys = np.concatenate([base, base[: n // 4]])  # repeated keys: counters, and contention on one run
+    keys = keys[W.sample_without_replacement(5200 + q, keys.size, keys.size)]  # interleave the copies
+    view = G.device_view()
+    st = torch.zeros(keys.size, dtype=torch.uint8, device="cuda")
+    run_update(example, view, dev_u64(keys), False, st)
+    assert not host(st).any()
+    O = oracle.GQF(q, r, seed=q + r)
+    O.insert(keys)
+    assert first_diff(G.export(), O.export()) is None
+    probe = np.concatenate([base[::5], W.uniform_keys(5300 + q, 3000)])
+    c = torch.zeros(probe.size, dtype=torch.int64, device="cuda")
+    run_example(example, view, dev_u64(probe), counts=c)
+    assert np.array_equal(host(c), O.count(probe))
+    # removes: stored keys (some twice), and absent ones
+    rem = np.concatenate([base[::2], base[: n // 8], W.uniform_keys(5400 + q, 500)])
+    st = torch.zeros(rem.size, dtype=torch.uint8, device="cuda")
+    run_update(example, view, dev_u64(rem), True, st)
+    fpr = O.fingerprints(rem)
+    want = O.remove(rem)
+    # which copy of a repeated remove finds nothing depends on the threads'
+    # order: compare the statuses per fingerprint
+    got = collections.Counter(zip(fpr.tolist(), host(st).tolist()))
+    assert got == collections.Counter(zip(fpr.tolist(), want.tolist()))
+    assert first_diff(G.export(), O.export()) is None
+    assert G.stats()["status_word"] == 0
+
+
+def test_point_gqf_full_table_reports_full_without_damage(gf, oracle, example):
+    """Point inserts into a table without room for all of them: the keys
+    reported OK are exactly the stored multiset, the table is the canonical
+    layout of that multiset (a consistent table, whatever order the threads
+    took), and the FULL ones are counted."""
+    import torch
+
+    q, r = 10, 8
+    G = gf.GQF(q, r, seed=3, max_batch=1 << 12)
+    view = G.device_view()
+    keys = W.uniform_keys(5500, 2 << q)
+    st = torch.zeros(keys.size, dtype=torch.uint8, device="cuda")
+    run_update(example, view, dev_u64(keys), False, st)
+    s = host(st)
+    assert set(np.unique(s)) <= {gf.KEY_OK, gf.KEY_FULL}
+    assert (s == gf.KEY_FULL).any()
+    O = oracle.GQF(q, r, seed=3)
+    fu, cnt = np.unique(O.fingerprints(keys[s == gf.KEY_OK]), return_counts=True)
+    fps, cnts = (host(t) for t in G.enumerate())
+    assert np.array_equal(fps, fu) and np.array_equal(cnts, cnt.astype(np.uint64))
+    assert O.insert_groups(fu, cnt) == fu.size
+    assert first_diff(G.export(), O.export()) is None
+    assert G.stats()["failed_keys"] == int((s == gf.KEY_FULL).sum())
