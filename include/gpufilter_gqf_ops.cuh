@@ -496,25 +496,35 @@ __device__ long long gv_push_end(const GView &g, long long x, long long need, lo
 // start of the region after next never meets another one. The insert checks
 // that its shift stops there, the delete that x's cluster ends there;
 // otherwise nothing changes and the key is reported FULL (insert) or BUSY.
+// Clusters stay far shorter than a region while the home slots are at most
+// about 95 % used (the bound the paper cites); past that, updates near the
+// end of a region start to report FULL / BUSY although the tail has room.
 // ---------------------------------------------------------------------------
 static constexpr long long GQF_LOCK_REGION = 8192;  // quotients per lock region
 static constexpr int GQF_LOCK_STRIDE = 32;          // 32-bit words from one lock to the next (128 bytes)
 static constexpr uint32_t GQF_LOCK_TRIES = 1u << 20;
 static constexpr int GQF_POINT_BUSY = 3;            // a lock wait gave up, or the cluster is too long
 
+// Test and test-and-set: waiters read the word (no atomic traffic on a held
+// lock) and try the compare-and-swap only when it reads free, backing off
+// exponentially; the wait gives up after GQF_LOCK_TRIES reads.
 __device__ __forceinline__ bool gqf_lock_take(uint32_t *l)
 {
-    uint32_t ns = 32;
+    uint32_t ns = 64;
     const uint32_t zero = 0, one = 1;
     for (uint32_t t = 0; t < GQF_LOCK_TRIES; t++) {
-        uint32_t old;
-        asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"
-                     : "=r"(old)
-                     : "l"(l), "r"(zero), "r"(one)
-                     : "memory");
-        if (old == 0) return true;
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
+        uint32_t cur;
+        asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(cur) : "l"(l) : "memory");
+        if (cur == 0) {
+            uint32_t old;
+            asm volatile("atom.acquire.gpu.global.cas.b32 %0, [%1], %2, %3;"
+                         : "=r"(old)
+                         : "l"(l), "r"(zero), "r"(one)
+                         : "memory");
+            if (old == 0) return true;
+        }
+        __nanosleep(ns + (threadIdx.x & 31) * 8);  // staggered, so that waiters do not retry together
+        if (ns < 4096) ns <<= 1;
     }
     return false;
 }
@@ -584,9 +594,13 @@ __device__ int gqf_point_remove(const GView &g, uint32_t *locks, uint64_t fp, un
     long long r0, limit;
     uint32_t *l0, *l1;
     if (x >= g.N || !gqf_lock_pair(g, locks, x, r0, limit, l0, l1)) return GQF_POINT_BUSY;
-    int rc = GQF_POINT_BUSY;
-    const long long ce = gv_push_end(g, x, 0, r0, limit);  // where the cluster from x ends
-    if (ce >= 0 && ce <= limit) rc = gv_delete<R>(g, fp, 1, status) ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND;
+    int rc = FILTER_KEY_NOT_FOUND;  // (no run: nothing stored)
+    if (gv_occ(g, x)) {
+        // the run of x ends at or after x: where the cluster from x ends
+        const long long ce = gv_push_end(g, x, 0, r0, limit);
+        rc = ce >= x && ce <= limit ? (gv_delete<R>(g, fp, 1, status) ? FILTER_KEY_OK : FILTER_KEY_NOT_FOUND)
+                                    : GQF_POINT_BUSY;
+    }
     gqf_unlock_pair(l0, l1);
     return rc;
 }

@@ -67,3 +67,23 @@ extern "C" int device_value_example(const filter_device_view *v, const uint64_t 
     device_value_kernel<<<grid, 256, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, values_in, out);
     return cudaGetLastError() == cudaSuccess ? 0 : 1;
 }
+
+// The same updates applied by one thread, key after key (no concurrency).
+__global__ void device_update_serial_kernel(filter_device_view v, const uint64_t *keys, uint64_t n, int remove,
+                                            uint8_t *status)
+{
+    for (uint64_t i = 0; i < n; i++) {
+        int st;
+        if (v.kind == FILTER_GQF) st = remove ? gf_device_gqf_remove(v, keys[i]) : gf_device_gqf_insert(v, keys[i]);
+        else st = remove ? gf_device_tcf_remove(v, keys[i]) : gf_device_tcf_insert(v, keys[i]);
+        if (status) status[i] = (uint8_t)st;
+    }
+}
+
+extern "C" int device_update_serial_example(const filter_device_view *v, const uint64_t *keys, uint64_t n, int remove,
+                                            uint8_t *status, void *stream)
+{
+    if (!v || n == 0) return 0;
+    device_update_serial_kernel<<<1, 1, 0, static_cast<cudaStream_t>(stream)>>>(*v, keys, n, remove, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : 1;
+}

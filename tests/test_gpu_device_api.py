@@ -46,6 +46,8 @@ def example(tmp_path_factory):
     lib.device_query_example.restype = C.c_int
     lib.device_update_example.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]
     lib.device_update_example.restype = C.c_int
+    lib.device_update_serial_example.argtypes = lib.device_update_example.argtypes
+    lib.device_update_serial_example.restype = C.c_int
     return lib
 
 
@@ -135,7 +137,36 @@ def test_point_tcf_updates_from_a_user_kernel(gf, oracle, example, f):
     assert (host(st3) == 1).all() and B.stats()["failed_keys"] == 0
 
 
-@pytest.mark.parametrize("q,r", [(14, 8), (16, 16)])
+@pytest.mark.parametrize("q,r", [(12, 8), (12, 16)])
+def test_point_gqf_updates_one_thread(gf, oracle, example, q, r):
+    """The point insert and remove, key after key from one thread: the
+    table equals the oracle's after each stage."""
+    import torch
+
+    G = gf.GQF(q, r, seed=q + 2 * r, max_batch=1 << 14)
+    n = int(0.68 * (1 << q))  # with the repeats (3 slots each): 85 % of the home slots
+    base = W.uniform_keys(5000 + q, n * 3 // 4)
+    keys = np.concatenate([base, base[: n // 4]])
+    view = G.device_view()
+    st = torch.zeros(keys.size, dtype=torch.uint8, device="cuda")
+    assert example.device_update_serial_example(C.byref(view), C.c_void_p(dev_u64(keys).data_ptr()), keys.size, 0,
+                                                C.c_void_p(st.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    O = oracle.GQF(q, r, seed=q + 2 * r)
+    want = O.insert(keys)
+    assert np.array_equal(host(st), want), np.unique(host(st), return_counts=True)
+    assert first_diff(G.export(), O.export()) is None
+    rem = np.concatenate([base[::2], base[: n // 8], W.uniform_keys(5050 + q, 300)])
+    d = dev_u64(rem)
+    st = torch.zeros(rem.size, dtype=torch.uint8, device="cuda")
+    assert example.device_update_serial_example(C.byref(view), C.c_void_p(d.data_ptr()), rem.size, 1,
+                                                C.c_void_p(st.data_ptr()), None) == 0
+    torch.cuda.synchronize()
+    assert np.array_equal(host(st), O.remove(rem))
+    assert first_diff(G.export(), O.export()) is None
+
+
+@pytest.mark.parametrize("q,r", [(18, 8), (17, 16), (14, 8)])
 def test_point_gqf_updates_from_a_user_kernel(gf, oracle, example, q, r):
     """Locked point GQF (Sec. 5.2): one key per thread, many threads on the
     same regions at once (repeated keys, neighbouring quotients). The table
@@ -145,14 +176,14 @@ def test_point_gqf_updates_from_a_user_kernel(gf, oracle, example, q, r):
     import torch
 
     G = gf.GQF(q, r, seed=q + r, max_batch=1 << 16)
-    n = int(0.85 * (1 << q))
+    n = int(0.68 * (1 << q))  # with the repeats (3 slots each): 85 % of the home slots
     base = W.uniform_keys(5100 + q, n * 3 // 4)
     keys = np.concatenate([base, base[: n // 4]])  # repeated keys: counters, and contention on one run
     keys = keys[W.sample_without_replacement(5200 + q, keys.size, keys.size)]  # interleave the copies
     view = G.device_view()
     st = torch.zeros(keys.size, dtype=torch.uint8, device="cuda")
     run_update(example, view, dev_u64(keys), False, st)
-    assert not host(st).any()
+    assert not host(st).any(), np.unique(host(st), return_counts=True)
     O = oracle.GQF(q, r, seed=q + r)
     O.insert(keys)
     assert first_diff(G.export(), O.export()) is None
