@@ -462,7 +462,14 @@ __global__ void __launch_bounds__(RS_T) rs_fp_hist(const uint64_t *__restrict__ 
 // in digit order, and the copy-out writes runs of consecutive addresses,
 // taking each key's global position from its digit's offset. Shared memory
 // and registers are sized for 3 CTAs per SM (2 with values).
-template <bool VALS, int DB>
+//
+// STABLE = false (the first pass of a sort without values): the order of keys
+// with equal digits does not matter, because keys that agree in every sorted
+// bit are identical (the callers sort fingerprints with nothing above the
+// sorted bits) and the later passes are stable. Each key then takes its rank
+// with one shared-memory atomic on its (warp, digit) counter instead of the
+// ballots.
+template <bool VALS, int DB, bool STABLE = true>
 __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t *__restrict__ kin,
                                                                  uint64_t *__restrict__ kout,
                                                                  const uint32_t *__restrict__ vin,
@@ -495,7 +502,26 @@ __global__ void __launch_bounds__(RS_T, VALS ? 2 : 3) rs_scatter(const uint64_t 
         if (VALS) val[r] = ok ? __ldcs(vin + i) : 0;
     }
 #pragma unroll
-    for (int r = 0; r < RS_I; r++) {
+    for (int r = 0; r < RS_I && !STABLE; r++) {
+        const uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
+        const bool ok = i < n;
+        const uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & (nb - 1)) : 0xffffu;
+        const uint32_t dprev = __shfl_up_sync(0xffffffffu, d, 1);
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(wcnt) + warp * (RS_MAXB / 2) + (d >> 1);
+        const uint32_t sh = (d & 1u) * 16u;  // the counters are 16-bit halves of 32-bit words; no half carries
+        if (__ballot_sync(0xffffffffu, lane == 0 || d != dprev) == 1u) {
+            // one run of one digit (skewed keys; a round is all valid or all
+            // past the end, whose digit differs): lane order, one update by lane 0
+            uint32_t b = 0;
+            if (lane == 0 && ok) b = atomicAdd(w32, 32u << sh) >> sh;
+            b = __shfl_sync(0xffffffffu, b, 0) & 0xffffu;
+            rank[r] = (uint16_t)(b + lane);
+        } else if (ok) {
+            rank[r] = (uint16_t)(atomicAdd(w32, 1u << sh) >> sh);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < RS_I && STABLE; r++) {
         uint64_t i = base + (uint64_t)warp * (RS_I * 32) + r * 32 + lane;
         bool ok = i < n;
         uint32_t d = ok ? ((uint32_t)(key[r] >> shift) & (nb - 1)) : 0xffffu;
@@ -598,10 +624,14 @@ static constexpr size_t rs_smem()
 template <bool VALS>
 static void launch_scatter(uint32_t db, uint64_t ntiles, const uint64_t *ks, uint64_t *kd, const uint32_t *vs,
                            uint32_t *vd, uint64_t n, uint32_t shift, uint32_t nb, const uint32_t *offs,
-                           cudaStream_t st)
+                           cudaStream_t st, bool stable)
 {
     const unsigned g = (unsigned)ntiles;
     const size_t sm = rs_smem<VALS>();
+    if (!VALS && !stable) {
+        rs_scatter<false, 0, false><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
+        return;
+    }
     if (db == 9) rs_scatter<VALS, 9><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
     else if (db == 8) rs_scatter<VALS, 8><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
     else rs_scatter<VALS, 0><<<g, RS_T, sm, st>>>(ks, kd, vs, vd, n, shift, nb, offs, ntiles);
@@ -637,6 +667,8 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         cudaFuncSetAttribute(rs_scatter<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
         cudaFuncSetAttribute(rs_scatter<true, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<true>());
         cudaFuncSetAttribute(rs_scatter<false, 9>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs_smem<false>());
+        cudaFuncSetAttribute(rs_scatter<false, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rs_smem<false>());
         attr_done = true;
     }
     const bool vals = vals_in != nullptr;
@@ -664,9 +696,9 @@ void radix_sort_u64(const uint64_t *keys_in, uint64_t *keys_out, uint64_t *keys_
         exclusive_scan_u32(tmp, tmp, ntiles * nb, scan_tmp, ctr, st);
         TraceScope ts_(vals ? "rs_scatter_kv" : "rs_scatter", n, st);
         if (vals)
-            launch_scatter<true>(db, ntiles, ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, st);
+            launch_scatter<true>(db, ntiles, ksrc, kdst, vsrc, vdst, n, shift, nb, tmp, st, true);
         else
-            launch_scatter<false>(db, ntiles, ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, st);
+            launch_scatter<false>(db, ntiles, ksrc, kdst, nullptr, nullptr, n, shift, nb, tmp, st, p > 0);
         ksrc = kdst;
         vsrc = vdst;
         shift += db;
