@@ -40,7 +40,6 @@ namespace gf {
 static constexpr int TPB = 256;
 static constexpr uint32_t BK_W = 8;  // backing bucket entries
 static constexpr int MAXSEL = 32;    // largest B
-static constexpr int GU = 4;         // candidates a grouping thread keeps in flight
 
 // ---------------------------------------------------------------------------
 // 32-byte block in registers
@@ -424,32 +423,19 @@ __global__ void __launch_bounds__(TPB) tcf_group_hist(const uint64_t *__restrict
         step = TPB;
         j = c0 + threadIdx.x;
     }
-    // GU candidates per thread and step, their loads and atomics in flight together
-    for (; j < c1; j += GU * step) {
-        uint64_t d[GU];
-#pragma unroll
-        for (int u = 0; u < GU; u++) {
-            const uint64_t jj = j + u * step;
-            d[u] = ~0ull;
-            if (jj < c1) {
-                uint64_t pw = 0, i = jj;
-                if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[jj];
-                if (SRC == SRC_PEND_U64) {
-                    pw = static_cast<const uint64_t *>(pend)[jj];
-                    i = pw & 0xffffffffu;
-                }
-                const KeyInfo k = key_at<DST>(keys, prep, i, G);
-                d[u] = dest_of(DST, k, pw, G, fill, prep, i);
-            }
+    for (; j < c1; j += step) {
+        uint64_t pw = 0, i = j;
+        if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[j];
+        if (SRC == SRC_PEND_U64) {
+            pw = static_cast<const uint64_t *>(pend)[j];
+            i = pw & 0xffffffffu;
         }
-#pragma unroll
-        for (int u = 0; u < GU; u++) {
-            if (d[u] == ~0ull) continue;
-            if (SPARSE) {
-                if (atomicAdd(&cnt[d[u]], 1u) == 0u) tlist[c0 + atomicAdd(&s_n, 1u)] = (uint32_t)d[u];
-            } else {
-                atomicAdd(&cnt[d[u]], 1u);  // no result used: a reduction the L2 applies without a reply
-            }
+        KeyInfo k = key_at<DST>(keys, prep, i, G);
+        const uint64_t d = dest_of(DST, k, pw, G, fill, prep, i);
+        if (SPARSE) {
+            if (atomicAdd(&cnt[d], 1u) == 0u) tlist[c0 + atomicAdd(&s_n, 1u)] = (uint32_t)d;
+        } else {
+            atomicAdd(&cnt[d], 1u);  // no result used: a reduction the L2 applies without a reply
         }
     }
     if (SPARSE) {
@@ -519,38 +505,21 @@ __global__ void __launch_bounds__(TPB) tcf_group_scatter(const uint64_t *__restr
 {
     const uint64_t n = (SRC == SRC_KEYS) ? n_keys : (uint64_t)*npend;
     note_units(units, n);
-    const uint64_t step = (uint64_t)gridDim.x * TPB;
-    // GU candidates per thread and step: their reads, atomics and offsets in flight together
-    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += GU * step) {
-        uint64_t d[GU], v[GU];
-        uint32_t ii[GU];
-#pragma unroll
-        for (int u = 0; u < GU; u++) {
-            const uint64_t jj = j + u * step;
-            d[u] = ~0ull;
-            if (jj < n) {
-                uint64_t pw = 0, i = jj;
-                if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[jj];
-                if (SRC == SRC_PEND_U64) {
-                    pw = static_cast<const uint64_t *>(pend)[jj];
-                    i = pw & 0xffffffffu;
-                }
-                const KeyInfo k = key_at<DST>(keys, prep, i, G);
-                d[u] = dest_of(DST, k, pw, G, fill, prep, i);
-                ii[u] = (uint32_t)i;
-                if (DST == DST_BUCKET) v[u] = prep.bt ? prep.e[i] : tcf_entry(k, G.f);
-                else v[u] = ((uint64_t)k.t << 32) | i;
-            }
+    for (uint64_t j = blockIdx.x * (uint64_t)TPB + threadIdx.x; j < n; j += (uint64_t)gridDim.x * TPB) {
+        uint64_t pw = 0, i = j;
+        if (SRC == SRC_PEND_U32) i = static_cast<const uint32_t *>(pend)[j];
+        if (SRC == SRC_PEND_U64) {
+            pw = static_cast<const uint64_t *>(pend)[j];
+            i = pw & 0xffffffffu;
         }
-        uint32_t pos[GU];
-#pragma unroll
-        for (int u = 0; u < GU; u++)
-            if (d[u] != ~0ull) pos[u] = off[d[u]] + atomicSub(&cnt[d[u]], 1u) - 1u;
-#pragma unroll
-        for (int u = 0; u < GU; u++) {
-            if (d[u] == ~0ull) continue;
-            rec[pos[u]] = v[u];
-            if (DST == DST_BUCKET) recI[pos[u]] = ii[u];
+        KeyInfo k = key_at<DST>(keys, prep, i, G);
+        uint64_t d = dest_of(DST, k, pw, G, fill, prep, i);
+        uint32_t pos = off[d] + atomicSub(&cnt[d], 1u) - 1u;
+        if (DST == DST_BUCKET) {
+            rec[pos] = prep.bt ? prep.e[i] : tcf_entry(k, G.f);
+            recI[pos] = (uint32_t)i;
+        } else {
+            rec[pos] = ((uint64_t)k.t << 32) | i;
         }
     }
 }
