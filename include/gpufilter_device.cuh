@@ -28,8 +28,9 @@
  * other (region locks, gpufilter_gqf_ops.cuh, shared with the library's
  * in-place bulk updates); they update the current table buffer in place, so
  * the view stays valid, but they must not overlap counts or the library's
- * own calls on the filter. The TCF functions restate the library's hashing,
- * table layouts and point-mode algorithm; GPU tests check them against the
+ * own calls on the filter. The hashing is the library's own
+ * (gpufilter_hash.cuh); the TCF block access and point-mode updates are
+ * restated here for one key per thread, and GPU tests check them against the
  * C ABI.
  */
 #pragma once
@@ -38,41 +39,16 @@
 
 #include "gpufilter.h"
 #include "gpufilter_gqf_ops.cuh"
+#include "gpufilter_hash.cuh"
 
 namespace gf_device {
 
-__device__ __forceinline__ uint64_t mix64(uint64_t x)
-{
-    x ^= x >> 33;
-    x *= 0xff51afd7ed558ccdull;
-    x ^= x >> 33;
-    x *= 0xc4ceb9fe1a85ec53ull;
-    x ^= x >> 33;
-    return x;
-}
+using gf::mix64;
 
-// The GQF fingerprint: the key folded to p bits (xor of its p-bit chunks),
-// xored with the seed, then xor-shift / odd-multiply rounds mod 2^p.
+// The GQF fingerprint (include/gpufilter_hash.cuh, the library's own)
 __device__ __forceinline__ uint64_t gqf_fingerprint(uint64_t key, uint32_t p, uint64_t seed)
 {
-    const uint64_t mask = p >= 64 ? ~0ull : ((1ull << p) - 1ull);
-    const uint32_t s = (p + 1) / 2;
-    uint64_t x = key;
-    if (p < 64) {
-        uint64_t r = 0;
-        while (x) {
-            r ^= x & mask;
-            x >>= p;
-        }
-        x = r;
-    }
-    x ^= seed & mask;
-    x ^= x >> s;
-    x = (x * 0xff51afd7ed558ccdull) & mask;
-    x ^= x >> s;
-    x = (x * 0xc4ceb9fe1a85ec53ull) & mask;
-    x ^= x >> s;
-    return x;
+    return gf::fingerprint(key, gf::phash_of(p, seed));
 }
 
 // the tag part of every f-bit lane of a word (a TCF with v value bits keeps
@@ -218,21 +194,15 @@ namespace gf_device {
 __device__ __forceinline__ void tcf_key(const filter_device_view &v, uint64_t key, uint64_t &b1, uint64_t &b2,
                                         uint32_t &t)
 {
-    const uint64_t nb = v.n_blocks;
-    const uint64_t h = mix64(key ^ v.seed);
-    uint32_t tag = (uint32_t)((h >> 44) & ((1u << (v.tag_bits - v.value_bits)) - 1u));
-    if (tag < 2) tag += 2;
-    b1 = h & (nb - 1);
-    uint64_t g = mix64((uint64_t)tag) & (nb - 1);
-    if (!g) g = 1;
-    b2 = b1 ^ g;
+    uint32_t tag;
+    gf::tcf_key_parts(key, v.seed, v.n_blocks, (1u << (v.tag_bits - v.value_bits)) - 1u, b1, b2, tag);
     t = tag << v.value_bits;
 }
 
 // the key's backing bucket (chosen by the entry without its value bits)
 __device__ __forceinline__ uint64_t *tcf_bucket_ptr(const filter_device_view &v, uint64_t e)
 {
-    return static_cast<uint64_t *>(v.aux) + (((mix64(e) >> 32) * v.n_aux) >> 32) * 8;
+    return static_cast<uint64_t *>(v.aux) + gf::tcf_bucket(e, v.n_aux) * 8;
 }
 
 }  // namespace gf_device

@@ -43,6 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     hdrs = [os.path.join(CSRC, h) for h in HEADERS]
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "gpufilter.h"))
     hdrs.append(os.path.join(os.path.dirname(HERE), "include", "gpufilter_gqf_ops.cuh"))
+    hdrs.append(os.path.join(os.path.dirname(HERE), "include", "gpufilter_hash.cuh"))
     jobs = []
     objs = []
     for src in SOURCES:

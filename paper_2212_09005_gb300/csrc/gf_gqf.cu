@@ -1255,10 +1255,7 @@ int gqf_setup(filter *F, uint64_t &table_bytes, uint64_t &scratch_bytes, bool pl
     Q.nslots = Q.N + Q.S;
     Q.nblk = Q.nslots / 64;
     Q.ntiles = (Q.nblk + TBLK - 1) / TBLK;
-    Q.H.p = Q.p;
-    Q.H.s = (Q.p + 1) / 2;
-    Q.H.mask = Q.p >= 64 ? ~0ull : ((1ull << Q.p) - 1ull);
-    Q.H.seed = c.hash_seed & Q.H.mask;
+    Q.H = phash_of(Q.p, c.hash_seed);
     const uint64_t M = c.max_batch ? c.max_batch : 1;
     if (M >= (1ull << 30)) return FILTER_ERR_ARG;  // 30-bit counts in the sort and group arrays
     const uint64_t metaB = Q.nblk * 32, remB = Q.nslots * (Q.r / 8);

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include "../../include/gpufilter.h"
+#include "../../include/gpufilter_hash.cuh"
 
 namespace gf {
 
@@ -53,43 +54,8 @@ static_assert(offsetof(DevCounters, cursor) == offsetof(DevCounters, touched) + 
 // Hashing (paper Sec. 5.1 fingerprint h; Sec. 4 block/tag hash). Bijective:
 // xor-shifts by s >= p/2 and products with odd constants mod 2^p.
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ uint64_t mix64(uint64_t x)
-{
-    x ^= x >> 33;
-    x *= 0xff51afd7ed558ccdull;
-    x ^= x >> 33;
-    x *= 0xc4ceb9fe1a85ec53ull;
-    x ^= x >> 33;
-    return x;
-}
-
-struct PHash {
-    uint64_t mask;  // 2^p - 1
-    uint64_t seed;  // seed mod 2^p
-    uint32_t p, s;  // width and shift ceil(p/2)
-};
-
-__host__ __device__ __forceinline__ uint64_t fold_p(uint64_t x, const PHash &H)
-{
-    if (H.p >= 64) return x;
-    uint64_t r = 0;
-    while (x) {
-        r ^= x & H.mask;
-        x >>= H.p;
-    }
-    return r;
-}
-
-__host__ __device__ __forceinline__ uint64_t fingerprint(uint64_t key, const PHash &H)
-{
-    uint64_t x = fold_p(key, H) ^ H.seed;
-    x ^= x >> H.s;
-    x = (x * 0xff51afd7ed558ccdull) & H.mask;
-    x ^= x >> H.s;
-    x = (x * 0xc4ceb9fe1a85ec53ull) & H.mask;
-    x ^= x >> H.s;
-    return x;
-}
+// mix64, PHash, fold_p, fingerprint, tcf_g, tcf_key_parts, tcf_bucket:
+// include/gpufilter_hash.cuh (shared with the device-side API)
 
 struct TcfGeom {
     uint64_t nb;      // blocks (power of two)
@@ -112,21 +78,12 @@ struct KeyInfo {
     uint32_t t;
 };
 
-__host__ __device__ __forceinline__ uint64_t tcf_g(uint32_t t, uint64_t nb)
-{
-    uint64_t g = mix64((uint64_t)t) & (nb - 1);
-    return g ? g : 1;
-}
-
 __host__ __device__ __forceinline__ KeyInfo tcf_keyinfo(uint64_t key, const TcfGeom &G)
 {
     KeyInfo k;
-    uint64_t h = mix64(key ^ G.seed);
-    uint32_t t = (uint32_t)((h >> 44) & G.tmask);
-    if (t < 2) t += 2;
+    uint32_t t;
+    tcf_key_parts(key, G.seed, G.nb, G.tmask, k.b1, k.b2, t);
     k.t = t << G.vbits;
-    k.b1 = h & (G.nb - 1);
-    k.b2 = k.b1 ^ tcf_g(t, G.nb);
     return k;
 }
 
@@ -134,11 +91,6 @@ __host__ __device__ __forceinline__ uint64_t tcf_entry(const KeyInfo &k, uint32_
 {
     uint64_t lo = k.b1 < k.b2 ? k.b1 : k.b2;
     return (lo << f) | k.t;
-}
-
-__host__ __device__ __forceinline__ uint64_t tcf_bucket(uint64_t e, uint64_t nbk)
-{
-    return ((mix64(e) >> 32) * nbk) >> 32;
 }
 
 // the bucket of an entry that may carry a value: chosen by the tag part only
