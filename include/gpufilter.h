@@ -23,7 +23,8 @@
  * Fingerprints and layouts
  *   TCF (paper Sec. 4): h = mix64(key ^ seed), block b1 = h mod nb, tag =
  *   bits 44.. of h (f bits, 0 and 1 moved to 2 and 3), b2 = b1 xor g(tag).
- *   nb = 2^log2_slots / B blocks of 32 bytes (B = 256 / f tags). Backing
+ *   nb = 2^log2_slots / B blocks of 32 bytes (B = 256 / f tags; other block
+ *   geometries: see filter_config.block_slots). Backing
  *   table: nbk buckets of 8 uint64 entries (min(b1,b2) << f | tag), nbk =
  *   max(8, ceil(ceil(N/100) / 8)) (Sec. 4.1, "backing table"). With
  *   value_bits v > 0 the tag is f - v bits wide and each slot holds
@@ -103,9 +104,11 @@ typedef struct filter_stats {
  * filter_create: validate *cfg, allocate the table and the scratch for
  * batches of up to cfg->max_batch keys on the current device, and clear the
  * table on `stream`. The filter owns this memory until filter_destroy.
- * Returns FILTER_ERR_ARG for a bad geometry (TCF: f in {8,16}, 2^log2_slots
- * >= 2 blocks, nb <= 2^32, value_bits <= min(f / 2, 7); GQF: r in {8,16},
- * 6 <= q <= 36, q + r <= 64, value_bits 0),
+ * Returns FILTER_ERR_ARG for a bad geometry (TCF: f in {8,16}, or f = 12 and
+ * the other (f, block_slots) pairs listed at filter_config in bulk mode
+ * without values; 2^log2_slots >= 2 blocks, nb <= 2^32, value_bits <=
+ * min(f / 2, 7); GQF: r in {8,16}, 6 <= q <= 36, q + r <= 64, value_bits and
+ * block_slots 0),
  * FILTER_ERR_OOM if an allocation fails (nothing is leaked).
  */
 int filter_create(const filter_config *cfg, void *stream, filter_t **out);
