@@ -2596,13 +2596,10 @@ __global__ void __launch_bounds__(TPB) tcf_group_query_kernel(const uint64_t *__
             G = member_geom(M, F);
         }
         const KeyInfo k = tcf_keyinfo(__ldcs(keys + c.i), G);
-        Blk<F> x;
+        Blk<F> x, y;
         x.load_ro(blocks, M.block0 + k.b1);
-        bool hit = x.has(k.t, 0xffffffffu);  // group members carry no values
-        if (!hit) {  // the second block only on a miss, as tcf_query_kernel
-            x.load_ro(blocks, M.block0 + k.b2);
-            hit = x.has(k.t, 0xffffffffu);
-        }
+        y.load_ro(blocks, M.block0 + k.b2);
+        bool hit = x.has(k.t, 0xffffffffu) || y.has(k.t, 0xffffffffu);  // group members carry no values
         if (!hit && backing) {
             const uint64_t e = tcf_entry(k, F);
             const ulonglong2 *p =
