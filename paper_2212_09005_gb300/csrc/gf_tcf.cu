@@ -303,12 +303,7 @@ __device__ __forceinline__ int topk_push(uint64_t *a, int have, int k, uint64_t 
 // ---------------------------------------------------------------------------
 // VAL: answer the smallest value stored with the key's fingerprint in its two
 // blocks and its backing bucket, 0xFF when there is none; else 1 / 0.
-// LAZY: the second block is read only when the tag is not in the first. Most
-// stored keys sit in their first block (the shortcut's target), so positive
-// queries skip one random block; past the L2 that is a DRAM burst saved
-// (2^28 slots: 29.7 against 26.0 Gops/s on a half-positive mix), and at
-// 2^26 slots it costs nothing (63.5 against 63.1).
-template <int F, bool VAL, bool LAZY = false>
+template <int F, bool VAL>
 __global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restrict__ keys, uint64_t n,
                                                         TcfGeom G, const uint8_t *__restrict__ blocks,
                                                         const uint64_t *__restrict__ bk,
@@ -322,24 +317,6 @@ __global__ void __launch_bounds__(TPB) tcf_query_kernel(const uint64_t *__restri
         KeyInfo k = tcf_keyinfo(__ldcs(keys + i), G);  // keys and answers stream past the L2
         Blk<F> x, y;
         x.load_ro(blocks, k.b1);
-        if (!VAL && LAZY) {
-            bool hit = x.has(k.t, lm);
-            if (!hit) {
-                y.load_ro(blocks, k.b2);
-                hit = y.has(k.t, lm);
-            }
-            if (!hit && backing) {
-                const uint64_t e = tcf_entry(k, G.f);
-                const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(bk + tcf_bucket_of(e, G) * BK_W);
-#pragma unroll
-                for (int s = 0; s < 4; s++) {
-                    const ulonglong2 v = __ldg(p + s);
-                    hit |= ((v.x & em) == e) | ((v.y & em) == e);
-                }
-            }
-            __stcs(out + i, (uint8_t)(hit ? 1 : 0));
-            continue;
-        }
         y.load_ro(blocks, k.b2);
         if (VAL) {
             uint32_t best = min(x.min_value(k.t, lm), y.min_value(k.t, lm));
@@ -2497,8 +2474,8 @@ int tcf_query(filter *F, const uint64_t *keys, uint64_t n, uint8_t *found, bool 
 #undef GF_GEOM_QUERY
     } else {
         gf::TraceScope ts_("tcf_query_kernel", n, st);
-        if (T.G.f == 16) tcf_query_kernel<16, false, true><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
-        else tcf_query_kernel<8, false, true><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+        if (T.G.f == 16) tcf_query_kernel<16, false><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
+        else tcf_query_kernel<8, false><<<g, TPB, 0, st>>>(keys, n, T.G, T.blocks, T.bk, F->ctr, found);
     }
     GF_CUDA(cudaGetLastError());
     return FILTER_OK;
