@@ -355,7 +355,7 @@ class FilterGroup:
         self.kind, self.tag_bits, self.log2_slots, self.seeds = kind, tag_bits, log2_slots, seeds
         self.max_total = max(1, int(max_total))
         total = sum(1 << lg for lg in log2_slots)
-        t = tuning.lookup(kind, total.bit_length() - 1)
+        t = tuning.lookup(kind, total.bit_length() - 1, group=True)
         if t:
             self.set_tuning(**t)
 

@@ -42,17 +42,29 @@ def table() -> dict:
     return _table
 
 
-def lookup(kind: int, log2_slots: int) -> dict:
-    """Knobs for a filter (or a group of that many slots in all)."""
-    from . import FILTER_TCF
-
-    rows = table().get("tcf" if kind == FILTER_TCF else "gqf", {})
-    best, knobs = -1, {}
+def _pick(rows: dict, log2_slots: int):
+    best, knobs = -1, None
     for k, v in rows.items():
         lg = int(k)
         if best < lg <= log2_slots:
             best, knobs = lg, {n: int(x) for n, x in v.items() if n in KNOBS}
     return knobs
+
+
+def lookup(kind: int, log2_slots: int, group: bool = False) -> dict:
+    """Knobs for a filter, or (group) for a filter group of that many slots in
+    all: a TCF group takes the measured group rows when one covers its size
+    (many small members behave unlike one table of their total size), else
+    the single-filter rows."""
+    from . import FILTER_TCF
+
+    t = table()
+    name = "tcf" if kind == FILTER_TCF else "gqf"
+    if group:
+        k = _pick(t.get(name + "_group", {}), log2_slots)
+        if k is not None:
+            return k
+    return _pick(t.get(name, {}), log2_slots) or {}
 
 
 def struct(knobs: dict):
@@ -125,6 +137,56 @@ def tune_tcf(lg: int, keys, torch) -> dict:
     return {**knobs, "ms": res, "batch": b}
 
 
+def tune_tcf_group(torch, n_filters: int = 2048, rounds: int = 8, seed: int = 78) -> tuple:
+    """A TCF group shaped like the batched workload (members of 2^10 .. 2^20
+    slots at 85-95 % load, keys in `rounds` per-member chunks), then a removal
+    of every member's first chunk: the path with the least total time.
+    Returns (log2 of the group's slots, entry)."""
+    import numpy as np
+
+    from . import FILTER_TCF, FilterGroup
+    from . import workloads as W
+
+    w = W.batched_workload(n_filters=2 * n_filters, seed=seed, tcf_rounds=rounds)
+    nt = w["n_tcf"]
+    off = w["offsets"][: nt + 1]
+    logs, seeds = w["log2_slots"][:nt], w["hash_seeds"][:nt]
+    keys = w["insert"][: off[-1]]
+    chunks = W.round_chunks(off, rounds)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+    calls = []
+    for j in range(rounds):
+        lens = chunks[j, :, 1] - chunks[j, :, 0]
+        o = np.zeros(nt + 1, np.int64)
+        np.cumsum(lens, out=o[1:])
+        calls.append((dev(o), dev(np.concatenate([keys[a:b] for a, b in chunks[j]]))))
+    mt = max(int(k.numel()) for _, k in calls)
+    G = FilterGroup(FILTER_TCF, logs, 16, seeds, max_total=mt)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    res = {}
+    for path in (1, 2):
+        G.set_tuning(tcf_path=path, tcf_tile_target=1024 if path == 2 else 0)
+
+        def run():
+            G.clear()
+            a, m, z = ev(), ev(), ev()
+            a.record()
+            for o, k in calls:
+                G.insert(o, k)
+            m.record()
+            G.remove(*calls[0])
+            z.record()
+            return [(a, m), (m, z)]
+
+        run()
+        res["block" if path == 1 else "tiled_1024"] = round(_timed(torch, run), 3)
+    G.close()
+    lg = int(sum(1 << int(x) for x in logs)).bit_length() - 1
+    best = min(res, key=res.get)
+    return lg, {**({"tcf_path": 1} if best == "block" else {"tcf_path": 2, "tcf_tile_target": 1024}), "ms": res,
+                "members": int(nt)}
+
+
 def tune_gqf(q: int, keys, torch) -> dict:
     """A GQF with 2^q home slots filled to 90 % in one batch; then a batch
     of min(2^24, n/16) distinct stored keys is removed and inserted again:
@@ -175,6 +237,9 @@ def autotune(tcf_classes=(20, 22, 24, 26, 27, 28), gqf_classes=(20, 22, 24, 26, 
     for q in gqf_classes:
         out["gqf"][str(q)] = tune_gqf(q, keys, torch)
     del keys
+    torch.cuda.empty_cache()
+    lg, entry = tune_tcf_group(torch)
+    out["tcf_group"] = {str(lg): entry}
     torch.cuda.empty_cache()
     if path:
         with open(path, "w") as f:

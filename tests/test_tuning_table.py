@@ -31,3 +31,14 @@ def test_missing_table_means_defaults(monkeypatch, tmp_path):
     monkeypatch.setattr(tuning, "TABLE_PATH", str(tmp_path / "none.json"))
     assert tuning.table() == {}
     assert tuning.lookup(gf.FILTER_TCF, 28) == {}
+
+
+def test_group_rows_cover_groups_from_their_class(monkeypatch):
+    monkeypatch.setattr(tuning, "_table", {
+        "tcf": {"20": {"tcf_path": 1}, "28": {"tcf_path": 2}},
+        "tcf_group": {"27": {"tcf_path": 1}},
+    })
+    assert tuning.lookup(gf.FILTER_TCF, 28) == {"tcf_path": 2}               # one filter
+    assert tuning.lookup(gf.FILTER_TCF, 28, group=True) == {"tcf_path": 1}   # a group of as many slots
+    assert tuning.lookup(gf.FILTER_TCF, 22, group=True) == {"tcf_path": 1}   # below the group class: filter rows
+    assert tuning.lookup(gf.FILTER_TCF, 12, group=True) == {}
