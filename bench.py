@@ -167,7 +167,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
     ap.add_argument("--no-target", action="store_true", help="skip the 2^28-slot, 90%%-load measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving-loop measurement")
-    ap.add_argument("--no-geometry", action="store_true", help="skip the TCF block-geometry sweep")
+    ap.add_argument("--no-geometry", action="store_true", help="skip the TCF block-geometry sweep and the GQF point updates")
     ap.add_argument("--case", default="full", choices=["full", "profile", "target", "batched", "serving", "kmer", "values"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
                          "keys) that fits an ncu capture; its line is not the benchmark figure")
@@ -508,6 +508,11 @@ def run_ours(args, rank, world, device_index):
         torch.cuda.empty_cache()
         geometry = run_geometry(args, device)
 
+    point = None
+    if args.case == "full" and not args.no_geometry:
+        torch.cuda.empty_cache()
+        point = run_point_gqf(args, device)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and args.case == "full":
         cpu = cpu_sample(inp)
@@ -522,7 +527,7 @@ def run_ours(args, rank, world, device_index):
                    "l2": "inputs larger than L2 (2.9 GB of keys), no flush", "parallelism": f"replicas x{world}"},
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
         "cpu_baseline": cpu, "random_gather": gather, "per_op": per_op, "kernels": kern, "checks": checks,
-        "target_2_28": target, "batched": batched, "serving": serving, "tcf_geometry": geometry,
+        "target_2_28": target, "batched": batched, "serving": serving, "tcf_geometry": geometry, "gqf_point": point,
     }
     return line
 
@@ -531,6 +536,56 @@ TARGET_WORKLOAD = ("target size, 2^28 slots at 90% load: TCF f=16 bulk, floor(0.
                    "batches, 2^24 pos + 2^24 neg queries, delete a random half in 2^24-key batches, re-query; GQF "
                    "r=8, as many uniform keys in one batch, count and query 2^24 inserted + 2^24 fresh keys, delete "
                    "2^24 distinct inserted keys, re-count")
+
+
+POINT_WORKLOAD = ("GQF point updates (paper Sec. 5.2 point API, one thread per key, region locks) against the bulk "
+                  "path on the same keys: 2^24 home slots, r=8, 2^20 distinct uniform keys (6 % load) inserted in one "
+                  "call into an empty table, then half of them removed in one call. Point updates serialise per "
+                  "8192-quotient region and shift clusters slot by slot, so they suit small scattered updates; "
+                  "filling 2^24 home slots to 85 % this way takes 2.3 s against 0.9 ms in bulk "
+                  "(tests/test_gpu_gqf_point.py covers that load for parity)")
+
+
+def run_point_gqf(args, device, q=24, n=1 << 20):
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+    from paper_2212_09005_gb300 import workloads as W
+
+    k = torch.from_numpy(W.uniform_keys(41, n).view(np.int64)).to(device)
+    half = k[: n // 2]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = {"workload": POINT_WORKLOAD}
+    imgs = []
+    for mode in ("point", "bulk"):
+        G = gf.GQF(q, 8, seed=42, max_batch=n)
+        best = None
+        for rep in range(3):
+            G.clear()
+            torch.cuda.synchronize()
+            a, m, z = ev(), ev(), ev()
+            a.record()
+            if mode == "point":
+                G.point_update(k)
+            else:
+                G.insert(k)
+            m.record()
+            if mode == "point":
+                G.point_update(half, remove=True)
+            else:
+                G.remove(half)
+            z.record()
+            torch.cuda.synchronize()
+            t = (a.elapsed_time(m), m.elapsed_time(z))
+            best = t if best is None or sum(t) < sum(best) else best
+        st = G.stats()
+        imgs.append(G.export())
+        out[mode] = {"insert_ms": round(best[0], 3), "insert_gops": round(n / best[0] / 1e6, 3),
+                     "remove_ms": round(best[1], 3), "remove_gops": round((n // 2) / best[1] / 1e6, 3),
+                     "status_word": st["status_word"], "failed_keys": st["failed_keys"]}
+        G.close()
+    out["tables_equal"] = bool(np.array_equal(imgs[0], imgs[1]))
+    return out
 
 
 GEOMETRY_WORKLOAD = ("TCF block-geometry sweep (paper Sec. 4.1 block sizes, Sec. 4.2 128-slot blocks, 12-bit tags): "

@@ -291,6 +291,25 @@ int filter_gqf_enumerate(filter_t *f, uint64_t *d_fingerprints, uint64_t *d_coun
                          uint64_t *n_groups, void *stream);
 int filter_gqf_keys_of(filter_t *f, const uint64_t *d_fingerprints, uint64_t n, uint64_t *d_keys, void *stream);
 
+/*
+ * filter_gqf_point_update: GQF point inserts (remove = 0) or removes
+ * (remove = 1) of n keys, one thread per key, in place on the current table
+ * (paper Sec. 5.2, the point insertion API: locks on regions of 8192
+ * quotients, the key's region and the next, taken in order with bounded
+ * waits). The keys of one call are applied in no particular order; the table
+ * is a function of the stored multiset, so it equals the table a bulk call
+ * would leave. Asynchronous, no host synchronisation (graph-capturable), no
+ * scratch. d_status (optional, n bytes): FILTER_KEY_OK, FILTER_KEY_FULL (the
+ * shift would leave the two lock regions or the table; nothing changed;
+ * counted), FILTER_KEY_NOT_FOUND (remove), or 3 (a lock wait gave up, or the
+ * key's cluster is longer than the locked span; nothing changed; the status
+ * word records FILTER_ERR_TIMEOUT). Meant for tables whose home slots are at
+ * most about 95 % used, where clusters stay far shorter than a lock region.
+ * FILTER_ERR_ARG for n > max_batch; FILTER_ERR_UNSUPPORTED for a TCF.
+ */
+int filter_gqf_point_update(filter_t *f, const uint64_t *d_keys, uint64_t n, int remove, uint8_t *d_status,
+                            void *stream);
+
 /* filter_export_size: bytes of the table image (see the layout above). */
 int filter_export_size(filter_t *f, uint64_t *nbytes);
 

@@ -420,8 +420,10 @@ __device__ __forceinline__ int gf_device_gqf_insert(const filter_device_view &v,
     const uint64_t fp = gqf_fingerprint(key, v.q + r, v.seed);
     const gf::GView g{static_cast<gf::Meta *>(v.table), static_cast<uint8_t *>(v.aux), 1ll << v.q,
                       (long long)v.n_aux, (long long)v.n_blocks};
-    const int rc = r == 8 ? gf::gqf_point_insert<8>(g, v.locks, fp, 1, v.counters)
-                          : gf::gqf_point_insert<16>(g, v.locks, fp, 1, v.counters);
+    const int rc = gf::gqf_warp_turns([&] {
+        return r == 8 ? gf::gqf_point_insert<8>(g, v.locks, fp, 1, v.counters)
+                      : gf::gqf_point_insert<16>(g, v.locks, fp, 1, v.counters);
+    });
     if (rc == FILTER_KEY_FULL) {
         atomicOr(v.counters, 1ull << FILTER_ERR_FULL);
         atomicAdd(v.counters + 1, 1ull);
@@ -441,8 +443,10 @@ __device__ __forceinline__ int gf_device_gqf_remove(const filter_device_view &v,
     const uint64_t fp = gqf_fingerprint(key, v.q + r, v.seed);
     const gf::GView g{static_cast<gf::Meta *>(v.table), static_cast<uint8_t *>(v.aux), 1ll << v.q,
                       (long long)v.n_aux, (long long)v.n_blocks};
-    const int rc = r == 8 ? gf::gqf_point_remove<8>(g, v.locks, fp, v.counters)
-                          : gf::gqf_point_remove<16>(g, v.locks, fp, v.counters);
+    const int rc = gf::gqf_warp_turns([&] {
+        return r == 8 ? gf::gqf_point_remove<8>(g, v.locks, fp, v.counters)
+                      : gf::gqf_point_remove<16>(g, v.locks, fp, v.counters);
+    });
     if (rc == gf::GQF_POINT_BUSY) atomicOr(v.counters, 1ull << FILTER_ERR_TIMEOUT);
     return rc;
 }

@@ -559,6 +559,23 @@ __device__ __forceinline__ void gqf_unlock_pair(uint32_t *l0, uint32_t *l1)
     gqf_lock_give(l0);
 }
 
+// The lanes of a warp that call together take their turns one after another
+// (lowest lane first): a lane that waits for a lock sleeps, and a sleeping
+// lane would hold up a lane of its own warp that holds a lock. f(lane) runs
+// the lane's update; returns its result.
+template <class Fn>
+__device__ __forceinline__ int gqf_warp_turns(Fn f)
+{
+    const unsigned active = __activemask();
+    const unsigned me = 1u << (threadIdx.x & 31);
+    int rc = 0;
+    for (unsigned todo = active; todo; todo &= todo - 1) {
+        if ((todo & (0u - todo)) == me) rc = f();
+        __syncwarp(active);
+    }
+    return rc;
+}
+
 // c copies of fingerprint fp: FILTER_KEY_OK, FILTER_KEY_FULL (no room before
 // the region after next, or past the table) or GQF_POINT_BUSY
 template <int R>

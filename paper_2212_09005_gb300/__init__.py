@@ -47,6 +47,7 @@ EXPORTS = [
     "filter_debug_fail_alloc", "filter_debug_live_allocations", "filter_debug_wait_timeout",
     "filter_batch_create", "filter_batch_run", "filter_batch_destroy",
     "filter_set_tuning", "filter_get_tuning", "filter_group_set_tuning",
+    "filter_gqf_point_update",
 ]
 
 TCF_PATH_AUTO, TCF_PATH_BLOCK, TCF_PATH_TILED = 0, 1, 2
@@ -159,6 +160,7 @@ def lib():
         L.filter_debug_wait_timeout.argtypes = [vp, C.c_uint32, vp]
         L.filter_server_destroy.argtypes = [vp]
         L.filter_set_tuning.argtypes = [vp, C.POINTER(FilterTuning)]
+        L.filter_gqf_point_update.argtypes = [vp, vp, u64, i32, vp, vp]
         L.filter_get_tuning.argtypes = [vp, C.POINTER(FilterTuning)]
         L.filter_group_set_tuning.argtypes = [vp, C.POINTER(FilterTuning)]
         L.filter_calibrate_gather.argtypes = [vp, u64, vp, u64, C.c_uint32, vp, vp]
@@ -215,6 +217,12 @@ class Filter:
         t = tuning.lookup(kind, log2_slots)
         if t:
             self.set_tuning(**t)
+
+    def point_update(self, keys, remove: bool = False, status=None, stream=None):
+        """GQF: locked point inserts (or removes) of the keys, one thread per
+        key, asynchronous and graph-capturable; status: uint8, one per key."""
+        _check(lib().filter_gqf_point_update(self._h, _dptr(keys, 8), keys.numel(), 1 if remove else 0,
+                                             _dptr(status, 1), _stream(stream)), "filter_gqf_point_update")
 
     def set_tuning(self, **knobs):
         """Kernel choices that never change results: tcf_path (TCF_PATH_*),

@@ -65,6 +65,15 @@ int filter_get_tuning(filter_t *f, filter_tuning *out)
     return FILTER_OK;
 }
 
+int filter_gqf_point_update(filter_t *f, const uint64_t *d_keys, uint64_t n, int remove, uint8_t *d_status,
+                            void *stream)
+{
+    if (!valid(f) || n > f->cfg.max_batch || (n && !d_keys) || (remove != 0 && remove != 1)) return FILTER_ERR_ARG;
+    if (f->cfg.kind != FILTER_GQF) return FILTER_ERR_UNSUPPORTED;
+    if (d_status && n) GF_CUDA(cudaMemsetAsync(d_status, 0, n, as_stream(stream)));
+    return gf::gqf_point_update(f, d_keys, n, remove, d_status, as_stream(stream));
+}
+
 int filter_create(const filter_config *cfg, void *stream, filter_t **out)
 {
     if (!cfg || !out) return FILTER_ERR_ARG;

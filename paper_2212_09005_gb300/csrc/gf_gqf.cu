@@ -1595,6 +1595,46 @@ int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uin
     return FILTER_OK;
 }
 
+// Point updates through the C ABI (Sec. 5.2's point insertion API): one
+// thread per key, the locked in-place update of the current buffer
+// (include/gpufilter_gqf_ops.cuh). Nothing is sorted and nothing synchronises
+// the host, so a call can be captured in a CUDA graph; keys of one call are
+// applied in no particular order (the table, a function of the stored
+// multiset, does not depend on it).
+template <int R>
+__global__ void __launch_bounds__(256) gqf_point_kernel(const uint64_t *__restrict__ keys, uint64_t n, PHash H,
+                                                        GView g, uint32_t *locks, int remove, uint8_t *status,
+                                                        DevCounters *ctr)
+{
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t fp = fingerprint(__ldcs(keys + i), H);
+        const int rc = gqf_warp_turns([&] {
+            return remove ? gqf_point_remove<R>(g, locks, fp, &ctr->status)
+                          : gqf_point_insert<R>(g, locks, fp, 1, &ctr->status);
+        });
+        if (rc == GQF_POINT_BUSY) atomicOr(&ctr->status, ST_TIMEOUT);
+        if (rc == FILTER_KEY_FULL) {
+            atomicOr(&ctr->status, ST_FULL);
+            atomicAdd(&ctr->failed, 1ull);
+        }
+        if (status) status[i] = (uint8_t)rc;
+    }
+}
+
+int gqf_point_update(filter *F, const uint64_t *keys, uint64_t n, int remove, uint8_t *status, cudaStream_t st)
+{
+    if (n == 0) return FILTER_OK;
+    GqfState &Q = F->gqf;
+    const GView g{reinterpret_cast<Meta *>(Q.meta[Q.cur]), Q.rem[Q.cur], (long long)Q.N, (long long)Q.nslots,
+                  (long long)Q.nblk};
+    const int grid = grid_for(n, 256, 8);
+    gf::TraceScope ts_(remove ? "gqf_point_remove" : "gqf_point_insert", n, st);
+    if (Q.r == 8) gqf_point_kernel<8><<<grid, 256, 0, st>>>(keys, n, Q.H, g, Q.locks, remove, status, F->ctr);
+    else gqf_point_kernel<16><<<grid, 256, 0, st>>>(keys, n, Q.H, g, Q.locks, remove, status, F->ctr);
+    GF_CUDA(cudaGetLastError());
+    return FILTER_OK;
+}
+
 // The fingerprint is invertible on p bits (Sec. 5.1): every xor-shift by
 // s >= p/2 is its own inverse and every product by an odd constant is undone
 // by the constant's inverse mod 2^p. A key below 2^p folds to itself, so it

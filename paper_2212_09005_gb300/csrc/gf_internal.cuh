@@ -437,6 +437,7 @@ int gqf_clear(filter *F, cudaStream_t st);
 int gqf_insert(filter *F, const uint64_t *keys, const uint32_t *counts, uint64_t n, uint8_t *status,
                cudaStream_t st);
 int gqf_remove(filter *F, const uint64_t *keys, uint64_t n, uint8_t *status, cudaStream_t st);
+int gqf_point_update(filter *F, const uint64_t *keys, uint64_t n, int remove, uint8_t *status, cudaStream_t st);
 int gqf_count(filter *F, const uint64_t *keys, uint64_t n, uint64_t *counts, uint8_t *found,
               cudaStream_t st);
 uint64_t gqf_image_bytes(const filter *F);
