@@ -167,6 +167,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 4096-filter group measurement")
     ap.add_argument("--no-target", action="store_true", help="skip the 2^28-slot, 90%%-load measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the reduced serving-loop measurement")
+    ap.add_argument("--no-tcf-point", action="store_true", help="skip the point-mode TCF (Alg. 1) measurement")
     ap.add_argument("--no-geometry", action="store_true", help="skip the TCF block-geometry sweep and the GQF point updates")
     ap.add_argument("--case", default="full", choices=["full", "profile", "target", "batched", "serving", "kmer", "values"],
                     help="profile: a reduced copy of the workload (TCF 2^24, GQF 2^25 with 3e7 Zipf "
@@ -484,6 +485,10 @@ def run_ours(args, rank, world, device_index):
     if not args.no_e2e:
         e2e = run_e2e(R, args, world, device)
 
+    tcf_point = None
+    if args.case == "full" and not args.no_tcf_point:
+        tcf_point = run_tcf_point(inp, device)
+
     target = None
     if args.case == "full" and not args.no_target:
         del R
@@ -528,6 +533,7 @@ def run_ours(args, rank, world, device_index):
         "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
         "cpu_baseline": cpu, "random_gather": gather, "per_op": per_op, "kernels": kern, "checks": checks,
         "target_2_28": target, "batched": batched, "serving": serving, "tcf_geometry": geometry, "gqf_point": point,
+        "tcf_point": tcf_point,
     }
     return line
 
@@ -586,6 +592,75 @@ def run_point_gqf(args, device, q=24, n=1 << 20):
         G.close()
     out["tables_equal"] = bool(np.array_equal(imgs[0], imgs[1]))
     return out
+
+
+TCF_POINT_WORKLOAD = ("TCF point mode (paper Alg. 1: one thread per key, a compare-and-swap into the first empty "
+                      "slot of b1 under the shortcut, else of the less full of b1 and b2, else a backing bucket; "
+                      "delete swaps in a tombstone) on the main step's TCF keys: 2^26 slots f=16, the same 15 "
+                      "insert batches, 2^24 pos + 2^24 neg queries, the same random-half delete, re-query")
+
+
+def run_tcf_point(inp, device, reps: int = 3):
+    """Per-operation rates of the point-mode TCF on the main step's TCF
+    inputs, best of `reps` passes after one warm-up pass. The table of a
+    point-mode TCF depends on the order of the threads' compare-and-swaps,
+    so the checks are the ones that hold for any order: every inserted key
+    is found before the delete, every key not deleted after it, and no
+    key is refused."""
+    import torch
+
+    import paper_2212_09005_gb300 as gf
+
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(device)
+    ins, probe, dels, B = to(inp["tcf_ins"]), to(inp["tcf_probe"]), to(inp["tcf_del"]), inp["tcf_batch"]
+    npos = inp["n_pos"]
+    f1 = torch.zeros(probe.numel(), dtype=torch.uint8, device=device)
+    f2 = torch.zeros_like(f1)
+    T = gf.TCF(inp["tcf_log2"], 16, gf.MODE_POINT, seed=inp.get("tcf_seed", 2), max_batch=B)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    best = None
+    for rep in range(reps + 1):
+        T.clear()
+        torch.cuda.synchronize()
+        e = [ev() for _ in range(5)]
+        e[0].record()
+        for s in range(0, ins.numel(), B):
+            T.insert(ins[s:s + B])
+        e[1].record()
+        T.query(probe, f1)
+        e[2].record()
+        for s in range(0, dels.numel(), B):
+            T.remove(dels[s:s + B])
+        e[3].record()
+        T.query(probe, f2)
+        e[4].record()
+        torch.cuda.synchronize()
+        t = [e[k].elapsed_time(e[k + 1]) for k in range(4)]
+        if rep > 0 and (best is None or sum(t) < sum(best)):
+            best = t
+    st = T.stats()
+    peak = peaks()[0]
+    n_ops = {"tcf_insert": (ins.numel(), best[0]), "tcf_query": (2 * probe.numel(), best[1] + best[3]),
+             "tcf_delete": (dels.numel(), best[2])}
+    per_op = {}
+    for name, (n, ms) in n_ops.items():
+        b32, b64 = OP_BYTES[name]
+        rate = n / (ms / 1e3)
+        per_op[name] = {"keys": n, "ms": round(ms, 3), "gops": round(rate / 1e9, 3), "bytes_per_op": b32,
+                        "frac": round(rate * b32 / 1e9 / peak, 4), "frac_64b": round(rate * b64 / 1e9 / peak, 4)}
+    # the positives are a sample of the inserted keys; deleted ones are
+    # those of the sample that appear in the delete set
+    pos = inp["tcf_probe"][:npos]
+    kept = ~np.isin(pos, inp["tcf_del"])
+    f1h, f2h = f1.cpu().numpy(), f2.cpu().numpy()
+    checks = {"pos_found": bool(f1h[:npos].all()), "kept_found_after_delete": bool(f2h[:npos][kept].all()),
+              "fpr": round(float(f1h[npos:].mean()), 6), "failed_keys": st["failed_keys"],
+              "status_word": st["status_word"], "backing_used": st["backing_used"]}
+    T.close()
+    total_ms = sum(best)
+    total_ops = ins.numel() + 2 * probe.numel() + dels.numel()
+    return {"workload": TCF_POINT_WORKLOAD, "gops": round(total_ops / total_ms / 1e6, 3),
+            "ms": round(total_ms, 3), "per_op": per_op, "checks": checks}
 
 
 GEOMETRY_WORKLOAD = ("TCF block-geometry sweep (paper Sec. 4.1 block sizes, Sec. 4.2 128-slot blocks, 12-bit tags): "
