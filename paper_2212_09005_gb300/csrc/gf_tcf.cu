@@ -576,8 +576,72 @@ __device__ __forceinline__ uint32_t warp_reserve(unsigned *counter, uint32_t min
     return base + incl - mine;
 }
 
+// Candidates that a per-block step passes on, collected per warp in shared
+// memory and written out with one reservation on the list's counter per
+// full buffer, instead of one returning atomic per warp and iteration. The
+// order of a pending list is free: every later phase orders its candidates
+// by (tag, batch index) itself. Exactly one of o32 / o64 is set; `n` is the
+// same in every lane, and every lane of the warp calls reserve and flush.
+static constexpr uint32_t SINK_CAP = 256;  // entries per warp
+
+struct RejSink {
+    uint64_t *buf;
+    uint32_t n;
+    uint32_t *o32;
+    uint64_t *o64;
+    unsigned *ctr;
+
+    __device__ __forceinline__ void flush()
+    {
+        const int lane = threadIdx.x & 31;
+        __syncwarp();
+        uint32_t base = 0;
+        if (lane == 0 && n) base = atomicAdd(ctr, n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t q = lane; q < n; q += 32) {
+            if (o64) o64[base + q] = buf[q];
+            else o32[base + q] = (uint32_t)buf[q];
+        }
+        __syncwarp();
+        n = 0;
+    }
+    // this lane's first position for `mine` entries; `direct` when the warp's
+    // entries exceed a buffer and go straight to the list
+    __device__ __forceinline__ uint32_t reserve(uint32_t mine, bool &direct)
+    {
+        const int lane = threadIdx.x & 31;
+        uint32_t incl = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (n + total > SINK_CAP) flush();
+        if (total > SINK_CAP) {
+            uint32_t base = 0;
+            if (lane == 31) base = atomicAdd(ctr, total);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            direct = true;
+            return base + incl - mine;
+        }
+        direct = false;
+        const uint32_t pos = n + incl - mine;
+        n += total;
+        return pos;
+    }
+    __device__ __forceinline__ void put(bool direct, uint32_t &slot, uint64_t v)
+    {
+        if (!direct) buf[slot] = v;
+        else if (o64) o64[slot] = v;
+        else o32[slot] = (uint32_t)v;
+        slot++;
+    }
+};
+
 // The grid-stride loops of the per-block kernels step whole warps, so that
-// every lane reaches warp_reserve in every iteration.
+// every lane reaches the sink's reserve in every iteration and its flush
+// after the last one.
 template <int F>
 __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *blocks, uint8_t *fill, PhaseDst P,
                                                         const uint64_t *__restrict__ rec, int phase,
@@ -586,14 +650,19 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
                                                         unsigned long long *units)
 {
     constexpr int B = Blk<F>::B;
+    __shared__ uint64_t s_sink[TPB / 32][SINK_CAP];
+    RejSink sink{s_sink[threadIdx.x >> 5], 0u, phase == 1 ? nullptr : pend32, phase == 1 ? pend64 : nullptr, npend};
     const uint64_t nd = phase_count(P, G.nb);
     if (P.dlist) note_units(units, nd);  // units: blocks with candidates
     const uint64_t stride = (uint64_t)gridDim.x * TPB;
     for (uint64_t j0 = blockIdx.x * (uint64_t)TPB + (threadIdx.x & ~31u); j0 < nd; j0 += stride) {
         const uint64_t j = j0 + (threadIdx.x & 31);
-        uint32_t s = 0, e = 0, k = 0;
+        uint32_t s = 0, e = 0, k = 0, f0 = 0;
         uint64_t b = 0, thr = 0;  // records <= thr are accepted
-        if (j < nd) b = phase_dst(P, j, s, e);
+        if (j < nd) {
+            b = phase_dst(P, j, s, e);
+            f0 = fill[b];  // dense phases: b = j, so this load goes out with the offsets'
+        }
         if (units && !P.dlist) {
             const unsigned t = __ballot_sync(0xffffffffu, s != e);
             if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
@@ -601,7 +670,6 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
         if (j < nd) {
             if (s != e) {
                 const uint32_t cnt = e - s;
-                const uint32_t f0 = fill[b];
                 k = cap > f0 ? min(cnt, cap - f0) : 0u;
                 if (k > 0 && cnt <= 8) {
                     // few candidates: all loads in flight at once, a sorting
@@ -648,7 +716,8 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
             }
         }
         const uint32_t nrej = (e - s) - k;
-        uint32_t slot = warp_reserve(npend, nrej);
+        bool direct;
+        uint32_t slot = sink.reserve(nrej, direct);
         if (nrej == 0) continue;
         for (uint32_t q = s; q < e; q++) {
             const uint64_t r = rec[q];
@@ -658,12 +727,13 @@ __global__ void __launch_bounds__(TPB) tcf_block_insert(TcfGeom G, uint8_t *bloc
                 // the other block of the pair: b1 + b2 - b
                 uint64_t alt = prep.bt ? (prep.bt[i] >> 32) + prep.b2[i] - b
                                        : b ^ tcf_g((uint32_t)(r >> 32) >> G.vbits, G.nb);
-                pend64[slot++] = (alt << 32) | i;
+                sink.put(direct, slot, (alt << 32) | i);
             } else {
-                pend32[slot++] = i;
+                sink.put(direct, slot, i);
             }
         }
     }
+    sink.flush();
 }
 
 // backing buckets: candidates (entry in rec, index in recI) taken in (entry,
@@ -748,6 +818,8 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
                                                         unsigned *npend, unsigned long long *units)
 {
     constexpr int B = Blk<F>::B;
+    __shared__ uint64_t s_sink[TPB / 32][SINK_CAP];
+    RejSink sink{s_sink[threadIdx.x >> 5], 0u, pend32, nullptr, npend};
     const uint64_t nd = phase_count(P, G.nb);
     if (P.dlist) note_units(units, nd);  // units: blocks with candidates
     const uint32_t lm = Blk<F>::lane_mask(G.vmask);
@@ -763,14 +835,17 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
         uint64_t thr[B];
         int ndt = 0;
         uint64_t b = 0;
-        if (j < nd) b = phase_dst(P, j, s, e);
+        uint32_t f0 = 0;
+        if (j < nd) {
+            b = phase_dst(P, j, s, e);
+            f0 = fill[b];  // dense phases: b = j, so this load goes out with the offsets'
+        }
         if (units && !P.dlist) {
             const unsigned t = __ballot_sync(0xffffffffu, s != e);
             if ((threadIdx.x & 31) == 0 && t) atomicAdd(units, (unsigned long long)__popc(t));
         }
         if (j < nd) {
             if (s != e) {
-                const uint32_t f0 = fill[b];
                 Blk<F> blk;
                 blk.load(blocks, b);
                 int removed = 0;
@@ -845,12 +920,13 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
             }
         }
         // unmatched candidates go on
-        uint32_t slot = warp_reserve(npend, nunm);
+        bool direct;
+        uint32_t slot = sink.reserve(nunm, direct);
         if (nunm == 0) continue;
         if (fast) {
 #pragma unroll
             for (int q = 0; q < 8; q++)
-                if ((unm >> q) & 1u) pend32[slot++] = (uint32_t)r8[q];
+                if ((unm >> q) & 1u) sink.put(direct, slot, (uint32_t)r8[q]);
         } else {
             for (uint32_t q = s; q < e; q++) {
                 const uint64_t r = rec[q];
@@ -858,10 +934,11 @@ __global__ void __launch_bounds__(TPB) tcf_block_remove(TcfGeom G, uint8_t *bloc
                 bool matched = false;
                 for (int d = 0; d < ndt; d++)
                     if (dt[d] == t && used[d] > 0 && r <= thr[d]) matched = true;
-                if (!matched) pend32[slot++] = (uint32_t)r;
+                if (!matched) sink.put(direct, slot, (uint32_t)r);
             }
         }
     }
+    sink.flush();
 }
 
 // ---------------------------------------------------------------------------
